@@ -1,0 +1,337 @@
+"""Seeded synthetic multiscreen geometries (inputs only).
+
+This module builds triangle meshes, nested coarse meshes and patch partitions
+for the workloads the solver is measured and tested on.  It holds none of the
+method's arithmetic: no sectors, no quadrature, no matrices.  Both the CUDA
+path (through the C ABI) and the CPU oracle consume its output, and nothing
+else is shared between them.
+
+Every generator returns a ``Geometry`` with
+
+* ``xyz``  float64 [nv, 3]  fine-mesh vertices,
+* ``tri``  int32   [nt, 3]  fine triangles (vertex ids),
+* ``coarse_xyz`` / ``coarse_tri``: the nested coarse mesh (mesh size H),
+* ``parent``  int32 [nt]: coarse triangle containing each fine triangle,
+* ``patch``   int32 [nt]: non-overlapping patch (substructure) of each fine
+  triangle, the face spaces of the two-level splitting (Sec. 5, eq. jumpSplit),
+* ``g``       float64 [3]: the constant Neumann datum of the workload.
+
+Geometries follow the shapes used in the paper's experiments (Sec. 2.2: the
+bow-tie multiscreen of Experiment 3) and the synthetic workloads the project is
+measured on (flat unit square, three-page book, disk with a perpendicular fin).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Geometry:
+    name: str
+    xyz: np.ndarray
+    tri: np.ndarray
+    coarse_xyz: np.ndarray
+    coarse_tri: np.ndarray
+    parent: np.ndarray
+    patch: np.ndarray
+    g: np.ndarray
+    h: float
+    H: float
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def nv(self) -> int:
+        return int(self.xyz.shape[0])
+
+    @property
+    def nt(self) -> int:
+        return int(self.tri.shape[0])
+
+
+# --------------------------------------------------------------------------
+# small mesh-building helpers (pure bookkeeping)
+# --------------------------------------------------------------------------
+
+class _MeshBuilder:
+    """Collects triangles given by vertex coordinates and merges coincident
+    vertices by rounded position, so that separately generated panels become
+    one conforming mesh."""
+
+    def __init__(self, decimals: int = 10):
+        self.decimals = decimals
+        self.key_to_id: dict = {}
+        self.pts: list = []
+        self.tris: list = []
+
+    def vid(self, p) -> int:
+        key = tuple(np.round(np.asarray(p, dtype=np.float64), self.decimals) + 0.0)
+        i = self.key_to_id.get(key)
+        if i is None:
+            i = len(self.pts)
+            self.key_to_id[key] = i
+            self.pts.append(np.asarray(p, dtype=np.float64))
+        return i
+
+    def add(self, a, b, c) -> int:
+        self.tris.append((self.vid(a), self.vid(b), self.vid(c)))
+        return len(self.tris) - 1
+
+    def arrays(self):
+        return (np.array(self.pts, dtype=np.float64).reshape(-1, 3),
+                np.array(self.tris, dtype=np.int32).reshape(-1, 3))
+
+
+def _grid_panel(mb: _MeshBuilder, origin, eu, ev, nu: int, nv: int, tags=None, tag_fn=None):
+    """Uniform grid on the parallelogram origin + [0,1]eu + [0,1]ev with nu x nv
+    cells, each split along the diagonal from (i, j) to (i+1, j+1)."""
+    origin = np.asarray(origin, float)
+    eu = np.asarray(eu, float)
+    ev = np.asarray(ev, float)
+
+    def P(i, j):
+        return origin + (i / nu) * eu + (j / nv) * ev
+
+    for j in range(nv):
+        for i in range(nu):
+            p00, p10, p11, p01 = P(i, j), P(i + 1, j), P(i + 1, j + 1), P(i, j + 1)
+            t0 = mb.add(p00, p10, p11)
+            t1 = mb.add(p00, p11, p01)
+            if tags is not None:
+                tags.append(tag_fn(i, j, 0))
+                tags.append(tag_fn(i, j, 1))
+
+
+def _subdivided_triangle(mb: _MeshBuilder, A, B, C, n: int):
+    """Uniform subdivision of triangle ABC into n^2 similar triangles; keeps
+    the orientation of ABC."""
+    A, B, C = (np.asarray(x, float) for x in (A, B, C))
+
+    def P(i, j):
+        return A + (i / n) * (B - A) + (j / n) * (C - A)
+
+    out = []
+    for j in range(n):
+        for i in range(n - j):
+            out.append(mb.add(P(i, j), P(i + 1, j), P(i, j + 1)))
+            if i + j + 1 < n:
+                out.append(mb.add(P(i + 1, j), P(i + 1, j + 1), P(i, j + 1)))
+    return out
+
+
+def _locate_parents(xyz, tri, cxyz, ctri) -> np.ndarray:
+    """Coarse triangle containing each fine triangle (by its centroid)."""
+    cen = xyz[tri].mean(axis=1)                      # [nt, 3]
+    A = cxyz[ctri[:, 0]]
+    B = cxyz[ctri[:, 1]]
+    C = cxyz[ctri[:, 2]]
+    e1 = B - A
+    e2 = C - A
+    nrm = np.cross(e1, e2)
+    area2 = np.linalg.norm(nrm, axis=1)
+    nhat = nrm / area2[:, None]
+    parent = np.full(tri.shape[0], -1, dtype=np.int32)
+    chunk = 4096
+    for s in range(0, cen.shape[0], chunk):
+        c = cen[s:s + chunk]                          # [m, 3]
+        d = c[:, None, :] - A[None, :, :]             # [m, nc, 3]
+        off = np.abs(np.einsum('mkj,kj->mk', d, nhat))
+        # barycentric coordinates in each coarse triangle's plane
+        d11 = np.einsum('kj,kj->k', e1, e1)
+        d12 = np.einsum('kj,kj->k', e1, e2)
+        d22 = np.einsum('kj,kj->k', e2, e2)
+        p1 = np.einsum('mkj,kj->mk', d, e1)
+        p2 = np.einsum('mkj,kj->mk', d, e2)
+        den = d11 * d22 - d12 * d12
+        l1 = (d22 * p1 - d12 * p2) / den
+        l2 = (d11 * p2 - d12 * p1) / den
+        l0 = 1.0 - l1 - l2
+        ok = (off < 1e-9) & (l0 > -1e-9) & (l1 > -1e-9) & (l2 > -1e-9)
+        cnt = ok.sum(axis=1)
+        if np.any(cnt != 1):
+            raise ValueError("fine mesh does not nest in the coarse mesh")
+        parent[s:s + chunk] = np.argmax(ok, axis=1)
+    return parent
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+def unit_square(n: int = 16, n_coarse: int = 2, patch_mode: str = "square",
+                g=(0.0, 0.0, 1.0)) -> Geometry:
+    """Flat screen [0,1]^2 in the plane z = 0 with h = 1/n, H = 1/n_coarse.
+
+    ``patch_mode``: 'square' -> one patch per coarse square (two coarse
+    triangles); 'coarse_tri' -> one patch per coarse triangle (the face spaces
+    of Sec. 5 taken literally)."""
+    if n % n_coarse:
+        raise ValueError("n must be a multiple of n_coarse")
+    r = n // n_coarse
+    mb = _MeshBuilder()
+    _grid_panel(mb, (0, 0, 0), (1, 0, 0), (0, 1, 0), n, n)
+    xyz, tri = mb.arrays()
+    cb = _MeshBuilder()
+    _grid_panel(cb, (0, 0, 0), (1, 0, 0), (0, 1, 0), n_coarse, n_coarse)
+    cxyz, ctri = cb.arrays()
+    parent = _locate_parents(xyz, tri, cxyz, ctri)
+    if patch_mode == "coarse_tri":
+        patch = parent.copy()
+    elif patch_mode == "square":
+        cen = xyz[tri].mean(axis=1)
+        I = np.minimum((cen[:, 0] * n_coarse).astype(int), n_coarse - 1)
+        J = np.minimum((cen[:, 1] * n_coarse).astype(int), n_coarse - 1)
+        patch = (J * n_coarse + I).astype(np.int32)
+    else:
+        raise ValueError(patch_mode)
+    return Geometry(f"unit_square_h1/{n}_H1/{n_coarse}", xyz, tri, cxyz, ctri, parent,
+                    patch, np.asarray(g, float), 1.0 / n, 1.0 / n_coarse,
+                    {"family": "square", "n": n, "n_coarse": n_coarse, "r": r})
+
+
+def _jittered_cuts(n: int, n_coarse: int, rng, jitter: bool):
+    r = n // n_coarse
+    cuts = []
+    for k in range(1, n_coarse):
+        c = k * r
+        if jitter:
+            c += int(rng.integers(-1, 2))
+        cuts.append(c)
+    return cuts
+
+
+def book(n: int = 64, n_coarse: int = 4, jitter: bool = True, seed: int = 0,
+         pages: int = 3, g=(1.0, 0.5, 0.25)) -> Geometry:
+    """'Three-page book': ``pages`` unit squares sharing the edge
+    {x = 0, y = 0, z in [0,1]}, at angles 2*pi*k/pages about the z-axis.
+
+    Each page carries an n x n grid (h = 1/n) and the nested coarse grid
+    n_coarse x n_coarse (H = 1/n_coarse).  Patches: n_coarse x n_coarse per
+    page, whose cut lines are shifted by a seeded random -1/0/+1 fine rows
+    (independently for every cut line of every page) so patch sizes are uneven.
+    """
+    rng = np.random.default_rng(seed)
+    mb = _MeshBuilder()
+    tags = []
+    cb = _MeshBuilder()
+    for k in range(pages):
+        th = 2.0 * math.pi * k / pages
+        er = (math.cos(th), math.sin(th), 0.0)
+        ez = (0.0, 0.0, 1.0)
+        cr = _jittered_cuts(n, n_coarse, rng, jitter)
+        cz = _jittered_cuts(n, n_coarse, rng, jitter)
+
+        def tag(i, j, t, k=k, cr=cr, cz=cz):
+            bi = sum(1 for c in cr if i >= c)
+            bj = sum(1 for c in cz if j >= c)
+            return (k * n_coarse + bj) * n_coarse + bi
+
+        _grid_panel(mb, (0, 0, 0), er, ez, n, n, tags, tag)
+        _grid_panel(cb, (0, 0, 0), er, ez, n_coarse, n_coarse)
+    xyz, tri = mb.arrays()
+    cxyz, ctri = cb.arrays()
+    parent = _locate_parents(xyz, tri, cxyz, ctri)
+    patch = np.array(tags, dtype=np.int32)
+    return Geometry(f"book{pages}_h1/{n}_H1/{n_coarse}" + ("_jit" if jitter else ""), xyz, tri,
+                    cxyz, ctri, parent, patch, np.asarray(g, float), 1.0 / n, 1.0 / n_coarse,
+                    {"family": "book", "n": n, "n_coarse": n_coarse, "pages": pages,
+                     "seed": seed, "jitter": jitter})
+
+
+def _hex_disk(mb: _MeshBuilder, n: int, a: float):
+    """Disk of radius a in z = 0: ring k (k = 1..n) holds 6k vertices at radius
+    a*k/n and equal angles; rings are joined sector by sector as in a
+    hexagonal grid, so the diameter on the x-axis is a union of mesh edges."""
+    def P(k, m):
+        if k == 0:
+            return (0.0, 0.0, 0.0)
+        m %= 6 * k
+        th = 2.0 * math.pi * m / (6 * k)
+        return (a * k / n * math.cos(th), a * k / n * math.sin(th), 0.0)
+
+    ids = []
+    for k in range(1, n + 1):
+        for s in range(6):
+            for t in range(k):
+                o0 = P(k, s * k + t)
+                o1 = P(k, s * k + t + 1)
+                i0 = P(k - 1, s * (k - 1) + t)
+                ids.append(mb.add(i0, o0, o1))
+                if t < k - 1:
+                    i1 = P(k - 1, s * (k - 1) + t + 1)
+                    ids.append(mb.add(i0, o1, i1))
+    return ids
+
+
+def disk(n: int = 8, a: float = 1.0, fin: bool = False, fin_half_height: float | None = None,
+         g=(0.0, 0.0, 1.0)) -> Geometry:
+    """Flat disk of radius a (n rings, h ~ a/n) in z = 0, optionally crossed by
+    a perpendicular rectangular fin {y = 0, |x| <= a, |z| <= b} along the
+    x-axis diameter.  For g = (0, 0, g_n) the exact jump is
+    (4/pi) g_n sqrt(a^2 - r^2) on the disk and 0 on the fin.
+
+    The coarse mesh is the single-level mesh itself (no coarse space is needed
+    for the closed-form tests); every triangle is its own patch parent."""
+    mb = _MeshBuilder()
+    _hex_disk(mb, n, a)
+    if fin:
+        b = a if fin_half_height is None else fin_half_height
+        mz = max(1, int(round(b / (a / n))))
+        _grid_panel(mb, (-a, 0.0, -b), (2 * a, 0.0, 0.0), (0.0, 0.0, 2 * b), 2 * n, 2 * mz)
+    xyz, tri = mb.arrays()
+    # enforce a consistent upward/forward orientation for readability
+    P0, P1, P2 = xyz[tri[:, 0]], xyz[tri[:, 1]], xyz[tri[:, 2]]
+    nrm = np.cross(P1 - P0, P2 - P0)
+    flip = (nrm[:, 2] < -1e-14) | ((np.abs(nrm[:, 2]) <= 1e-14) & (nrm[:, 1] < 0))
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    parent = np.arange(tri.shape[0], dtype=np.int32)
+    return Geometry(("diskfin" if fin else "disk") + f"_n{n}", xyz, tri, xyz.copy(), tri.copy(),
+                    parent, np.zeros(tri.shape[0], np.int32), np.asarray(g, float), a / n, a,
+                    {"family": "disk", "n": n, "a": a, "fin": fin})
+
+
+def bowtie(n: int = 8, n_coarse: int = 2, g=(1.0, 0.5, 0.25)) -> Geometry:
+    """The bow-tie of Experiment 3 (Sec. 2.2): two unit equilateral triangles in
+    perpendicular planes sharing a median.  Each is pre-split along that
+    median so the junction is a mesh line; the four halves are subdivided
+    uniformly (coarse level n_coarse, fine level n, nested).  Patches are the
+    coarse triangles (the face spaces of Sec. 5)."""
+    if n % n_coarse:
+        raise ValueError("n must be a multiple of n_coarse")
+    top = (0.0, 0.0, math.sqrt(3.0) / 2.0)
+    mid = (0.0, 0.0, 0.0)
+    halves = [((-0.5, 0.0, 0.0), mid, top), (mid, (0.5, 0.0, 0.0), top),
+              ((0.0, -0.5, 0.0), mid, top), (mid, (0.0, 0.5, 0.0), top)]
+    mb = _MeshBuilder()
+    cb = _MeshBuilder()
+    for (A, B, C) in halves:
+        _subdivided_triangle(mb, A, B, C, n)
+        _subdivided_triangle(cb, A, B, C, n_coarse)
+    xyz, tri = mb.arrays()
+    cxyz, ctri = cb.arrays()
+    parent = _locate_parents(xyz, tri, cxyz, ctri)
+    return Geometry(f"bowtie_n{n}_nc{n_coarse}", xyz, tri, cxyz, ctri, parent, parent.copy(),
+                    np.asarray(g, float), 1.0 / n, 1.0 / n_coarse,
+                    {"family": "bowtie", "n": n, "n_coarse": n_coarse})
+
+
+def flat_config() -> Geometry:
+    """Plain FP64 flat-screen workload: unit square h = 1/16 (225 interior
+    dofs), 2 x 2 substructuring (H = 1/2) plus the coarse space, g = (0,0,1)."""
+    return unit_square(16, 2, "square", g=(0.0, 0.0, 1.0))
+
+
+def book_config() -> Geometry:
+    """Three-page book, h = 1/64 (12,033 dofs), 48 jittered patches (4 x 4 per
+    page, seed 0), coarse H = 1/4, g = (1, 0.5, 0.25)."""
+    return book(64, 4, jitter=True, seed=0, g=(1.0, 0.5, 0.25))
+
+
+def rotate(geom: Geometry, R: np.ndarray, shift=(0.0, 0.0, 0.0)) -> Geometry:
+    """Rigidly moved copy of a geometry (vertices and g rotated by R)."""
+    R = np.asarray(R, float)
+    s = np.asarray(shift, float)
+    return dataclasses.replace(geom, name=geom.name + "_rot", xyz=geom.xyz @ R.T + s,
+                               coarse_xyz=geom.coarse_xyz @ R.T + s, g=R @ geom.g)
