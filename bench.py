@@ -1,0 +1,366 @@
+"""Benchmark: PCG solves/s of the multiscreen hypersingular BEM hot path on GB300.
+
+One step = one pass of the whole hot path on the three-page book workload
+(h = 1/64, 12,033 dofs, 24,576 triangles, 48 jittered patches, coarse H = 1/4,
+g = (1, 0.5, 0.25)): assembly of W (far field, near field, contraction),
+set-up of the two-level additive Schwarz preconditioner, and the PCG solve to
+relative residual 1e-8.  The geometry's topology is built once at upload
+(per-geometry setup); it is inside the end-to-end number, which also copies
+the mesh from pinned host memory and reads the density back every step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own replica (no data-path
+collective: the solves are independent), timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG solves/s and p50/p99 latency at rel. residual 1e-8 vs plain FP64 GPU PCG"
+UNIT = "solves/s"
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# double-float far-field kernel: FP32-pipe operations per unordered pair
+# (36 evaluations x 82 + 6 x 45 per-point updates), counted from far_df.cu
+FP32_OPS_PER_FAR_PAIR = 36 * 82 + 6 * 45
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--far-kernel", type=int, default=0, help="0 double-float (default), 1 native FP64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="book64", choices=["book64", "book32", "flat"],
+                    help="book64 is the measured workload; book32 (h=1/32) and flat are for profiling")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from paper_2310_09204_gb300 import workloads as WL
+    if name == "book64":
+        return WL.book_config()
+    if name == "book32":
+        return WL.book(32, 4, jitter=True, seed=0)
+    return WL.flat_config()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float, device=None) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+
+def oracle_step_seconds(geom, state: dict) -> tuple[float, dict]:
+    """One oracle solve of the workload on the host cores.  The pair matrix V
+    (the dominant phase) is timed on a sample of 1/8 of its rows and scaled;
+    topology, contraction, preconditioner set-up and PCG run in full on the
+    oracle's own W (assembled once, untimed, the first time)."""
+    from oracle import core, solver
+    from oracle.topology import Topology
+    t0 = time.perf_counter()
+    top = Topology(geom.xyz, geom.tri)
+    t_topo = time.perf_counter() - t0
+    nt = geom.nt
+    frac = 8
+    rows = np.arange(state.get("row_offset", 0), nt, frac, dtype=np.int64)
+    state["row_offset"] = (state.get("row_offset", 0) + 1) % frac
+    R = np.repeat(rows, nt)
+    C = np.tile(np.arange(nt, dtype=np.int64), rows.size)
+    t0 = time.perf_counter()
+    core.V_entries(geom.xyz, geom.tri, R, C)
+    t_V = (time.perf_counter() - t0) * nt / rows.size / 2.0      # upper half of V suffices
+    del R, C
+    if "pb" not in state:
+        state["pb"] = solver.Problem(geom)
+    pb = state["pb"]
+    t0 = time.perf_counter()
+    solver.assemble_W(top, pb.V)
+    t_W = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pb.factor()
+    t_f = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res = pb.solve(rtol=1e-8)
+    t_s = time.perf_counter() - t0
+    total = t_topo + t_V + t_W + t_f + t_s
+    return total, {"topology_s": t_topo, "V_s_scaled": t_V, "contract_s": t_W, "factor_s": t_f,
+                   "solve_s": t_s, "iters": res.iters}
+
+
+def cores_used() -> int:
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return
+    from oracle import core
+    from paper_2310_09204_gb300 import workloads as WL
+    core.build()
+    geom = WL.book_config()
+    state = {}
+    for _ in range(args.warmup):
+        # untimed warm-up: the topology and one V row (cheap) plus the one-time W
+        from oracle import solver
+        if "pb" not in state:
+            state["pb"] = solver.Problem(geom)
+    times, details = [], []
+    for _ in range(args.steps):
+        t, d = oracle_step_seconds(geom, state)
+        times.append(t)
+        details.append(d)
+    total = sum(times)
+    value = args.steps / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "three-page book h=1/64, N=12033 dofs, 48 jittered patches, coarse H=1/4, "
+                                   "g=(1,0.5,0.25), rtol 1e-8", "global_batch": 1, "seq_len": 12033,
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                             "sample": "V on 1/8 of its rows (scaled); topology, contraction, "
+                                       "preconditioner and PCG in full", "phases": details[-1]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    import paper_2310_09204_gb300 as M
+    from paper_2310_09204_gb300 import build as B
+    from paper_2310_09204_gb300 import workloads as WL
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    geom = make_workload(args.workload)
+    g = geom.g
+
+    S = M.Solver(geom, device=local, stream=stream.cuda_stream)
+    N = S.n
+    dens = torch.empty(N, dtype=torch.float64, device=dev)
+
+    def step():
+        S.assemble(far_kernel=args.far_kernel)
+        S.factor()
+        return S.solve(g, rtol=1e-8, out=dens)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    launches0 = S.counters()["launches"]
+    clocks = Clocks(local)
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    far_ms, phase, iters = [], [], []
+    for k in range(args.steps):
+        out = step()
+        ev[k + 1].record(stream)
+        t = S.timings()
+        far_ms.append(t["far_ms"])
+        phase.append(t)
+        iters.append(out["iters"])
+    torch.cuda.synchronize()
+    barrier(pg)
+    ck = clocks.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_s = sum(step_ms) / 1e3
+    launches = (S.counters()["launches"] - launches0) / args.steps
+    total_s = max_over_ranks(pg, total_s, dev)
+    value = world * args.steps / total_s
+    far_pairs = S.counters()["far_pairs"]
+    far_avg_s = statistics.mean(far_ms) / 1e3
+    ops = far_pairs * FP32_OPS_PER_FAR_PAIR
+    peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6
+    achieved = ops / far_avg_s
+    kernel = "far_df_kernel (double-float on FP32 pipe)" if args.far_kernel == 0 else "far_fp64_kernel"
+
+    # end to end through the C ABI with host buffers: upload (host topology +
+    # H2D from pinned memory) + assemble + factor + solve + D2H of the density
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+               for k, v in (("xyz", geom.xyz), ("tri", geom.tri.astype(np.int32)),
+                            ("cxyz", geom.coarse_xyz), ("ctri", geom.coarse_tri.astype(np.int32)),
+                            ("parent", geom.parent.astype(np.int32)), ("patch", geom.patch.astype(np.int32)))}
+        host_out = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+        h2d = sum(a.nbytes for a in pin.values())
+        E = M.Solver(None, device=local, stream=stream.cuda_stream)
+
+        def e2e_step():
+            E.upload(pin["xyz"], pin["tri"], pin["cxyz"], pin["ctri"], pin["parent"], pin["patch"])
+            E.assemble(far_kernel=args.far_kernel)
+            E.factor()
+            r = E.solve(g, rtol=1e-8, out=host_out)
+            E.free_geometry()
+            return r
+
+        e2e_step()
+        barrier(pg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(pg)
+        t_e2e = max_over_ranks(pg, time.perf_counter() - t0, dev)
+        E.close()
+        e2e = {"value": world * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(N * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import core
+        core.build()
+        t, d = oracle_step_seconds(geom, {})
+        cpu = {"value": 1.0 / t, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+               "sample": "one solve of the same workload; V timed on 1/8 of its rows and scaled, "
+                         "topology, contraction, preconditioner set-up and PCG in full",
+               "phases": d}
+
+    if rank == 0:
+        lat = sorted(step_ms)
+        p50 = lat[len(lat) // 2]
+        p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (double-float far field)" if args.far_kernel == 0 else "f64",
+            "data": "synthetic",
+            "config": {"workload": ("three-page book h=1/64, N=12033 dofs, 24576 triangles, 48 jittered "
+                                    "patches (seed 0), coarse H=1/4 (33 dofs), g=(1,0.5,0.25), rtol 1e-8")
+                       if args.workload == "book64" else f"{geom.name} (profiling case)",
+                       "global_batch": world, "seq_len": N, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (W 1.16 GB, V 4.8 GB)"},
+            "latency_ms": {"p50": p50, "p99": p99},
+            "phases_ms": {k: statistics.mean(p[k] for p in phase) for k in phase[0]},
+            "pcg_iters": iters[-1],
+            "roofline": {"kernel": kernel, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (FP32-pipe ops/s)",
+                         "ops_per_launch": ops, "launch_ms": far_avg_s * 1e3},
+            "clocks": ck,
+            "gpu_launches": int(launches),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    S.close()
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank, pg)
+        else:
+            run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * msbem.h -- C ABI of the GB300 multiscreen hypersingular BEM library.
+ *
+ * The library solves the Galerkin system  W Phi = L  of the Laplace
+ * hypersingular operator on a polygonal multiscreen Gamma (Averseng, Claeys,
+ * Hiptmair, "Boundary Element Methods for the Laplace Hypersingular Integral
+ * Equation on Multiscreens: a two-level Substructuring Preconditioner"),
+ * by preconditioned conjugate gradients under the two-level additive Schwarz
+ * (substructuring) preconditioner of the paper, on one GPU.
+ *
+ * Problem statement (Sec. 1 eq. PDE_intro, Sec. 3.3 Thm. thmBVP): find the
+ * jump phi with a(phi, psi) = l_g(psi) for all psi, where a is the
+ * hypersingular form (Def. defa) and l_g(psi) = <<gamma u, pi_n g>> (eq. defRhs).
+ *
+ * Conventions shared by every call
+ *   - All functions return 0 (MSBEM_OK) on success or a negative status.
+ *     After a failure msbem_last_error(ctx) holds a one-line message.
+ *   - Host arrays passed in are only read during the call and copied; the
+ *     caller keeps ownership.  Device memory is owned by the library and freed
+ *     by msbem_geom_free / msbem_destroy.
+ *   - A context is bound to one device and one CUDA stream; it is not thread
+ *     safe (one host thread per context at a time).
+ *   - Triangles are int32 vertex-id triples; vertices are float64 xyz triples
+ *     (row-major, 3 per vertex).  Normals n_T = (x1-x0) x (x2-x0) orient each
+ *     triangle; the side (T,+) is the one n_T points into (Def. Mstar).
+ *   - Dof numbering (Sec. 4.2 eq. defCurlyHtildeGamma): dofs are the
+ *     generalized vertices (i,j), j < q_i, of the vertices with q_i > 1, in
+ *     increasing vertex id, then increasing sector index; sectors of a vertex are
+ *     numbered by the smallest key 2*T + (0 for side +, 1 for side -) of their
+ *     oriented triangles, so sector q_i is the one with the largest such key.
+ */
+#ifndef MSBEM_H
+#define MSBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSBEM_OK 0
+#define MSBEM_INVALID_ARG (-1)     /* bad pointer, size or option            */
+#define MSBEM_NONCONFORMING (-2)   /* degenerate/duplicate/overlapping tris,  */
+                                   /* or fine mesh not nested in coarse mesh  */
+#define MSBEM_POINT_CONTACT (-3)   /* vertex whose triangles are not edge-    */
+                                   /* connected (excluded, Sec. 4.3 footnote) */
+#define MSBEM_OOM (-4)             /* device allocation failed                */
+#define MSBEM_NOT_CONVERGED (-5)   /* maxit reached; density still written    */
+#define MSBEM_BREAKDOWN (-6)       /* p^T W p <= 0 or non-finite in PCG       */
+#define MSBEM_DEVICE_TIMEOUT (-7)  /* a bounded device-side wait expired      */
+#define MSBEM_CUDA_ERROR (-8)      /* a CUDA call failed                      */
+#define MSBEM_NOT_READY (-9)       /* call order violated (e.g. solve before  */
+                                   /* assemble)                               */
+
+typedef struct msbem_ctx msbem_ctx;
+typedef struct msbem_geom msbem_geom;
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the
+ * handle.  Errors: INVALID_ARG, CUDA_ERROR. */
+int msbem_create(msbem_ctx** ctx, int device, void* cuda_stream);
+
+/* Destroy a context and every geometry still attached to it. */
+int msbem_destroy(msbem_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none).  The string is
+ * owned by the context and valid until the next call on it. */
+const char* msbem_last_error(const msbem_ctx* ctx);
+
+/* Upload a multiscreen and its substructuring (Sec. 3.1 Def. polygonalMS,
+ * Sec. 5 "Coarse mesh", eq. jumpSplit).
+ *   xyz[3*nv], tri[3*nt]           fine mesh M_{Gamma,h}
+ *   coarse_xyz[3*ncv], coarse_tri[3*nct]  coarse mesh M_{Gamma,H}; the fine
+ *                                  mesh must refine it (nested)
+ *   parent_coarse_tri[nt]          coarse triangle containing each fine one
+ *   patch_of_tri[nt]               patch id (>= 0) of each fine triangle; the
+ *                                  face space of patch p holds the dofs whose
+ *                                  vertex has all incident triangles in p, the
+ *                                  remaining dofs form the wire basket
+ * Builds the topology on the host (sectors by angular wedge linking around
+ * every edge, dofs, surface-curl lists, pair classes, face/wire-basket classes,
+ * coarse prolongation) and copies the mesh data to the device.
+ * Errors: INVALID_ARG, NONCONFORMING, POINT_CONTACT, OOM, CUDA_ERROR. */
+int msbem_upload(msbem_ctx* ctx, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                 const double* coarse_xyz, int64_t ncv, const int32_t* coarse_tri, int64_t nct,
+                 const int32_t* parent_coarse_tri, const int32_t* patch_of_tri, msbem_geom** out);
+
+/* Host-only mesh analysis (no context, no GPU): builds the topology of a
+ * triangle mesh exactly as msbem_upload does (sectors, Sec. 4.2 generalized
+ * vertices, dofs) and reports the dof count and, if cap >= *ndof, the dof map
+ * (vertex id and sector index of every dof).  errbuf (may be NULL) receives a
+ * message of at most errcap bytes on failure.
+ * Errors: INVALID_ARG, NONCONFORMING, POINT_CONTACT. */
+int msbem_mesh_dofs(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int64_t* ndof,
+                    int32_t* vertex_of_dof, int32_t* sector_of_dof, int64_t cap, char* errbuf,
+                    int errcap);
+
+/* Release a geometry and its device memory. */
+int msbem_geom_free(msbem_geom* g);
+
+/* Number of dofs N = |H~([Gamma])| (Sec. 4.2). */
+int msbem_ndofs(const msbem_geom* g, int64_t* n);
+
+/* Dof map (host arrays of length N): vertex id and 0-based sector index of
+ * every dof, in the numbering described at the top of this file. */
+int msbem_dof_map(const msbem_geom* g, int32_t* vertex_of_dof, int32_t* sector_of_dof);
+
+/* Sizes of the splitting (eq. jumpSplit): number of face spaces (patches with
+ * at least one dof), wire-basket size, coarse-space size, largest face block.
+ * Any pointer may be NULL. */
+int msbem_split_info(const msbem_geom* g, int64_t* n_faces, int64_t* n_wire_basket,
+                     int64_t* n_coarse, int64_t* max_face);
+
+typedef struct msbem_assemble_opts {
+  int ss_order;    /* Gauss-Legendre points per dimension of the singular     */
+                   /* (Sauter-Schwab-type) rules, 1..16; default 5            */
+  int far_kernel;  /* 0 = double-float arithmetic on the FP32 pipe (default), */
+                   /* 1 = native FP64                                         */
+} msbem_assemble_opts;
+
+/* Assemble W[nu,nu'] = a(psi~_nu, psi~_nu') (Sec. 4.3 eq. eval_a_phiij with
+ * Cor. corW): W = sum_{T,T'} V_{TT'} s_{T,nu} . s_{T',nu'}, V_{TT'} =
+ * int_T int_T' 1/(4 pi |x-y|), with the 6-point degree-4 rule on pairs that
+ * share no vertex and Sauter-Schwab-type rules on the others.  opts may be
+ * NULL (defaults).  W (N x N, float64, row-major, leading dimension N) stays
+ * on the device.  Errors: NOT_READY, OOM, CUDA_ERROR. */
+int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts);
+
+/* Copy rows [row0, row0+nrows) of W into out (host or device, nrows*N
+ * doubles, row-major).  Errors: NOT_READY, INVALID_ARG, CUDA_ERROR. */
+int msbem_copy_matrix(const msbem_geom* g, int64_t row0, int64_t nrows, double* out);
+
+/* Right-hand side L_nu = l_g(psi~_nu) = sum_T (c_+ - c_-)(g . n_T)|T|/3 for a
+ * constant Neumann datum g (Sec. 4.3, last display) into out[N] (host or
+ * device). */
+int msbem_rhs(const msbem_geom* g, const double gvec[3], double* out);
+
+typedef struct msbem_precond_opts {
+  int wire_basket;   /* 0 = exact solve on the wire basket (Thm. main),      */
+                     /* 1 = diagonal ("pointwise scalar product", Remark     */
+                     /*     "Approximate solvers", Sec. 2.1)                  */
+  int use_coarse;    /* 1 (default) = include the coarse space V~_H          */
+} msbem_precond_opts;
+
+/* Set up M(H;h) (Sec. 2.1 Remark on PCG, eq. jumpSplit): the principal blocks
+ * A_F = W[F,F] of every face space and A_W of the wire basket, and the coarse
+ * matrix A_H = P^T W P, all inverted (FP64).  opts may be NULL.
+ * Errors: NOT_READY (no W), BREAKDOWN (a block is not positive definite), OOM,
+ * CUDA_ERROR. */
+int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts);
+
+typedef struct msbem_solve_opts {
+  double rtol;        /* stop when ||L - W Phi_k|| <= rtol ||L|| (default 1e-8)*/
+  int maxit;          /* iteration cap (default 1000)                          */
+  int fixed_iters;    /* 1: run exactly maxit iterations (parity checks)       */
+  int precondition;   /* 1 (default): PCG with M(H;h); 0: plain CG             */
+} msbem_solve_opts;
+
+/* Solve W Phi = L for constant Neumann data g by PCG from Phi_0 = 0
+ * (Sec. 2.1 Remark "Bound on the number of PCG iterations").
+ *   density[N]      output Phi (host or device pointer)
+ *   iters           iterations performed
+ *   resid_hist      relative residual after 0..iters iterations (first
+ *                   min(hist_cap, iters+1) entries written; may be NULL)
+ *   kappa_est       condition number of the Lanczos tridiagonal built from the
+ *                   PCG coefficients (may be NULL)
+ * opts may be NULL.  Returns NOT_CONVERGED (density still written) if maxit is
+ * reached first, BREAKDOWN on p^T W p <= 0 or a non-finite value. */
+int msbem_solve(msbem_geom* g, const double gvec[3], const msbem_solve_opts* opts, double* density,
+                int* iters, double* resid_hist, int hist_cap, double* kappa_est);
+
+/* Timing of the last assemble / factor / solve on this geometry, in
+ * milliseconds measured with CUDA events on the context's stream:
+ * t[0] far field, t[1] near field, t[2] contraction to W, t[3] factor,
+ * t[4] solve.  Any entry not yet measured is 0. */
+int msbem_last_timings(const msbem_geom* g, double t[5]);
+
+/* Counters of this geometry: *launches = number of CUDA kernels the library
+ * has launched for it so far (all calls), *far_pairs = number of unordered
+ * triangle pairs sharing no vertex (the units of the far-field kernel).
+ * Either pointer may be NULL. */
+int msbem_counters(const msbem_geom* g, int64_t* launches, int64_t* far_pairs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSBEM_H */

@@ -29,8 +29,9 @@ def assemble_W(top: Topology, V: np.ndarray) -> np.ndarray:
     """W = sum_k S_k^T V S_k with the dense pair matrix V."""
     W = np.zeros((top.ndof, top.ndof))
     for Sk in top.S_matrices():
-        VS = (Sk.T @ V.T).T          # V @ S_k  (nt x ndof)
-        W += np.asarray(Sk.T @ VS)
+        SkT = Sk.T.tocsr()
+        Y = np.asarray(SkT @ V)          # S_k^T V            (ndof x nt)
+        W += np.asarray(SkT @ Y.T).T     # (S_k^T (S_k^T V)^T)^T = S_k^T V S_k  (V symmetric)
     return W
 
 

@@ -1,0 +1,256 @@
+"""GB300-native multiscreen hypersingular BEM: Python binding of libmsbem.
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+(``csrc/``, C ABI in ``include/msbem.h``).  There is no CPU fallback; if the
+library is missing or cannot be loaded, ``lib()`` raises.
+
+Low-level names mirror the C ABI (``msbem_create``, ``msbem_upload``, ...);
+``Solver`` wraps one context + one geometry for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmsbem.so")
+_lib = None
+
+MSBEM_OK = 0
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NONCONFORMING", -3: "POINT_CONTACT", -4: "OOM",
+          -5: "NOT_CONVERGED", -6: "BREAKDOWN", -7: "DEVICE_TIMEOUT", -8: "CUDA_ERROR",
+          -9: "NOT_READY"}
+
+
+class MsbemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class AssembleOpts(ctypes.Structure):
+    _fields_ = [("ss_order", ctypes.c_int), ("far_kernel", ctypes.c_int)]
+
+
+class PrecondOpts(ctypes.Structure):
+    _fields_ = [("wire_basket", ctypes.c_int), ("use_coarse", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int),
+                ("precondition", ctypes.c_int)]
+
+
+def lib():
+    """Load libmsbem.so (built by ``paper_2310_09204_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libmsbem.so not built ({LIB_PATH}); run paper_2310_09204_gb300/build.py")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "msbem_create": ([ctypes.POINTER(P), i32, P], i32),
+        "msbem_destroy": ([P], i32),
+        "msbem_last_error": ([P], ctypes.c_char_p),
+        "msbem_upload": ([P, P, i64, P, i64, P, i64, P, i64, P, P, ctypes.POINTER(P)], i32),
+        "msbem_geom_free": ([P], i32),
+        "msbem_ndofs": ([P, ctypes.POINTER(i64)], i32),
+        "msbem_dof_map": ([P, P, P], i32),
+        "msbem_split_info": ([P, P, P, P, P], i32),
+        "msbem_assemble": ([P, ctypes.POINTER(AssembleOpts)], i32),
+        "msbem_copy_matrix": ([P, i64, i64, P], i32),
+        "msbem_rhs": ([P, P, P], i32),
+        "msbem_factor": ([P, ctypes.POINTER(PrecondOpts)], i32),
+        "msbem_solve": ([P, P, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(i32), P, i32,
+                         ctypes.POINTER(d)], i32),
+        "msbem_last_timings": ([P, P], i32),
+        "msbem_counters": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
+        "msbem_mesh_dofs": ([P, i64, P, i64, ctypes.POINTER(i64), P, P, i64, ctypes.c_char_p, i32], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return _lib
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+def _check(ctx, st: int):
+    if st != MSBEM_OK:
+        raise MsbemError(st, lib().msbem_last_error(ctx).decode())
+
+
+# ---- low-level wrappers with the C names ------------------------------------
+
+def msbem_create(device: int = 0, stream: int = 0):
+    h = ctypes.c_void_p()
+    st = lib().msbem_create(ctypes.byref(h), device, stream)
+    if st != MSBEM_OK:
+        raise MsbemError(st, "msbem_create failed")
+    return h
+
+
+def msbem_destroy(ctx):
+    return lib().msbem_destroy(ctx)
+
+
+def msbem_upload(ctx, xyz, tri, coarse_xyz, coarse_tri, parent, patch):
+    xyz = np.ascontiguousarray(xyz, np.float64)
+    tri = np.ascontiguousarray(tri, np.int32)
+    cxyz = np.ascontiguousarray(coarse_xyz, np.float64)
+    ctri = np.ascontiguousarray(coarse_tri, np.int32)
+    parent = np.ascontiguousarray(parent, np.int32)
+    patch = np.ascontiguousarray(patch, np.int32)
+    g = ctypes.c_void_p()
+    st = lib().msbem_upload(ctx, _ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0], _ptr(cxyz),
+                            cxyz.shape[0], _ptr(ctri), ctri.shape[0], _ptr(parent), _ptr(patch),
+                            ctypes.byref(g))
+    _check(ctx, st)
+    return g
+
+
+def msbem_mesh_dofs(xyz, tri):
+    """Host-only topology of a mesh: (ndof, vertex_of_dof, sector_of_dof)."""
+    xyz = np.ascontiguousarray(xyz, np.float64)
+    tri = np.ascontiguousarray(tri, np.int32)
+    n = ctypes.c_int64()
+    buf = ctypes.create_string_buffer(256)
+    st = lib().msbem_mesh_dofs(_ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0], ctypes.byref(n),
+                               None, None, 0, buf, 256)
+    if st != MSBEM_OK:
+        raise MsbemError(st, buf.value.decode())
+    v = np.zeros(n.value, np.int32)
+    s = np.zeros(n.value, np.int32)
+    st = lib().msbem_mesh_dofs(_ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0], ctypes.byref(n),
+                               _ptr(v), _ptr(s), n.value, buf, 256)
+    if st != MSBEM_OK:
+        raise MsbemError(st, buf.value.decode())
+    return int(n.value), v, s
+
+
+def msbem_ndofs(geom) -> int:
+    n = ctypes.c_int64()
+    lib().msbem_ndofs(geom, ctypes.byref(n))
+    return int(n.value)
+
+
+class Solver:
+    """One context + one uploaded geometry."""
+
+    def __init__(self, geom=None, device: int = 0, stream: int | None = None, **arrays):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:  # pragma: no cover - torch without CUDA
+                stream = 0
+        self.ctx = msbem_create(device, stream)
+        self.geom = None
+        if geom is not None:
+            self.upload(geom.xyz, geom.tri, geom.coarse_xyz, geom.coarse_tri, geom.parent, geom.patch)
+        elif arrays:
+            self.upload(**arrays)
+
+    def upload(self, xyz, tri, coarse_xyz, coarse_tri, parent, patch):
+        self.free_geometry()
+        self.geom = msbem_upload(self.ctx, xyz, tri, coarse_xyz, coarse_tri, parent, patch)
+        self.n = msbem_ndofs(self.geom)
+        return self
+
+    def close(self):
+        if self.ctx is not None:
+            lib().msbem_destroy(self.ctx)
+            self.ctx = None
+            self.geom = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- queries
+    def dof_map(self):
+        v = np.zeros(self.n, np.int32)
+        s = np.zeros(self.n, np.int32)
+        _check(self.ctx, lib().msbem_dof_map(self.geom, _ptr(v), _ptr(s)))
+        return v, s
+
+    def split_info(self):
+        vals = [ctypes.c_int64() for _ in range(4)]
+        _check(self.ctx, lib().msbem_split_info(self.geom, *[ctypes.byref(v) for v in vals]))
+        return dict(zip(("n_faces", "n_wire_basket", "n_coarse", "max_face"), (v.value for v in vals)))
+
+    def counters(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.ctx, lib().msbem_counters(self.geom, ctypes.byref(a), ctypes.byref(b)))
+        return {"launches": int(a.value), "far_pairs": int(b.value)}
+
+    def free_geometry(self):
+        if self.geom is not None:
+            _check(self.ctx, lib().msbem_geom_free(self.geom))
+            self.geom = None
+
+    def timings(self):
+        t = np.zeros(5)
+        lib().msbem_last_timings(self.geom, _ptr(t))
+        return dict(zip(("far_ms", "near_ms", "contract_ms", "factor_ms", "solve_ms"), t.tolist()))
+
+    # --- the hot path
+    def assemble(self, ss_order: int = 5, far_kernel: int = 0):
+        o = AssembleOpts(ss_order, far_kernel)
+        _check(self.ctx, lib().msbem_assemble(self.geom, ctypes.byref(o)))
+        return self
+
+    def matrix(self, row0: int = 0, nrows: int | None = None, out=None):
+        nrows = self.n - row0 if nrows is None else nrows
+        if out is None:
+            out = np.empty((nrows, self.n), np.float64)
+        _check(self.ctx, lib().msbem_copy_matrix(self.geom, row0, nrows, _ptr(out)))
+        return out
+
+    def rhs(self, g, out=None):
+        gv = np.ascontiguousarray(g, np.float64)
+        if out is None:
+            out = np.empty(self.n, np.float64)
+        _check(self.ctx, lib().msbem_rhs(self.geom, _ptr(gv), _ptr(out)))
+        return out
+
+    def factor(self, wire_basket: int = 0, use_coarse: int = 1):
+        o = PrecondOpts(wire_basket, use_coarse)
+        _check(self.ctx, lib().msbem_factor(self.geom, ctypes.byref(o)))
+        return self
+
+    def solve(self, g, rtol: float = 1e-8, maxit: int = 1000, fixed: bool = False,
+              precondition: bool = True, out=None, hist_cap: int = 4096, raise_on_status=True):
+        gv = np.ascontiguousarray(g, np.float64)
+        if out is None:
+            out = np.empty(self.n, np.float64)
+        it = ctypes.c_int()
+        kap = ctypes.c_double()
+        hist = np.zeros(hist_cap, np.float64)
+        o = SolveOpts(rtol, maxit, int(fixed), int(precondition))
+        st = lib().msbem_solve(self.geom, _ptr(gv), ctypes.byref(o), _ptr(out), ctypes.byref(it),
+                               _ptr(hist), hist_cap, ctypes.byref(kap))
+        if raise_on_status:
+            _check(self.ctx, st)
+        n_it = int(it.value)
+        return {"density": out, "iters": n_it, "hist": hist[: min(hist_cap, n_it + 1)].copy(),
+                "kappa": float(kap.value), "status": st}

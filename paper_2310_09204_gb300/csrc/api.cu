@@ -1,0 +1,472 @@
+// C ABI of the msbem library (include/msbem.h): context and geometry handles,
+// host topology at upload, orchestration of the device kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "msbem_internal.h"
+
+using namespace msbem;
+
+struct msbem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::vector<msbem_geom*> geoms;
+  cudaEvent_t ev[8] = {};
+};
+
+struct msbem_geom {
+  msbem_ctx* ctx = nullptr;
+  Topo fine, coarse;
+  Split split;
+  DevGeom dev;
+  std::vector<int64_t> bptr;
+  int ss_order = 5;
+};
+
+namespace {
+
+int fail(msbem_ctx* c, int status, const std::string& msg) {
+  if (c) c->err = msg;
+  return status;
+}
+
+int cuda_fail(msbem_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(c, MSBEM_OOM, std::string(where) + ": out of device memory");
+  return fail(c, MSBEM_CUDA_ERROR, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n, cudaStream_t s) {
+  return cudaMallocAsync((void**)p, sizeof(T) * std::max<size_t>(n, 1), s);
+}
+
+template <class T>
+cudaError_t dput(T** p, const std::vector<T>& h, cudaStream_t s) {
+  cudaError_t e = dalloc(p, h.size(), s);
+  if (e != cudaSuccess || h.empty()) return e;
+  return cudaMemcpyAsync(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_dev(DevGeom& d, cudaStream_t s) {
+  void* ptrs[] = {d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
+                  d.d_jptr, d.d_jtri, d.d_jvec, d.d_jrhs, d.d_W, d.d_bptr, d.d_bdofs, d.d_boff,
+                  d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval,
+                  d.d_WP, d.d_vec, d.d_scal};
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, s);
+  cudaStreamSynchronize(s);
+  d = DevGeom();
+}
+
+// Extreme eigenvalues of the symmetric tridiagonal (d, e) by Sturm bisection.
+double sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (q < 0) ++cnt;
+  for (size_t i = 1; i < d.size(); ++i) {
+    double qq = (q == 0.0) ? 1e-300 : q;
+    q = d[i] - x - e[i - 1] * e[i - 1] / qq;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+double tridiag_kappa(const std::vector<double>& alpha, const std::vector<double>& beta) {
+  const size_t m = alpha.size();
+  if (m == 0) return NAN;
+  std::vector<double> d(m), e(m > 1 ? m - 1 : 0);
+  for (size_t j = 0; j < m; ++j) {
+    d[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+    if (j + 1 < m) e[j] = std::sqrt(beta[j]) / alpha[j];
+  }
+  double lo = 1e300, hi = -1e300;
+  for (size_t j = 0; j < m; ++j) {  // Gershgorin bounds
+    double r = (j > 0 ? std::fabs(e[j - 1]) : 0.0) + (j + 1 < m ? std::fabs(e[j]) : 0.0);
+    lo = std::min(lo, d[j] - r);
+    hi = std::max(hi, d[j] + r);
+  }
+  auto kth = [&](int k) {  // k-th smallest eigenvalue, 0-based
+    double a = lo, b = hi;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (a + b);
+      if (sturm_count(d, e, mid) > k) b = mid; else a = mid;
+      if (b - a <= 1e-15 * std::max(std::fabs(a), std::fabs(b))) break;
+    }
+    return 0.5 * (a + b);
+  };
+  return kth((int)m - 1) / kth(0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int msbem_create(msbem_ctx** ctx, int device, void* stream) {
+  if (!ctx) return MSBEM_INVALID_ARG;
+  *ctx = nullptr;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return MSBEM_CUDA_ERROR;
+  auto* c = new msbem_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  for (auto& ev : c->ev) cudaEventCreate(&ev);
+  *ctx = c;
+  return MSBEM_OK;
+}
+
+int msbem_destroy(msbem_ctx* c) {
+  if (!c) return MSBEM_INVALID_ARG;
+  cudaSetDevice(c->device);
+  for (auto* g : c->geoms) {
+    free_dev(g->dev, c->stream);
+    delete g;
+  }
+  for (auto& ev : c->ev) cudaEventDestroy(ev);
+  delete c;
+  return MSBEM_OK;
+}
+
+const char* msbem_last_error(const msbem_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                 const double* cxyz, int64_t ncv, const int32_t* ctri, int64_t nct,
+                 const int32_t* parent, const int32_t* patch, msbem_geom** out) {
+  if (!c) return MSBEM_INVALID_ARG;
+  if (!out || !xyz || !tri || !cxyz || !ctri || !parent || !patch || nv <= 0 || nt <= 0 ||
+      ncv <= 0 || nct <= 0)
+    return fail(c, MSBEM_INVALID_ARG, "msbem_upload: null pointer or empty mesh");
+  *out = nullptr;
+  cudaSetDevice(c->device);
+  auto g = std::make_unique<msbem_geom>();
+  g->ctx = c;
+  std::string err;
+  int st = build_topology(xyz, nv, tri, nt, g->fine, err);
+  if (st) return fail(c, st, "fine mesh: " + err);
+  st = build_topology(cxyz, ncv, ctri, nct, g->coarse, err);
+  if (st) return fail(c, st, "coarse mesh: " + err);
+  st = build_split(g->fine, g->coarse, parent, patch, g->split, err);
+  if (st) return fail(c, st, err);
+  std::vector<NearPair> near;
+  build_near_pairs(g->fine, near);
+  const Topo& f = g->fine;
+  const Split& sp = g->split;
+  DevGeom& d = g->dev;
+  cudaStream_t s = c->stream;
+  d.nt = nt;
+  d.nt_pad = (nt + 63) / 64 * 64;
+  d.ndof = f.ndof;
+  // triangle data: quadrature points, centroids, offsets
+  double bary[6][3], w6[6];
+  six_point_rule(bary, w6);
+  std::vector<double> qp(d.nt_pad * 18, 0.0), cen(d.nt_pad * 3, 0.0), area(d.nt_pad, 0.0);
+  std::vector<float> qoff(d.nt_pad * 36, 0.0f);
+  std::vector<int32_t> tpad(d.nt_pad * 3, -1);
+  for (int64_t T = 0; T < nt; ++T) {
+    const double* X[3] = {&f.xyz[3 * f.tri[3 * T]], &f.xyz[3 * f.tri[3 * T + 1]],
+                          &f.xyz[3 * f.tri[3 * T + 2]]};
+    for (int k = 0; k < 3; ++k) cen[3 * T + k] = (X[0][k] + X[1][k] + X[2][k]) / 3.0;
+    for (int p = 0; p < 6; ++p)
+      for (int k = 0; k < 3; ++k) {
+        double v = bary[p][0] * X[0][k] + bary[p][1] * X[1][k] + bary[p][2] * X[2][k];
+        qp[T * 18 + 3 * p + k] = v;
+        double off = v - cen[3 * T + k];
+        float hi = (float)off;
+        float lo = (float)(off - (double)hi);
+        qoff[T * 36 + 6 * p + 2 * k] = hi;
+        qoff[T * 36 + 6 * p + 2 * k + 1] = lo;
+      }
+    area[T] = f.area[T];
+    for (int a = 0; a < 3; ++a) tpad[3 * T + a] = f.tri[3 * T + a];
+  }
+  // curl vectors s_{T,nu} = coef (x_{a+1} - x_{a+2}) / (2|T|) and RHS weights
+  const int64_t ne = f.jptr[f.ndof];
+  std::vector<double> jvec(3 * ne), jrhs(3 * ne);
+  for (int64_t k = 0; k < ne; ++k) {
+    int64_t T = f.jtri[k];
+    int a = f.jloc[k];
+    const double* xa1 = &f.xyz[3 * f.tri[3 * T + (a + 1) % 3]];
+    const double* xa2 = &f.xyz[3 * f.tri[3 * T + (a + 2) % 3]];
+    for (int m = 0; m < 3; ++m) {
+      jvec[3 * k + m] = f.jcoef[k] * (xa1[m] - xa2[m]) / (2.0 * f.area[T]);
+      jrhs[3 * k + m] = f.jcoef[k] * f.area[T] / 3.0 * f.normal[3 * T + m];
+    }
+  }
+  // coarse prolongation in CSC form
+  const int64_t NH = sp.n_coarse;
+  std::vector<int64_t> cptr(NH + 1, 0);
+  std::vector<int32_t> crow(sp.p_col.size());
+  std::vector<double> cval(sp.p_col.size());
+  for (int32_t col : sp.p_col) cptr[col + 1]++;
+  for (int64_t m = 0; m < NH; ++m) cptr[m + 1] += cptr[m];
+  {
+    std::vector<int64_t> pos(cptr.begin(), cptr.end() - 1);
+    for (int64_t r = 0; r < f.ndof; ++r)
+      for (int64_t k = sp.p_ptr[r]; k < sp.p_ptr[r + 1]; ++k) {
+        int64_t dst = pos[sp.p_col[k]]++;
+        crow[dst] = (int32_t)r;
+        cval[dst] = sp.p_val[k];
+      }
+  }
+  g->bptr = sp.block_ptr;
+  d.n_blocks = (int64_t)sp.block_ptr.size() - 1;
+  d.n_coarse = NH;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chk(dput(&d.d_qp, qp, s));
+  chk(dput(&d.d_cen, cen, s));
+  chk(dput(&d.d_qoff, qoff, s));
+  chk(dput(&d.d_area, area, s));
+  chk(dput(&d.d_tri, tpad, s));
+  chk(dput(&d.d_xyz, f.xyz, s));
+  d.n_near = (int64_t)near.size();
+  {
+    int64_t ident = 0;
+    for (const NearPair& np : near) ident += (np.cls == 3);
+    d.n_far_pairs = nt * (nt - 1) / 2 - (d.n_near - ident);
+  }
+  chk(dput(&d.d_near, near, s));
+  chk(dput(&d.d_jptr, f.jptr, s));
+  chk(dput(&d.d_jtri, f.jtri, s));
+  chk(dput(&d.d_jvec, jvec, s));
+  chk(dput(&d.d_jrhs, jrhs, s));
+  chk(dput(&d.d_bptr, sp.block_ptr, s));
+  chk(dput(&d.d_bdofs, sp.block_dofs, s));
+  chk(dput(&d.d_pptr, sp.p_ptr, s));
+  chk(dput(&d.d_pcol, sp.p_col, s));
+  chk(dput(&d.d_pval, sp.p_val, s));
+  chk(dput(&d.d_cptr, cptr, s));
+  chk(dput(&d.d_crow, crow, s));
+  chk(dput(&d.d_cval, cval, s));
+  const int64_t N = f.ndof;
+  chk(dalloc(&d.d_V, (size_t)nt * nt, s));
+  chk(dalloc(&d.d_W, (size_t)N * N, s));
+  chk(dalloc(&d.d_WP, (size_t)std::max<int64_t>(NH, 1) * N, s));
+  chk(dalloc(&d.d_vec, (size_t)(5 * N + 2 * std::max<int64_t>(NH, 1) + 8), s));
+  chk(dalloc(&d.d_scal, (size_t)(8 + std::max<int64_t>(256, N / 8 + 8)), s));
+  chk(cudaStreamSynchronize(s));
+  if (e != cudaSuccess) {
+    free_dev(d, s);
+    return cuda_fail(c, e, "msbem_upload");
+  }
+  c->geoms.push_back(g.get());
+  *out = g.release();
+  return MSBEM_OK;
+}
+
+int msbem_mesh_dofs(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int64_t* ndof,
+                    int32_t* vertex_of_dof, int32_t* sector_of_dof, int64_t cap, char* errbuf,
+                    int errcap) {
+  if (errbuf && errcap > 0) errbuf[0] = 0;
+  if (!ndof) return MSBEM_INVALID_ARG;
+  Topo t;
+  std::string err;
+  int st = build_topology(xyz, nv, tri, nt, t, err);
+  if (st) {
+    if (errbuf && errcap > 0) {
+      std::strncpy(errbuf, err.c_str(), (size_t)errcap - 1);
+      errbuf[errcap - 1] = 0;
+    }
+    return st;
+  }
+  *ndof = t.ndof;
+  if (cap >= t.ndof) {
+    if (vertex_of_dof) std::memcpy(vertex_of_dof, t.dof_vertex.data(), sizeof(int32_t) * t.ndof);
+    if (sector_of_dof) std::memcpy(sector_of_dof, t.dof_sector.data(), sizeof(int32_t) * t.ndof);
+  }
+  return MSBEM_OK;
+}
+
+int msbem_geom_free(msbem_geom* g) {
+  if (!g) return MSBEM_INVALID_ARG;
+  msbem_ctx* c = g->ctx;
+  cudaSetDevice(c->device);
+  free_dev(g->dev, c->stream);
+  c->geoms.erase(std::remove(c->geoms.begin(), c->geoms.end(), g), c->geoms.end());
+  delete g;
+  return MSBEM_OK;
+}
+
+int msbem_ndofs(const msbem_geom* g, int64_t* n) {
+  if (!g || !n) return MSBEM_INVALID_ARG;
+  *n = g->fine.ndof;
+  return MSBEM_OK;
+}
+
+int msbem_dof_map(const msbem_geom* g, int32_t* vertex_of_dof, int32_t* sector_of_dof) {
+  if (!g) return MSBEM_INVALID_ARG;
+  if (vertex_of_dof) std::memcpy(vertex_of_dof, g->fine.dof_vertex.data(), sizeof(int32_t) * g->fine.ndof);
+  if (sector_of_dof) std::memcpy(sector_of_dof, g->fine.dof_sector.data(), sizeof(int32_t) * g->fine.ndof);
+  return MSBEM_OK;
+}
+
+int msbem_split_info(const msbem_geom* g, int64_t* n_faces, int64_t* n_wb, int64_t* n_coarse,
+                     int64_t* max_face) {
+  if (!g) return MSBEM_INVALID_ARG;
+  if (n_faces) *n_faces = g->split.n_faces;
+  if (n_wb) *n_wb = g->split.n_wb;
+  if (n_coarse) *n_coarse = g->split.n_coarse;
+  if (max_face) *max_face = g->split.max_face;
+  return MSBEM_OK;
+}
+
+int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
+  if (!g) return MSBEM_INVALID_ARG;
+  msbem_ctx* c = g->ctx;
+  cudaSetDevice(c->device);
+  int n = opts && opts->ss_order > 0 ? opts->ss_order : 5;
+  int far_kernel = opts ? opts->far_kernel : 0;
+  if (n < 2 || n > 16) return fail(c, MSBEM_INVALID_ARG, "ss_order must be in [2, 16]");
+  if (far_kernel < 0 || far_kernel > 1) return fail(c, MSBEM_INVALID_ARG, "far_kernel must be 0 or 1");
+  g->ss_order = n;
+  DevGeom& d = g->dev;
+  cudaStream_t s = c->stream;
+  double bary[6][3], w6[6], glx[16], glw[16];
+  six_point_rule(bary, w6);
+  gauss_legendre01(n, glx, glw);
+  cudaError_t e = set_far_constants(bary, w6);
+  if (e == cudaSuccess) e = set_far_df_constants(w6);
+  if (e != cudaSuccess) return cuda_fail(c, e, "far constants");
+  cudaEventRecord(c->ev[0], s);
+  e = (far_kernel == 1) ? launch_far_fp64(d, s) : launch_far_df(d, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "far field");
+  cudaEventRecord(c->ev[1], s);
+  e = launch_near(d, n, glx, glw, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "near field");
+  cudaEventRecord(c->ev[2], s);
+  e = launch_contract(d, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+  cudaEventRecord(c->ev[3], s);
+  d.launches += 1 + (d.n_near > 0) + (d.ndof > 0);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "assemble");
+  float t;
+  cudaEventElapsedTime(&t, c->ev[0], c->ev[1]); d.times[0] = t;
+  cudaEventElapsedTime(&t, c->ev[1], c->ev[2]); d.times[1] = t;
+  cudaEventElapsedTime(&t, c->ev[2], c->ev[3]); d.times[2] = t;
+  d.assembled = 1;
+  d.factored = 0;
+  return MSBEM_OK;
+}
+
+int msbem_copy_matrix(const msbem_geom* g, int64_t row0, int64_t nrows, double* out) {
+  if (!g || !out) return MSBEM_INVALID_ARG;
+  msbem_ctx* c = g->ctx;
+  if (!g->dev.assembled) return fail(c, MSBEM_NOT_READY, "msbem_copy_matrix: not assembled");
+  const int64_t N = g->fine.ndof;
+  if (row0 < 0 || nrows < 0 || row0 + nrows > N) return fail(c, MSBEM_INVALID_ARG, "row range");
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaMemcpyAsync(out, g->dev.d_W + row0 * N, sizeof(double) * nrows * N,
+                                  cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? MSBEM_OK : cuda_fail(c, e, "msbem_copy_matrix");
+}
+
+int msbem_rhs(const msbem_geom* g, const double gv[3], double* out) {
+  if (!g || !gv || !out) return MSBEM_INVALID_ARG;
+  msbem_ctx* c = g->ctx;
+  cudaSetDevice(c->device);
+  const int64_t N = g->fine.ndof;
+  double* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&tmp, sizeof(double) * std::max<int64_t>(N, 1), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "msbem_rhs");
+  e = launch_rhs(g->dev, gv, tmp, c->stream);
+  const_cast<msbem_geom*>(g)->dev.launches += (N > 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(double) * N, cudaMemcpyDefault, c->stream);
+  cudaFreeAsync(tmp, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? MSBEM_OK : cuda_fail(c, e, "msbem_rhs");
+}
+
+int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts) {
+  if (!g) return MSBEM_INVALID_ARG;
+  msbem_ctx* c = g->ctx;
+  if (!g->dev.assembled) return fail(c, MSBEM_NOT_READY, "msbem_factor: call msbem_assemble first");
+  cudaSetDevice(c->device);
+  DevGeom& d = g->dev;
+  int wb_diag = opts ? opts->wire_basket : 0;
+  d.use_coarse = opts ? (opts->use_coarse != 0) : 1;
+  if (wb_diag < 0 || wb_diag > 1) return fail(c, MSBEM_INVALID_ARG, "wire_basket must be 0 or 1");
+  d.wb_diag = (g->split.n_wb > 0) ? 0 : -1;  // marks whether the last block is the wire basket
+  cudaEventRecord(c->ev[4], c->stream);
+  int not_spd = 0;
+  cudaError_t e = factor_blocks(d, g->bptr, (g->split.n_wb > 0) ? wb_diag : 0, c->stream, &not_spd);
+  if (e != cudaSuccess) return cuda_fail(c, e, "msbem_factor");
+  const int nblk = (int)g->bptr.size() - 1;
+  int64_t off = 0;
+  for (int b = 0; b < nblk; ++b) off += (g->bptr[b + 1] - g->bptr[b]) * (g->bptr[b + 1] - g->bptr[b]);
+  d.d_AHinv = d.d_binv + off;
+  cudaEventRecord(c->ev[5], c->stream);
+  cudaStreamSynchronize(c->stream);
+  float t;
+  cudaEventElapsedTime(&t, c->ev[4], c->ev[5]);
+  d.times[3] = t;
+  if (not_spd) return fail(c, MSBEM_BREAKDOWN, "msbem_factor: a block is not positive definite");
+  d.factored = 1;
+  return MSBEM_OK;
+}
+
+int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts, double* density,
+                int* iters, double* hist, int hist_cap, double* kappa) {
+  if (!g || !gv || !density) return MSBEM_INVALID_ARG;
+  msbem_ctx* c = g->ctx;
+  DevGeom& d = g->dev;
+  double rtol = opts ? opts->rtol : 1e-8;
+  int maxit = opts ? opts->maxit : 1000;
+  int fixed = opts ? opts->fixed_iters : 0;
+  int prec = opts ? opts->precondition : 1;
+  if (!(rtol >= 0.0) || maxit < 1) return fail(c, MSBEM_INVALID_ARG, "rtol >= 0 and maxit >= 1 required");
+  if (!d.assembled) return fail(c, MSBEM_NOT_READY, "msbem_solve: not assembled");
+  if (prec && !d.factored) return fail(c, MSBEM_NOT_READY, "msbem_solve: call msbem_factor first");
+  cudaSetDevice(c->device);
+  const int64_t N = g->fine.ndof;
+  const bool dev_out = is_device_ptr(density);
+  PcgOut po;
+  cudaEventRecord(c->ev[6], c->stream);
+  cudaError_t e = run_pcg(d, gv, rtol, maxit, fixed, prec, d.d_vec, po, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "msbem_solve");
+  e = cudaMemcpyAsync(density, d.d_vec, sizeof(double) * N,
+                      dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  cudaEventRecord(c->ev[7], c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "msbem_solve copy-out");
+  float t;
+  cudaEventElapsedTime(&t, c->ev[6], c->ev[7]);
+  d.times[4] = t;
+  if (iters) *iters = po.iters;
+  if (hist && hist_cap > 0)
+    for (int i = 0; i < hist_cap && i < (int)po.hist.size(); ++i) hist[i] = po.hist[i];
+  if (kappa) *kappa = tridiag_kappa(po.alpha, po.beta);
+  if (po.status == MSBEM_NOT_CONVERGED) return fail(c, po.status, "msbem_solve: maxit reached");
+  if (po.status == MSBEM_BREAKDOWN) return fail(c, po.status, "msbem_solve: PCG breakdown");
+  return MSBEM_OK;
+}
+
+int msbem_counters(const msbem_geom* g, int64_t* launches, int64_t* far_pairs) {
+  if (!g) return MSBEM_INVALID_ARG;
+  if (launches) *launches = g->dev.launches;
+  if (far_pairs) *far_pairs = g->dev.n_far_pairs;
+  return MSBEM_OK;
+}
+
+int msbem_last_timings(const msbem_geom* g, double t[5]) {
+  if (!g || !t) return MSBEM_INVALID_ARG;
+  for (int i = 0; i < 5; ++i) t[i] = g->dev.times[i];
+  return MSBEM_OK;
+}
+
+}  // extern "C"

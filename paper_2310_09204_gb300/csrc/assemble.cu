@@ -1,0 +1,306 @@
+// Assembly of the hypersingular Galerkin matrix on sm_103a.
+//
+// a(psi~_nu, psi~_nu') = sum_{T,T'} V_{TT'} s_{T,nu} . s_{T',nu'}   (Sec. 4.3,
+// eq. eval_a_phiij with Cor. corW), where s_{T,nu} is the constant surface curl
+// of the jump of psi_nu on T and V_{TT'} = int_T int_T' 1/(4 pi |x-y|).
+//
+// Kernels:
+//   far_fp64_kernel  V_{TT'} for all pairs of a 64x64 triangle tile, 6x6 points
+//                    (native FP64); tiles on and above the diagonal only, the
+//                    lower half written by a shared-memory transpose.
+//   near_kernel      pairs sharing a vertex: Sauter-Schwab-type rules (identical
+//                    6 regions, edge 4, vertex 2) with Gauss-Legendre order n.
+//                    For a kernel of x - y on flat triangles the rules' integrand
+//                    does not depend on some of the [0,1]^4 coordinates, and is a
+//                    polynomial in the radial one; those coordinates are summed in
+//                    closed form (1/3 * 1/2, 1/6, 1/3), which is exact for
+//                    Gauss-Legendre of any order >= 2.  One warp per pair,
+//                    warp-shuffle reduction over the quadrature points.
+//   contract_kernel  W[nu,nu'] = sum_{k in J(nu)} sum_{k' in J(nu')} V[T_k,T_k'] s_k.s_k'
+//   rhs_kernel       L_nu = sum_{k in J(nu)} (c_+ - c_-)(g.n_T)|T|/3
+#include <cstdio>
+
+#include "msbem_internal.h"
+
+namespace msbem {
+
+#define FAR_TILE 64
+__constant__ double c_far_w[6];        // 6-point rule weights (sum 1)
+
+cudaError_t set_far_constants(const double bary[6][3], const double w[6]) {
+  (void)bary;
+  return cudaMemcpyToSymbol(c_far_w, w, sizeof(double) * 6);
+}
+
+// tile index -> (bi, bj) with bi <= bj, row-major over the upper triangle
+__device__ __forceinline__ void tile_coords(int64_t t, int nb, int& bi, int& bj) {
+  // rows have nb, nb-1, ... tiles; solve for bi
+  double disc = (2.0 * nb + 1.0) * (2.0 * nb + 1.0) - 8.0 * (double)t;
+  int r = (int)floor(((2.0 * nb + 1.0) - sqrt(disc)) * 0.5);
+  if (r < 0) r = 0;
+  auto start = [nb](int64_t row) { return row * (int64_t)nb - row * (row - 1) / 2; };
+  while (r > 0 && start(r) > t) --r;
+  while (r + 1 < nb && start(r + 1) <= t) ++r;
+  bi = r;
+  bj = (int)(r + (t - start(r)));
+}
+
+__global__ void __launch_bounds__(256) far_fp64_kernel(const double* __restrict__ qp,
+                                                       const double* __restrict__ area,
+                                                       const int32_t* __restrict__ tri, int nb,
+                                                       int64_t nt, int64_t ldv,
+                                                       double* __restrict__ V) {
+  __shared__ double s_q[FAR_TILE * 18];
+  __shared__ double s_area[FAR_TILE];
+  __shared__ int32_t s_tri[FAR_TILE * 3];
+  __shared__ double s_out[FAR_TILE][FAR_TILE + 1];
+  int bi, bj;
+  tile_coords(blockIdx.x, nb, bi, bj);
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)bi * FAR_TILE, col0 = (int64_t)bj * FAR_TILE;
+  for (int i = tid; i < FAR_TILE * 18; i += blockDim.x) s_q[i] = qp[col0 * 18 + i];
+  for (int i = tid; i < FAR_TILE; i += blockDim.x) s_area[i] = area[col0 + i];
+  for (int i = tid; i < FAR_TILE * 3; i += blockDim.x) s_tri[i] = tri[col0 * 3 + i];
+  const int r = tid & 63;
+  const int cgrp = tid >> 6;  // 4 groups of 16 columns
+  const int64_t T = row0 + r;
+  double x[18];
+#pragma unroll
+  for (int k = 0; k < 18; ++k) x[k] = qp[T * 18 + k];
+  const double aT = area[T];
+  const int32_t t0 = tri[T * 3], t1 = tri[T * 3 + 1], t2 = tri[T * 3 + 2];
+  __syncthreads();
+  for (int cc = 0; cc < 16; ++cc) {
+    const int c = cgrp * 16 + cc;
+    const double* y = &s_q[c * 18];
+    double acc = 0.0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      double inner = 0.0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        double dx = x[3 * p] - y[3 * q];
+        double dy = x[3 * p + 1] - y[3 * q + 1];
+        double dz = x[3 * p + 2] - y[3 * q + 2];
+        double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        inner = fma(c_far_w[q], rsqrt(r2), inner);
+      }
+      acc = fma(c_far_w[p], inner, acc);
+    }
+    const int32_t u0 = s_tri[3 * c], u1 = s_tri[3 * c + 1], u2 = s_tri[3 * c + 2];
+    bool touch = (t0 == u0) | (t0 == u1) | (t0 == u2) | (t1 == u0) | (t1 == u1) | (t1 == u2) |
+                 (t2 == u0) | (t2 == u1) | (t2 == u2) | (t0 < 0) | (u0 < 0);
+    double v = touch ? 0.0 : aT * s_area[c] * acc * (0.25 / M_PI);
+    s_out[r][c] = v;
+  }
+  __syncthreads();
+  // coalesced stores of the tile and of its transpose
+  for (int i = tid; i < FAR_TILE * FAR_TILE; i += blockDim.x) {
+    int rr = i / FAR_TILE, c = i % FAR_TILE;
+    int64_t R = row0 + rr, C = col0 + c;
+    if (R < nt && C < nt) V[R * ldv + C] = s_out[rr][c];
+  }
+  if (bi != bj) {
+    for (int i = tid; i < FAR_TILE * FAR_TILE; i += blockDim.x) {
+      int c = i / FAR_TILE, rr = i % FAR_TILE;
+      int64_t R = row0 + rr, C = col0 + c;
+      if (R < nt && C < nt) V[C * ldv + R] = s_out[rr][c];
+    }
+  }
+}
+
+cudaError_t launch_far_fp64(const DevGeom& g, cudaStream_t s) {
+  int nb = (int)(g.nt_pad / FAR_TILE);
+  int64_t tiles = (int64_t)nb * (nb + 1) / 2;
+  if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
+  far_fp64_kernel<<<(unsigned)tiles, 256, 0, s>>>(g.d_qp, g.d_area, g.d_tri, nb, g.nt, g.nt, g.d_V);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Near field
+// ---------------------------------------------------------------------------
+#define NEAR_MAXN 16
+__constant__ double c_gl_x[NEAR_MAXN], c_gl_w[NEAR_MAXN];
+
+__device__ __forceinline__ double inv_norm3(double a, double b, double c) {
+  return rsqrt(fma(c, c, fma(b, b, a * a)));
+}
+
+__device__ __forceinline__ double tri_area_d(const double* P) {
+  double e1x = P[3] - P[0], e1y = P[4] - P[1], e1z = P[5] - P[2];
+  double e2x = P[6] - P[0], e2y = P[7] - P[1], e2z = P[8] - P[2];
+  double cx = e1y * e2z - e1z * e2y, cy = e1z * e2x - e1x * e2z, cz = e1x * e2y - e1y * e2x;
+  return 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+}
+
+__global__ void __launch_bounds__(256) near_kernel(const NearPair* __restrict__ pairs, int64_t npairs,
+                                                   const double* __restrict__ xyz, int n, int64_t ldv,
+                                                   double* __restrict__ V) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= npairs) return;
+  const NearPair pr = pairs[w];
+  double P[9], Q[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      P[3 * i + k] = xyz[3 * (int64_t)pr.v[i] + k];
+      Q[3 * i + k] = xyz[3 * (int64_t)pr.v[3 + i] + k];
+    }
+  const double aT = tri_area_d(P), aS = tri_area_d(Q);
+  double sum = 0.0, pref;
+  if (pr.cls == 3) {
+    // identical: 1/|x-y| = 1/(xi |J w(eta)|); sectors s and s+3 coincide
+    const double e1[3] = {P[3] - P[0], P[4] - P[1], P[5] - P[2]};
+    const double e2[3] = {P[6] - P[3], P[7] - P[4], P[8] - P[5]};
+    for (int idx = lane; idx < 3 * n; idx += 32) {
+      int s = idx / n, j = idx % n;
+      double et = c_gl_x[j];
+      double a0, a1;  // J w = a0 e1 + a1 e2
+      if (s == 0) { a0 = 1.0; a1 = et; }
+      else if (s == 1) { a0 = 1.0 - et; a1 = 1.0; }
+      else { a0 = -et; a1 = 1.0 - et; }
+      sum += c_gl_w[j] * inv_norm3(a0 * e1[0] + a1 * e2[0], a0 * e1[1] + a1 * e2[1],
+                                   a0 * e1[2] + a1 * e2[2]);
+    }
+    pref = aT * aT / (3.0 * M_PI);
+  } else if (pr.cls == 2) {
+    // edge: x - y = xi (-f_u e + f_v c - f_w d) on 4 cones
+    const double e[3] = {P[3] - P[0], P[4] - P[1], P[5] - P[2]};
+    const double c[3] = {P[6] - P[3], P[7] - P[4], P[8] - P[5]};
+    const double d[3] = {Q[6] - Q[3], Q[7] - Q[4], Q[8] - Q[5]};
+    const int nn = n * n;
+    for (int idx = lane; idx < 4 * nn; idx += 32) {
+      int reg = idx / nn, rem = idx % nn, i1 = rem / n, i2 = rem % n;
+      double sg = c_gl_x[i1], ta = c_gl_x[i2], wq = c_gl_w[i1] * c_gl_w[i2];
+      double fu, fv, fw, J;
+      if (reg == 0) { fu = sg; fv = 1.0 - sg; fw = ta; J = 1.0; }
+      else if (reg == 1) { fu = sg * (1.0 - ta); fv = sg * ta; fw = 1.0; J = sg; }
+      else if (reg == 2) { fu = -sg * (1.0 - ta); fv = 1.0; fw = sg * ta; J = sg; }
+      else { fu = -sg; fv = ta; fw = 1.0 - sg; J = 1.0; }
+      double gx = -fu * e[0] + fv * c[0] - fw * d[0];
+      double gy = -fu * e[1] + fv * c[1] - fw * d[1];
+      double gz = -fu * e[2] + fv * c[2] - fw * d[2];
+      sum += wq * J * inv_norm3(gx, gy, gz);
+    }
+    pref = aT * aS / (6.0 * M_PI);
+  } else {
+    // vertex: 2 regions, x - y = xi g(e1,e2,e3)
+    const double p1[3] = {P[3] - P[0], P[4] - P[1], P[5] - P[2]};
+    const double p2[3] = {P[6] - P[3], P[7] - P[4], P[8] - P[5]};
+    const double q1[3] = {Q[3] - Q[0], Q[4] - Q[1], Q[5] - Q[2]};
+    const double q2[3] = {Q[6] - Q[3], Q[7] - Q[4], Q[8] - Q[5]};
+    const int nnn = n * n * n;
+    for (int idx = lane; idx < 2 * nnn; idx += 32) {
+      int reg = idx / nnn, rem = idx % nnn;
+      int i1 = rem / (n * n), i2 = (rem / n) % n, i3 = rem % n;
+      double a1 = c_gl_x[i1], a2 = c_gl_x[i2], a3 = c_gl_x[i3];
+      double wq = c_gl_w[i1] * c_gl_w[i2] * c_gl_w[i3] * a2;
+      double s1, s2, t1, t2;
+      if (reg == 0) { s1 = 1.0; s2 = a1; t1 = a2; t2 = a2 * a3; }
+      else { t1 = 1.0; t2 = a1; s1 = a2; s2 = a2 * a3; }
+      double gx = s1 * p1[0] + s2 * p2[0] - t1 * q1[0] - t2 * q2[0];
+      double gy = s1 * p1[1] + s2 * p2[1] - t1 * q1[1] - t2 * q2[1];
+      double gz = s1 * p1[2] + s2 * p2[2] - t1 * q1[2] - t2 * q2[2];
+      sum += wq * inv_norm3(gx, gy, gz);
+    }
+    pref = aT * aS / (3.0 * M_PI);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if (lane == 0) {
+    double v = pref * sum;
+    V[(int64_t)pr.T * ldv + pr.S] = v;
+    V[(int64_t)pr.S * ldv + pr.T] = v;
+  }
+}
+
+cudaError_t launch_near(const DevGeom& g, int n, const double* gl_x, const double* gl_w,
+                        cudaStream_t s) {
+  if (n < 2 || n > NEAR_MAXN) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_gl_x, gl_x, sizeof(double) * n, 0,
+                                          cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbolAsync(c_gl_w, gl_w, sizeof(double) * n, 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  if (g.n_near == 0) return cudaSuccess;
+  int64_t blocks = (g.n_near + 7) / 8;
+  near_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Contraction W = sum S^T V S (gather form, upper triangle then mirrored)
+// ---------------------------------------------------------------------------
+#define CT 32
+__global__ void __launch_bounds__(256) contract_kernel(const double* __restrict__ V, int64_t ldv,
+                                                       const int64_t* __restrict__ jptr,
+                                                       const int32_t* __restrict__ jtri,
+                                                       const double* __restrict__ jvec, int64_t N,
+                                                       int nbt, double* __restrict__ W) {
+  __shared__ double s_out[CT][CT + 1];
+  int bi, bj;
+  tile_coords(blockIdx.x, nbt, bi, bj);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t col = (int64_t)bj * CT + tx;
+  for (int rr = ty; rr < CT; rr += 8) {
+    const int64_t row = (int64_t)bi * CT + rr;
+    double acc = 0.0;
+    if (row < N && col < N) {
+      const int64_t k0 = jptr[row], k1 = jptr[row + 1];
+      const int64_t m0 = jptr[col], m1 = jptr[col + 1];
+      for (int64_t k = k0; k < k1; ++k) {
+        const double* vrow = V + (int64_t)jtri[k] * ldv;
+        const double sx = jvec[3 * k], sy = jvec[3 * k + 1], sz = jvec[3 * k + 2];
+        for (int64_t m = m0; m < m1; ++m) {
+          double dot = fma(sz, jvec[3 * m + 2], fma(sy, jvec[3 * m + 1], sx * jvec[3 * m]));
+          acc = fma(vrow[jtri[m]], dot, acc);
+        }
+      }
+    }
+    s_out[rr][tx] = acc;
+  }
+  __syncthreads();
+  // diagonal tiles keep their upper half and mirror it, so W is exactly symmetric
+  for (int rr = ty; rr < CT; rr += 8) {
+    int64_t row = (int64_t)bi * CT + rr, c = (int64_t)bj * CT + tx;
+    double v = (bi == bj && tx < rr) ? s_out[tx][rr] : s_out[rr][tx];
+    if (row < N && c < N) W[row * N + c] = v;
+  }
+  if (bi != bj) {
+    for (int cc = ty; cc < CT; cc += 8) {
+      int64_t R = (int64_t)bj * CT + cc, C = (int64_t)bi * CT + tx;
+      if (R < N && C < N) W[R * N + C] = s_out[tx][cc];
+    }
+  }
+}
+
+cudaError_t launch_contract(const DevGeom& g, cudaStream_t s) {
+  int nbt = (int)((g.ndof + CT - 1) / CT);
+  int64_t tiles = (int64_t)nbt * (nbt + 1) / 2;
+  if (tiles == 0) return cudaSuccess;
+  contract_kernel<<<(unsigned)tiles, 256, 0, s>>>(g.d_V, g.nt, g.d_jptr, g.d_jtri, g.d_jvec, g.ndof,
+                                                  nbt, g.d_W);
+  return cudaGetLastError();
+}
+
+__global__ void rhs_kernel(const int64_t* __restrict__ jptr, const double* __restrict__ jrhs,
+                           int64_t N, double gx, double gy, double gz, double* __restrict__ L) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double acc = 0.0;
+  for (int64_t k = jptr[i]; k < jptr[i + 1]; ++k)
+    acc += jrhs[3 * k] * gx + jrhs[3 * k + 1] * gy + jrhs[3 * k + 2] * gz;
+  L[i] = acc;
+}
+
+cudaError_t launch_rhs(const DevGeom& g, const double gv[3], double* out, cudaStream_t s) {
+  if (g.ndof == 0) return cudaSuccess;
+  rhs_kernel<<<(unsigned)((g.ndof + 255) / 256), 256, 0, s>>>(g.d_jptr, g.d_jrhs, g.ndof, gv[0],
+                                                               gv[1], gv[2], out);
+  return cudaGetLastError();
+}
+
+}  // namespace msbem

@@ -1,0 +1,145 @@
+// Internal declarations of the msbem library (not part of the C ABI).
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/msbem.h"
+
+namespace msbem {
+
+// ---------------------------------------------------------------------------
+// Host topology of a triangle mesh (Sec. 4.2-4.3): sectors at every vertex,
+// generalized vertices, dofs and the constant surface curls of the jumps of
+// the basis functions on every triangle.
+// ---------------------------------------------------------------------------
+struct Topo {
+  int64_t nv = 0, nt = 0;
+  std::vector<double> xyz;       // 3*nv
+  std::vector<int32_t> tri;      // 3*nt
+  std::vector<double> area;      // nt
+  std::vector<double> normal;    // 3*nt, unit, n_T = (x1-x0) x (x2-x0) / |.|
+  std::vector<int32_t> q;        // sectors per vertex
+  std::vector<int32_t> sector;   // 6*nt: sector[(T*2+side)*3 + a] at vertex tri[3T+a]
+  std::vector<int64_t> first_dof;  // nv+1
+  int64_t ndof = 0;
+  std::vector<int32_t> dof_vertex, dof_sector;
+  // jump coefficients: for dof nu, entries k in [jptr[nu], jptr[nu+1]):
+  // triangle jtri[k], local vertex jloc[k], coefficient jcoef[k] = c_+ - c_-
+  std::vector<int64_t> jptr;
+  std::vector<int32_t> jtri, jloc;
+  std::vector<double> jcoef;
+};
+
+// Builds the topology; returns MSBEM_OK or an error status with a message.
+int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, Topo& out,
+                   std::string& err);
+
+// Near pairs (pairs sharing at least one vertex, including T = T), with the
+// canonical local vertex orderings used by the singular rules:
+//   identical: (v0,v1,v2) as stored;
+//   edge:      A = smaller shared vertex id, B = larger, C / D the others;
+//   vertex:    O shared, then its cyclic successors in each triangle.
+// The triangle with the smaller index comes first.
+struct NearPair {
+  int32_t T, S;       // T <= S
+  int32_t cls;        // 3 identical, 2 edge, 1 vertex
+  int32_t v[6];       // canonical vertex ids: T's three then S's three
+};
+void build_near_pairs(const Topo& t, std::vector<NearPair>& out);
+
+// Face / wire-basket split (Sec. 5, eq. jumpSplit) and coarse prolongation.
+struct Split {
+  int64_t n_faces = 0;
+  std::vector<int64_t> block_ptr;    // n_blocks+1 (faces first, wire basket last)
+  std::vector<int32_t> block_dofs;   // dofs of every block, ascending within a block
+  int64_t n_wb = 0;
+  int64_t max_face = 0;
+  // coarse prolongation P (N x NH), CSR by fine row
+  int64_t n_coarse = 0;
+  std::vector<int64_t> p_ptr;
+  std::vector<int32_t> p_col;
+  std::vector<double> p_val;
+};
+int build_split(const Topo& fine, const Topo& coarse, const int32_t* parent, const int32_t* patch,
+                Split& out, std::string& err);
+
+// Quadrature constants computed on the host (own implementation).
+void gauss_legendre01(int n, double* x, double* w);
+void six_point_rule(double bary[6][3], double w[6]);
+
+// ---------------------------------------------------------------------------
+// Device-side state of one geometry
+// ---------------------------------------------------------------------------
+struct DevGeom {
+  // triangle data for the far field, arranged in tiles of 64 triangles
+  int64_t nt = 0, nt_pad = 0;
+  double* d_qp = nullptr;        // [nt_pad][6][3] quadrature points (FP64)
+  double* d_cen = nullptr;       // [nt_pad][3] centroids
+  float* d_qoff = nullptr;       // [nt_pad][6][3][2] point - centroid as (hi, lo) floats
+  double* d_area = nullptr;      // [nt_pad]
+  int32_t* d_tri = nullptr;      // [nt_pad][3] (padding: -1)
+  double* d_xyz = nullptr;       // [nv][3]
+  NearPair* d_near = nullptr;    // [n_near]
+  int64_t n_near = 0;
+  double* d_V = nullptr;         // [nt][nt] pair matrix (scratch between kernels)
+  // jump/curl lists
+  int64_t ndof = 0;
+  int64_t* d_jptr = nullptr;
+  int32_t* d_jtri = nullptr;
+  double* d_jvec = nullptr;      // [entries][3] curl vectors s_{T,nu}
+  double* d_jrhs = nullptr;      // [entries][3] coef |T|/3 n_T (RHS weights)
+  double* d_W = nullptr;         // [N][N]
+  // preconditioner
+  int64_t n_blocks = 0;
+  int64_t* d_bptr = nullptr;     // n_blocks+1
+  int32_t* d_bdofs = nullptr;
+  int64_t* d_boff = nullptr;     // offset of each block's inverse in d_binv
+  double* d_binv = nullptr;
+  int64_t binv_size = 0;
+  int wb_diag = 0;
+  int64_t n_coarse = 0;
+  int64_t* d_pptr = nullptr;     // P in CSR (by fine row)
+  int32_t* d_pcol = nullptr;
+  double* d_pval = nullptr;
+  int64_t* d_cptr = nullptr;     // P in CSC (by coarse column)
+  int32_t* d_crow = nullptr;
+  double* d_cval = nullptr;
+  double* d_AHinv = nullptr;     // [NH][NH]
+  double* d_WP = nullptr;        // [NH][N] scratch
+  int use_coarse = 1;
+  // PCG vectors
+  double* d_vec = nullptr;       // 6 vectors of N: x r z p q scratch
+  double* d_scal = nullptr;      // device scalars
+  int assembled = 0, factored = 0;
+  int64_t launches = 0;          // kernels launched by this geometry so far
+  int64_t n_far_pairs = 0;       // unordered pairs sharing no vertex
+  float times[5] = {0, 0, 0, 0, 0};
+};
+
+// launch wrappers (assemble.cu, factor.cu, pcg.cu); all return cudaError_t
+cudaError_t launch_far_fp64(const DevGeom& g, cudaStream_t s);
+cudaError_t launch_far_df(const DevGeom& g, cudaStream_t s);
+cudaError_t launch_near(const DevGeom& g, int ss_order, const double* gl_x, const double* gl_w,
+                        cudaStream_t s);
+cudaError_t launch_contract(const DevGeom& g, cudaStream_t s);
+cudaError_t launch_rhs(const DevGeom& g, const double gvec[3], double* out, cudaStream_t s);
+cudaError_t set_far_constants(const double bary[6][3], const double w[6]);
+cudaError_t set_far_df_constants(const double w[6]);
+
+cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag,
+                          cudaStream_t s, int* not_spd);
+
+struct PcgOut {
+  int iters = 0;
+  int status = 0;
+  std::vector<double> hist, alpha, beta;
+};
+cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, int fixed,
+                    int precondition, double* x_out_dev, PcgOut& out, cudaStream_t s);
+
+}  // namespace msbem

@@ -1,0 +1,60 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/msbem.h declares, and its host topology (the same code that
+msbem_upload runs) reproduces the oracle's dof numbering bit for bit."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+import paper_2310_09204_gb300 as M
+from paper_2310_09204_gb300 import build as B
+from paper_2310_09204_gb300 import workloads as WL
+from oracle.topology import Topology
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return M.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    hdr = open(os.path.join(ROOT, "include", "msbem.h")).read()
+    names = re.findall(r"^\w[\w\s\*]*?\b(msbem_\w+)\s*\(", hdr, re.M)
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("geom", [WL.flat_config(), WL.book(8, 2), WL.disk(5, fin=True), WL.bowtie(6, 2),
+                                  WL.book_config()], ids=lambda g: g.name)
+def test_dof_map_matches_oracle(L, geom):
+    n, v, s = M.msbem_mesh_dofs(geom.xyz, geom.tri)
+    top = Topology(geom.xyz, geom.tri)
+    assert n == top.ndof
+    assert np.array_equal(v, top.dof_vertex)
+    assert np.array_equal(s, top.dof_sector)
+
+
+def test_rejects_bad_meshes(L):
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [-1, 0, 0.5], [0, -1, 0.5]], float)
+    with pytest.raises(M.MsbemError) as e:
+        M.msbem_mesh_dofs(xyz, np.array([[0, 1, 2], [0, 3, 4]]))
+    assert e.value.status == -3                               # point contact
+    with pytest.raises(M.MsbemError) as e:
+        M.msbem_mesh_dofs(xyz, np.array([[0, 1, 2], [1, 2, 0]]))
+    assert e.value.status == -2                               # duplicate triangle
+    with pytest.raises(M.MsbemError) as e:
+        M.msbem_mesh_dofs(np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0]], float), np.array([[0, 1, 2]]))
+    assert e.value.status == -2                               # degenerate
+    with pytest.raises(M.MsbemError) as e:
+        M.msbem_mesh_dofs(xyz, np.array([[0, 1, 7]]))
+    assert e.value.status == -1                               # bad vertex id
+
+
+def test_single_triangle_has_no_dofs(L):
+    n, v, s = M.msbem_mesh_dofs(np.eye(3), np.array([[0, 1, 2]]))
+    assert n == 0
