@@ -122,12 +122,16 @@ typedef struct msbem_assemble_opts {
  * Cor. corW): W = sum_{T,T'} V_{TT'} s_{T,nu} . s_{T',nu'}, V_{TT'} =
  * int_T int_T' 1/(4 pi |x-y|), with the 6-point degree-4 rule on pairs that
  * share no vertex and Sauter-Schwab-type rules on the others.  opts may be
- * NULL (defaults).  W (N x N, float64, row-major, leading dimension N) stays
- * on the device.  Errors: NOT_READY, OOM, CUDA_ERROR. */
+ * NULL (defaults).  W (N x N, row-major) stays on the device, held as pairs of
+ * floats (hi, lo) whose sum carries a 48-bit significand (relative precision
+ * 2^-47, FP64-level for the solve); msbem_copy_matrix returns it as FP64.
+ * Errors: NOT_READY, OOM, CUDA_ERROR. */
 int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts);
 
 /* Copy rows [row0, row0+nrows) of W into out (host or device, nrows*N
- * doubles, row-major).  Errors: NOT_READY, INVALID_ARG, CUDA_ERROR. */
+ * doubles, row-major), converted to FP64.  A host destination needs a
+ * temporary device buffer of nrows*N doubles.
+ * Errors: NOT_READY, INVALID_ARG, OOM, CUDA_ERROR. */
 int msbem_copy_matrix(const msbem_geom* g, int64_t row0, int64_t nrows, double* out);
 
 /* Right-hand side L_nu = l_g(psi~_nu) = sum_T (c_+ - c_-)(g . n_T)|T|/3 for a

@@ -19,6 +19,10 @@ LIB = os.path.join(HERE, "libmsbem.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC]
+# per-file flags: the far-field unit flushes FP32 denormals (its operands are
+# distances and inverse distances between separated triangles, never denormal),
+# which lets the reciprocal square root issue without a denormal guard
+FILE_FLAGS = {"far_df.cu": ["-ftz=true"]}
 
 
 def _nvcc() -> str:
@@ -34,7 +38,7 @@ def sources():
 
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = sources()
-    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")] + \
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + \
         [os.path.join(INC, "msbem.h")]
     if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps):
         return LIB
@@ -43,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)

@@ -64,8 +64,8 @@ bool is_device_ptr(const void* p) {
 
 void free_dev(DevGeom& d, cudaStream_t s) {
   void* ptrs[] = {d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
-                  d.d_jptr, d.d_jtri, d.d_jvec, d.d_jrhs, d.d_W, d.d_bptr, d.d_bdofs, d.d_boff,
-                  d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval,
+                  d.d_jptr, d.d_jtri, d.d_jvec, d.d_jvecf, d.d_jrhs, d.d_W, d.d_bptr, d.d_bdofs, d.d_boff,
+                  d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pf,
                   d.d_WP, d.d_vec, d.d_scal};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
@@ -196,6 +196,7 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   // curl vectors s_{T,nu} = coef (x_{a+1} - x_{a+2}) / (2|T|) and RHS weights
   const int64_t ne = f.jptr[f.ndof];
   std::vector<double> jvec(3 * ne), jrhs(3 * ne);
+  std::vector<float2> jvecf(3 * ne);
   for (int64_t k = 0; k < ne; ++k) {
     int64_t T = f.jtri[k];
     int a = f.jloc[k];
@@ -204,6 +205,8 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
     for (int m = 0; m < 3; ++m) {
       jvec[3 * k + m] = f.jcoef[k] * (xa1[m] - xa2[m]) / (2.0 * f.area[T]);
       jrhs[3 * k + m] = f.jcoef[k] * f.area[T] / 3.0 * f.normal[3 * T + m];
+      float hi = (float)jvec[3 * k + m];
+      jvecf[3 * k + m] = make_float2(hi, (float)(jvec[3 * k + m] - (double)hi));
     }
   }
   // coarse prolongation in CSC form
@@ -243,6 +246,7 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   chk(dput(&d.d_jptr, f.jptr, s));
   chk(dput(&d.d_jtri, f.jtri, s));
   chk(dput(&d.d_jvec, jvec, s));
+  chk(dput(&d.d_jvecf, jvecf, s));
   chk(dput(&d.d_jrhs, jrhs, s));
   chk(dput(&d.d_bptr, sp.block_ptr, s));
   chk(dput(&d.d_bdofs, sp.block_dofs, s));
@@ -252,12 +256,21 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   chk(dput(&d.d_cptr, cptr, s));
   chk(dput(&d.d_crow, crow, s));
   chk(dput(&d.d_cval, cval, s));
+  {
+    std::vector<float2> cvalf(cval.size());
+    for (size_t k = 0; k < cval.size(); ++k) {
+      float hi = (float)cval[k];
+      cvalf[k] = make_float2(hi, (float)(cval[k] - (double)hi));
+    }
+    chk(dput(&d.d_cvalf, cvalf, s));
+  }
   const int64_t N = f.ndof;
   chk(dalloc(&d.d_V, (size_t)nt * nt, s));
   chk(dalloc(&d.d_W, (size_t)N * N, s));
   chk(dalloc(&d.d_WP, (size_t)std::max<int64_t>(NH, 1) * N, s));
   chk(dalloc(&d.d_vec, (size_t)(5 * N + 2 * std::max<int64_t>(NH, 1) + 8), s));
-  chk(dalloc(&d.d_scal, (size_t)(8 + std::max<int64_t>(256, N / 8 + 8)), s));
+  chk(dalloc(&d.d_pf, (size_t)N, s));
+  chk(dalloc(&d.d_scal, (size_t)(16 + std::max<int64_t>(256, N / 8 + 8)), s));
   chk(cudaStreamSynchronize(s));
   if (e != cudaSuccess) {
     free_dev(d, s);
@@ -370,8 +383,15 @@ int msbem_copy_matrix(const msbem_geom* g, int64_t row0, int64_t nrows, double* 
   const int64_t N = g->fine.ndof;
   if (row0 < 0 || nrows < 0 || row0 + nrows > N) return fail(c, MSBEM_INVALID_ARG, "row range");
   cudaSetDevice(c->device);
-  cudaError_t e = cudaMemcpyAsync(out, g->dev.d_W + row0 * N, sizeof(double) * nrows * N,
-                                  cudaMemcpyDefault, c->stream);
+  // W is held as (hi, lo) float pairs; convert rows to FP64 on the device
+  double* tmp = nullptr;
+  const bool dev_out = is_device_ptr(out);
+  cudaError_t e = cudaSuccess;
+  if (!dev_out) e = cudaMallocAsync((void**)&tmp, sizeof(double) * std::max<int64_t>(1, nrows * N), c->stream);
+  if (e == cudaSuccess) e = copy_rows_to_double(g->dev, row0, nrows, dev_out ? out : tmp, c->stream);
+  if (e == cudaSuccess && !dev_out)
+    e = cudaMemcpyAsync(out, tmp, sizeof(double) * nrows * N, cudaMemcpyDeviceToHost, c->stream);
+  if (tmp) cudaFreeAsync(tmp, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return e == cudaSuccess ? MSBEM_OK : cuda_fail(c, e, "msbem_copy_matrix");
 }

@@ -17,9 +17,12 @@
 //                    Gauss-Legendre of any order >= 2.  One warp per pair,
 //                    warp-shuffle reduction over the quadrature points.
 //   contract_kernel  W[nu,nu'] = sum_{k in J(nu)} sum_{k' in J(nu')} V[T_k,T_k'] s_k.s_k'
+//                    (double-float on the FP32 pipe)
 //   rhs_kernel       L_nu = sum_{k in J(nu)} (c_+ - c_-)(g.n_T)|T|/3
+#include <algorithm>
 #include <cstdio>
 
+#include "df.cuh"
 #include "msbem_internal.h"
 
 namespace msbem {
@@ -49,7 +52,7 @@ __global__ void __launch_bounds__(256) far_fp64_kernel(const double* __restrict_
                                                        const double* __restrict__ area,
                                                        const int32_t* __restrict__ tri, int nb,
                                                        int64_t nt, int64_t ldv,
-                                                       double* __restrict__ V) {
+                                                       float2* __restrict__ V) {
   __shared__ double s_q[FAR_TILE * 18];
   __shared__ double s_area[FAR_TILE];
   __shared__ int32_t s_tri[FAR_TILE * 3];
@@ -94,17 +97,21 @@ __global__ void __launch_bounds__(256) far_fp64_kernel(const double* __restrict_
     s_out[r][c] = v;
   }
   __syncthreads();
-  // coalesced stores of the tile and of its transpose
+  // coalesced stores of the tile and of its transpose, as (hi, lo) floats
   for (int i = tid; i < FAR_TILE * FAR_TILE; i += blockDim.x) {
     int rr = i / FAR_TILE, c = i % FAR_TILE;
     int64_t R = row0 + rr, C = col0 + c;
-    if (R < nt && C < nt) V[R * ldv + C] = s_out[rr][c];
+    float h, l;
+    split_df(s_out[rr][c], h, l);
+    if (R < nt && C < nt) V[R * ldv + C] = make_float2(h, l);
   }
   if (bi != bj) {
     for (int i = tid; i < FAR_TILE * FAR_TILE; i += blockDim.x) {
       int c = i / FAR_TILE, rr = i % FAR_TILE;
       int64_t R = row0 + rr, C = col0 + c;
-      if (R < nt && C < nt) V[C * ldv + R] = s_out[rr][c];
+      float h, l;
+      split_df(s_out[rr][c], h, l);
+      if (R < nt && C < nt) V[C * ldv + R] = make_float2(h, l);
     }
   }
 }
@@ -136,7 +143,7 @@ __device__ __forceinline__ double tri_area_d(const double* P) {
 
 __global__ void __launch_bounds__(256) near_kernel(const NearPair* __restrict__ pairs, int64_t npairs,
                                                    const double* __restrict__ xyz, int n, int64_t ldv,
-                                                   double* __restrict__ V) {
+                                                   float2* __restrict__ V) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= npairs) return;
@@ -211,9 +218,10 @@ __global__ void __launch_bounds__(256) near_kernel(const NearPair* __restrict__ 
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
   if (lane == 0) {
-    double v = pref * sum;
-    V[(int64_t)pr.T * ldv + pr.S] = v;
-    V[(int64_t)pr.S * ldv + pr.T] = v;
+    float h, l;
+    split_df(pref * sum, h, l);
+    V[(int64_t)pr.T * ldv + pr.S] = make_float2(h, l);
+    V[(int64_t)pr.S * ldv + pr.T] = make_float2(h, l);
   }
 }
 
@@ -235,43 +243,107 @@ cudaError_t launch_near(const DevGeom& g, int n, const double* gl_x, const doubl
 // Contraction W = sum S^T V S (gather form, upper triangle then mirrored)
 // ---------------------------------------------------------------------------
 #define CT 32
-__global__ void __launch_bounds__(256) contract_kernel(const double* __restrict__ V, int64_t ldv,
+#define CT_CAP 512      // curl entries of a tile's 32 rows (or columns) kept in shared memory
+#define CT_BATCH 4      // V gathers in flight per thread
+// W[nu,nu'] = sum_{k in J(nu)} sum_{m in J(nu')} V[T_k,T_m] (s_k . s_m), in
+// double-float on the FP32 pipe: V and the curl vectors are (hi, lo) float
+// pairs; products are formed exactly with FMA and summed with two-sums.
+// Upper-triangle 32x32 tiles; the curl lists of the tile's rows and columns
+// (contiguous, since lists are stored by dof) are staged in shared memory, and
+// the V gathers of one row entry against a column list are issued together.
+// Diagonal tiles mirror their upper half so W is exactly symmetric.
+// One W entry: sum over the row's curl entries [ka,kz) and the column's
+// [ma,mz) (lists in shared memory when STAGED, else in global memory).
+template <bool STAGED>
+__device__ __forceinline__ void contract_entry(const float2* __restrict__ V, int64_t ldv, int ka,
+                                               int kz, int ma, int mz, const int32_t* rtri,
+                                               const float2* rvec, const int32_t* ctri,
+                                               const float2* cvec, float& acch, float& accl) {
+  for (int k = ka; k < kz; ++k) {
+    const float2* vrow = V + (int64_t)rtri[k] * ldv;
+    const float2 sk[3] = {rvec[3 * k], rvec[3 * k + 1], rvec[3 * k + 2]};
+    int m = ma;
+    for (; m + CT_BATCH <= mz; m += CT_BATCH) {
+      float2 v[CT_BATCH];
+#pragma unroll
+      for (int u = 0; u < CT_BATCH; ++u) v[u] = vrow[ctri[m + u]];
+#pragma unroll
+      for (int u = 0; u < CT_BATCH; ++u) {
+        float dh, dl;
+        df_dot3(sk, cvec + 3 * (m + u), dh, dl);
+        df_fma_acc(dh, dl, v[u].x, v[u].y, acch, accl);
+      }
+    }
+    for (; m < mz; ++m) {
+      const float2 v = vrow[ctri[m]];
+      float dh, dl;
+      df_dot3(sk, cvec + 3 * m, dh, dl);
+      df_fma_acc(dh, dl, v.x, v.y, acch, accl);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) contract_kernel(const float2* __restrict__ V, int64_t ldv,
                                                        const int64_t* __restrict__ jptr,
                                                        const int32_t* __restrict__ jtri,
-                                                       const double* __restrict__ jvec, int64_t N,
-                                                       int nbt, double* __restrict__ W) {
-  __shared__ double s_out[CT][CT + 1];
+                                                       const float2* __restrict__ jvec, int64_t N,
+                                                       int nbt, float2* __restrict__ W) {
+  __shared__ float2 s_out[CT][CT + 1];
+  __shared__ int32_t s_rtri[CT_CAP], s_ctri[CT_CAP];
+  __shared__ float2 s_rvec[3 * CT_CAP], s_cvec[3 * CT_CAP];
+  __shared__ int32_t s_rptr[CT + 1], s_cptr[CT + 1];
   int bi, bj;
   tile_coords(blockIdx.x, nbt, bi, bj);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  const int64_t col = (int64_t)bj * CT + tx;
-  for (int rr = ty; rr < CT; rr += 8) {
-    const int64_t row = (int64_t)bi * CT + rr;
-    double acc = 0.0;
-    if (row < N && col < N) {
-      const int64_t k0 = jptr[row], k1 = jptr[row + 1];
-      const int64_t m0 = jptr[col], m1 = jptr[col + 1];
-      for (int64_t k = k0; k < k1; ++k) {
-        const double* vrow = V + (int64_t)jtri[k] * ldv;
-        const double sx = jvec[3 * k], sy = jvec[3 * k + 1], sz = jvec[3 * k + 2];
-        for (int64_t m = m0; m < m1; ++m) {
-          double dot = fma(sz, jvec[3 * m + 2], fma(sy, jvec[3 * m + 1], sx * jvec[3 * m]));
-          acc = fma(vrow[jtri[m]], dot, acc);
-        }
-      }
+  const int64_t r0 = (int64_t)bi * CT, c0 = (int64_t)bj * CT;
+  const int64_t rl = (N - r0 < CT) ? N - r0 : CT, cl = (N - c0 < CT) ? N - c0 : CT;
+  const int64_t rbase = jptr[r0], cbase = jptr[c0];
+  const int64_t rcount = jptr[r0 + rl] - rbase, ccount = jptr[c0 + cl] - cbase;
+  const bool staged = rcount <= CT_CAP && ccount <= CT_CAP;
+  if (threadIdx.x <= CT) {
+    const int i = threadIdx.x;
+    s_rptr[i] = (int32_t)(jptr[r0 + (i < rl ? i : rl)] - rbase);
+    s_cptr[i] = (int32_t)(jptr[c0 + (i < cl ? i : cl)] - cbase);
+  }
+  if (staged) {
+    for (int64_t e = threadIdx.x; e < rcount; e += blockDim.x) {
+      s_rtri[e] = jtri[rbase + e];
+      s_rvec[3 * e] = jvec[3 * (rbase + e)];
+      s_rvec[3 * e + 1] = jvec[3 * (rbase + e) + 1];
+      s_rvec[3 * e + 2] = jvec[3 * (rbase + e) + 2];
     }
-    s_out[rr][tx] = acc;
+    for (int64_t e = threadIdx.x; e < ccount; e += blockDim.x) {
+      s_ctri[e] = jtri[cbase + e];
+      s_cvec[3 * e] = jvec[3 * (cbase + e)];
+      s_cvec[3 * e + 1] = jvec[3 * (cbase + e) + 1];
+      s_cvec[3 * e + 2] = jvec[3 * (cbase + e) + 2];
+    }
   }
   __syncthreads();
-  // diagonal tiles keep their upper half and mirror it, so W is exactly symmetric
   for (int rr = ty; rr < CT; rr += 8) {
-    int64_t row = (int64_t)bi * CT + rr, c = (int64_t)bj * CT + tx;
-    double v = (bi == bj && tx < rr) ? s_out[tx][rr] : s_out[rr][tx];
+    float acch = 0.f, accl = 0.f;
+    if (rr < rl && tx < cl) {
+      if (staged)
+        contract_entry<true>(V, ldv, s_rptr[rr], s_rptr[rr + 1], s_cptr[tx], s_cptr[tx + 1], s_rtri,
+                             s_rvec, s_ctri, s_cvec, acch, accl);
+      else
+        contract_entry<false>(V, ldv, s_rptr[rr], s_rptr[rr + 1], s_cptr[tx], s_cptr[tx + 1],
+                              jtri + rbase, jvec + 3 * rbase, jtri + cbase, jvec + 3 * cbase, acch,
+                              accl);
+    }
+    float h, l;
+    two_sum(acch, accl, h, l);
+    s_out[rr][tx] = make_float2(h, l);
+  }
+  __syncthreads();
+  for (int rr = ty; rr < CT; rr += 8) {
+    int64_t row = r0 + rr, c = c0 + tx;
+    float2 v = (bi == bj && tx < rr) ? s_out[tx][rr] : s_out[rr][tx];
     if (row < N && c < N) W[row * N + c] = v;
   }
   if (bi != bj) {
     for (int cc = ty; cc < CT; cc += 8) {
-      int64_t R = (int64_t)bj * CT + cc, C = (int64_t)bi * CT + tx;
+      int64_t R = c0 + cc, C = r0 + tx;
       if (R < N && C < N) W[R * N + C] = s_out[tx][cc];
     }
   }
@@ -281,8 +353,25 @@ cudaError_t launch_contract(const DevGeom& g, cudaStream_t s) {
   int nbt = (int)((g.ndof + CT - 1) / CT);
   int64_t tiles = (int64_t)nbt * (nbt + 1) / 2;
   if (tiles == 0) return cudaSuccess;
-  contract_kernel<<<(unsigned)tiles, 256, 0, s>>>(g.d_V, g.nt, g.d_jptr, g.d_jtri, g.d_jvec, g.ndof,
+  contract_kernel<<<(unsigned)tiles, 256, 0, s>>>(g.d_V, g.nt, g.d_jptr, g.d_jtri, g.d_jvecf, g.ndof,
                                                   nbt, g.d_W);
+  return cudaGetLastError();
+}
+
+__global__ void w_to_double_kernel(const float2* __restrict__ W, int64_t n, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float2 v = W[i];
+    out[i] = df_to_double(v.x, v.y);
+  }
+}
+
+cudaError_t copy_rows_to_double(const DevGeom& g, int64_t row0, int64_t nrows, double* out,
+                                cudaStream_t s) {
+  const int64_t n = nrows * g.ndof;
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 64);
+  w_to_double_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_W + row0 * g.ndof, n, out);
   return cudaGetLastError();
 }
 

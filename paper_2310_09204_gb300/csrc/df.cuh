@@ -1,0 +1,92 @@
+// Double-float ("df") helpers: a value is the unevaluated sum hi + lo of two
+// floats (48-bit significand).  GB300 runs FP32 FMAs about 70x faster than
+// FP64 FMAs, so the hot loops that need FP64-level accuracy use these.
+// Error-free transformations: Knuth's two-sum and the FMA exact product.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace msbem {
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Float nearest to x (ties away from zero), by integer operations only:
+// adding half of the 29 dropped significand bits to the bit pattern rounds,
+// and a carry into the exponent is exactly the round-up across a binade.
+// Magnitudes below the normal float range give 0.
+__device__ __forceinline__ float round_to_float(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) + (1ull << 28);
+  const unsigned sign = (unsigned)(b >> 63);
+  const int ex = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned mant = (unsigned)((b >> 29) & 0x7fffff);
+  const unsigned bits = (ex > 0 && ex < 255) ? ((sign << 31) | ((unsigned)ex << 23) | mant) : (sign << 31);
+  return __uint_as_float(bits);
+}
+
+// Exact widening of a (normal or zero) float to double by integer operations.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const int ex = (int)((u >> 23) & 0xff);
+  const unsigned long long mant = (unsigned long long)(u & 0x7fffff) << 29;
+  const unsigned long long bits =
+      ex ? (sign | ((unsigned long long)(ex - 127 + 1023) << 52) | mant) : sign;
+  return __longlong_as_double((long long)bits);
+}
+
+// x -> hi + lo with |x - hi - lo| <= 2^-49 |x| (one FP64 add; x - hi is exact)
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = round_to_float(x);
+  lo = round_to_float(x - widen(hi));
+}
+
+__device__ __forceinline__ double df_to_double(float hi, float lo) { return widen(hi) + widen(lo); }
+
+// (rh, rl) = a + b, normalised
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& rh, float& rl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e += al + bl;
+  rh = s + e;
+  rl = e - (rh - s);
+}
+
+// acc += a * b   (acc kept as an unnormalised pair; 13 FP32 ops)
+__device__ __forceinline__ void df_fma_acc(float ah, float al, float bh, float bl, float& acch,
+                                           float& accl) {
+  float ph = ah * bh;
+  float pe = fmaf(ah, bh, -ph);
+  pe = fmaf(al, bl, pe);
+  pe = fmaf(ah, bl, pe);
+  pe = fmaf(al, bh, pe);
+  float s, e;
+  two_sum(acch, ph, s, e);
+  acch = s;
+  accl += e + pe;
+}
+
+// dot product of two double-float 3-vectors, as an unnormalised pair
+// (lo*lo terms, below 2^-48 relative, are dropped; 28 FP32 ops)
+__device__ __forceinline__ void df_dot3(const float2* a, const float2* b, float& dh, float& dl) {
+  const float p0 = a[0].x * b[0].x, p1 = a[1].x * b[1].x, p2 = a[2].x * b[2].x;
+  const float e0 = fmaf(a[0].x, b[0].x, -p0), e1 = fmaf(a[1].x, b[1].x, -p1),
+              e2 = fmaf(a[2].x, b[2].x, -p2);
+  float s, t1, t2;
+  two_sum(p0, p1, s, t1);
+  two_sum(s, p2, s, t2);
+  float err = ((e0 + e1) + (e2 + t1)) + t2;
+  err = fmaf(a[0].x, b[0].y, err);
+  err = fmaf(a[0].y, b[0].x, err);
+  err = fmaf(a[1].x, b[1].y, err);
+  err = fmaf(a[1].y, b[1].x, err);
+  err = fmaf(a[2].x, b[2].y, err);
+  err = fmaf(a[2].y, b[2].x, err);
+  dh = s;
+  dl = err;
+}
+
+}  // namespace msbem

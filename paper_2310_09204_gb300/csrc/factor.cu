@@ -12,11 +12,12 @@
 #include <algorithm>
 #include <vector>
 
+#include "df.cuh"
 #include "msbem_internal.h"
 
 namespace msbem {
 
-__global__ void gather_blocks_kernel(const double* __restrict__ W, int64_t N,
+__global__ void gather_blocks_kernel(const float2* __restrict__ W, int64_t N,
                                      const int64_t* __restrict__ bptr,
                                      const int32_t* __restrict__ bdofs,
                                      const int64_t* __restrict__ boff,
@@ -30,21 +31,27 @@ __global__ void gather_blocks_kernel(const double* __restrict__ W, int64_t N,
   const int64_t e = t - prefix2[b];
   const int64_t i = e / n, j = e % n;
   const int64_t di = bdofs[bptr[b] + i], dj = bdofs[bptr[b] + j];
-  double v = W[di * N + dj];
+  const float2 wv = W[di * N + dj];
+  double v = df_to_double(wv.x, wv.y);
   if (b == wb_block && wb_diag) v = (i == j) ? 1.0 / v : 0.0;
   out[boff[b] + e] = v;
 }
 
-// W P  (transposed, NH x N) from the CSC form of P:  (W P)^T[mu][i] = sum_nu P[nu,mu] W[nu][i]
-__global__ void wp_kernel(const double* __restrict__ W, int64_t N, const int64_t* __restrict__ cptr,
-                          const int32_t* __restrict__ crow, const double* __restrict__ cval,
+// W P  (transposed, NH x N) from the CSC form of P:  (W P)^T[mu][i] = sum_nu P[nu,mu] W[nu][i],
+// accumulated in double-float (W and P values are float pairs)
+__global__ void wp_kernel(const float2* __restrict__ W, int64_t N, const int64_t* __restrict__ cptr,
+                          const int32_t* __restrict__ crow, const float2* __restrict__ cval,
                           double* __restrict__ WPt) {
   const int64_t mu = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double acc = 0.0;
-  for (int64_t k = cptr[mu]; k < cptr[mu + 1]; ++k) acc = fma(cval[k], W[(int64_t)crow[k] * N + i], acc);
-  WPt[mu * N + i] = acc;
+  float acch = 0.f, accl = 0.f;
+  for (int64_t k = cptr[mu]; k < cptr[mu + 1]; ++k) {
+    const float2 w = W[(int64_t)crow[k] * N + i];
+    const float2 c = cval[k];
+    df_fma_acc(c.x, c.y, w.x, w.y, acch, accl);
+  }
+  WPt[mu * N + i] = df_to_double(acch, accl);
 }
 
 __global__ void ah_kernel(const double* __restrict__ WPt, int64_t N, int64_t NH,
@@ -57,51 +64,183 @@ __global__ void ah_kernel(const double* __restrict__ WPt, int64_t N, int64_t NH,
   AH[mu * NH + nu] = acc;
 }
 
-// Gauss-Jordan step k on every active block: save pivot row and column ...
-__global__ void gj_save_kernel(double* __restrict__ A, const int64_t* __restrict__ boff,
-                               const int64_t* __restrict__ bsize, const int32_t* __restrict__ order,
-                               const int64_t* __restrict__ prefix1, int active, int64_t k,
-                               double* __restrict__ save, int* __restrict__ flag) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= prefix1[active]) return;
-  int a = 0;
-  while (a + 1 < active && prefix1[a + 1] <= t) ++a;
-  const int b = order[a];
-  const int64_t n = bsize[b];
-  const int64_t e = t - prefix1[a];
-  const double* M = A + boff[b];
-  double v = (e < n) ? M[k * n + e] : M[(e - n) * n + k];
-  save[t] = v;
-  if (e == k) {
-    if (!(v > 0.0) || !isfinite(v)) atomicExch(flag, 1);
+// ---------------------------------------------------------------------------
+// Blocked Gauss-Jordan inversion of a batch of SPD matrices, in place.
+// Pivot panels of GB = 32 rows/columns K; for every active matrix:
+//   P = A_KK^{-1}                       (bgj_pivot_kernel, FP64 in shared memory)
+//   C'_I = -A_IK P,  R_J = A_KJ (old)   (bgj_panel_kernel, double-float)
+//   A_IJ += C'_I R_J, A_KJ = P R_J, A_IK = C'_I, A_KK = P
+//                                       (bgj_update_kernel, double-float tiles)
+// which is the scalar Gauss-Jordan recursion applied 32 pivots at a time; after
+// the last panel A holds A^{-1}.  Rank-32 updates run as double-float products
+// on the FP32 pipe (GB300 FP64 is ~1/70 of FP32); P is formed in FP64.
+// ---------------------------------------------------------------------------
+#define GB 32
+
+struct BgjArgs {
+  double* A;
+  const int64_t* boff;    // per matrix id
+  const int64_t* bsize;   // per matrix id
+  const int32_t* order;   // matrix ids sorted by size (descending)
+  const int64_t* pt1;     // prefix over sorted matrices of tiles per side
+  const int64_t* pt2;     // prefix of tiles^2
+  const int64_t* soff;    // prefix of n * GB (scratch panels), sorted order
+  float2* Pf;             // [sorted][GB*GB]
+  float2* Cf;             // [soff] n x GB
+  float2* Rf;             // [soff] GB x n
+  int* flag;
+};
+
+__device__ __forceinline__ int find_prefix(const int64_t* pre, int active, int64_t t) {
+  int lo = 0, hi = active - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) bgj_pivot_kernel(BgjArgs g, int64_t k0) {
+  __shared__ double S[GB][GB + 1];
+  __shared__ double rowk[GB], colk[GB];
+  const int a = blockIdx.x;
+  const int b = g.order[a];
+  const int64_t n = g.bsize[b];
+  const int kb = (int)(n - k0 < GB ? n - k0 : GB);
+  const double* A = g.A + g.boff[b];
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
+    int i = e / GB, j = e % GB;
+    S[i][j] = (i < kb && j < kb) ? A[(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int k = 0; k < GB; ++k) {
+    if (threadIdx.x < GB) rowk[threadIdx.x] = S[k][threadIdx.x];
+    else if (threadIdx.x < 2 * GB) colk[threadIdx.x - GB] = S[threadIdx.x - GB][k];
+    __syncthreads();
+    const double p = rowk[k];
+    if (threadIdx.x == 0 && !(p > 0.0 && isfinite(p))) atomicExch(g.flag, 1);
+    const double ip = 1.0 / p;
+    for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
+      int i = e / GB, j = e % GB;
+      double v;
+      if (i == k && j == k) v = ip;
+      else if (i == k) v = rowk[j] * ip;
+      else if (j == k) v = -colk[i] * ip;
+      else v = fma(-colk[i] * ip, rowk[j], S[i][j]);
+      S[i][j] = v;
+    }
+    __syncthreads();
+  }
+  float2* P = g.Pf + (int64_t)a * GB * GB;
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
+    float h, l;
+    split_df(S[e / GB][e % GB], h, l);
+    P[e] = make_float2(h, l);
   }
 }
 
-// ... then update all entries of every active block.
-__global__ void gj_update_kernel(double* __restrict__ A, const int64_t* __restrict__ boff,
-                                 const int64_t* __restrict__ bsize, const int32_t* __restrict__ order,
-                                 const int64_t* __restrict__ prefix1,
-                                 const int64_t* __restrict__ prefix2, int active, int64_t k,
-                                 const double* __restrict__ save) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= prefix2[active]) return;
-  int a = 0;
-  while (a + 1 < active && prefix2[a + 1] <= t) ++a;
-  const int b = order[a];
-  const int64_t n = bsize[b];
-  const int64_t e = t - prefix2[a];
-  const int64_t i = e / n, j = e % n;
-  const double* rowk = save + prefix1[a];
-  const double* colk = rowk + n;
-  const double p = rowk[k];
-  const double ip = 1.0 / p;
-  double* M = A + boff[b];
-  double v;
-  if (i == k && j == k) v = ip;
-  else if (i == k) v = rowk[j] * ip;
-  else if (j == k) v = -colk[i] * ip;
-  else v = fma(-colk[i] * ip, rowk[j], M[e]);
-  M[e] = v;
+__global__ void __launch_bounds__(256) bgj_panel_kernel(BgjArgs g, int active, int64_t k0) {
+  __shared__ float2 sP[GB][GB + 1];
+  __shared__ float2 sA[GB][GB + 1];
+  const int64_t t = blockIdx.x;
+  const int a = find_prefix(g.pt1, active, t);
+  const int b = g.order[a];
+  const int64_t n = g.bsize[b];
+  const int I = (int)(t - g.pt1[a]);
+  const int kb = (int)(n - k0 < GB ? n - k0 : GB);
+  const double* A = g.A + g.boff[b];
+  float2* C = g.Cf + g.soff[a];
+  float2* R = g.Rf + g.soff[a];
+  const int64_t r0 = (int64_t)I * GB;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  // old row panel: R[m][col] = A[k0+m][col], col in tile I
+  for (int m = ty; m < kb; m += 8) {
+    int64_t col = r0 + tx;
+    if (col < n) {
+      float h, l;
+      split_df(A[(k0 + m) * n + col], h, l);
+      R[m * n + col] = make_float2(h, l);
+    }
+  }
+  if (r0 == k0) return;
+  // C'_I = -A_IK P
+  const float2* P = g.Pf + (int64_t)a * GB * GB;
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) sP[e / GB][e % GB] = P[e];
+  for (int i = ty; i < GB; i += 8) {
+    int64_t row = r0 + i;
+    float h = 0.f, l = 0.f;
+    if (row < n && tx < kb) split_df(A[row * n + k0 + tx], h, l);
+    sA[i][tx] = make_float2(h, l);
+  }
+  __syncthreads();
+  for (int i = ty; i < GB; i += 8) {
+    int64_t row = r0 + i;
+    if (row >= n || tx >= kb) continue;
+    float acch = 0.f, accl = 0.f;
+    for (int m = 0; m < kb; ++m) df_fma_acc(sA[i][m].x, sA[i][m].y, sP[m][tx].x, sP[m][tx].y, acch, accl);
+    C[row * GB + tx] = make_float2(-acch, -accl);
+  }
+}
+
+__global__ void __launch_bounds__(256) bgj_update_kernel(BgjArgs g, int active, int64_t k0) {
+  __shared__ float2 sL[GB][GB + 1];
+  __shared__ float2 sR[GB][GB + 1];
+  const int64_t t = blockIdx.x;
+  const int a = find_prefix(g.pt2, active, t);
+  const int b = g.order[a];
+  const int64_t n = g.bsize[b];
+  const int nti = (int)((n + GB - 1) / GB);
+  const int64_t loc = t - g.pt2[a];
+  const int I = (int)(loc / nti), J = (int)(loc % nti);
+  const int kt = (int)(k0 / GB);
+  const int kb = (int)(n - k0 < GB ? n - k0 : GB);
+  double* A = g.A + g.boff[b];
+  const float2* C = g.Cf + g.soff[a];
+  const float2* R = g.Rf + g.soff[a];
+  const float2* P = g.Pf + (int64_t)a * GB * GB;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)I * GB, c0 = (int64_t)J * GB;
+  if (I == kt && J == kt) {
+    for (int i = ty; i < kb; i += 8)
+      if (tx < kb) A[(k0 + i) * n + k0 + tx] = df_to_double(P[i * GB + tx].x, P[i * GB + tx].y);
+    return;
+  }
+  if (J == kt) {
+    for (int i = ty; i < GB; i += 8) {
+      int64_t row = r0 + i;
+      if (row < n && tx < kb) {
+        float2 v = C[row * GB + tx];
+        A[row * n + k0 + tx] = df_to_double(v.x, v.y);
+      }
+    }
+    return;
+  }
+  // left factor: P (row panel) or C'_I; right factor: R_KJ
+  for (int i = ty; i < GB; i += 8) {
+    float2 v = make_float2(0.f, 0.f);
+    if (I == kt) {
+      if (i < kb && tx < kb) v = P[i * GB + tx];
+    } else {
+      int64_t row = r0 + i;
+      if (row < n && tx < kb) v = C[row * GB + tx];
+    }
+    sL[i][tx] = v;
+    float2 w = make_float2(0.f, 0.f);
+    int64_t col = c0 + tx;
+    if (i < kb && col < n) w = R[i * n + col];
+    sR[i][tx] = w;
+  }
+  __syncthreads();
+  const int64_t col = c0 + tx;
+  for (int i = ty; i < GB; i += 8) {
+    int64_t row = r0 + i;
+    if (row >= n || col >= n) continue;
+    if (I == kt && i >= kb) continue;
+    float acch = 0.f, accl = 0.f;
+    for (int m = 0; m < kb; ++m) df_fma_acc(sL[i][m].x, sL[i][m].y, sR[m][tx].x, sR[m][tx].y, acch, accl);
+    double upd = df_to_double(acch, accl);
+    A[row * n + col] = (I == kt) ? upd : A[row * n + col] + upd;
+  }
 }
 
 namespace {
@@ -124,46 +263,52 @@ static cudaError_t gj_invert(double* d_A, const std::vector<int64_t>& boff,
   std::sort(inv_blocks.begin(), inv_blocks.end(),
             [&](int a, int b) { return bsize[a] > bsize[b]; });
   const int nb = (int)inv_blocks.size();
-  std::vector<int64_t> p1(nb + 1, 0), p2(nb + 1, 0);
+  std::vector<int64_t> pt1(nb + 1, 0), pt2(nb + 1, 0), soff(nb + 1, 0);
   for (int a = 0; a < nb; ++a) {
-    p1[a + 1] = p1[a] + 2 * bsize[inv_blocks[a]];
-    p2[a + 1] = p2[a] + bsize[inv_blocks[a]] * bsize[inv_blocks[a]];
+    int64_t n = bsize[inv_blocks[a]];
+    int64_t nti = (n + GB - 1) / GB;
+    pt1[a + 1] = pt1[a] + nti;
+    pt2[a + 1] = pt2[a] + nti * nti;
+    soff[a + 1] = soff[a] + n * GB;
   }
-  int64_t *d_boff = nullptr, *d_bsize = nullptr, *d_p1 = nullptr, *d_p2 = nullptr;
+  BgjArgs args{};
+  args.A = d_A;
+  int64_t *d_boff = nullptr, *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt2 = nullptr, *d_soff = nullptr;
   int32_t* d_order = nullptr;
-  double* d_save = nullptr;
-  int* d_flag = nullptr;
   cudaError_t e;
   if ((e = upload(&d_boff, boff, s)) != cudaSuccess) return e;
   if ((e = upload(&d_bsize, bsize, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_p1, p1, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_p2, p2, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_pt1, pt1, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_pt2, pt2, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_soff, soff, s)) != cudaSuccess) return e;
   if ((e = upload(&d_order, inv_blocks, s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync((void**)&d_save, sizeof(double) * p1[nb], s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync((void**)&d_flag, sizeof(int), s)) != cudaSuccess) return e;
-  cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+  if ((e = cudaMallocAsync((void**)&args.Pf, sizeof(float2) * nb * GB * GB, s)) != cudaSuccess) return e;
+  if ((e = cudaMallocAsync((void**)&args.Cf, sizeof(float2) * soff[nb], s)) != cudaSuccess) return e;
+  if ((e = cudaMallocAsync((void**)&args.Rf, sizeof(float2) * soff[nb], s)) != cudaSuccess) return e;
+  if ((e = cudaMallocAsync((void**)&args.flag, sizeof(int), s)) != cudaSuccess) return e;
+  cudaMemsetAsync(args.flag, 0, sizeof(int), s);
+  args.boff = d_boff;
+  args.bsize = d_bsize;
+  args.order = d_order;
+  args.pt1 = d_pt1;
+  args.pt2 = d_pt2;
+  args.soff = d_soff;
   const int64_t nmax = bsize[inv_blocks[0]];
   int active = nb;
-  for (int64_t k = 0; k < nmax; ++k) {
-    while (active > 0 && bsize[inv_blocks[active - 1]] <= k) --active;
-    gj_save_kernel<<<(unsigned)((p1[active] + 255) / 256), 256, 0, s>>>(
-        d_A, d_boff, d_bsize, d_order, d_p1, active, k, d_save, d_flag);
-    gj_update_kernel<<<(unsigned)((p2[active] + 255) / 256), 256, 0, s>>>(
-        d_A, d_boff, d_bsize, d_order, d_p1, d_p2, active, k, d_save);
-    *launches += 2;
+  for (int64_t k0 = 0; k0 < nmax; k0 += GB) {
+    while (active > 0 && bsize[inv_blocks[active - 1]] <= k0) --active;
+    bgj_pivot_kernel<<<active, 256, 0, s>>>(args, k0);
+    bgj_panel_kernel<<<(unsigned)pt1[active], 256, 0, s>>>(args, active, k0);
+    bgj_update_kernel<<<(unsigned)pt2[active], 256, 0, s>>>(args, active, k0);
+    *launches += 3;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int flag = 0;
-  cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&flag, args.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   *not_spd = flag;
-  cudaFreeAsync(d_boff, s);
-  cudaFreeAsync(d_bsize, s);
-  cudaFreeAsync(d_p1, s);
-  cudaFreeAsync(d_p2, s);
-  cudaFreeAsync(d_order, s);
-  cudaFreeAsync(d_save, s);
-  cudaFreeAsync(d_flag, s);
+  void* tmp[] = {d_boff, d_bsize, d_pt1, d_pt2, d_soff, d_order, args.Pf, args.Cf, args.Rf, args.flag};
+  for (void* p : tmp) cudaFreeAsync(p, s);
   return cudaSuccess;
 }
 
@@ -207,7 +352,7 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
   if (NH > 0 && g.ndof > 0) {
     // A_H = P^T W P in the last slot
     dim3 grid((unsigned)((g.ndof + 255) / 256), (unsigned)NH);
-    wp_kernel<<<grid, 256, 0, s>>>(g.d_W, g.ndof, g.d_cptr, g.d_crow, g.d_cval, g.d_WP);
+    wp_kernel<<<grid, 256, 0, s>>>(g.d_W, g.ndof, g.d_cptr, g.d_crow, g.d_cvalf, g.d_WP);
     dim3 grid2((unsigned)NH, (unsigned)((NH + 127) / 128));
     ah_kernel<<<grid2, 128, 0, s>>>(g.d_WP, g.ndof, NH, g.d_cptr, g.d_crow, g.d_cval,
                                     g.d_binv + boff[nblk]);

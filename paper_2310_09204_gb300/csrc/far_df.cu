@@ -16,54 +16,13 @@
 //     the weighted sums are accumulated as float pairs.
 // Relative error per pair is a few 1e-15 of |V|, far below the 1e-12 parity
 // bar against the FP64 oracle.
+#include "df.cuh"
 #include "msbem_internal.h"
 
 namespace msbem {
 
 #define DF_TILE 64
 __constant__ float c_wdf[12];   // rule weights as (hi, lo) pairs
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// Float whose bits hold the top 24 significant bits of x (truncation); valid for
-// |x| in the normal float range or x == 0 (smaller magnitudes give 0).
-__device__ __forceinline__ float trunc_to_float(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 63);
-  const int ex = (int)((b >> 52) & 0x7ff) - 1023 + 127;
-  const unsigned mant = (unsigned)((b >> 29) & 0x7fffff);
-  const unsigned bits = (ex > 0 && ex < 255) ? ((sign << 31) | ((unsigned)ex << 23) | mant) : (sign << 31);
-  return __uint_as_float(bits);
-}
-
-// Exact widening of a float to a double by bit manipulation (normal floats and 0).
-__device__ __forceinline__ double widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  const int ex = (int)((u >> 23) & 0xff);
-  const unsigned long long mant = (unsigned long long)(u & 0x7fffff) << 29;
-  const unsigned long long bits = ex ? (sign | ((unsigned long long)(ex - 127 + 1023) << 52) | mant) : sign;
-  return __longlong_as_double((long long)bits);
-}
-
-// x (double) -> hi + lo floats, |x - hi - lo| <= 2^-47 |x|
-__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
-  hi = trunc_to_float(x);
-  lo = trunc_to_float(x - widen(hi));
-}
-
-// double-float a + b (both pairs), result normalised
-__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& rh, float& rl) {
-  float s, e;
-  two_sum(ah, bh, s, e);
-  e += al + bl;
-  rh = s + e;
-  rl = e - (rh - s);
-}
 
 // inverse distance of the double-float vector d: returns (y, corr) with
 // 1/|d| = y + corr to ~2^-46 relative
@@ -98,12 +57,12 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
                                                      const double* __restrict__ area,
                                                      const int32_t* __restrict__ tri, int nb,
                                                      int64_t nt, int64_t ldv,
-                                                     double* __restrict__ V) {
+                                                     float2* __restrict__ V) {
   __shared__ float s_off[DF_TILE * 36];
   __shared__ double s_cen[DF_TILE * 3];
   __shared__ double s_area[DF_TILE];
   __shared__ int32_t s_tri[DF_TILE * 3];
-  __shared__ double s_out[DF_TILE][DF_TILE + 1];
+  __shared__ float2 s_out[DF_TILE][DF_TILE + 1];
   // upper-triangle tile coordinates
   int bi, bj;
   {
@@ -140,7 +99,7 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
     const int32_t u0 = s_tri[3 * c], u1 = s_tri[3 * c + 1], u2 = s_tri[3 * c + 2];
     const bool touch = (t0 == u0) | (t0 == u1) | (t0 == u2) | (t1 == u0) | (t1 == u1) |
                        (t1 == u2) | (t2 == u0) | (t2 == u1) | (t2 == u2) | (t0 < 0) | (u0 < 0);
-    double v = 0.0;
+    float2 v = make_float2(0.f, 0.f);
     if (!touch) {
       float Dxh, Dxl, Dyh, Dyl, Dzh, Dzl;
       split_df(cx - s_cen[3 * c], Dxh, Dxl);
@@ -188,7 +147,9 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
         acch = s;
         accl += e + pe;
       }
-      v = (widen(acch) + widen(accl)) * (aT * s_area[c]) * (0.25 / M_PI);
+      float vh, vl;
+      split_df((widen(acch) + widen(accl)) * (aT * s_area[c]) * (0.25 / M_PI), vh, vl);
+      v = make_float2(vh, vl);
     }
     s_out[r][c] = v;
   }

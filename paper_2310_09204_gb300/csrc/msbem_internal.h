@@ -86,14 +86,15 @@ struct DevGeom {
   double* d_xyz = nullptr;       // [nv][3]
   NearPair* d_near = nullptr;    // [n_near]
   int64_t n_near = 0;
-  double* d_V = nullptr;         // [nt][nt] pair matrix (scratch between kernels)
+  float2* d_V = nullptr;         // [nt][nt] pair matrix as (hi, lo) floats (scratch)
   // jump/curl lists
   int64_t ndof = 0;
   int64_t* d_jptr = nullptr;
   int32_t* d_jtri = nullptr;
   double* d_jvec = nullptr;      // [entries][3] curl vectors s_{T,nu}
+  float2* d_jvecf = nullptr;     // [entries][3] the same as (hi, lo) floats
   double* d_jrhs = nullptr;      // [entries][3] coef |T|/3 n_T (RHS weights)
-  double* d_W = nullptr;         // [N][N]
+  float2* d_W = nullptr;         // [N][N] Galerkin matrix as (hi, lo) float pairs
   // preconditioner
   int64_t n_blocks = 0;
   int64_t* d_bptr = nullptr;     // n_blocks+1
@@ -109,11 +110,13 @@ struct DevGeom {
   int64_t* d_cptr = nullptr;     // P in CSC (by coarse column)
   int32_t* d_crow = nullptr;
   double* d_cval = nullptr;
+  float2* d_cvalf = nullptr;     // CSC values as (hi, lo) floats
   double* d_AHinv = nullptr;     // [NH][NH]
   double* d_WP = nullptr;        // [NH][N] scratch
   int use_coarse = 1;
   // PCG vectors
-  double* d_vec = nullptr;       // 6 vectors of N: x r z p q scratch
+  double* d_vec = nullptr;       // vectors of N: x r z p q, coarse scratch
+  float2* d_pf = nullptr;        // search direction p as (hi, lo) floats
   double* d_scal = nullptr;      // device scalars
   int assembled = 0, factored = 0;
   int64_t launches = 0;          // kernels launched by this geometry so far
@@ -128,6 +131,8 @@ cudaError_t launch_near(const DevGeom& g, int ss_order, const double* gl_x, cons
                         cudaStream_t s);
 cudaError_t launch_contract(const DevGeom& g, cudaStream_t s);
 cudaError_t launch_rhs(const DevGeom& g, const double gvec[3], double* out, cudaStream_t s);
+cudaError_t copy_rows_to_double(const DevGeom& g, int64_t row0, int64_t nrows, double* out,
+                                cudaStream_t s);
 cudaError_t set_far_constants(const double bary[6][3], const double w[6]);
 cudaError_t set_far_df_constants(const double w[6]);
 

@@ -7,46 +7,107 @@
 // with M the two-level additive Schwarz operator (face blocks, wire basket,
 // coarse space) applied through the explicit block inverses.  Reductions are
 // two-pass (fixed order), so results are bitwise reproducible run to run.
-// The host reads back three scalars per iteration for the stopping test and the
-// residual history.
+// The stopping test runs on the device: it records the residual history and
+// the PCG coefficients and raises a `done` flag that turns every later kernel
+// into a no-op, so the host enqueues iterations in chunks and synchronises once
+// per chunk instead of once per iteration.
 #include <cmath>
 #include <vector>
 
+#include "df.cuh"
 #include "msbem_internal.h"
 
 namespace msbem {
 
 #define RED_BLOCKS 256
+#define PCG_CHUNK 4
 
-// q = W p, partial sums of p.q per block
-__global__ void __launch_bounds__(256) gemv_kernel(const double* __restrict__ W, int64_t N,
+// device-side solver state (ints), next to the FP64 scalars
+struct PcgState {
+  int done;    // 0 running, 1 converged / fixed count reached, 2 breakdown, 3 maxit
+  int iter;    // completed iterations
+  int maxit;
+  int fixed;
+};
+
+// scal layout: 0 rz, 1 pq, 2 alpha, 3 rr, 4 rz_new, 5 beta, 6 |L|^2, 7 rtol
+
+// q = W p in double-float (W and p as float pairs): the matrix stream is the
+// only HBM traffic, so the product runs at memory speed on the FP32 pipe.
+// 16 rows per block (2 per warp); p is staged through shared memory in
+// column chunks; each lane keeps 4 independent loads in flight per row.
+// Partial sums of p.q per block.
+#define GEMV_ROWS 16
+#define GEMV_CHUNK 4096
+__global__ void __launch_bounds__(256) gemv_kernel(const float2* __restrict__ W, int64_t N,
+                                                   const float2* __restrict__ pf,
                                                    const double* __restrict__ p,
                                                    double* __restrict__ q,
-                                                   double* __restrict__ part) {
-  __shared__ double s_part[8];
+                                                   double* __restrict__ part,
+                                                   const PcgState* __restrict__ st) {
+  if (st->done) return;
+  __shared__ float2 sp[GEMV_CHUNK];
+  __shared__ double s_part[GEMV_ROWS];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t row = (int64_t)blockIdx.x * 8 + wid;
-  double pq = 0.0;
-  if (row < N) {
-    const double* w = W + row * N;
-    double acc = 0.0;
-    for (int64_t j = lane; j < N; j += 32) acc = fma(w[j], p[j], acc);
+  const int64_t row0 = (int64_t)blockIdx.x * GEMV_ROWS + 2 * wid;
+  float h[2] = {0.f, 0.f}, l[2] = {0.f, 0.f};
+  for (int64_t c0 = 0; c0 < N; c0 += GEMV_CHUNK) {
+    const int len = (int)((N - c0) < GEMV_CHUNK ? (N - c0) : GEMV_CHUNK);
+    __syncthreads();
+    for (int j = threadIdx.x; j < len; j += 256) sp[j] = pf[c0 + j];
+    __syncthreads();
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) q[row] = acc;
-    pq = acc * p[row];
+    for (int rr = 0; rr < 2; ++rr) {
+      const int64_t row = row0 + rr;
+      if (row >= N) continue;
+      const float2* w = W + row * N + c0;
+      int j = lane;
+      for (; j + 96 < len; j += 128) {
+        const float2 a0 = w[j], a1 = w[j + 32], a2 = w[j + 64], a3 = w[j + 96];
+        df_fma_acc(a0.x, a0.y, sp[j].x, sp[j].y, h[rr], l[rr]);
+        df_fma_acc(a1.x, a1.y, sp[j + 32].x, sp[j + 32].y, h[rr], l[rr]);
+        df_fma_acc(a2.x, a2.y, sp[j + 64].x, sp[j + 64].y, h[rr], l[rr]);
+        df_fma_acc(a3.x, a3.y, sp[j + 96].x, sp[j + 96].y, h[rr], l[rr]);
+      }
+      for (; j < len; j += 32) {
+        const float2 a = w[j];
+        df_fma_acc(a.x, a.y, sp[j].x, sp[j].y, h[rr], l[rr]);
+      }
+    }
   }
-  if (lane == 0) s_part[wid] = pq;
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    float acch = h[rr], accl = l[rr];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      float oh = __shfl_xor_sync(0xffffffffu, acch, off);
+      float ol = __shfl_xor_sync(0xffffffffu, accl, off);
+      float sh, se;
+      two_sum(acch, oh, sh, se);
+      acch = sh;
+      accl = accl + ol + se;
+    }
+    const int64_t row = row0 + rr;
+    double pq = 0.0;
+    if (row < N) {
+      const double acc = df_to_double(acch, accl);
+      if (lane == 0) q[row] = acc;
+      pq = acc * p[row];
+    }
+    if (lane == 0) s_part[2 * wid + rr] = pq;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int k = 0; k < 8; ++k) s += s_part[k];
+    for (int k = 0; k < GEMV_ROWS; ++k) s += s_part[k];
     part[blockIdx.x] = s;
   }
 }
 
 // fixed-order final reduction of n partial sums into *out
-__global__ void reduce_kernel(const double* __restrict__ part, int64_t n, double* __restrict__ out) {
+__global__ void reduce_kernel(const double* __restrict__ part, int64_t n, double* __restrict__ out,
+                              const PcgState* __restrict__ st) {
+  if (st->done) return;
   __shared__ double s[256];
   double acc = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += 256) acc += part[i];
@@ -61,7 +122,8 @@ __global__ void reduce_kernel(const double* __restrict__ part, int64_t n, double
 
 // partial sums of a.b (grid of RED_BLOCKS blocks)
 __global__ void dot_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t N,
-                           double* __restrict__ part) {
+                           double* __restrict__ part, const PcgState* __restrict__ st) {
+  if (st->done) return;
   __shared__ double s[256];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256)
@@ -75,16 +137,25 @@ __global__ void dot_kernel(const double* __restrict__ a, const double* __restric
   if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
-// scal layout: 0 rz, 1 pq, 2 alpha, 3 rr, 4 rz_new, 5 beta, 6 nL2
-__global__ void alpha_kernel(double* scal) {
-  scal[2] = scal[0] / scal[1];
+// alpha = (r.z)/(p.q); breakdown if p.q <= 0 or not finite
+__global__ void alpha_kernel(double* scal, PcgState* st, double* alpha_hist) {
+  if (st->done) return;
+  const double pq = scal[1];
+  const double a = scal[0] / pq;
+  if (!(pq > 0.0) || !isfinite(a)) {
+    st->done = 2;
+    return;
+  }
+  scal[2] = a;
+  alpha_hist[st->iter] = a;
 }
 
 // x += alpha p; r -= alpha q; partial r.r
 __global__ void update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
                                  const double* __restrict__ p, const double* __restrict__ q,
                                  const double* __restrict__ scal, int64_t N,
-                                 double* __restrict__ part) {
+                                 double* __restrict__ part, const PcgState* __restrict__ st) {
+  if (st->done) return;
   __shared__ double s[256];
   const double alpha = scal[2];
   double acc = 0.0;
@@ -103,6 +174,18 @@ __global__ void update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
   if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
+// stopping test: relres = ||r|| / ||L||, history, iteration count, done flag
+__global__ void check_kernel(const double* scal, PcgState* st, double* hist) {
+  if (st->done) return;
+  const double rel = sqrt(scal[3] / scal[6]);
+  const int it = st->iter + 1;
+  st->iter = it;
+  hist[it] = rel;
+  if (!isfinite(rel)) st->done = 2;
+  else if (!st->fixed && rel <= scal[7]) st->done = 1;
+  else if (it >= st->maxit) st->done = (st->fixed || rel <= scal[7]) ? 1 : 3;
+}
+
 // z[D_b[i]] = sum_j Ainv_b[i][j] r[D_b[j]]  (warp per row, rows of all blocks)
 __global__ void __launch_bounds__(256) block_apply_kernel(const double* __restrict__ Ainv,
                                                           const int64_t* __restrict__ boff,
@@ -110,7 +193,9 @@ __global__ void __launch_bounds__(256) block_apply_kernel(const double* __restri
                                                           const int32_t* __restrict__ bdofs,
                                                           int nblk, int64_t N,
                                                           const double* __restrict__ r,
-                                                          double* __restrict__ z) {
+                                                          double* __restrict__ z,
+                                                          const PcgState* __restrict__ st) {
+  if (st->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t rho = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (rho >= N) return;
@@ -134,7 +219,9 @@ __global__ void __launch_bounds__(256) block_apply_kernel(const double* __restri
 // t = P^T r (CSC of P), warp per coarse dof
 __global__ void restrict_kernel(const int64_t* __restrict__ cptr, const int32_t* __restrict__ crow,
                                 const double* __restrict__ cval, int64_t NH,
-                                const double* __restrict__ r, double* __restrict__ t) {
+                                const double* __restrict__ r, double* __restrict__ t,
+                                const PcgState* __restrict__ st) {
+  if (st->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t mu = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (mu >= NH) return;
@@ -147,7 +234,9 @@ __global__ void restrict_kernel(const int64_t* __restrict__ cptr, const int32_t*
 
 // u = AHinv t (warp per row)
 __global__ void coarse_solve_kernel(const double* __restrict__ AHinv, int64_t NH,
-                                    const double* __restrict__ t, double* __restrict__ u) {
+                                    const double* __restrict__ t, double* __restrict__ u,
+                                    const PcgState* __restrict__ st) {
+  if (st->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (i >= NH) return;
@@ -161,7 +250,9 @@ __global__ void coarse_solve_kernel(const double* __restrict__ AHinv, int64_t NH
 // z += P u (CSR of P by fine row)
 __global__ void prolong_kernel(const int64_t* __restrict__ pptr, const int32_t* __restrict__ pcol,
                                const double* __restrict__ pval, int64_t N,
-                               const double* __restrict__ u, double* __restrict__ z) {
+                               const double* __restrict__ u, double* __restrict__ z,
+                               const PcgState* __restrict__ st) {
+  if (st->done) return;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double acc = 0.0;
@@ -170,40 +261,52 @@ __global__ void prolong_kernel(const int64_t* __restrict__ pptr, const int32_t* 
 }
 
 // beta = rz_new / rz; rz = rz_new
-__global__ void beta_kernel(double* scal) {
-  scal[5] = scal[4] / scal[0];
+__global__ void beta_kernel(double* scal, const PcgState* st, double* beta_hist) {
+  if (st->done) return;
+  const double b = scal[4] / scal[0];
+  scal[5] = b;
   scal[0] = scal[4];
+  beta_hist[st->iter - 1] = b;
 }
 
-// p = z + beta p
-__global__ void update_p_kernel(double* __restrict__ p, const double* __restrict__ z,
-                                const double* __restrict__ scal, int64_t N) {
-  const double beta = scal[5];
-  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256)
-    p[i] = fma(beta, p[i], z[i]);
+// p = z + beta p (and its float-pair copy for the matrix-vector product)
+__global__ void update_p_kernel(double* __restrict__ p, float2* __restrict__ pf,
+                                const double* __restrict__ z, const double* __restrict__ scal,
+                                int64_t N, int first, const PcgState* __restrict__ st) {
+  if (st->done) return;
+  const double beta = first ? 0.0 : scal[5];
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256) {
+    const double v = first ? z[i] : fma(beta, p[i], z[i]);
+    p[i] = v;
+    float h, l;
+    split_df(v, h, l);
+    pf[i] = make_float2(h, l);
+  }
 }
 
-__global__ void copy_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t N) {
+__global__ void copy_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t N,
+                            const PcgState* __restrict__ st) {
+  if (st->done) return;
   for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256)
     dst[i] = src[i];
 }
 
 static void apply_M(DevGeom& g, const double* r, double* z, double* t, double* u, int precondition,
-                    cudaStream_t s) {
+                    const PcgState* st, cudaStream_t s) {
   const int64_t N = g.ndof;
   if (!precondition) {
-    copy_kernel<<<RED_BLOCKS, 256, 0, s>>>(z, r, N);
+    copy_kernel<<<RED_BLOCKS, 256, 0, s>>>(z, r, N, st);
     ++g.launches;
     return;
   }
-  ++g.launches;
   block_apply_kernel<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(g.d_binv, g.d_boff, g.d_bptr, g.d_bdofs,
-                                                              (int)g.n_blocks, N, r, z);
+                                                              (int)g.n_blocks, N, r, z, st);
+  ++g.launches;
   const int64_t NH = g.use_coarse ? g.n_coarse : 0;
   if (NH > 0) {
-    restrict_kernel<<<(unsigned)((NH + 7) / 8), 256, 0, s>>>(g.d_cptr, g.d_crow, g.d_cval, NH, r, t);
-    coarse_solve_kernel<<<(unsigned)((NH + 7) / 8), 256, 0, s>>>(g.d_AHinv, NH, t, u);
-    prolong_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(g.d_pptr, g.d_pcol, g.d_pval, N, u, z);
+    restrict_kernel<<<(unsigned)((NH + 7) / 8), 256, 0, s>>>(g.d_cptr, g.d_crow, g.d_cval, NH, r, t, st);
+    coarse_solve_kernel<<<(unsigned)((NH + 7) / 8), 256, 0, s>>>(g.d_AHinv, NH, t, u, st);
+    prolong_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(g.d_pptr, g.d_pcol, g.d_pval, N, u, z, st);
     g.launches += 3;
   }
 }
@@ -220,68 +323,83 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
   double* t = q + N;          // coarse scratch (NH)
   double* u = t + std::max<int64_t>(g.n_coarse, 1);
   double* scal = g.d_scal;    // 8 scalars
-  double* part = scal + 8;    // partial sums (>= max(RED_BLOCKS, N/8+1))
-  const unsigned gemv_blocks = (unsigned)((N + 7) / 8);
+  PcgState* st = (PcgState*)(scal + 8);
+  double* part = scal + 16;   // partial sums (>= max(RED_BLOCKS, N/8+1))
+  const unsigned gemv_blocks = (unsigned)((N + GEMV_ROWS - 1) / GEMV_ROWS);
   cudaError_t e;
   if (N == 0) {  // nothing to solve (no launch may have an empty grid)
     out.hist.push_back(0.0);
     out.status = MSBEM_OK;
     return cudaStreamSynchronize(s);
   }
+  double* hist = nullptr;  // [maxit+1] relres, [maxit] alpha, [maxit] beta
+  if ((e = cudaMallocAsync((void**)&hist, sizeof(double) * (3 * (size_t)maxit + 1), s)) != cudaSuccess)
+    return e;
+  double* alpha_h = hist + maxit + 1;
+  double* beta_h = alpha_h + maxit;
+  PcgState h_st = {0, 0, maxit, fixed};
+  cudaMemcpyAsync(st, &h_st, sizeof(PcgState), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(x, 0, sizeof(double) * N, s);
   if ((e = launch_rhs(g, gvec, r, s)) != cudaSuccess) return e;
-  dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, r, N, part);
-  reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 6);
-  apply_M(g, r, z, t, u, precondition, s);
-  copy_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, z, N);
-  dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part);
-  reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 0);
-  g.launches += 5 + (N > 0);
-  double h[8];
-  if ((e = cudaMemcpyAsync(h, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, r, N, part, st);
+  reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 6, st);
+  apply_M(g, r, z, t, u, precondition, st, s);
+  update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, g.d_pf, z, scal, N, 1, st);
+  dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
+  reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 0, st);
+  cudaMemcpyAsync(scal + 7, &rtol, sizeof(double), cudaMemcpyHostToDevice, s);
+  g.launches += 6;
+  double nL2 = 0.0;
+  if ((e = cudaMemcpyAsync(&nL2, scal + 6, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  const double nL = std::sqrt(h[6]);
-  out.hist.push_back(nL > 0 ? 1.0 : 0.0);
-  if (nL == 0.0) {
-    if (x_out != x) cudaMemcpyAsync(x_out, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  if (nL2 == 0.0) {
+    out.hist.push_back(0.0);
     out.status = MSBEM_OK;
+    cudaFreeAsync(hist, s);
+    if (x_out != x) cudaMemcpyAsync(x_out, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
     return cudaStreamSynchronize(s);
   }
-  out.status = MSBEM_NOT_CONVERGED;
-  for (int it = 0; it < maxit; ++it) {
-    gemv_kernel<<<gemv_blocks, 256, 0, s>>>(g.d_W, N, p, q, part);
-    reduce_kernel<<<1, 256, 0, s>>>(part, gemv_blocks, scal + 1);
-    alpha_kernel<<<1, 1, 0, s>>>(scal);
-    update_xr_kernel<<<RED_BLOCKS, 256, 0, s>>>(x, r, p, q, scal, N, part);
-    reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 3);
-    apply_M(g, r, z, t, u, precondition, s);
-    dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part);
-    reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 4);
-    beta_kernel<<<1, 1, 0, s>>>(scal);
-    update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, z, scal, N);
-    g.launches += 9;
-    if ((e = cudaMemcpyAsync(h, scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  int enq = 0;
+  while (enq < maxit) {
+    const int chunk = std::min(PCG_CHUNK, maxit - enq);
+    for (int c = 0; c < chunk; ++c) {
+      gemv_kernel<<<gemv_blocks, 256, 0, s>>>(g.d_W, N, g.d_pf, p, q, part, st);
+      reduce_kernel<<<1, 256, 0, s>>>(part, gemv_blocks, scal + 1, st);
+      alpha_kernel<<<1, 1, 0, s>>>(scal, st, alpha_h);
+      update_xr_kernel<<<RED_BLOCKS, 256, 0, s>>>(x, r, p, q, scal, N, part, st);
+      reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 3, st);
+      check_kernel<<<1, 1, 0, s>>>(scal, st, hist);
+      apply_M(g, r, z, t, u, precondition, st, s);
+      dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
+      reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 4, st);
+      beta_kernel<<<1, 1, 0, s>>>(scal, st, beta_h);
+      update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, g.d_pf, z, scal, N, 0, st);
+      g.launches += 10;
+    }
+    enq += chunk;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(&h_st, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    const double pq = h[1], alpha = h[2], rel = std::sqrt(h[3]) / nL, beta = h[5];
-    out.iters = it + 1;
-    if (!(pq > 0.0) || !std::isfinite(alpha) || !std::isfinite(rel)) {
-      out.status = MSBEM_BREAKDOWN;
-      break;
-    }
-    out.alpha.push_back(alpha);
-    out.hist.push_back(rel);
-    if (rel <= rtol) {
-      out.status = MSBEM_OK;
-      if (!fixed) break;
-    }
-    if (it + 1 == maxit) break;
-    out.beta.push_back(beta);
+    if (h_st.done) break;
   }
+  const int it = h_st.iter;
+  std::vector<double> h(3 * (size_t)maxit + 1);
+  cudaMemcpyAsync(h.data(), hist, sizeof(double) * (3 * (size_t)maxit + 1), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(hist, s);
   if (x_out != x) cudaMemcpyAsync(x_out, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
-  if (fixed && out.iters == maxit && out.status != MSBEM_BREAKDOWN) out.status = MSBEM_OK;
-  return cudaStreamSynchronize(s);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  out.iters = it;
+  out.hist.assign(1, 1.0);
+  for (int k = 1; k <= it; ++k) out.hist.push_back(h[k]);
+  out.alpha.assign(h.begin() + maxit + 1, h.begin() + maxit + 1 + it);
+  const int nbeta = (h_st.done == 1 && !fixed && it < maxit) || h_st.done == 3 || h_st.done == 1 ? it - 1 : it;
+  out.beta.assign(h.begin() + 2 * maxit + 1, h.begin() + 2 * maxit + 1 + std::max(0, nbeta));
+  if (h_st.done == 2) out.status = MSBEM_BREAKDOWN;
+  else if (h_st.done == 3) out.status = MSBEM_NOT_CONVERGED;
+  else out.status = MSBEM_OK;
+  return cudaSuccess;
 }
 
 }  // namespace msbem
