@@ -179,6 +179,32 @@ int msbem_solve(msbem_geom* g, const double gvec[3], const msbem_solve_opts* opt
  * t[4] solve.  Any entry not yet measured is 0. */
 int msbem_last_timings(const msbem_geom* g, double t[5]);
 
+/* Largest matrix order msbem_spd_inverse_noalloc accepts. */
+#define MSBEM_NOALLOC_MAX_N 2048
+
+/* Inverse of one symmetric positive definite matrix, allocating no device
+ * memory.  The paper has no counterpart: this is for callers that cannot
+ * allocate, such as a process that has reserved all of its GPU memory for its
+ * own pool up front, or a latency-critical loop that cannot afford cudaMalloc /
+ * cudaFree (they synchronize the device and can fail under memory pressure).
+ *   A[n*n]     device pointer, row-major FP64, symmetric positive definite
+ *   Ainv[n*n]  device pointer receiving A^{-1} (may equal A: in place)
+ *   n          1 <= n <= MSBEM_NOALLOC_MAX_N, else INVALID_ARG
+ *   cuda_stream  stream for all work (NULL = legacy default stream)
+ * The method is the same blocked Gauss-Jordan recursion msbem_factor uses
+ * (32-wide panels, rank-32 updates in double-float).  Its scratch -- about
+ * 1 MiB: the pivot block, two n x 32 panels, index words and the breakdown
+ * flag -- is one file-scope device array that every GPU loading the library
+ * holds until exit.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  Every call shares the array and clears what must
+ * start at zero, so calls that overlap on the GPU (on different streams or
+ * from different threads) race and must not be issued.  The call copies a few
+ * index words from the host and waits for the stream to read the breakdown
+ * flag.  Returns BREAKDOWN if a pivot is not positive, CUDA_ERROR on a CUDA
+ * failure. */
+int msbem_spd_inverse_noalloc(const double* A, int64_t n, double* Ainv, void* cuda_stream);
+
 /* Counters of this geometry: *launches = number of CUDA kernels the library
  * has launched for it so far (all calls), *far_pairs = number of unordered
  * triangle pairs sharing no vertex (the units of the far-field kernel).

@@ -69,6 +69,7 @@ def lib():
                          ctypes.POINTER(d)], i32),
         "msbem_last_timings": ([P, P], i32),
         "msbem_counters": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
+        "msbem_spd_inverse_noalloc": ([P, i64, P, P], i32),
         "msbem_mesh_dofs": ([P, i64, P, i64, ctypes.POINTER(i64), P, P, i64, ctypes.c_char_p, i32], i32),
     }
     for name, (args, res) in sig.items():
@@ -137,6 +138,16 @@ def msbem_mesh_dofs(xyz, tri):
     if st != MSBEM_OK:
         raise MsbemError(st, buf.value.decode())
     return int(n.value), v, s
+
+
+NOALLOC_MAX_N = 2048
+
+
+def msbem_spd_inverse_noalloc(A, Ainv, stream: int = 0) -> int:
+    """Inverse of an SPD matrix (device tensors, n x n FP64) without any
+    device allocation; returns the C status (0 on success)."""
+    n = int(A.shape[0])
+    return lib().msbem_spd_inverse_noalloc(_ptr(A), n, _ptr(Ainv), stream)
 
 
 def msbem_ndofs(geom) -> int:

@@ -312,6 +312,53 @@ static cudaError_t gj_invert(double* d_A, const std::vector<int64_t>& boff,
   return cudaSuccess;
 }
 
+// Blocked Gauss-Jordan inversion of one SPD matrix A (n x n, row-major,
+// device) in place, with all scratch (pivot block, the two panels, index
+// arrays, breakdown flag) carved from the caller's device buffer `scratch` of
+// `bytes` bytes; allocates nothing.  Needs bgj_scratch_bytes(n) bytes.
+size_t bgj_scratch_bytes(int64_t n) {
+  return sizeof(float2) * GB * GB + 2 * sizeof(float2) * (size_t)n * GB + 256;
+}
+
+cudaError_t bgj_invert_single(double* A, int64_t n, unsigned char* scratch, size_t bytes,
+                              cudaStream_t s, int* not_spd) {
+  *not_spd = 0;
+  if (n < 1 || bytes < bgj_scratch_bytes(n)) return cudaErrorInvalidValue;
+  const int64_t nti = (n + GB - 1) / GB;
+  BgjArgs args{};
+  args.A = A;
+  args.Pf = (float2*)scratch;
+  args.Cf = args.Pf + GB * GB;
+  args.Rf = args.Cf + n * GB;
+  int64_t* idx = (int64_t*)(args.Rf + n * GB);
+  int32_t* tail = (int32_t*)(idx + 9);
+  // boff[1] bsize[1] pt1[2] pt2[2] soff[2] (one spare slot) | order[1] flag[1]
+  const int64_t h_idx[9] = {0, n, 0, nti, 0, nti * nti, 0, n * GB, 0};
+  const int32_t h_tail[2] = {0, 0};
+  args.boff = idx;
+  args.bsize = idx + 1;
+  args.pt1 = idx + 2;
+  args.pt2 = idx + 4;
+  args.soff = idx + 6;
+  args.order = tail;
+  args.flag = tail + 1;
+  cudaError_t e = cudaMemcpyAsync(idx, h_idx, sizeof(h_idx), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tail, h_tail, sizeof(h_tail), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  for (int64_t k0 = 0; k0 < n; k0 += GB) {
+    bgj_pivot_kernel<<<1, 256, 0, s>>>(args, k0);
+    bgj_panel_kernel<<<(unsigned)nti, 256, 0, s>>>(args, 1, k0);
+    bgj_update_kernel<<<(unsigned)(nti * nti), 256, 0, s>>>(args, 1, k0);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int flag = 0;
+  e = cudaMemcpyAsync(&flag, args.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  *not_spd = flag;
+  return cudaSuccess;
+}
+
 // Gathers face / wire-basket blocks and the coarse matrix into g.d_binv and
 // inverts them.  bptr: block pointer (faces first, wire basket last if any).
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag, cudaStream_t s,

@@ -139,6 +139,12 @@ cudaError_t set_far_df_constants(const double w[6]);
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag,
                           cudaStream_t s, int* not_spd);
 
+// Single-matrix blocked Gauss-Jordan inversion with caller-provided scratch
+// (factor.cu); used by the allocation-free entry point.
+size_t bgj_scratch_bytes(int64_t n);
+cudaError_t bgj_invert_single(double* A, int64_t n, unsigned char* scratch, size_t bytes,
+                              cudaStream_t s, int* not_spd);
+
 struct PcgOut {
   int iters = 0;
   int status = 0;
