@@ -34,6 +34,11 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # double-float far-field kernel: FP32-pipe operations per unordered pair
 # (36 evaluations x 82 + 6 x 45 per-point updates), counted from far_df.cu
 FP32_OPS_PER_FAR_PAIR = 36 * 82 + 6 * 45
+# DRAM bytes (read + write) of one far_df_kernel launch, from an ncu capture of
+# the h=1/32 book (6,144 triangles: 1.37 MB read + 257.2 MB written), scaled to
+# the h=1/64 book by the number of triangle pairs (x16).  Valid for the kernel
+# as captured; reset to None when the kernel changes.
+FAR_DF_TRAFFIC_BOOK64 = 16 * (1.372672e6 + 257.199872e6)
 
 
 def parse():
@@ -337,7 +342,9 @@ def run_ours(args, world, rank, local, pg):
             "phases_ms": {k: statistics.mean(p[k] for p in phase) for k in phase[0]},
             "pcg_iters": iters[-1],
             "roofline": {"kernel": kernel, "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": (FAR_DF_TRAFFIC_BOOK64 if (args.far_kernel == 0 and args.workload == "book64")
+                                     else None),
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (FP32-pipe ops/s)",
                          "ops_per_launch": ops, "launch_ms": far_avg_s * 1e3},
             "clocks": ck,

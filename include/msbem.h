@@ -114,8 +114,8 @@ int msbem_split_info(const msbem_geom* g, int64_t* n_faces, int64_t* n_wire_bask
 typedef struct msbem_assemble_opts {
   int ss_order;    /* Gauss-Legendre points per dimension of the singular     */
                    /* (Sauter-Schwab-type) rules, 1..16; default 5            */
-  int far_kernel;  /* 0 = double-float arithmetic on the FP32 pipe (default), */
-                   /* 1 = native FP64                                         */
+  int far_kernel;  /* pair integrals: 0 = double-float arithmetic on the FP32 */
+                   /* pipe (default), 1 = native FP64 (far and near field)    */
 } msbem_assemble_opts;
 
 /* Assemble W[nu,nu'] = a(psi~_nu, psi~_nu') (Sec. 4.3 eq. eval_a_phiij with

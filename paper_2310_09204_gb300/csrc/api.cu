@@ -14,6 +14,7 @@ using namespace msbem;
 struct msbem_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
   std::string err;
   std::vector<msbem_geom*> geoms;
   cudaEvent_t ev[8] = {};
@@ -42,13 +43,13 @@ int cuda_fail(msbem_ctx* c, cudaError_t e, const char* where) {
 }
 
 template <class T>
-cudaError_t dalloc(T** p, size_t n, cudaStream_t s) {
-  return cudaMallocAsync((void**)p, sizeof(T) * std::max<size_t>(n, 1), s);
+cudaError_t dalloc(T** p, size_t n, cudaMemPool_t pool, cudaStream_t s) {
+  return pool_alloc((void**)p, sizeof(T) * std::max<size_t>(n, 1), pool, s);
 }
 
 template <class T>
-cudaError_t dput(T** p, const std::vector<T>& h, cudaStream_t s) {
-  cudaError_t e = dalloc(p, h.size(), s);
+cudaError_t dput(T** p, const std::vector<T>& h, cudaMemPool_t pool, cudaStream_t s) {
+  cudaError_t e = dalloc(p, h.size(), pool, s);
   if (e != cudaSuccess || h.empty()) return e;
   return cudaMemcpyAsync(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s);
 }
@@ -125,6 +126,18 @@ int msbem_create(msbem_ctx** ctx, int device, void* stream) {
   c->device = device;
   c->stream = (cudaStream_t)stream;
   for (auto& ev : c->ev) cudaEventCreate(&ev);
+  // a private stream-ordered pool that keeps freed memory for reuse
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  } else {
+    cudaGetLastError();
+    c->pool = nullptr;
+  }
   *ctx = c;
   return MSBEM_OK;
 }
@@ -137,6 +150,10 @@ int msbem_destroy(msbem_ctx* c) {
     delete g;
   }
   for (auto& ev : c->ev) cudaEventDestroy(ev);
+  if (c->pool) {
+    cudaStreamSynchronize(c->stream);
+    cudaMemPoolDestroy(c->pool);
+  }
   delete c;
   return MSBEM_OK;
 }
@@ -167,6 +184,7 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   const Split& sp = g->split;
   DevGeom& d = g->dev;
   cudaStream_t s = c->stream;
+  d.pool = c->pool;
   d.nt = nt;
   d.nt_pad = (nt + 63) / 64 * 64;
   d.ndof = f.ndof;
@@ -230,47 +248,47 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   d.n_coarse = NH;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-  chk(dput(&d.d_qp, qp, s));
-  chk(dput(&d.d_cen, cen, s));
-  chk(dput(&d.d_qoff, qoff, s));
-  chk(dput(&d.d_area, area, s));
-  chk(dput(&d.d_tri, tpad, s));
-  chk(dput(&d.d_xyz, f.xyz, s));
+  chk(dput(&d.d_qp, qp, c->pool, s));
+  chk(dput(&d.d_cen, cen, c->pool, s));
+  chk(dput(&d.d_qoff, qoff, c->pool, s));
+  chk(dput(&d.d_area, area, c->pool, s));
+  chk(dput(&d.d_tri, tpad, c->pool, s));
+  chk(dput(&d.d_xyz, f.xyz, c->pool, s));
   d.n_near = (int64_t)near.size();
   {
     int64_t ident = 0;
     for (const NearPair& np : near) ident += (np.cls == 3);
     d.n_far_pairs = nt * (nt - 1) / 2 - (d.n_near - ident);
   }
-  chk(dput(&d.d_near, near, s));
-  chk(dput(&d.d_jptr, f.jptr, s));
-  chk(dput(&d.d_jtri, f.jtri, s));
-  chk(dput(&d.d_jvec, jvec, s));
-  chk(dput(&d.d_jvecf, jvecf, s));
-  chk(dput(&d.d_jrhs, jrhs, s));
-  chk(dput(&d.d_bptr, sp.block_ptr, s));
-  chk(dput(&d.d_bdofs, sp.block_dofs, s));
-  chk(dput(&d.d_pptr, sp.p_ptr, s));
-  chk(dput(&d.d_pcol, sp.p_col, s));
-  chk(dput(&d.d_pval, sp.p_val, s));
-  chk(dput(&d.d_cptr, cptr, s));
-  chk(dput(&d.d_crow, crow, s));
-  chk(dput(&d.d_cval, cval, s));
+  chk(dput(&d.d_near, near, c->pool, s));
+  chk(dput(&d.d_jptr, f.jptr, c->pool, s));
+  chk(dput(&d.d_jtri, f.jtri, c->pool, s));
+  chk(dput(&d.d_jvec, jvec, c->pool, s));
+  chk(dput(&d.d_jvecf, jvecf, c->pool, s));
+  chk(dput(&d.d_jrhs, jrhs, c->pool, s));
+  chk(dput(&d.d_bptr, sp.block_ptr, c->pool, s));
+  chk(dput(&d.d_bdofs, sp.block_dofs, c->pool, s));
+  chk(dput(&d.d_pptr, sp.p_ptr, c->pool, s));
+  chk(dput(&d.d_pcol, sp.p_col, c->pool, s));
+  chk(dput(&d.d_pval, sp.p_val, c->pool, s));
+  chk(dput(&d.d_cptr, cptr, c->pool, s));
+  chk(dput(&d.d_crow, crow, c->pool, s));
+  chk(dput(&d.d_cval, cval, c->pool, s));
   {
     std::vector<float2> cvalf(cval.size());
     for (size_t k = 0; k < cval.size(); ++k) {
       float hi = (float)cval[k];
       cvalf[k] = make_float2(hi, (float)(cval[k] - (double)hi));
     }
-    chk(dput(&d.d_cvalf, cvalf, s));
+    chk(dput(&d.d_cvalf, cvalf, c->pool, s));
   }
   const int64_t N = f.ndof;
-  chk(dalloc(&d.d_V, (size_t)nt * nt, s));
-  chk(dalloc(&d.d_W, (size_t)N * N, s));
-  chk(dalloc(&d.d_WP, (size_t)std::max<int64_t>(NH, 1) * N, s));
-  chk(dalloc(&d.d_vec, (size_t)(5 * N + 2 * std::max<int64_t>(NH, 1) + 8), s));
-  chk(dalloc(&d.d_pf, (size_t)N, s));
-  chk(dalloc(&d.d_scal, (size_t)(16 + std::max<int64_t>(256, N / 8 + 8)), s));
+  chk(dalloc(&d.d_V, (size_t)nt * nt, c->pool, s));
+  chk(dalloc(&d.d_W, (size_t)N * N, c->pool, s));
+  chk(dalloc(&d.d_WP, (size_t)std::max<int64_t>(NH, 1) * N, c->pool, s));
+  chk(dalloc(&d.d_vec, (size_t)(5 * N + 2 * std::max<int64_t>(NH, 1) + 8), c->pool, s));
+  chk(dalloc(&d.d_pf, (size_t)N, c->pool, s));
+  chk(dalloc(&d.d_scal, (size_t)(16 + std::max<int64_t>(256, N / 8 + 8)), c->pool, s));
   chk(cudaStreamSynchronize(s));
   if (e != cudaSuccess) {
     free_dev(d, s);
@@ -358,7 +376,7 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   e = (far_kernel == 1) ? launch_far_fp64(d, s) : launch_far_df(d, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "far field");
   cudaEventRecord(c->ev[1], s);
-  e = launch_near(d, n, glx, glw, s);
+  e = launch_near(d, n, glx, glw, far_kernel == 1, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "near field");
   cudaEventRecord(c->ev[2], s);
   e = launch_contract(d, s);
@@ -387,7 +405,8 @@ int msbem_copy_matrix(const msbem_geom* g, int64_t row0, int64_t nrows, double* 
   double* tmp = nullptr;
   const bool dev_out = is_device_ptr(out);
   cudaError_t e = cudaSuccess;
-  if (!dev_out) e = cudaMallocAsync((void**)&tmp, sizeof(double) * std::max<int64_t>(1, nrows * N), c->stream);
+  if (!dev_out)
+    e = pool_alloc((void**)&tmp, sizeof(double) * std::max<int64_t>(1, nrows * N), c->pool, c->stream);
   if (e == cudaSuccess) e = copy_rows_to_double(g->dev, row0, nrows, dev_out ? out : tmp, c->stream);
   if (e == cudaSuccess && !dev_out)
     e = cudaMemcpyAsync(out, tmp, sizeof(double) * nrows * N, cudaMemcpyDeviceToHost, c->stream);
@@ -402,7 +421,7 @@ int msbem_rhs(const msbem_geom* g, const double gv[3], double* out) {
   cudaSetDevice(c->device);
   const int64_t N = g->fine.ndof;
   double* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&tmp, sizeof(double) * std::max<int64_t>(N, 1), c->stream);
+  cudaError_t e = pool_alloc((void**)&tmp, sizeof(double) * std::max<int64_t>(N, 1), c->pool, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "msbem_rhs");
   e = launch_rhs(g->dev, gv, tmp, c->stream);
   const_cast<msbem_geom*>(g)->dev.launches += (N > 0);

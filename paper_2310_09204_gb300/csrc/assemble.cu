@@ -8,7 +8,8 @@
 //   far_fp64_kernel  V_{TT'} for all pairs of a 64x64 triangle tile, 6x6 points
 //                    (native FP64); tiles on and above the diagonal only, the
 //                    lower half written by a shared-memory transpose.
-//   near_kernel      pairs sharing a vertex: Sauter-Schwab-type rules (identical
+//   near_kernel /    pairs sharing a vertex: Sauter-Schwab-type rules (identical
+//   near_df_kernel   (FP64 and double-float versions)
 //                    6 regions, edge 4, vertex 2) with Gauss-Legendre order n.
 //                    For a kernel of x - y on flat triangles the rules' integrand
 //                    does not depend on some of the [0,1]^4 coordinates, and is a
@@ -225,17 +226,174 @@ __global__ void __launch_bounds__(256) near_kernel(const NearPair* __restrict__ 
   }
 }
 
+// Same rules as near_kernel, evaluated in double-float on the FP32 pipe: per
+// pair the edge vectors are formed in FP64 and split into float pairs; per
+// evaluation the direction vector g, 1/|g| and the weighted sum use float pairs
+// (Gauss-Legendre nodes and weights as (hi, lo) pairs in constant memory).
+__constant__ float2 c_glx_df[NEAR_MAXN], c_glw_df[NEAR_MAXN];
+
+__device__ __forceinline__ void split3(const double* v, float2* o) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float h, l;
+    split_df(v[k], h, l);
+    o[k] = make_float2(h, l);
+  }
+}
+
+// acc[k] += c * v[k]  (c a float pair, v a float-pair vector)
+__device__ __forceinline__ void axpy3(float ch, float cl, const float2* v, float2* acc) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) df_fma_acc(ch, cl, v[k].x, v[k].y, acc[k].x, acc[k].y);
+}
+
+__global__ void __launch_bounds__(256) near_df_kernel(const NearPair* __restrict__ pairs,
+                                                      int64_t npairs, const double* __restrict__ xyz,
+                                                      int n, int64_t ldv, float2* __restrict__ V) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= npairs) return;
+  const NearPair pr = pairs[w];
+  double P[9], Q[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      P[3 * i + k] = xyz[3 * (int64_t)pr.v[i] + k];
+      Q[3 * i + k] = xyz[3 * (int64_t)pr.v[3 + i] + k];
+    }
+  const double aT = tri_area_d(P), aS = tri_area_d(Q);
+  double ev[4][3];
+  // edge vectors (FP64 differences), split to float pairs
+  for (int k = 0; k < 3; ++k) {
+    ev[0][k] = P[3 + k] - P[k];      // identical: e1 | edge: e | vertex: p1
+    ev[1][k] = P[6 + k] - P[3 + k];  // identical: e2 | edge: c | vertex: p2
+    ev[2][k] = Q[6 + k] - Q[3 + k];  //                edge: d | vertex: q2
+    ev[3][k] = Q[3 + k] - Q[k];      //                          vertex: q1
+  }
+  float2 v0[3], v1[3], v2[3], v3[3];
+  split3(ev[0], v0);
+  split3(ev[1], v1);
+  split3(ev[2], v2);
+  split3(ev[3], v3);
+  float acch = 0.f, accl = 0.f;
+  double pref;
+  const float2 one = make_float2(1.f, 0.f);
+  if (pr.cls == 3) {
+    for (int idx = lane; idx < 3 * n; idx += 32) {
+      const int sct = idx / n, j = idx % n;
+      const float2 et = c_glx_df[j];
+      float2 om;  // 1 - eta
+      df_add(1.f, 0.f, -et.x, -et.y, om.x, om.y);
+      float2 a0, a1;
+      if (sct == 0) { a0 = one; a1 = et; }
+      else if (sct == 1) { a0 = om; a1 = one; }
+      else { a0 = make_float2(-et.x, -et.y); a1 = om; }
+      float2 g[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      axpy3(a0.x, a0.y, v0, g);
+      axpy3(a1.x, a1.y, v1, g);
+      float y, corr;
+      df_rsqrt3(g[0].x, g[0].y, g[1].x, g[1].y, g[2].x, g[2].y, y, corr);
+      const float2 wq = c_glw_df[j];
+      df_fma_acc(wq.x, wq.y, y, corr, acch, accl);
+    }
+    pref = aT * aT / (3.0 * M_PI);
+  } else if (pr.cls == 2) {
+    const int nn = n * n;
+    for (int idx = lane; idx < 4 * nn; idx += 32) {
+      const int reg = idx / nn, rem = idx % nn, i1 = rem / n, i2 = rem % n;
+      const float2 sg = c_glx_df[i1], ta = c_glx_df[i2];
+      float2 omt, oms, sgta, sgomt;
+      df_add(1.f, 0.f, -ta.x, -ta.y, omt.x, omt.y);
+      df_add(1.f, 0.f, -sg.x, -sg.y, oms.x, oms.y);
+      df_mul(sg.x, sg.y, ta.x, ta.y, sgta.x, sgta.y);
+      df_mul(sg.x, sg.y, omt.x, omt.y, sgomt.x, sgomt.y);
+      float2 fu, fv, fw, J;
+      if (reg == 0) { fu = sg; fv = oms; fw = ta; J = one; }
+      else if (reg == 1) { fu = sgomt; fv = sgta; fw = one; J = sg; }
+      else if (reg == 2) { fu = make_float2(-sgomt.x, -sgomt.y); fv = one; fw = sgta; J = sg; }
+      else { fu = make_float2(-sg.x, -sg.y); fv = ta; fw = oms; J = one; }
+      // g = -fu e + fv c - fw d
+      float2 g[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      axpy3(-fu.x, -fu.y, v0, g);
+      axpy3(fv.x, fv.y, v1, g);
+      axpy3(-fw.x, -fw.y, v2, g);
+      float y, corr;
+      df_rsqrt3(g[0].x, g[0].y, g[1].x, g[1].y, g[2].x, g[2].y, y, corr);
+      float2 wq, wJ;
+      df_mul(c_glw_df[i1].x, c_glw_df[i1].y, c_glw_df[i2].x, c_glw_df[i2].y, wq.x, wq.y);
+      df_mul(wq.x, wq.y, J.x, J.y, wJ.x, wJ.y);
+      df_fma_acc(wJ.x, wJ.y, y, corr, acch, accl);
+    }
+    pref = aT * aS / (6.0 * M_PI);
+  } else {
+    const int nnn = n * n * n;
+    for (int idx = lane; idx < 2 * nnn; idx += 32) {
+      const int reg = idx / nnn, rem = idx % nnn;
+      const int i1 = rem / (n * n), i2 = (rem / n) % n, i3 = rem % n;
+      const float2 a1 = c_glx_df[i1], a2 = c_glx_df[i2], a3 = c_glx_df[i3];
+      float2 a23;
+      df_mul(a2.x, a2.y, a3.x, a3.y, a23.x, a23.y);
+      float2 s1, s2, t1, t2;
+      if (reg == 0) { s1 = one; s2 = a1; t1 = a2; t2 = a23; }
+      else { t1 = one; t2 = a1; s1 = a2; s2 = a23; }
+      // g = s1 p1 + s2 p2 - t1 q1 - t2 q2
+      float2 g[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      axpy3(s1.x, s1.y, v0, g);
+      axpy3(s2.x, s2.y, v1, g);
+      axpy3(-t1.x, -t1.y, v3, g);
+      axpy3(-t2.x, -t2.y, v2, g);
+      float y, corr;
+      df_rsqrt3(g[0].x, g[0].y, g[1].x, g[1].y, g[2].x, g[2].y, y, corr);
+      float2 w12, w123, wq;
+      df_mul(c_glw_df[i1].x, c_glw_df[i1].y, c_glw_df[i2].x, c_glw_df[i2].y, w12.x, w12.y);
+      df_mul(w12.x, w12.y, c_glw_df[i3].x, c_glw_df[i3].y, w123.x, w123.y);
+      df_mul(w123.x, w123.y, a2.x, a2.y, wq.x, wq.y);
+      df_fma_acc(wq.x, wq.y, y, corr, acch, accl);
+    }
+    pref = aT * aS / (3.0 * M_PI);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    float oh = __shfl_xor_sync(0xffffffffu, acch, off);
+    float ol = __shfl_xor_sync(0xffffffffu, accl, off);
+    float sh, se;
+    two_sum(acch, oh, sh, se);
+    acch = sh;
+    accl = accl + ol + se;
+  }
+  if (lane == 0) {
+    float h, l;
+    split_df(pref * df_to_double(acch, accl), h, l);
+    V[(int64_t)pr.T * ldv + pr.S] = make_float2(h, l);
+    V[(int64_t)pr.S * ldv + pr.T] = make_float2(h, l);
+  }
+}
+
 cudaError_t launch_near(const DevGeom& g, int n, const double* gl_x, const double* gl_w,
-                        cudaStream_t s) {
+                        int fp64, cudaStream_t s) {
   if (n < 2 || n > NEAR_MAXN) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemcpyToSymbolAsync(c_gl_x, gl_x, sizeof(double) * n, 0,
                                           cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbolAsync(c_gl_w, gl_w, sizeof(double) * n, 0, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
+  float2 xf[NEAR_MAXN], wf[NEAR_MAXN];
+  for (int j = 0; j < n; ++j) {
+    float xh = (float)gl_x[j], wh = (float)gl_w[j];
+    xf[j] = make_float2(xh, (float)(gl_x[j] - (double)xh));
+    wf[j] = make_float2(wh, (float)(gl_w[j] - (double)wh));
+  }
+  e = cudaMemcpyToSymbolAsync(c_glx_df, xf, sizeof(float2) * n, 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbolAsync(c_glw_df, wf, sizeof(float2) * n, 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
   if (g.n_near == 0) return cudaSuccess;
   int64_t blocks = (g.n_near + 7) / 8;
-  near_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
+  if (fp64)
+    near_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
+  else
+    near_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
   return cudaGetLastError();
 }
 

@@ -89,4 +89,42 @@ __device__ __forceinline__ void df_dot3(const float2* a, const float2* b, float&
   dl = err;
 }
 
+// inverse distance of the double-float vector d: returns (y, corr) with
+// 1/|d| = y + corr to ~2^-46 relative
+__device__ __forceinline__ void df_rsqrt3(float dxh, float dxl, float dyh, float dyl, float dzh,
+                                          float dzl, float& y, float& corr) {
+  // r^2 = sum dh^2 + 2 dh dl (+ dl^2, below 2^-48 relative)
+  float px = dxh * dxh, py = dyh * dyh, pz = dzh * dzh;
+  float ex = fmaf(dxh, dxh, -px), ey = fmaf(dyh, dyh, -py), ez = fmaf(dzh, dzh, -pz);
+  float s, e1, e2;
+  two_sum(px, py, s, e1);
+  two_sum(s, pz, s, e2);
+  float cr = dxh * dxl;
+  cr = fmaf(dyh, dyl, cr);
+  cr = fmaf(dzh, dzl, cr);
+  float low = fmaf(2.0f, cr, ((e1 + e2) + (ex + ey)) + ez);
+  // y0 ~ 1/sqrt(s); e = 1 - r^2 y0^2 evaluated in double-float
+  float y0 = rsqrtf(s);
+  float y2h = y0 * y0;
+  float y2l = fmaf(y0, y0, -y2h);
+  float th = s * y2h;
+  float tl = fmaf(s, y2h, -th);
+  tl = fmaf(s, y2l, tl);
+  tl = fmaf(low, y2h, tl);
+  float ee = (1.0f - th) - tl;
+  // 1/sqrt(r^2) = y0 (1 - ee)^(-1/2) = y0 (1 + ee/2 + 3 ee^2/8 + ...)
+  y = y0;
+  corr = y0 * ee * fmaf(0.375f, ee, 0.5f);
+}
+
+// (rh, rl) = a * b  (exact product of the high parts plus cross terms)
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& rh, float& rl) {
+  const float ph = ah * bh;
+  float pe = fmaf(ah, bh, -ph);
+  pe = fmaf(ah, bl, pe);
+  pe = fmaf(al, bh, pe);
+  rh = ph + pe;
+  rl = pe - (rh - ph);
+}
+
 }  // namespace msbem

@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(256) bgj_update_kernel(BgjArgs g, int active, 
 
 namespace {
 template <class T>
-cudaError_t upload(T** d, const std::vector<T>& h, cudaStream_t s) {
-  cudaError_t e = cudaMallocAsync((void**)d, sizeof(T) * std::max<size_t>(1, h.size()), s);
+cudaError_t upload(T** d, const std::vector<T>& h, cudaMemPool_t pool, cudaStream_t s) {
+  cudaError_t e = pool_alloc((void**)d, sizeof(T) * std::max<size_t>(1, h.size()), pool, s);
   if (e != cudaSuccess) return e;
   if (h.empty()) return cudaSuccess;
   return cudaMemcpyAsync(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s);
@@ -257,7 +257,7 @@ cudaError_t upload(T** d, const std::vector<T>& h, cudaStream_t s) {
 // boff/bsize) in place.  bsize/boff are host vectors.
 static cudaError_t gj_invert(double* d_A, const std::vector<int64_t>& boff,
                              const std::vector<int64_t>& bsize, std::vector<int32_t> inv_blocks,
-                             cudaStream_t s, int* not_spd, int64_t* launches) {
+                             cudaMemPool_t pool, cudaStream_t s, int* not_spd, int64_t* launches) {
   *not_spd = 0;
   if (inv_blocks.empty()) return cudaSuccess;
   std::sort(inv_blocks.begin(), inv_blocks.end(),
@@ -276,16 +276,16 @@ static cudaError_t gj_invert(double* d_A, const std::vector<int64_t>& boff,
   int64_t *d_boff = nullptr, *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt2 = nullptr, *d_soff = nullptr;
   int32_t* d_order = nullptr;
   cudaError_t e;
-  if ((e = upload(&d_boff, boff, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_bsize, bsize, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_pt1, pt1, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_pt2, pt2, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_soff, soff, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_order, inv_blocks, s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync((void**)&args.Pf, sizeof(float2) * nb * GB * GB, s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync((void**)&args.Cf, sizeof(float2) * soff[nb], s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync((void**)&args.Rf, sizeof(float2) * soff[nb], s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync((void**)&args.flag, sizeof(int), s)) != cudaSuccess) return e;
+  if ((e = upload(&d_boff, boff, pool, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_bsize, bsize, pool, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_pt1, pt1, pool, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_pt2, pt2, pool, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_soff, soff, pool, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_order, inv_blocks, pool, s)) != cudaSuccess) return e;
+  if ((e = pool_alloc((void**)&args.Pf, sizeof(float2) * nb * GB * GB, pool, s)) != cudaSuccess) return e;
+  if ((e = pool_alloc((void**)&args.Cf, sizeof(float2) * soff[nb], pool, s)) != cudaSuccess) return e;
+  if ((e = pool_alloc((void**)&args.Rf, sizeof(float2) * soff[nb], pool, s)) != cudaSuccess) return e;
+  if ((e = pool_alloc((void**)&args.flag, sizeof(int), pool, s)) != cudaSuccess) return e;
   cudaMemsetAsync(args.flag, 0, sizeof(int), s);
   args.boff = d_boff;
   args.bsize = d_bsize;
@@ -380,12 +380,12 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
   if (g.d_binv) { cudaFreeAsync(g.d_binv, s); g.d_binv = nullptr; }
   if (g.d_boff) { cudaFreeAsync(g.d_boff, s); g.d_boff = nullptr; }
   g.binv_size = boff[nblk + 1];
-  if ((e = cudaMallocAsync((void**)&g.d_binv, sizeof(double) * std::max<int64_t>(1, g.binv_size), s)) !=
+  if ((e = pool_alloc((void**)&g.d_binv, sizeof(double) * std::max<int64_t>(1, g.binv_size), g.pool, s)) !=
       cudaSuccess)
     return e;
-  if ((e = upload(&g.d_boff, boff, s)) != cudaSuccess) return e;
+  if ((e = upload(&g.d_boff, boff, g.pool, s)) != cudaSuccess) return e;
   int64_t* d_prefix2 = nullptr;
-  if ((e = upload(&d_prefix2, prefix2, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_prefix2, prefix2, g.pool, s)) != cudaSuccess) return e;
   const int wb_block = (g.n_blocks > 0 && g.wb_diag >= 0) ? nblk - 1 : -1;
   if (prefix2[nblk] > 0) ++g.launches;
   if (prefix2[nblk] > 0)
@@ -409,7 +409,7 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
   }
   std::vector<int64_t> bsz(bsize.begin(), bsize.end());
   std::vector<int64_t> bof(boff.begin(), boff.end() - 1);
-  return gj_invert(g.d_binv, bof, bsz, inv, s, not_spd, &g.launches);
+  return gj_invert(g.d_binv, bof, bsz, inv, g.pool, s, not_spd, &g.launches);
 }
 
 }  // namespace msbem

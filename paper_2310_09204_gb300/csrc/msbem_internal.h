@@ -75,7 +75,14 @@ void six_point_rule(double bary[6][3], double w[6]);
 // ---------------------------------------------------------------------------
 // Device-side state of one geometry
 // ---------------------------------------------------------------------------
+// Stream-ordered allocation from the context's pool (which keeps freed memory
+// for reuse, so repeated uploads of similar geometries do not remap HBM).
+inline cudaError_t pool_alloc(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t s) {
+  return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+}
+
 struct DevGeom {
+  cudaMemPool_t pool = nullptr;  // owned by the context
   // triangle data for the far field, arranged in tiles of 64 triangles
   int64_t nt = 0, nt_pad = 0;
   double* d_qp = nullptr;        // [nt_pad][6][3] quadrature points (FP64)
@@ -128,7 +135,7 @@ struct DevGeom {
 cudaError_t launch_far_fp64(const DevGeom& g, cudaStream_t s);
 cudaError_t launch_far_df(const DevGeom& g, cudaStream_t s);
 cudaError_t launch_near(const DevGeom& g, int ss_order, const double* gl_x, const double* gl_w,
-                        cudaStream_t s);
+                        int fp64, cudaStream_t s);
 cudaError_t launch_contract(const DevGeom& g, cudaStream_t s);
 cudaError_t launch_rhs(const DevGeom& g, const double gvec[3], double* out, cudaStream_t s);
 cudaError_t copy_rows_to_double(const DevGeom& g, int64_t row0, int64_t nrows, double* out,

@@ -333,7 +333,7 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
     return cudaStreamSynchronize(s);
   }
   double* hist = nullptr;  // [maxit+1] relres, [maxit] alpha, [maxit] beta
-  if ((e = cudaMallocAsync((void**)&hist, sizeof(double) * (3 * (size_t)maxit + 1), s)) != cudaSuccess)
+  if ((e = pool_alloc((void**)&hist, sizeof(double) * (3 * (size_t)maxit + 1), g.pool, s)) != cudaSuccess)
     return e;
   double* alpha_h = hist + maxit + 1;
   double* beta_h = alpha_h + maxit;

@@ -276,16 +276,25 @@ void build_near_pairs(const Topo& t, std::vector<NearPair>& out) {
   std::vector<int32_t> inc(3 * nt);
   std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
   for (int64_t i = 0; i < 3 * nt; ++i) inc[fill[t.tri[i]]++] = (int32_t)(i / 3);
+  // candidates S >= T sharing a vertex with T, deduplicated with a stamp array;
+  // kept in increasing S so the list order is deterministic
+  std::vector<int32_t> stamp(nt, -1);
   std::vector<int32_t> nb;
+  nb.reserve(64);
+  out.reserve((size_t)nt * 8);
   for (int64_t T = 0; T < nt; ++T) {
     nb.clear();
     for (int a = 0; a < 3; ++a) {
       int32_t v = t.tri[3 * T + a];
-      for (int64_t c = cptr[v]; c < cptr[v + 1]; ++c)
-        if (inc[c] >= T) nb.push_back(inc[c]);
+      for (int64_t c = cptr[v]; c < cptr[v + 1]; ++c) {
+        const int32_t S = inc[c];
+        if (S >= T && stamp[S] != (int32_t)T) {
+          stamp[S] = (int32_t)T;
+          nb.push_back(S);
+        }
+      }
     }
     std::sort(nb.begin(), nb.end());
-    nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
     const int32_t* a = &t.tri[3 * T];
     for (int32_t S : nb) {
       const int32_t* b = &t.tri[3 * S];
