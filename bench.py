@@ -142,6 +142,13 @@ def max_over_ranks(pg, x: float, device=None) -> float:
     return float(t.item())
 
 
+def aggregate(pg, world: int, steps: int, local_seconds: float, device=None):
+    """Whole-job throughput of N independent replicas: every rank ran `steps`
+    solves; the job time is the slowest rank's.  Returns (solves/s, seconds)."""
+    t = max_over_ranks(pg, local_seconds, device)
+    return world * steps / t, t
+
+
 # --------------------------------------------------------------------------
 # oracle timing (cpu_baseline and the reference arm)
 # --------------------------------------------------------------------------
@@ -270,10 +277,8 @@ def run_ours(args, world, rank, local, pg):
     barrier(pg)
     ck = clocks.stop()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_s = sum(step_ms) / 1e3
     launches = (S.counters()["launches"] - launches0) / args.steps
-    total_s = max_over_ranks(pg, total_s, dev)
-    value = world * args.steps / total_s
+    value, total_s = aggregate(pg, world, args.steps, sum(step_ms) / 1e3, dev)
     far_pairs = S.counters()["far_pairs"]
     far_avg_s = statistics.mean(far_ms) / 1e3
     ops = far_pairs * FP32_OPS_PER_FAR_PAIR
@@ -309,9 +314,9 @@ def run_ours(args, world, rank, local, pg):
             e2e_step()
         torch.cuda.synchronize()
         barrier(pg)
-        t_e2e = max_over_ranks(pg, time.perf_counter() - t0, dev)
+        e2e_value, _ = aggregate(pg, world, args.steps, time.perf_counter() - t0, dev)
         E.close()
-        e2e = {"value": world * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(N * 8)}
 
     cpu = None

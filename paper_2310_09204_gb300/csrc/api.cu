@@ -66,7 +66,7 @@ bool is_device_ptr(const void* p) {
 void free_dev(DevGeom& d, cudaStream_t s) {
   void* ptrs[] = {d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
                   d.d_jptr, d.d_jtri, d.d_jvec, d.d_jvecf, d.d_jrhs, d.d_W, d.d_bptr, d.d_bdofs, d.d_boff,
-                  d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pf,
+                  d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pf, d.d_rf, d.d_binvf,
                   d.d_WP, d.d_vec, d.d_scal};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
@@ -288,6 +288,7 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   chk(dalloc(&d.d_WP, (size_t)std::max<int64_t>(NH, 1) * N, c->pool, s));
   chk(dalloc(&d.d_vec, (size_t)(5 * N + 2 * std::max<int64_t>(NH, 1) + 8), c->pool, s));
   chk(dalloc(&d.d_pf, (size_t)N, c->pool, s));
+  chk(dalloc(&d.d_rf, (size_t)N, c->pool, s));
   chk(dalloc(&d.d_scal, (size_t)(16 + std::max<int64_t>(256, N / 8 + 8)), c->pool, s));
   chk(cudaStreamSynchronize(s));
   if (e != cudaSuccess) {

@@ -102,7 +102,8 @@ __device__ __forceinline__ int find_prefix(const int64_t* pre, int active, int64
 
 __global__ void __launch_bounds__(256) bgj_pivot_kernel(BgjArgs g, int64_t k0) {
   __shared__ double S[GB][GB + 1];
-  __shared__ double rowk[GB], colk[GB];
+  __shared__ double rowk[GB], colk[GB];  // pivot row scaled by 1/p, pivot column
+  __shared__ double s_ip;
   const int a = blockIdx.x;
   const int b = g.order[a];
   const int64_t n = g.bsize[b];
@@ -114,19 +115,25 @@ __global__ void __launch_bounds__(256) bgj_pivot_kernel(BgjArgs g, int64_t k0) {
   }
   __syncthreads();
   for (int k = 0; k < GB; ++k) {
-    if (threadIdx.x < GB) rowk[threadIdx.x] = S[k][threadIdx.x];
-    else if (threadIdx.x < 2 * GB) colk[threadIdx.x - GB] = S[threadIdx.x - GB][k];
+    // one warp forms 1/p, the scaled pivot row and the pivot column
+    if (threadIdx.x < 32) {
+      const double p = S[k][k];
+      const double ip = 1.0 / p;
+      if (threadIdx.x == 0) {
+        s_ip = ip;
+        if (!(p > 0.0 && isfinite(p))) atomicExch(g.flag, 1);
+      }
+      rowk[threadIdx.x] = S[k][threadIdx.x] * ip;
+      colk[threadIdx.x] = S[threadIdx.x][k];
+    }
     __syncthreads();
-    const double p = rowk[k];
-    if (threadIdx.x == 0 && !(p > 0.0 && isfinite(p))) atomicExch(g.flag, 1);
-    const double ip = 1.0 / p;
+    const double ip = s_ip;
     for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
-      int i = e / GB, j = e % GB;
+      const int i = e / GB, j = e % GB;
       double v;
-      if (i == k && j == k) v = ip;
-      else if (i == k) v = rowk[j] * ip;
+      if (i == k) v = (j == k) ? ip : rowk[j];
       else if (j == k) v = -colk[i] * ip;
-      else v = fma(-colk[i] * ip, rowk[j], S[i][j]);
+      else v = fma(-colk[i], rowk[j], S[i][j]);
       S[i][j] = v;
     }
     __syncthreads();
@@ -240,6 +247,15 @@ __global__ void __launch_bounds__(256) bgj_update_kernel(BgjArgs g, int active, 
     for (int m = 0; m < kb; ++m) df_fma_acc(sL[i][m].x, sL[i][m].y, sR[m][tx].x, sR[m][tx].y, acch, accl);
     double upd = df_to_double(acch, accl);
     A[row * n + col] = (I == kt) ? upd : A[row * n + col] + upd;
+  }
+}
+
+__global__ void to_float_pairs_kernel(const double* __restrict__ x, float2* __restrict__ xf, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float h, l;
+    split_df(x[i], h, l);
+    xf[i] = make_float2(h, l);
   }
 }
 
@@ -409,7 +425,20 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
   }
   std::vector<int64_t> bsz(bsize.begin(), bsize.end());
   std::vector<int64_t> bof(boff.begin(), boff.end() - 1);
-  return gj_invert(g.d_binv, bof, bsz, inv, g.pool, s, not_spd, &g.launches);
+  e = gj_invert(g.d_binv, bof, bsz, inv, g.pool, s, not_spd, &g.launches);
+  if (e != cudaSuccess) return e;
+  // float-pair copy of the face / wire-basket inverses for the preconditioner
+  if (g.d_binvf) { cudaFreeAsync(g.d_binvf, s); g.d_binvf = nullptr; }
+  const int64_t nf = boff[nblk];
+  if ((e = pool_alloc((void**)&g.d_binvf, sizeof(float2) * std::max<int64_t>(1, nf), g.pool, s)) !=
+      cudaSuccess)
+    return e;
+  if (nf > 0) {
+    to_float_pairs_kernel<<<(unsigned)std::min<int64_t>((nf + 255) / 256, 152 * 32), 256, 0, s>>>(
+        g.d_binv, g.d_binvf, nf);
+    ++g.launches;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace msbem

@@ -108,6 +108,7 @@ struct DevGeom {
   int32_t* d_bdofs = nullptr;
   int64_t* d_boff = nullptr;     // offset of each block's inverse in d_binv
   double* d_binv = nullptr;
+  float2* d_binvf = nullptr;     // float-pair copy of the face / wire-basket inverses
   int64_t binv_size = 0;
   int wb_diag = 0;
   int64_t n_coarse = 0;
@@ -124,6 +125,7 @@ struct DevGeom {
   // PCG vectors
   double* d_vec = nullptr;       // vectors of N: x r z p q, coarse scratch
   float2* d_pf = nullptr;        // search direction p as (hi, lo) floats
+  float2* d_rf = nullptr;        // residual r as (hi, lo) floats
   double* d_scal = nullptr;      // device scalars
   int assembled = 0, factored = 0;
   int64_t launches = 0;          // kernels launched by this geometry so far

@@ -186,13 +186,14 @@ __global__ void check_kernel(const double* scal, PcgState* st, double* hist) {
   else if (it >= st->maxit) st->done = (st->fixed || rel <= scal[7]) ? 1 : 3;
 }
 
-// z[D_b[i]] = sum_j Ainv_b[i][j] r[D_b[j]]  (warp per row, rows of all blocks)
-__global__ void __launch_bounds__(256) block_apply_kernel(const double* __restrict__ Ainv,
+// z[D_b[i]] = sum_j Ainv_b[i][j] r[D_b[j]]  (warp per row, rows of all blocks),
+// in double-float from float-pair copies of the block inverses and of r
+__global__ void __launch_bounds__(256) block_apply_kernel(const float2* __restrict__ Ainv,
                                                           const int64_t* __restrict__ boff,
                                                           const int64_t* __restrict__ bptr,
                                                           const int32_t* __restrict__ bdofs,
                                                           int nblk, int64_t N,
-                                                          const double* __restrict__ r,
+                                                          const float2* __restrict__ rf,
                                                           double* __restrict__ z,
                                                           const PcgState* __restrict__ st) {
   if (st->done) return;
@@ -207,29 +208,57 @@ __global__ void __launch_bounds__(256) block_apply_kernel(const double* __restri
   const int b = lo;
   const int64_t n = bptr[b + 1] - bptr[b];
   const int64_t i = rho - bptr[b];
-  const double* a = Ainv + boff[b] + i * n;
+  const float2* a = Ainv + boff[b] + i * n;
   const int32_t* d = bdofs + bptr[b];
-  double acc = 0.0;
-  for (int64_t j = lane; j < n; j += 32) acc = fma(a[j], r[d[j]], acc);
+  float acch = 0.f, accl = 0.f;
+  for (int64_t j = lane; j < n; j += 32) {
+    const float2 x = a[j], y = rf[d[j]];
+    df_fma_acc(x.x, x.y, y.x, y.y, acch, accl);
+  }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (lane == 0) z[d[i]] = acc;
+  for (int off = 16; off > 0; off >>= 1) {
+    float oh = __shfl_xor_sync(0xffffffffu, acch, off);
+    float ol = __shfl_xor_sync(0xffffffffu, accl, off);
+    float sh, se;
+    two_sum(acch, oh, sh, se);
+    acch = sh;
+    accl = accl + ol + se;
+  }
+  if (lane == 0) z[d[i]] = df_to_double(acch, accl);
 }
 
-// t = P^T r (CSC of P), warp per coarse dof
+// float-pair copy of a vector
+__global__ void to_df_kernel(const double* __restrict__ x, float2* __restrict__ xf, int64_t N,
+                             const PcgState* __restrict__ st) {
+  if (st->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256) {
+    float h, l;
+    split_df(x[i], h, l);
+    xf[i] = make_float2(h, l);
+  }
+}
+
+// t = P^T r (CSC of P), one block per coarse dof (columns of P hold
+// thousands of fine entries)
 __global__ void restrict_kernel(const int64_t* __restrict__ cptr, const int32_t* __restrict__ crow,
                                 const double* __restrict__ cval, int64_t NH,
                                 const double* __restrict__ r, double* __restrict__ t,
                                 const PcgState* __restrict__ st) {
   if (st->done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t mu = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (mu >= NH) return;
+  __shared__ double s[8];
+  const int64_t mu = blockIdx.x;
   double acc = 0.0;
-  for (int64_t k = cptr[mu] + lane; k < cptr[mu + 1]; k += 32) acc = fma(cval[k], r[crow[k]], acc);
+  for (int64_t k = cptr[mu] + threadIdx.x; k < cptr[mu + 1]; k += blockDim.x)
+    acc = fma(cval[k], r[crow[k]], acc);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (lane == 0) t[mu] = acc;
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s[w];
+    t[mu] = v;
+  }
 }
 
 // u = AHinv t (warp per row)
@@ -299,12 +328,13 @@ static void apply_M(DevGeom& g, const double* r, double* z, double* t, double* u
     ++g.launches;
     return;
   }
-  block_apply_kernel<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(g.d_binv, g.d_boff, g.d_bptr, g.d_bdofs,
-                                                              (int)g.n_blocks, N, r, z, st);
-  ++g.launches;
+  to_df_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, g.d_rf, N, st);
+  block_apply_kernel<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
+                                                              (int)g.n_blocks, N, g.d_rf, z, st);
+  g.launches += 2;
   const int64_t NH = g.use_coarse ? g.n_coarse : 0;
   if (NH > 0) {
-    restrict_kernel<<<(unsigned)((NH + 7) / 8), 256, 0, s>>>(g.d_cptr, g.d_crow, g.d_cval, NH, r, t, st);
+    restrict_kernel<<<(unsigned)NH, 256, 0, s>>>(g.d_cptr, g.d_crow, g.d_cval, NH, r, t, st);
     coarse_solve_kernel<<<(unsigned)((NH + 7) / 8), 256, 0, s>>>(g.d_AHinv, NH, t, u, st);
     prolong_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(g.d_pptr, g.d_pcol, g.d_pval, N, u, z, st);
     g.launches += 3;
