@@ -173,6 +173,19 @@ typedef struct msbem_solve_opts {
 int msbem_solve(msbem_geom* g, const double gvec[3], const msbem_solve_opts* opts, double* density,
                 int* iters, double* resid_hist, int hist_cap, double* kappa_est);
 
+/* Solve W Phi_c = L(g_c) for k constant Neumann data g_c at once (block PCG):
+ * every column follows the recursion of msbem_solve (own scalars and stopping
+ * test) while the k columns share each pass over W (and over the block
+ * inverses of the preconditioner), so k solves cost far less than k calls of
+ * msbem_solve.  Columns are processed in groups of up to 16.
+ *   gvecs[3*k]         the data g_c
+ *   densities[k*N]     output, row c = Phi_c (host or device pointer)
+ *   iters[k], relres[k], kappa_est[k]  per-column results (each may be NULL)
+ * Returns the worst status over the columns (NOT_CONVERGED / BREAKDOWN as in
+ * msbem_solve; densities always written). */
+int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_solve_opts* opts,
+                      double* densities, int* iters, double* relres, double* kappa_est);
+
 /* Timing of the last assemble / factor / solve on this geometry, in
  * milliseconds measured with CUDA events on the context's stream:
  * t[0] far field, t[1] near field, t[2] contraction to W, t[3] factor,

@@ -70,6 +70,7 @@ def lib():
         "msbem_last_timings": ([P, P], i32),
         "msbem_counters": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
         "msbem_spd_inverse_noalloc": ([P, i64, P, P], i32),
+        "msbem_solve_batch": ([P, P, i32, ctypes.POINTER(SolveOpts), P, P, P, P], i32),
         "msbem_mesh_dofs": ([P, i64, P, i64, ctypes.POINTER(i64), P, P, i64, ctypes.c_char_p, i32], i32),
     }
     for name, (args, res) in sig.items():
@@ -248,6 +249,23 @@ class Solver:
         o = PrecondOpts(wire_basket, use_coarse)
         _check(self.ctx, lib().msbem_factor(self.geom, ctypes.byref(o)))
         return self
+
+    def solve_batch(self, G, rtol: float = 1e-8, maxit: int = 1000, fixed: bool = False,
+                    precondition: bool = True, out=None, raise_on_status=True):
+        """k solves sharing the matrix-vector products; G is k x 3."""
+        G = np.ascontiguousarray(G, np.float64).reshape(-1, 3)
+        k = G.shape[0]
+        if out is None:
+            out = np.empty((k, self.n), np.float64)
+        iters = np.zeros(k, np.int32)
+        rel = np.zeros(k, np.float64)
+        kap = np.zeros(k, np.float64)
+        o = SolveOpts(rtol, maxit, int(fixed), int(precondition))
+        st = lib().msbem_solve_batch(self.geom, _ptr(G), k, ctypes.byref(o), _ptr(out), _ptr(iters),
+                                     _ptr(rel), _ptr(kap))
+        if raise_on_status:
+            _check(self.ctx, st)
+        return {"density": out, "iters": iters, "relres": rel, "kappa": kap, "status": st}
 
     def solve(self, g, rtol: float = 1e-8, maxit: int = 1000, fixed: bool = False,
               precondition: bool = True, out=None, hist_cap: int = 4096, raise_on_status=True):

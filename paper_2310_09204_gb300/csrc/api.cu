@@ -14,6 +14,7 @@ using namespace msbem;
 struct msbem_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream for CUDA-graph capture
   cudaMemPool_t pool = nullptr;
   std::string err;
   std::vector<msbem_geom*> geoms;
@@ -64,9 +65,10 @@ bool is_device_ptr(const void* p) {
 }
 
 void free_dev(DevGeom& d, cudaStream_t s) {
-  void* ptrs[] = {d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
-                  d.d_jptr, d.d_jtri, d.d_jvec, d.d_jvecf, d.d_jrhs, d.d_W, d.d_bptr, d.d_bdofs, d.d_boff,
-                  d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pf, d.d_rf, d.d_binvf,
+  drop_pcg_graphs(d);
+  void* ptrs[] = {d.d_hist, d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
+                  d.d_jptr, d.d_jtri, d.d_jvec, d.d_jvecf, d.d_jrhs, d.d_Wh, d.d_bptr, d.d_bdofs, d.d_boff,
+                  d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pfp, d.d_rf, d.d_binvf,
                   d.d_WP, d.d_vec, d.d_scal};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
@@ -126,6 +128,10 @@ int msbem_create(msbem_ctx** ctx, int device, void* stream) {
   c->device = device;
   c->stream = (cudaStream_t)stream;
   for (auto& ev : c->ev) cudaEventCreate(&ev);
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+  }
   // a private stream-ordered pool that keeps freed memory for reuse
   cudaMemPoolProps props = {};
   props.allocType = cudaMemAllocationTypePinned;
@@ -154,6 +160,7 @@ int msbem_destroy(msbem_ctx* c) {
     cudaStreamSynchronize(c->stream);
     cudaMemPoolDestroy(c->pool);
   }
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return MSBEM_OK;
 }
@@ -185,6 +192,7 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   DevGeom& d = g->dev;
   cudaStream_t s = c->stream;
   d.pool = c->pool;
+  d.cap_stream = c->cap_stream;
   d.nt = nt;
   d.nt_pad = (nt + 63) / 64 * 64;
   d.ndof = f.ndof;
@@ -283,12 +291,22 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
     chk(dput(&d.d_cvalf, cvalf, c->pool, s));
   }
   const int64_t N = f.ndof;
-  chk(dalloc(&d.d_V, (size_t)nt * nt, c->pool, s));
-  chk(dalloc(&d.d_W, (size_t)N * N, c->pool, s));
+  d.ldw = (N + 31) / 32 * 32;
+  chk(dalloc(&d.d_Wh, (size_t)2 * N * d.ldw, c->pool, s));
+  if (N > 0) chk(cudaMemsetAsync(d.d_Wh, 0, sizeof(float) * 2 * N * d.ldw, s));
   chk(dalloc(&d.d_WP, (size_t)std::max<int64_t>(NH, 1) * N, c->pool, s));
   chk(dalloc(&d.d_vec, (size_t)(5 * N + 2 * std::max<int64_t>(NH, 1) + 8), c->pool, s));
-  chk(dalloc(&d.d_pf, (size_t)N, c->pool, s));
+  chk(dalloc(&d.d_pfp, (size_t)2 * d.ldw, c->pool, s));
+  if (N > 0) {
+    chk(matvec_init());
+    chk(cudaMemsetAsync(d.d_pfp, 0, sizeof(float) * 2 * d.ldw, s));
+    chk(encode_planes(&d.tm_W, d.d_Wh, d.ldw, N, N * d.ldw, 2, 16));
+    chk(encode_planes(&d.tm_Whi, d.d_Wh, d.ldw, N, N * d.ldw, 1, 16));
+    chk(encode_planes(&d.tm_p, d.d_pfp, d.ldw, 1, d.ldw, 2, 1));
+  }
   chk(dalloc(&d.d_rf, (size_t)N, c->pool, s));
+  d.hist_cap = 1024;
+  chk(dalloc(&d.d_hist, (size_t)(3 * d.hist_cap + 1), c->pool, s));
   chk(dalloc(&d.d_scal, (size_t)(16 + std::max<int64_t>(256, N / 8 + 8)), c->pool, s));
   chk(cudaStreamSynchronize(s));
   if (e != cudaSuccess) {
@@ -373,6 +391,15 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   cudaError_t e = set_far_constants(bary, w6);
   if (e == cudaSuccess) e = set_far_df_constants(w6);
   if (e != cudaSuccess) return cuda_fail(c, e, "far constants");
+  // V (nt^2 float pairs) is scratch of the assembly only: taken from the pool
+  // here and returned once W is formed, so a resident geometry holds W alone
+  if (!d.d_V) {
+    e = pool_alloc((void**)&d.d_V, sizeof(float2) * std::max<int64_t>(1, d.nt * d.nt), d.pool, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, MSBEM_OOM, "assemble: no room for the pair matrix V");
+    }
+  }
   cudaEventRecord(c->ev[0], s);
   e = (far_kernel == 1) ? launch_far_fp64(d, s) : launch_far_df(d, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "far field");
@@ -384,6 +411,8 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
   cudaEventRecord(c->ev[3], s);
   d.launches += 1 + (d.n_near > 0) + (d.ndof > 0);
+  cudaFreeAsync(d.d_V, s);
+  d.d_V = nullptr;
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "assemble");
   float t;
@@ -442,6 +471,7 @@ int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts) {
   d.use_coarse = opts ? (opts->use_coarse != 0) : 1;
   if (wb_diag < 0 || wb_diag > 1) return fail(c, MSBEM_INVALID_ARG, "wire_basket must be 0 or 1");
   d.wb_diag = (g->split.n_wb > 0) ? 0 : -1;  // marks whether the last block is the wire basket
+  drop_pcg_graphs(d);  // the captured iterations address the old inverses
   cudaEventRecord(c->ev[4], c->stream);
   int not_spd = 0;
   cudaError_t e = factor_blocks(d, g->bptr, (g->split.n_wb > 0) ? wb_diag : 0, c->stream, &not_spd);
@@ -493,6 +523,8 @@ int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts,
   if (kappa) *kappa = tridiag_kappa(po.alpha, po.beta);
   if (po.status == MSBEM_NOT_CONVERGED) return fail(c, po.status, "msbem_solve: maxit reached");
   if (po.status == MSBEM_BREAKDOWN) return fail(c, po.status, "msbem_solve: PCG breakdown");
+  if (po.status == MSBEM_DEVICE_TIMEOUT)
+    return fail(c, po.status, "msbem_solve: a matrix copy did not complete in time");
   return MSBEM_OK;
 }
 
@@ -500,6 +532,51 @@ int msbem_counters(const msbem_geom* g, int64_t* launches, int64_t* far_pairs) {
   if (!g) return MSBEM_INVALID_ARG;
   if (launches) *launches = g->dev.launches;
   if (far_pairs) *far_pairs = g->dev.n_far_pairs;
+  return MSBEM_OK;
+}
+
+int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_solve_opts* opts,
+                      double* density, int* iters, double* relres, double* kappa) {
+  if (!g || !gvecs || !density || k < 1) return MSBEM_INVALID_ARG;
+  msbem_ctx* c = g->ctx;
+  DevGeom& d = g->dev;
+  double rtol = opts ? opts->rtol : 1e-8;
+  int maxit = opts ? opts->maxit : 1000;
+  int fixed = opts ? opts->fixed_iters : 0;
+  int prec = opts ? opts->precondition : 1;
+  if (!(rtol >= 0.0) || maxit < 1) return fail(c, MSBEM_INVALID_ARG, "rtol >= 0 and maxit >= 1 required");
+  if (!d.assembled) return fail(c, MSBEM_NOT_READY, "msbem_solve_batch: not assembled");
+  if (prec && !d.factored) return fail(c, MSBEM_NOT_READY, "msbem_solve_batch: call msbem_factor first");
+  cudaSetDevice(c->device);
+  const int64_t N = g->fine.ndof;
+  const bool dev_out = is_device_ptr(density);
+  int worst = MSBEM_OK;
+  cudaEventRecord(c->ev[6], c->stream);
+  for (int c0 = 0; c0 < k; c0 += 16) {
+    const int kb = std::min(16, k - c0);
+    std::vector<PcgOut> outs;
+    cudaError_t e = run_pcg_batch(d, gvecs + 3 * c0, kb, rtol, maxit, fixed, prec,
+                                  density + (size_t)c0 * N, dev_out, outs, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msbem_solve_batch");
+    for (int j = 0; j < kb; ++j) {
+      const PcgOut& o = outs[j];
+      if (iters) iters[c0 + j] = o.iters;
+      if (relres) relres[c0 + j] = o.hist.empty() ? 0.0 : o.hist.back();
+      if (kappa) kappa[c0 + j] = tridiag_kappa(o.alpha, o.beta);
+      if (o.status == MSBEM_DEVICE_TIMEOUT) worst = MSBEM_DEVICE_TIMEOUT;
+      else if (o.status == MSBEM_BREAKDOWN && worst != MSBEM_DEVICE_TIMEOUT) worst = MSBEM_BREAKDOWN;
+      else if (o.status == MSBEM_NOT_CONVERGED && worst == MSBEM_OK) worst = MSBEM_NOT_CONVERGED;
+    }
+  }
+  cudaEventRecord(c->ev[7], c->stream);
+  cudaStreamSynchronize(c->stream);
+  float t;
+  cudaEventElapsedTime(&t, c->ev[6], c->ev[7]);
+  d.times[4] = t;
+  if (worst == MSBEM_DEVICE_TIMEOUT)
+    return fail(c, worst, "msbem_solve_batch: a matrix copy did not complete in time");
+  if (worst == MSBEM_BREAKDOWN) return fail(c, worst, "msbem_solve_batch: PCG breakdown");
+  if (worst == MSBEM_NOT_CONVERGED) return fail(c, worst, "msbem_solve_batch: maxit reached");
   return MSBEM_OK;
 }
 

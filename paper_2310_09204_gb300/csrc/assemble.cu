@@ -445,7 +445,8 @@ __global__ void __launch_bounds__(256) contract_kernel(const float2* __restrict_
                                                        const int64_t* __restrict__ jptr,
                                                        const int32_t* __restrict__ jtri,
                                                        const float2* __restrict__ jvec, int64_t N,
-                                                       int nbt, float2* __restrict__ W) {
+                                                       int nbt, float* __restrict__ Wh,
+                                                       float* __restrict__ Wl, int64_t ldw) {
   __shared__ float2 s_out[CT][CT + 1];
   __shared__ int32_t s_rtri[CT_CAP], s_ctri[CT_CAP];
   __shared__ float2 s_rvec[3 * CT_CAP], s_cvec[3 * CT_CAP];
@@ -497,12 +498,19 @@ __global__ void __launch_bounds__(256) contract_kernel(const float2* __restrict_
   for (int rr = ty; rr < CT; rr += 8) {
     int64_t row = r0 + rr, c = c0 + tx;
     float2 v = (bi == bj && tx < rr) ? s_out[tx][rr] : s_out[rr][tx];
-    if (row < N && c < N) W[row * N + c] = v;
+    if (row < N && c < N) {
+      Wh[row * ldw + c] = v.x;
+      Wl[row * ldw + c] = v.y;
+    }
   }
   if (bi != bj) {
     for (int cc = ty; cc < CT; cc += 8) {
       int64_t R = c0 + cc, C = r0 + tx;
-      if (R < N && C < N) W[R * N + C] = s_out[tx][cc];
+      if (R < N && C < N) {
+        const float2 v = s_out[tx][cc];
+        Wh[R * ldw + C] = v.x;
+        Wl[R * ldw + C] = v.y;
+      }
     }
   }
 }
@@ -512,15 +520,20 @@ cudaError_t launch_contract(const DevGeom& g, cudaStream_t s) {
   int64_t tiles = (int64_t)nbt * (nbt + 1) / 2;
   if (tiles == 0) return cudaSuccess;
   contract_kernel<<<(unsigned)tiles, 256, 0, s>>>(g.d_V, g.nt, g.d_jptr, g.d_jtri, g.d_jvecf, g.ndof,
-                                                  nbt, g.d_W);
+                                                  nbt, g.d_Wh, g.wlo(), g.ldw);
   return cudaGetLastError();
 }
 
-__global__ void w_to_double_kernel(const float2* __restrict__ W, int64_t n, double* __restrict__ out) {
+// rows row0 .. row0+nrows-1 of W as dense FP64 rows of length N
+__global__ void w_to_double_kernel(const float* __restrict__ Wh, const float* __restrict__ Wl,
+                                   int64_t ldw, int64_t N, int64_t row0, int64_t nrows,
+                                   double* __restrict__ out) {
+  const int64_t n = nrows * N;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    float2 v = W[i];
-    out[i] = df_to_double(v.x, v.y);
+    const int64_t r = i / N, c = i - r * N;
+    const int64_t o = (row0 + r) * ldw + c;
+    out[i] = df_to_double(Wh[o], Wl[o]);
   }
 }
 
@@ -529,7 +542,7 @@ cudaError_t copy_rows_to_double(const DevGeom& g, int64_t row0, int64_t nrows, d
   const int64_t n = nrows * g.ndof;
   if (n == 0) return cudaSuccess;
   int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 64);
-  w_to_double_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_W + row0 * g.ndof, n, out);
+  w_to_double_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_Wh, g.wlo(), g.ldw, g.ndof, row0, nrows, out);
   return cudaGetLastError();
 }
 

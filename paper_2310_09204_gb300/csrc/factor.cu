@@ -17,7 +17,8 @@
 
 namespace msbem {
 
-__global__ void gather_blocks_kernel(const float2* __restrict__ W, int64_t N,
+__global__ void gather_blocks_kernel(const float* __restrict__ Wh, const float* __restrict__ Wl,
+                                     int64_t ldw,
                                      const int64_t* __restrict__ bptr,
                                      const int32_t* __restrict__ bdofs,
                                      const int64_t* __restrict__ boff,
@@ -31,15 +32,15 @@ __global__ void gather_blocks_kernel(const float2* __restrict__ W, int64_t N,
   const int64_t e = t - prefix2[b];
   const int64_t i = e / n, j = e % n;
   const int64_t di = bdofs[bptr[b] + i], dj = bdofs[bptr[b] + j];
-  const float2 wv = W[di * N + dj];
-  double v = df_to_double(wv.x, wv.y);
+  double v = df_to_double(Wh[di * ldw + dj], Wl[di * ldw + dj]);
   if (b == wb_block && wb_diag) v = (i == j) ? 1.0 / v : 0.0;
   out[boff[b] + e] = v;
 }
 
 // W P  (transposed, NH x N) from the CSC form of P:  (W P)^T[mu][i] = sum_nu P[nu,mu] W[nu][i],
 // accumulated in double-float (W and P values are float pairs)
-__global__ void wp_kernel(const float2* __restrict__ W, int64_t N, const int64_t* __restrict__ cptr,
+__global__ void wp_kernel(const float* __restrict__ Wh, const float* __restrict__ Wl, int64_t ldw,
+                          int64_t N, const int64_t* __restrict__ cptr,
                           const int32_t* __restrict__ crow, const float2* __restrict__ cval,
                           double* __restrict__ WPt) {
   const int64_t mu = blockIdx.y;
@@ -47,9 +48,9 @@ __global__ void wp_kernel(const float2* __restrict__ W, int64_t N, const int64_t
   if (i >= N) return;
   float acch = 0.f, accl = 0.f;
   for (int64_t k = cptr[mu]; k < cptr[mu + 1]; ++k) {
-    const float2 w = W[(int64_t)crow[k] * N + i];
+    const int64_t o = (int64_t)crow[k] * ldw + i;
     const float2 c = cval[k];
-    df_fma_acc(c.x, c.y, w.x, w.y, acch, accl);
+    df_fma_acc(c.x, c.y, Wh[o], Wl[o], acch, accl);
   }
   WPt[mu * N + i] = df_to_double(acch, accl);
 }
@@ -406,7 +407,7 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
   if (prefix2[nblk] > 0) ++g.launches;
   if (prefix2[nblk] > 0)
     gather_blocks_kernel<<<(unsigned)((prefix2[nblk] + 255) / 256), 256, 0, s>>>(
-        g.d_W, g.ndof, g.d_bptr, g.d_bdofs, g.d_boff, d_prefix2, nblk, wb_block, wb_diag, g.d_binv);
+        g.d_Wh, g.wlo(), g.ldw, g.d_bptr, g.d_bdofs, g.d_boff, d_prefix2, nblk, wb_block, wb_diag, g.d_binv);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   cudaFreeAsync(d_prefix2, s);
   std::vector<int32_t> inv;
@@ -415,7 +416,7 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
   if (NH > 0 && g.ndof > 0) {
     // A_H = P^T W P in the last slot
     dim3 grid((unsigned)((g.ndof + 255) / 256), (unsigned)NH);
-    wp_kernel<<<grid, 256, 0, s>>>(g.d_W, g.ndof, g.d_cptr, g.d_crow, g.d_cvalf, g.d_WP);
+    wp_kernel<<<grid, 256, 0, s>>>(g.d_Wh, g.wlo(), g.ldw, g.ndof, g.d_cptr, g.d_crow, g.d_cvalf, g.d_WP);
     dim3 grid2((unsigned)NH, (unsigned)((NH + 127) / 128));
     ah_kernel<<<grid2, 128, 0, s>>>(g.d_WP, g.ndof, NH, g.d_cptr, g.d_crow, g.d_cval,
                                     g.d_binv + boff[nblk]);

@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/msbem.h"
@@ -101,7 +102,13 @@ struct DevGeom {
   double* d_jvec = nullptr;      // [entries][3] curl vectors s_{T,nu}
   float2* d_jvecf = nullptr;     // [entries][3] the same as (hi, lo) floats
   double* d_jrhs = nullptr;      // [entries][3] coef |T|/3 n_T (RHS weights)
-  float2* d_W = nullptr;         // [N][N] Galerkin matrix as (hi, lo) float pairs
+  // Galerkin matrix as two FP32 planes [2][N][ldw] (hi, then lo; W = hi + lo
+  // to ~2^-48 relative), ldw = N rounded up to 32, padding columns zero
+  int64_t ldw = 0;
+  float* d_Wh = nullptr;
+  float* wlo() const { return d_Wh + ndof * ldw; }
+  CUtensorMap tm_W;              // 16 x 128 x 2 boxes of both planes (matvec.cu)
+  CUtensorMap tm_Whi;            // 16 x 128 x 1 boxes of the hi plane
   // preconditioner
   int64_t n_blocks = 0;
   int64_t* d_bptr = nullptr;     // n_blocks+1
@@ -124,10 +131,17 @@ struct DevGeom {
   int use_coarse = 1;
   // PCG vectors
   double* d_vec = nullptr;       // vectors of N: x r z p q, coarse scratch
-  float2* d_pf = nullptr;        // search direction p as (hi, lo) floats
+  float* d_pfp = nullptr;        // search direction p as planes [2][ldw] (hi, lo; zero padding)
+  CUtensorMap tm_p;              // 1 x 128 x 2 boxes of d_pfp
   float2* d_rf = nullptr;        // residual r as (hi, lo) floats
   double* d_scal = nullptr;      // device scalars
   int assembled = 0, factored = 0;
+  // PCG iteration chunk captured as a CUDA graph (one per preconditioning mode),
+  // valid until the next factorisation; captured on a private stream
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};
+  double* d_hist = nullptr;      // persistent residual / alpha / beta history
+  int hist_cap = 0;              // iterations the persistent history can hold
   int64_t launches = 0;          // kernels launched by this geometry so far
   int64_t n_far_pairs = 0;       // unordered pairs sharing no vertex
   float times[5] = {0, 0, 0, 0, 0};
@@ -145,6 +159,19 @@ cudaError_t copy_rows_to_double(const DevGeom& g, int64_t row0, int64_t nrows, d
 cudaError_t set_far_constants(const double bary[6][3], const double w[6]);
 cudaError_t set_far_df_constants(const double w[6]);
 
+// Q = W P for kb <= 16 vectors (matvec.cu): mode 0 double-float on both W
+// planes (tmW over both), mode 1 FP32 on the hi plane (tmW over one plane);
+// tmP boxes are 128 x kb x planes.  Partial sums of p_c . q_c go to
+// part[c * matvec_blocks(N) + block].  The kernel returns at once when *stop
+// is non-zero and sets *err when a copy never completes.
+cudaError_t encode_planes(CUtensorMap* map, const float* base, int64_t ld, int64_t rows,
+                          int64_t plane_stride, int nplanes, int box_rows);
+unsigned matvec_blocks(int64_t N);
+cudaError_t matvec_init();   // per device, before the first launch_matvec
+cudaError_t launch_matvec(int mode, const CUtensorMap& tmW, const CUtensorMap& tmP, int64_t N, int kb,
+                          const double* P, double* Q, double* part, const int* stop, int* err,
+                          cudaStream_t s);
+
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag,
                           cudaStream_t s, int* not_spd);
 
@@ -161,5 +188,11 @@ struct PcgOut {
 };
 cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, int fixed,
                     int precondition, double* x_out_dev, PcgOut& out, cudaStream_t s);
+void drop_pcg_graphs(DevGeom& g);
+// k <= 16 independent right-hand sides sharing the matrix-vector products
+// (pcg_batch.cu); X_out is k x N (row c = density of g_c)
+cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, int fixed,
+                          int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
+                          cudaStream_t s);
 
 }  // namespace msbem

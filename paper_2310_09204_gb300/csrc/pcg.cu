@@ -24,85 +24,18 @@ namespace msbem {
 
 // device-side solver state (ints), next to the FP64 scalars
 struct PcgState {
-  int done;    // 0 running, 1 converged / fixed count reached, 2 breakdown, 3 maxit
+  int done;    // 0 running, 1 converged / fixed count reached, 2 breakdown, 3 maxit,
+               // 5 device timeout (a matrix copy never completed)
   int iter;    // completed iterations
   int maxit;
   int fixed;
+  int err;     // set by the matrix-vector product when a copy never completed
 };
 
 // scal layout: 0 rz, 1 pq, 2 alpha, 3 rr, 4 rz_new, 5 beta, 6 |L|^2, 7 rtol
 
-// q = W p in double-float (W and p as float pairs): the matrix stream is the
-// only HBM traffic, so the product runs at memory speed on the FP32 pipe.
-// 16 rows per block (2 per warp); p is staged through shared memory in
-// column chunks; each lane keeps 4 independent loads in flight per row.
-// Partial sums of p.q per block.
-#define GEMV_ROWS 16
-#define GEMV_CHUNK 4096
-__global__ void __launch_bounds__(256) gemv_kernel(const float2* __restrict__ W, int64_t N,
-                                                   const float2* __restrict__ pf,
-                                                   const double* __restrict__ p,
-                                                   double* __restrict__ q,
-                                                   double* __restrict__ part,
-                                                   const PcgState* __restrict__ st) {
-  if (st->done) return;
-  __shared__ float2 sp[GEMV_CHUNK];
-  __shared__ double s_part[GEMV_ROWS];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t row0 = (int64_t)blockIdx.x * GEMV_ROWS + 2 * wid;
-  float h[2] = {0.f, 0.f}, l[2] = {0.f, 0.f};
-  for (int64_t c0 = 0; c0 < N; c0 += GEMV_CHUNK) {
-    const int len = (int)((N - c0) < GEMV_CHUNK ? (N - c0) : GEMV_CHUNK);
-    __syncthreads();
-    for (int j = threadIdx.x; j < len; j += 256) sp[j] = pf[c0 + j];
-    __syncthreads();
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-      const int64_t row = row0 + rr;
-      if (row >= N) continue;
-      const float2* w = W + row * N + c0;
-      int j = lane;
-      for (; j + 96 < len; j += 128) {
-        const float2 a0 = w[j], a1 = w[j + 32], a2 = w[j + 64], a3 = w[j + 96];
-        df_fma_acc(a0.x, a0.y, sp[j].x, sp[j].y, h[rr], l[rr]);
-        df_fma_acc(a1.x, a1.y, sp[j + 32].x, sp[j + 32].y, h[rr], l[rr]);
-        df_fma_acc(a2.x, a2.y, sp[j + 64].x, sp[j + 64].y, h[rr], l[rr]);
-        df_fma_acc(a3.x, a3.y, sp[j + 96].x, sp[j + 96].y, h[rr], l[rr]);
-      }
-      for (; j < len; j += 32) {
-        const float2 a = w[j];
-        df_fma_acc(a.x, a.y, sp[j].x, sp[j].y, h[rr], l[rr]);
-      }
-    }
-  }
-#pragma unroll
-  for (int rr = 0; rr < 2; ++rr) {
-    float acch = h[rr], accl = l[rr];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      float oh = __shfl_xor_sync(0xffffffffu, acch, off);
-      float ol = __shfl_xor_sync(0xffffffffu, accl, off);
-      float sh, se;
-      two_sum(acch, oh, sh, se);
-      acch = sh;
-      accl = accl + ol + se;
-    }
-    const int64_t row = row0 + rr;
-    double pq = 0.0;
-    if (row < N) {
-      const double acc = df_to_double(acch, accl);
-      if (lane == 0) q[row] = acc;
-      pq = acc * p[row];
-    }
-    if (lane == 0) s_part[2 * wid + rr] = pq;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < GEMV_ROWS; ++k) s += s_part[k];
-    part[blockIdx.x] = s;
-  }
-}
+// q = W p: matvec.cu (TMA-fed, double-float on the FP32 pipe, 8 bytes of W
+// per entry from HBM), with per-block partial sums of p.q.
 
 // fixed-order final reduction of n partial sums into *out
 __global__ void reduce_kernel(const double* __restrict__ part, int64_t n, double* __restrict__ out,
@@ -181,7 +114,8 @@ __global__ void check_kernel(const double* scal, PcgState* st, double* hist) {
   const int it = st->iter + 1;
   st->iter = it;
   hist[it] = rel;
-  if (!isfinite(rel)) st->done = 2;
+  if (st->err) st->done = 5;
+  else if (!isfinite(rel)) st->done = 2;
   else if (!st->fixed && rel <= scal[7]) st->done = 1;
   else if (it >= st->maxit) st->done = (st->fixed || rel <= scal[7]) ? 1 : 3;
 }
@@ -299,7 +233,7 @@ __global__ void beta_kernel(double* scal, const PcgState* st, double* beta_hist)
 }
 
 // p = z + beta p (and its float-pair copy for the matrix-vector product)
-__global__ void update_p_kernel(double* __restrict__ p, float2* __restrict__ pf,
+__global__ void update_p_kernel(double* __restrict__ p, float* __restrict__ pf, int64_t ldp,
                                 const double* __restrict__ z, const double* __restrict__ scal,
                                 int64_t N, int first, const PcgState* __restrict__ st) {
   if (st->done) return;
@@ -309,7 +243,8 @@ __global__ void update_p_kernel(double* __restrict__ p, float2* __restrict__ pf,
     p[i] = v;
     float h, l;
     split_df(v, h, l);
-    pf[i] = make_float2(h, l);
+    pf[i] = h;
+    pf[ldp + i] = l;
   }
 }
 
@@ -341,6 +276,50 @@ static void apply_M(DevGeom& g, const double* r, double* z, double* t, double* u
   }
 }
 
+// one PCG iteration (all kernels guard on the device-side done flag); with a
+// null stream only the launch counter is advanced
+static void enqueue_iteration(DevGeom& g, int precondition, double* hist, int hcap, cudaStream_t s) {
+  const int64_t N = g.ndof;
+  double* x = g.d_vec;
+  double* r = x + N;
+  double* z = r + N;
+  double* p = z + N;
+  double* q = p + N;
+  double* t = q + N;
+  double* u = t + std::max<int64_t>(g.n_coarse, 1);
+  double* scal = g.d_scal;
+  PcgState* st = (PcgState*)(scal + 8);
+  double* part = scal + 16;
+  const unsigned gemv_blocks = matvec_blocks(N);
+  if (!s) {
+    g.launches += 10 + 1 + (precondition ? 1 : 0) +
+                  ((precondition && g.use_coarse && g.n_coarse > 0) ? 3 : 0);
+    return;
+  }
+  double* alpha_h = hist + hcap + 1;
+  double* beta_h = alpha_h + hcap;
+  launch_matvec(0, g.tm_W, g.tm_p, N, 1, p, q, part, &st->done, &st->err, s);
+  reduce_kernel<<<1, 256, 0, s>>>(part, gemv_blocks, scal + 1, st);
+  alpha_kernel<<<1, 1, 0, s>>>(scal, st, alpha_h);
+  update_xr_kernel<<<RED_BLOCKS, 256, 0, s>>>(x, r, p, q, scal, N, part, st);
+  reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 3, st);
+  check_kernel<<<1, 1, 0, s>>>(scal, st, hist);
+  apply_M(g, r, z, t, u, precondition, st, s);
+  dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
+  reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 4, st);
+  beta_kernel<<<1, 1, 0, s>>>(scal, st, beta_h);
+  update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, g.d_pfp, g.ldw, z, scal, N, 0, st);
+  g.launches += 10;
+}
+
+void drop_pcg_graphs(DevGeom& g) {
+  for (auto& ex : g.pcg_exec)
+    if (ex) {
+      cudaGraphExecDestroy(ex);
+      ex = nullptr;
+    }
+}
+
 cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, int fixed,
                     int precondition, double* x_out, PcgOut& out, cudaStream_t s) {
   const int64_t N = g.ndof;
@@ -355,26 +334,29 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
   double* scal = g.d_scal;    // 8 scalars
   PcgState* st = (PcgState*)(scal + 8);
   double* part = scal + 16;   // partial sums (>= max(RED_BLOCKS, N/8+1))
-  const unsigned gemv_blocks = (unsigned)((N + GEMV_ROWS - 1) / GEMV_ROWS);
   cudaError_t e;
   if (N == 0) {  // nothing to solve (no launch may have an empty grid)
     out.hist.push_back(0.0);
     out.status = MSBEM_OK;
     return cudaStreamSynchronize(s);
   }
-  double* hist = nullptr;  // [maxit+1] relres, [maxit] alpha, [maxit] beta
-  if ((e = pool_alloc((void**)&hist, sizeof(double) * (3 * (size_t)maxit + 1), g.pool, s)) != cudaSuccess)
-    return e;
-  double* alpha_h = hist + maxit + 1;
-  double* beta_h = alpha_h + maxit;
-  PcgState h_st = {0, 0, maxit, fixed};
+  // residual / alpha / beta history: the persistent per-geometry buffer (laid
+  // out for hist_cap iterations, so the captured graph can address it) when
+  // maxit fits, else a temporary one
+  const int hcap = maxit <= g.hist_cap ? g.hist_cap : maxit;
+  double* hist = g.d_hist;
+  if (maxit > g.hist_cap || !hist) {
+    if ((e = pool_alloc((void**)&hist, sizeof(double) * (3 * (size_t)hcap + 1), g.pool, s)) != cudaSuccess)
+      return e;
+  }
+  PcgState h_st = {0, 0, maxit, fixed, 0};
   cudaMemcpyAsync(st, &h_st, sizeof(PcgState), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(x, 0, sizeof(double) * N, s);
   if ((e = launch_rhs(g, gvec, r, s)) != cudaSuccess) return e;
   dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, r, N, part, st);
   reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 6, st);
   apply_M(g, r, z, t, u, precondition, st, s);
-  update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, g.d_pf, z, scal, N, 1, st);
+  update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, g.d_pfp, g.ldw, z, scal, N, 1, st);
   dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
   reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 0, st);
   cudaMemcpyAsync(scal + 7, &rtol, sizeof(double), cudaMemcpyHostToDevice, s);
@@ -386,28 +368,38 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
   if (nL2 == 0.0) {
     out.hist.push_back(0.0);
     out.status = MSBEM_OK;
-    cudaFreeAsync(hist, s);
+    if (hist != g.d_hist) cudaFreeAsync(hist, s);
     if (x_out != x) cudaMemcpyAsync(x_out, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
     return cudaStreamSynchronize(s);
   }
+  const bool graphed = hist == g.d_hist && g.cap_stream != nullptr;
+  if (graphed && !g.pcg_exec[precondition ? 1 : 0]) {
+    // capture one chunk of iterations on the private stream
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamBeginCapture(g.cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return e;
+    const int64_t before = g.launches;
+    for (int c = 0; c < PCG_CHUNK; ++c) enqueue_iteration(g, precondition, hist, hcap, g.cap_stream);
+    g.launches = before;
+    if ((e = cudaStreamEndCapture(g.cap_stream, &graph)) != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&g.pcg_exec[precondition ? 1 : 0], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+  }
   int enq = 0;
   while (enq < maxit) {
-    const int chunk = std::min(PCG_CHUNK, maxit - enq);
-    for (int c = 0; c < chunk; ++c) {
-      gemv_kernel<<<gemv_blocks, 256, 0, s>>>(g.d_W, N, g.d_pf, p, q, part, st);
-      reduce_kernel<<<1, 256, 0, s>>>(part, gemv_blocks, scal + 1, st);
-      alpha_kernel<<<1, 1, 0, s>>>(scal, st, alpha_h);
-      update_xr_kernel<<<RED_BLOCKS, 256, 0, s>>>(x, r, p, q, scal, N, part, st);
-      reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 3, st);
-      check_kernel<<<1, 1, 0, s>>>(scal, st, hist);
-      apply_M(g, r, z, t, u, precondition, st, s);
-      dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
-      reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 4, st);
-      beta_kernel<<<1, 1, 0, s>>>(scal, st, beta_h);
-      update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, g.d_pf, z, scal, N, 0, st);
-      g.launches += 10;
+    if (graphed) {
+      const int64_t before = g.launches;
+      enqueue_iteration(g, precondition, hist, hcap, nullptr);  // count only
+      const int64_t per_iter = g.launches - before;
+      g.launches = before + per_iter * PCG_CHUNK;
+      if ((e = cudaGraphLaunch(g.pcg_exec[precondition ? 1 : 0], s)) != cudaSuccess) return e;
+      enq += PCG_CHUNK;
+    } else {
+      const int chunk = std::min(PCG_CHUNK, maxit - enq);
+      for (int c = 0; c < chunk; ++c) enqueue_iteration(g, precondition, hist, hcap, s);
+      enq += chunk;
     }
-    enq += chunk;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(&h_st, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return e;
@@ -415,19 +407,20 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
     if (h_st.done) break;
   }
   const int it = h_st.iter;
-  std::vector<double> h(3 * (size_t)maxit + 1);
-  cudaMemcpyAsync(h.data(), hist, sizeof(double) * (3 * (size_t)maxit + 1), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(hist, s);
+  std::vector<double> h(3 * (size_t)hcap + 1);
+  cudaMemcpyAsync(h.data(), hist, sizeof(double) * (3 * (size_t)hcap + 1), cudaMemcpyDeviceToHost, s);
+  if (hist != g.d_hist) cudaFreeAsync(hist, s);
   if (x_out != x) cudaMemcpyAsync(x_out, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   out.iters = it;
   out.hist.assign(1, 1.0);
   for (int k = 1; k <= it; ++k) out.hist.push_back(h[k]);
-  out.alpha.assign(h.begin() + maxit + 1, h.begin() + maxit + 1 + it);
-  const int nbeta = (h_st.done == 1 && !fixed && it < maxit) || h_st.done == 3 || h_st.done == 1 ? it - 1 : it;
-  out.beta.assign(h.begin() + 2 * maxit + 1, h.begin() + 2 * maxit + 1 + std::max(0, nbeta));
+  out.alpha.assign(h.begin() + hcap + 1, h.begin() + hcap + 1 + it);
+  const int nbeta = (h_st.done == 1 || h_st.done == 3) ? it - 1 : it;
+  out.beta.assign(h.begin() + 2 * hcap + 1, h.begin() + 2 * hcap + 1 + std::max(0, nbeta));
   if (h_st.done == 2) out.status = MSBEM_BREAKDOWN;
   else if (h_st.done == 3) out.status = MSBEM_NOT_CONVERGED;
+  else if (h_st.done == 5) out.status = MSBEM_DEVICE_TIMEOUT;
   else out.status = MSBEM_OK;
   return cudaSuccess;
 }
