@@ -158,6 +158,19 @@ typedef struct msbem_solve_opts {
   int maxit;          /* iteration cap (default 1000)                          */
   int fixed_iters;    /* 1: run exactly maxit iterations (parity checks)       */
   int precondition;   /* 1 (default): PCG with M(H;h); 0: plain CG             */
+  int precision;      /* arithmetic of the matrix-vector products:             */
+                      /*  0 (default) double-float W (hi + lo FP32 planes,     */
+                      /*    FP64-equivalent accuracy) and double-float         */
+                      /*    preconditioner;                                    */
+                      /*  1 plain FP64: an FP64 copy of W (made on first use,  */
+                      /*    N*N*8 more bytes) and the FP64 block inverses;     */
+                      /*  2 mixed: iterative refinement whose residual is the  */
+                      /*    double-float product and whose correction equation */
+                      /*    is solved by PCG with FP32 products (hi plane of   */
+                      /*    W) to inner_rtol; iters counts inner iterations,   */
+                      /*    resid_hist holds the true relative residual after  */
+                      /*    each refinement step; fixed_iters is not allowed   */
+  double inner_rtol;  /* precision 2: inner tolerance (<= 0: default 1e-4)     */
 } msbem_solve_opts;
 
 /* Solve W Phi = L for constant Neumann data g by PCG from Phi_0 = 0

@@ -40,7 +40,11 @@ class PrecondOpts(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int),
-                ("precondition", ctypes.c_int)]
+                ("precondition", ctypes.c_int), ("precision", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
+
+
+#: arithmetic of the solve's matrix-vector products (msbem_solve_opts.precision)
+PRECISION = {"df": 0, "fp64": 1, "mixed": 2}
 
 
 def lib():
@@ -251,7 +255,8 @@ class Solver:
         return self
 
     def solve_batch(self, G, rtol: float = 1e-8, maxit: int = 1000, fixed: bool = False,
-                    precondition: bool = True, out=None, raise_on_status=True):
+                    precondition: bool = True, out=None, raise_on_status=True, precision="df",
+                    inner_rtol: float = 0.0):
         """k solves sharing the matrix-vector products; G is k x 3."""
         G = np.ascontiguousarray(G, np.float64).reshape(-1, 3)
         k = G.shape[0]
@@ -260,7 +265,7 @@ class Solver:
         iters = np.zeros(k, np.int32)
         rel = np.zeros(k, np.float64)
         kap = np.zeros(k, np.float64)
-        o = SolveOpts(rtol, maxit, int(fixed), int(precondition))
+        o = SolveOpts(rtol, maxit, int(fixed), int(precondition), PRECISION[precision], inner_rtol)
         st = lib().msbem_solve_batch(self.geom, _ptr(G), k, ctypes.byref(o), _ptr(out), _ptr(iters),
                                      _ptr(rel), _ptr(kap))
         if raise_on_status:
@@ -268,18 +273,24 @@ class Solver:
         return {"density": out, "iters": iters, "relres": rel, "kappa": kap, "status": st}
 
     def solve(self, g, rtol: float = 1e-8, maxit: int = 1000, fixed: bool = False,
-              precondition: bool = True, out=None, hist_cap: int = 4096, raise_on_status=True):
+              precondition: bool = True, out=None, hist_cap: int = 4096, raise_on_status=True,
+              precision="df", inner_rtol: float = 0.0):
+        """One solve.  precision: "df" (double-float products, default), "fp64"
+        (the plain FP64 comparator) or "mixed" (FP32 inner PCG inside
+        double-float iterative refinement; hist then holds the true relative
+        residual after each refinement step and iters the inner iterations)."""
         gv = np.ascontiguousarray(g, np.float64)
         if out is None:
             out = np.empty(self.n, np.float64)
         it = ctypes.c_int()
         kap = ctypes.c_double()
-        hist = np.zeros(hist_cap, np.float64)
-        o = SolveOpts(rtol, maxit, int(fixed), int(precondition))
+        hist = np.full(hist_cap, np.nan)
+        o = SolveOpts(rtol, maxit, int(fixed), int(precondition), PRECISION[precision], inner_rtol)
         st = lib().msbem_solve(self.geom, _ptr(gv), ctypes.byref(o), _ptr(out), ctypes.byref(it),
                                _ptr(hist), hist_cap, ctypes.byref(kap))
         if raise_on_status:
             _check(self.ctx, st)
         n_it = int(it.value)
-        return {"density": out, "iters": n_it, "hist": hist[: min(hist_cap, n_it + 1)].copy(),
+        nh = int(np.argmax(np.isnan(hist))) if np.isnan(hist).any() else hist_cap
+        return {"density": out, "iters": n_it, "hist": hist[:nh].copy(),
                 "kappa": float(kap.value), "status": st}

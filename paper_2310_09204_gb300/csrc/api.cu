@@ -69,7 +69,7 @@ void free_dev(DevGeom& d, cudaStream_t s) {
   void* ptrs[] = {d.d_hist, d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
                   d.d_jptr, d.d_jtri, d.d_jvec, d.d_jvecf, d.d_jrhs, d.d_Wh, d.d_bptr, d.d_bdofs, d.d_boff,
                   d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pfp, d.d_rf, d.d_binvf,
-                  d.d_WP, d.d_vec, d.d_scal};
+                  d.d_btile, d.d_W64, d.d_WP, d.d_vec, d.d_scal};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
@@ -393,6 +393,11 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   if (e != cudaSuccess) return cuda_fail(c, e, "far constants");
   // V (nt^2 float pairs) is scratch of the assembly only: taken from the pool
   // here and returned once W is formed, so a resident geometry holds W alone
+  drop_pcg_graphs(d);
+  if (d.d_W64) {  // the FP64 copy follows W
+    cudaFreeAsync(d.d_W64, s);
+    d.d_W64 = nullptr;
+  }
   if (!d.d_V) {
     e = pool_alloc((void**)&d.d_V, sizeof(float2) * std::max<int64_t>(1, d.nt * d.nt), d.pool, s);
     if (e != cudaSuccess) {
@@ -499,7 +504,12 @@ int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts,
   int maxit = opts ? opts->maxit : 1000;
   int fixed = opts ? opts->fixed_iters : 0;
   int prec = opts ? opts->precondition : 1;
+  const int precision = opts ? opts->precision : 0;
+  const double inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-4;
   if (!(rtol >= 0.0) || maxit < 1) return fail(c, MSBEM_INVALID_ARG, "rtol >= 0 and maxit >= 1 required");
+  if (precision < 0 || precision > 2) return fail(c, MSBEM_INVALID_ARG, "precision must be 0, 1 or 2");
+  if (precision == 2 && (fixed || !(inner < 1.0)))
+    return fail(c, MSBEM_INVALID_ARG, "precision 2: no fixed_iters, inner_rtol < 1");
   if (!d.assembled) return fail(c, MSBEM_NOT_READY, "msbem_solve: not assembled");
   if (prec && !d.factored) return fail(c, MSBEM_NOT_READY, "msbem_solve: call msbem_factor first");
   cudaSetDevice(c->device);
@@ -507,7 +517,14 @@ int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts,
   const bool dev_out = is_device_ptr(density);
   PcgOut po;
   cudaEventRecord(c->ev[6], c->stream);
-  cudaError_t e = run_pcg(d, gv, rtol, maxit, fixed, prec, d.d_vec, po, c->stream);
+  cudaError_t e;
+  if (precision == 2) {
+    std::vector<PcgOut> outs;
+    e = run_ir_batch(d, gv, 1, rtol, maxit, inner, prec, d.d_vec, true, outs, nullptr, c->stream);
+    if (e == cudaSuccess) po = outs[0];
+  } else {
+    e = run_pcg(d, gv, rtol, maxit, fixed, prec, precision, d.d_vec, po, c->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "msbem_solve");
   e = cudaMemcpyAsync(density, d.d_vec, sizeof(double) * N,
                       dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
@@ -544,7 +561,12 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
   int maxit = opts ? opts->maxit : 1000;
   int fixed = opts ? opts->fixed_iters : 0;
   int prec = opts ? opts->precondition : 1;
+  const int precision = opts ? opts->precision : 0;
+  const double inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-4;
   if (!(rtol >= 0.0) || maxit < 1) return fail(c, MSBEM_INVALID_ARG, "rtol >= 0 and maxit >= 1 required");
+  if (precision < 0 || precision > 2) return fail(c, MSBEM_INVALID_ARG, "precision must be 0, 1 or 2");
+  if (precision == 2 && (fixed || !(inner < 1.0)))
+    return fail(c, MSBEM_INVALID_ARG, "precision 2: no fixed_iters, inner_rtol < 1");
   if (!d.assembled) return fail(c, MSBEM_NOT_READY, "msbem_solve_batch: not assembled");
   if (prec && !d.factored) return fail(c, MSBEM_NOT_READY, "msbem_solve_batch: call msbem_factor first");
   cudaSetDevice(c->device);
@@ -552,11 +574,24 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
   const bool dev_out = is_device_ptr(density);
   int worst = MSBEM_OK;
   cudaEventRecord(c->ev[6], c->stream);
-  for (int c0 = 0; c0 < k; c0 += 16) {
-    const int kb = std::min(16, k - c0);
+  for (int c0 = 0, kb = 0; c0 < k; c0 += kb) {
+    kb = precision == 1 ? 1 : std::min(16, k - c0);
     std::vector<PcgOut> outs;
-    cudaError_t e = run_pcg_batch(d, gvecs + 3 * c0, kb, rtol, maxit, fixed, prec,
-                                  density + (size_t)c0 * N, dev_out, outs, c->stream);
+    cudaError_t e;
+    if (precision == 1) {  // the plain comparator: one request at a time
+      outs.resize(1);
+      e = run_pcg(d, gvecs + 3 * c0, rtol, maxit, fixed, prec, 1, d.d_vec, outs[0], c->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(density + (size_t)c0 * N, d.d_vec, sizeof(double) * N,
+                            dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    } else if (precision == 2) {
+      e = run_ir_batch(d, gvecs + 3 * c0, kb, rtol, maxit, inner, prec, density + (size_t)c0 * N, dev_out,
+                       outs, nullptr, c->stream);
+    } else {
+      e = run_pcg_batch(d, gvecs + 3 * c0, kb, rtol, maxit, fixed, prec, density + (size_t)c0 * N, dev_out,
+                        outs, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "msbem_solve_batch");
     for (int j = 0; j < kb; ++j) {
       const PcgOut& o = outs[j];

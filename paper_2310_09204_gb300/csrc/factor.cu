@@ -439,6 +439,17 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
         g.d_binv, g.d_binvf, nf);
     ++g.launches;
   }
+  // 16-row tiles of the face / wire-basket blocks (block id, first row) for
+  // the multi-vector preconditioner application
+  std::vector<int32_t> tiles;
+  for (int b = 0; b < nblk; ++b)
+    for (int64_t r0 = 0; r0 < bsize[b]; r0 += 16) {
+      tiles.push_back(b);
+      tiles.push_back((int32_t)r0);
+    }
+  if (g.d_btile) { cudaFreeAsync(g.d_btile, s); g.d_btile = nullptr; }
+  g.n_btiles = (int64_t)tiles.size() / 2;
+  if ((e = upload(&g.d_btile, tiles, g.pool, s)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

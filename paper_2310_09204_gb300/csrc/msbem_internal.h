@@ -109,6 +109,7 @@ struct DevGeom {
   float* wlo() const { return d_Wh + ndof * ldw; }
   CUtensorMap tm_W;              // 16 x 128 x 2 boxes of both planes (matvec.cu)
   CUtensorMap tm_Whi;            // 16 x 128 x 1 boxes of the hi plane
+  double* d_W64 = nullptr;       // FP64 copy of W for the plain comparator (made on first use)
   // preconditioner
   int64_t n_blocks = 0;
   int64_t* d_bptr = nullptr;     // n_blocks+1
@@ -117,6 +118,8 @@ struct DevGeom {
   double* d_binv = nullptr;
   float2* d_binvf = nullptr;     // float-pair copy of the face / wire-basket inverses
   int64_t binv_size = 0;
+  int32_t* d_btile = nullptr;    // 16-row tiles of the blocks: (block, first row) pairs
+  int64_t n_btiles = 0;
   int wb_diag = 0;
   int64_t n_coarse = 0;
   int64_t* d_pptr = nullptr;     // P in CSR (by fine row)
@@ -139,7 +142,7 @@ struct DevGeom {
   // PCG iteration chunk captured as a CUDA graph (one per preconditioning mode),
   // valid until the next factorisation; captured on a private stream
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};
+  cudaGraphExec_t pcg_exec[4] = {nullptr, nullptr, nullptr, nullptr};  // [precondition + 2 plain]
   double* d_hist = nullptr;      // persistent residual / alpha / beta history
   int hist_cap = 0;              // iterations the persistent history can hold
   int64_t launches = 0;          // kernels launched by this geometry so far
@@ -186,13 +189,21 @@ struct PcgOut {
   int status = 0;
   std::vector<double> hist, alpha, beta;
 };
+// precision: 0 double-float matrix products (default), 1 the plain FP64
+// comparator (FP64 copy of W, FP64 block inverses)
 cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, int fixed,
-                    int precondition, double* x_out_dev, PcgOut& out, cudaStream_t s);
+                    int precondition, int precision, double* x_out_dev, PcgOut& out, cudaStream_t s);
+cudaError_t ensure_w64(DevGeom& g, cudaStream_t s);
 void drop_pcg_graphs(DevGeom& g);
 // k <= 16 independent right-hand sides sharing the matrix-vector products
 // (pcg_batch.cu); X_out is k x N (row c = density of g_c)
 cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, int fixed,
                           int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
                           cudaStream_t s);
+// mixed precision: FP32 inner PCG inside double-float iterative refinement
+// (pcg_batch.cu); *refinements receives the number of refinement steps
+cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, double inner_rtol,
+                         int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
+                         int* refinements, cudaStream_t s);
 
 }  // namespace msbem

@@ -161,6 +161,80 @@ __global__ void __launch_bounds__(256) block_apply_kernel(const float2* __restri
   if (lane == 0) z[d[i]] = df_to_double(acch, accl);
 }
 
+// ---- plain FP64 comparator: W and the block inverses read as FP64 -----------
+// q = W p with an FP64 copy of W (N x N), warp per row pair, FP64 FMAs
+__global__ void __launch_bounds__(256) gemv64_kernel(const double* __restrict__ W, int64_t N,
+                                                     const double* __restrict__ p,
+                                                     double* __restrict__ q,
+                                                     double* __restrict__ part,
+                                                     const PcgState* __restrict__ st) {
+  if (st->done) return;
+  __shared__ double s_part[16];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * 16 + 2 * wid;
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    const int64_t row = row0 + rr;
+    double acc = 0.0;
+    if (row < N) {
+      const double* w = W + row * N;
+      int64_t j = lane;
+      for (; j + 96 < N; j += 128) {
+        const double a0 = w[j], a1 = w[j + 32], a2 = w[j + 64], a3 = w[j + 96];
+        acc = fma(a0, p[j], acc);
+        acc = fma(a1, p[j + 32], acc);
+        acc = fma(a2, p[j + 64], acc);
+        acc = fma(a3, p[j + 96], acc);
+      }
+      for (; j < N; j += 32) acc = fma(w[j], p[j], acc);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    double pq = 0.0;
+    if (row < N) {
+      if (lane == 0) q[row] = acc;
+      pq = acc * p[row];
+    }
+    if (lane == 0) s_part[2 * wid + rr] = pq;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 16; ++k) t += s_part[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+// z[D_b[i]] = sum_j Ainv_b[i][j] r[D_b[j]] with the FP64 inverses
+__global__ void __launch_bounds__(256) block_apply64_kernel(const double* __restrict__ Ainv,
+                                                            const int64_t* __restrict__ boff,
+                                                            const int64_t* __restrict__ bptr,
+                                                            const int32_t* __restrict__ bdofs,
+                                                            int nblk, int64_t N,
+                                                            const double* __restrict__ r,
+                                                            double* __restrict__ z,
+                                                            const PcgState* __restrict__ st) {
+  if (st->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t rho = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (rho >= N) return;
+  int lo = 0, hi = nblk - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (bptr[mid] <= rho) lo = mid; else hi = mid - 1;
+  }
+  const int b = lo;
+  const int64_t n = bptr[b + 1] - bptr[b];
+  const int64_t i = rho - bptr[b];
+  const double* a = Ainv + boff[b] + i * n;
+  const int32_t* d = bdofs + bptr[b];
+  double acc = 0.0;
+  for (int64_t j = lane; j < n; j += 32) acc = fma(a[j], r[d[j]], acc);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) z[d[i]] = acc;
+}
+
 // float-pair copy of a vector
 __global__ void to_df_kernel(const double* __restrict__ x, float2* __restrict__ xf, int64_t N,
                              const PcgState* __restrict__ st) {
@@ -256,17 +330,23 @@ __global__ void copy_kernel(double* __restrict__ dst, const double* __restrict__
 }
 
 static void apply_M(DevGeom& g, const double* r, double* z, double* t, double* u, int precondition,
-                    const PcgState* st, cudaStream_t s) {
+                    bool plain, const PcgState* st, cudaStream_t s) {
   const int64_t N = g.ndof;
   if (!precondition) {
     copy_kernel<<<RED_BLOCKS, 256, 0, s>>>(z, r, N, st);
     ++g.launches;
     return;
   }
-  to_df_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, g.d_rf, N, st);
-  block_apply_kernel<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
-                                                              (int)g.n_blocks, N, g.d_rf, z, st);
-  g.launches += 2;
+  if (plain) {
+    block_apply64_kernel<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(g.d_binv, g.d_boff, g.d_bptr, g.d_bdofs,
+                                                                  (int)g.n_blocks, N, r, z, st);
+    g.launches += 1;
+  } else {
+    to_df_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, g.d_rf, N, st);
+    block_apply_kernel<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
+                                                                (int)g.n_blocks, N, g.d_rf, z, st);
+    g.launches += 2;
+  }
   const int64_t NH = g.use_coarse ? g.n_coarse : 0;
   if (NH > 0) {
     restrict_kernel<<<(unsigned)NH, 256, 0, s>>>(g.d_cptr, g.d_crow, g.d_cval, NH, r, t, st);
@@ -278,7 +358,8 @@ static void apply_M(DevGeom& g, const double* r, double* z, double* t, double* u
 
 // one PCG iteration (all kernels guard on the device-side done flag); with a
 // null stream only the launch counter is advanced
-static void enqueue_iteration(DevGeom& g, int precondition, double* hist, int hcap, cudaStream_t s) {
+static void enqueue_iteration(DevGeom& g, int precondition, bool plain, double* hist, int hcap,
+                              cudaStream_t s) {
   const int64_t N = g.ndof;
   double* x = g.d_vec;
   double* r = x + N;
@@ -292,19 +373,22 @@ static void enqueue_iteration(DevGeom& g, int precondition, double* hist, int hc
   double* part = scal + 16;
   const unsigned gemv_blocks = matvec_blocks(N);
   if (!s) {
-    g.launches += 10 + 1 + (precondition ? 1 : 0) +
+    g.launches += 10 + 1 + ((precondition && !plain) ? 1 : 0) +
                   ((precondition && g.use_coarse && g.n_coarse > 0) ? 3 : 0);
     return;
   }
   double* alpha_h = hist + hcap + 1;
   double* beta_h = alpha_h + hcap;
-  launch_matvec(0, g.tm_W, g.tm_p, N, 1, p, q, part, &st->done, &st->err, s);
-  reduce_kernel<<<1, 256, 0, s>>>(part, gemv_blocks, scal + 1, st);
+  if (plain)
+    gemv64_kernel<<<(unsigned)((N + 15) / 16), 256, 0, s>>>(g.d_W64, N, p, q, part, st);
+  else
+    launch_matvec(0, g.tm_W, g.tm_p, N, 1, p, q, part, &st->done, &st->err, s);
+  reduce_kernel<<<1, 256, 0, s>>>(part, plain ? (unsigned)((N + 15) / 16) : gemv_blocks, scal + 1, st);
   alpha_kernel<<<1, 1, 0, s>>>(scal, st, alpha_h);
   update_xr_kernel<<<RED_BLOCKS, 256, 0, s>>>(x, r, p, q, scal, N, part, st);
   reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 3, st);
   check_kernel<<<1, 1, 0, s>>>(scal, st, hist);
-  apply_M(g, r, z, t, u, precondition, st, s);
+  apply_M(g, r, z, t, u, precondition, plain, st, s);
   dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
   reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 4, st);
   beta_kernel<<<1, 1, 0, s>>>(scal, st, beta_h);
@@ -320,8 +404,17 @@ void drop_pcg_graphs(DevGeom& g) {
     }
 }
 
+cudaError_t ensure_w64(DevGeom& g, cudaStream_t s) {
+  if (g.d_W64 || g.ndof == 0) return cudaSuccess;
+  cudaError_t e = pool_alloc((void**)&g.d_W64, sizeof(double) * g.ndof * g.ndof, g.pool, s);
+  if (e != cudaSuccess) return e;
+  ++g.launches;
+  return copy_rows_to_double(g, 0, g.ndof, g.d_W64, s);
+}
+
 cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, int fixed,
-                    int precondition, double* x_out, PcgOut& out, cudaStream_t s) {
+                    int precondition, int precision, double* x_out, PcgOut& out, cudaStream_t s) {
+  const bool plain = precision == 1;
   const int64_t N = g.ndof;
   out = PcgOut();
   double* x = g.d_vec;
@@ -355,7 +448,8 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
   if ((e = launch_rhs(g, gvec, r, s)) != cudaSuccess) return e;
   dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, r, N, part, st);
   reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 6, st);
-  apply_M(g, r, z, t, u, precondition, st, s);
+  if (plain && (e = ensure_w64(g, s)) != cudaSuccess) return e;
+  apply_M(g, r, z, t, u, precondition, plain, st, s);
   update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, g.d_pfp, g.ldw, z, scal, N, 1, st);
   dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
   reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 0, st);
@@ -373,16 +467,17 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
     return cudaStreamSynchronize(s);
   }
   const bool graphed = hist == g.d_hist && g.cap_stream != nullptr;
-  if (graphed && !g.pcg_exec[precondition ? 1 : 0]) {
+  const int gi = (precondition ? 1 : 0) + (plain ? 2 : 0);
+  if (graphed && !g.pcg_exec[gi]) {
     // capture one chunk of iterations on the private stream
     cudaGraph_t graph = nullptr;
     if ((e = cudaStreamBeginCapture(g.cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return e;
     const int64_t before = g.launches;
-    for (int c = 0; c < PCG_CHUNK; ++c) enqueue_iteration(g, precondition, hist, hcap, g.cap_stream);
+    for (int c = 0; c < PCG_CHUNK; ++c) enqueue_iteration(g, precondition, plain, hist, hcap, g.cap_stream);
     g.launches = before;
     if ((e = cudaStreamEndCapture(g.cap_stream, &graph)) != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&g.pcg_exec[precondition ? 1 : 0], graph, 0);
+    e = cudaGraphInstantiate(&g.pcg_exec[gi], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return e;
   }
@@ -390,14 +485,14 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
   while (enq < maxit) {
     if (graphed) {
       const int64_t before = g.launches;
-      enqueue_iteration(g, precondition, hist, hcap, nullptr);  // count only
+      enqueue_iteration(g, precondition, plain, hist, hcap, nullptr);  // count only
       const int64_t per_iter = g.launches - before;
       g.launches = before + per_iter * PCG_CHUNK;
-      if ((e = cudaGraphLaunch(g.pcg_exec[precondition ? 1 : 0], s)) != cudaSuccess) return e;
+      if ((e = cudaGraphLaunch(g.pcg_exec[gi], s)) != cudaSuccess) return e;
       enq += PCG_CHUNK;
     } else {
       const int chunk = std::min(PCG_CHUNK, maxit - enq);
-      for (int c = 0; c < chunk; ++c) enqueue_iteration(g, precondition, hist, hcap, s);
+      for (int c = 0; c < chunk; ++c) enqueue_iteration(g, precondition, plain, hist, hcap, s);
       enq += chunk;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -154,52 +154,94 @@ __global__ void bto_df_kernel(const double* __restrict__ X, float2* __restrict__
   }
 }
 
-// Z[D_b[i]][c] = sum_j Ainv_b[i][j] R[D_b[j]][c] for all columns (warp per row)
-__global__ void __launch_bounds__(256) bblock_apply_kernel(const float2* __restrict__ Ainv,
-                                                           const int64_t* __restrict__ boff,
-                                                           const int64_t* __restrict__ bptr,
-                                                           const int32_t* __restrict__ bdofs, int nblk,
-                                                           int64_t N, const float2* __restrict__ Rf,
-                                                           double* __restrict__ Z, int kb,
-                                                           const BatchState* __restrict__ bs) {
+// Z[D_b[i]][c] = sum_j Ainv_b[i][j] R[D_b[j]][c] for all columns, in
+// double-float.  One CTA per 16-row tile of a block (two rows per warp); the
+// block's residual rows are gathered chunk by chunk (128 dofs x kb columns)
+// into shared memory, transposed and split into hi / lo planes, so each is
+// read from L2 once per tile instead of once per row; lane l takes the chunk's
+// dofs 4l .. 4l+3.
+#define BA_KC 128
+#define BA_PAD 132   // row pitch of the staged planes (keeps float4 reads aligned, staging 2-way)
+__global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restrict__ Ainv,
+                                                          const int64_t* __restrict__ boff,
+                                                          const int64_t* __restrict__ bptr,
+                                                          const int32_t* __restrict__ bdofs,
+                                                          const int32_t* __restrict__ tiles,
+                                                          const float2* __restrict__ Rf,
+                                                          double* __restrict__ Z, int kb,
+                                                          const BatchState* __restrict__ bs) {
   if (bs->all_done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t rho = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (rho >= N) return;
-  int lo = 0, hi = nblk - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (bptr[mid] <= rho) lo = mid; else hi = mid - 1;
-  }
-  const int b = lo;
+  __shared__ __align__(16) float sRh[BK * BA_PAD];
+  __shared__ __align__(16) float sRl[BK * BA_PAD];
+  const int b = tiles[2 * blockIdx.x];
+  const int64_t r0 = tiles[2 * blockIdx.x + 1];
   const int64_t n = bptr[b + 1] - bptr[b];
-  const int64_t i = rho - bptr[b];
-  const float2* a = Ainv + boff[b] + i * n;
   const int32_t* d = bdofs + bptr[b];
-  float h[BK], l[BK];
+  const float2* A = Ainv + boff[b];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t i0 = r0 + 2 * wid;
+  const bool ok0 = i0 < n, ok1 = i0 + 1 < n;
+  const float2* a0 = A + (ok0 ? i0 : 0) * n;
+  const float2* a1 = A + (ok1 ? i0 + 1 : 0) * n;
+  float h[2][BK], l[2][BK];
 #pragma unroll
-  for (int c = 0; c < BK; ++c) { h[c] = 0.f; l[c] = 0.f; }
-  for (int64_t j = lane; j < n; j += 32) {
-    const float2 x = a[j];
-    const float2* rr = Rf + (int64_t)d[j] * kb;
+  for (int r = 0; r < 2; ++r)
 #pragma unroll
-    for (int c = 0; c < BK; ++c)
-      if (c < kb) df_fma_acc(x.x, x.y, rr[c].x, rr[c].y, h[c], l[c]);
+    for (int c = 0; c < BK; ++c) { h[r][c] = 0.f; l[r][c] = 0.f; }
+  for (int64_t j0 = 0; j0 < n; j0 += BA_KC) {
+    const int len = (int)((n - j0) < BA_KC ? (n - j0) : BA_KC);
+    __syncthreads();
+    for (int e = threadIdx.x; e < BA_KC * kb; e += 256) {
+      const int jj = e / kb, c = e - jj * kb;
+      float2 v = make_float2(0.f, 0.f);
+      if (jj < len) v = Rf[(int64_t)d[j0 + jj] * kb + c];
+      sRh[c * BA_PAD + jj] = v.x;
+      sRl[c * BA_PAD + jj] = v.y;
+    }
+    __syncthreads();
+    float2 w0[4], w1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int jj = 4 * lane + q;
+      const bool in = jj < len;
+      w0[q] = (ok0 && in) ? a0[j0 + jj] : make_float2(0.f, 0.f);
+      w1[q] = (ok1 && in) ? a1[j0 + jj] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int c = 0; c < BK; ++c) {
+      if (c < kb) {
+        const float4 rh = *(const float4*)(sRh + c * BA_PAD + 4 * lane);
+        const float4 rl = *(const float4*)(sRl + c * BA_PAD + 4 * lane);
+        df_fma_acc(w0[0].x, w0[0].y, rh.x, rl.x, h[0][c], l[0][c]);
+        df_fma_acc(w1[0].x, w1[0].y, rh.x, rl.x, h[1][c], l[1][c]);
+        df_fma_acc(w0[1].x, w0[1].y, rh.y, rl.y, h[0][c], l[0][c]);
+        df_fma_acc(w1[1].x, w1[1].y, rh.y, rl.y, h[1][c], l[1][c]);
+        df_fma_acc(w0[2].x, w0[2].y, rh.z, rl.z, h[0][c], l[0][c]);
+        df_fma_acc(w1[2].x, w1[2].y, rh.z, rl.z, h[1][c], l[1][c]);
+        df_fma_acc(w0[3].x, w0[3].y, rh.w, rl.w, h[0][c], l[0][c]);
+        df_fma_acc(w1[3].x, w1[3].y, rh.w, rl.w, h[1][c], l[1][c]);
+      }
+    }
   }
 #pragma unroll
-  for (int c = 0; c < BK; ++c) {
-    if (c >= kb) break;
-    float acch = h[c], accl = l[c];
+  for (int r = 0; r < 2; ++r) {
+    const bool ok = r == 0 ? ok0 : ok1;
+    const int64_t i = i0 + r;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      float oh = __shfl_xor_sync(0xffffffffu, acch, off);
-      float ol = __shfl_xor_sync(0xffffffffu, accl, off);
-      float sh, se;
-      two_sum(acch, oh, sh, se);
-      acch = sh;
-      accl = accl + ol + se;
+    for (int c = 0; c < BK; ++c) {
+      if (c >= kb) break;
+      float acch = h[r][c], accl = l[r][c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, acch, off);
+        const float ol = __shfl_xor_sync(0xffffffffu, accl, off);
+        float sh, se;
+        two_sum(acch, oh, sh, se);
+        acch = sh;
+        accl = accl + ol + se;
+      }
+      if (ok && lane == 0) Z[(int64_t)d[i] * kb + c] = df_to_double(acch, accl);
     }
-    if (lane == 0) Z[(int64_t)d[i] * kb + c] = df_to_double(acch, accl);
   }
 }
 
@@ -342,9 +384,12 @@ static void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precond
     return;
   }
   bto_df_kernel<<<kStrideBlocks, 256, 0, s>>>(b.R, b.Rf, N * kb, b.bs);
-  bblock_apply_kernel<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
-                                                               (int)g.n_blocks, N, b.Rf, b.Z, kb, b.bs);
-  g.launches += 2;
+  if (g.n_btiles > 0) {
+    bblock_tile_kernel<<<(unsigned)g.n_btiles, 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
+                                                            g.d_btile, b.Rf, b.Z, kb, b.bs);
+    ++g.launches;
+  }
+  ++g.launches;
   const int64_t NH = g.use_coarse ? g.n_coarse : 0;
   if (NH > 0) {
     brestrict_kernel<<<(unsigned)NH, 256, 0, s>>>(g.d_cptr, g.d_crow, g.d_cval, b.R, kb, b.T, b.bs);
@@ -355,44 +400,105 @@ static void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precond
   }
 }
 
-cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, int fixed,
-                          int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
-                          cudaStream_t s) {
+// ---- small kernels of the drivers ------------------------------------------
+// out[c] = sum of the nparts partial sums of column c (fixed order)
+__global__ void bsum_kernel(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  __shared__ double sm[256];
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 256) acc += part[(int64_t)c * nparts + i];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sm[0];
+}
+
+// Rm = R with the columns flagged in skip[] set to zero
+__global__ void bmask_kernel(const double* __restrict__ R, int64_t n, int kb, const int* __restrict__ skip,
+                             double* __restrict__ Rm) {
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)gridDim.x * 256)
+    Rm[e] = skip[e % kb] ? 0.0 : R[e];
+}
+
+// X += D
+__global__ void baxpy_kernel(double* __restrict__ X, const double* __restrict__ D, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)gridDim.x * 256)
+    X[e] += D[e];
+}
+
+// float-pair planes of an N x kb block, transposed: Xf[plane][c][i]
+__global__ void bsplit_kernel(const double* __restrict__ X, float* __restrict__ Xf, int64_t ldp, int64_t N,
+                              int kb) {
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < N * kb; e += (int64_t)gridDim.x * 256) {
+    const int64_t i = e / kb;
+    const int c = (int)(e - i * kb);
+    float h, l;
+    split_df(X[e], h, l);
+    Xf[(int64_t)c * ldp + i] = h;
+    Xf[(int64_t)(kb + c) * ldp + i] = l;
+  }
+}
+
+// R = L - Q
+__global__ void bresid_kernel(const double* __restrict__ L, const double* __restrict__ Q, int64_t n,
+                              double* __restrict__ R) {
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)gridDim.x * 256)
+    R[e] = L[e] - Q[e];
+}
+
+namespace {
+// carves one pool allocation into 16-byte aligned pieces
+struct Carver {
+  char* cur;
+  template <class T>
+  T* take(size_t n) {
+    T* p = (T*)cur;
+    cur += (sizeof(T) * n + 15) / 16 * 16;
+    return p;
+  }
+};
+}  // namespace
+
+// PCG from X = 0 on the kb right-hand sides Rin (device, N x kb row-major);
+// the iterates are written to X (device, N x kb).  mv_mode 0: double-float
+// products with W; 1: FP32 products with the hi plane (inner solves of the
+// iterative refinement).  Each column's relative residual is measured against
+// its own ||Rin_c||.
+static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, int fixed, int precondition,
+                                  int mv_mode, const double* Rin, double* X, std::vector<PcgOut>& outs,
+                                  cudaStream_t s) {
   const int64_t N = g.ndof;
   outs.assign(kb, PcgOut());
-  if (kb < 1 || kb > BK) return cudaErrorInvalidValue;
-  if (N == 0) {
-    for (auto& o : outs) { o.hist.push_back(0.0); o.status = MSBEM_OK; }
-    return cudaStreamSynchronize(s);
-  }
   const int64_t NH = std::max<int64_t>(g.n_coarse, 1);
   const unsigned gemv_blocks = matvec_blocks(N);
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, BRED);
   const size_t hsz = (size_t)kb * (maxit + 1) + 2 * (size_t)kb * maxit;
-  const size_t bytes = sizeof(double) * (5 * nvec + 2 * NH * kb + nparts + 3 * kb + hsz) +
+  const size_t bytes = sizeof(double) * (4 * nvec + 2 * NH * kb + nparts + hsz) +
                        sizeof(float) * 2 * kb * g.ldw + sizeof(float2) * nvec + sizeof(ColState) * kb +
                        sizeof(BatchState) + 512;
   char* base = nullptr;
   cudaError_t e = pool_alloc((void**)&base, bytes, g.pool, s);
   if (e != cudaSuccess) return e;
+  Carver cv{base};
   BatchBuffers b;
-  char* cur = base;
-  auto take = [&](size_t n) { char* p = cur; cur += (n + 15) / 16 * 16; return p; };
-  b.X = (double*)take(sizeof(double) * nvec);
-  b.R = (double*)take(sizeof(double) * nvec);
-  b.Z = (double*)take(sizeof(double) * nvec);
-  b.P = (double*)take(sizeof(double) * nvec);
-  b.Q = (double*)take(sizeof(double) * nvec);
-  b.T = (double*)take(sizeof(double) * NH * kb);
-  b.U = (double*)take(sizeof(double) * NH * kb);
-  b.part = (double*)take(sizeof(double) * nparts);
-  b.gv = (double*)take(sizeof(double) * 3 * kb);
-  b.hist = (double*)take(sizeof(double) * hsz);
-  b.Pf = (float*)take(sizeof(float) * 2 * kb * g.ldw);
-  b.Rf = (float2*)take(sizeof(float2) * nvec);
-  b.cs = (ColState*)take(sizeof(ColState) * kb);
-  b.bs = (BatchState*)take(sizeof(BatchState));
+  b.X = X;
+  b.R = cv.take<double>(nvec);
+  b.Z = cv.take<double>(nvec);
+  b.P = cv.take<double>(nvec);
+  b.Q = cv.take<double>(nvec);
+  b.T = cv.take<double>(NH * kb);
+  b.U = cv.take<double>(NH * kb);
+  b.part = cv.take<double>(nparts);
+  b.hist = cv.take<double>(hsz);
+  b.gv = nullptr;
+  b.Pf = cv.take<float>(2 * kb * g.ldw);
+  b.Rf = cv.take<float2>(nvec);
+  b.cs = cv.take<ColState>(kb);
+  b.bs = cv.take<BatchState>(1);
   double* rel_h = b.hist;                                   // kb x (maxit+1)
   double* alpha_h = rel_h + (size_t)kb * (maxit + 1);       // kb x maxit
   double* beta_h = alpha_h + (size_t)kb * maxit;            // kb x maxit
@@ -400,16 +506,17 @@ cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, 
   for (auto& c : h_cs) c = ColState{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   BatchState h_bs{0, kb, maxit, fixed, rtol, 0};
   CUtensorMap tmP;
-  if ((e = encode_planes(&tmP, b.Pf, g.ldw, kb, kb * g.ldw, 2, kb)) != cudaSuccess) {
+  const int planes = mv_mode == 0 ? 2 : 1;
+  if ((e = encode_planes(&tmP, b.Pf, g.ldw, kb, kb * g.ldw, planes, kb)) != cudaSuccess) {
     cudaFreeAsync(base, s);
     return e;
   }
+  const CUtensorMap& tmW = mv_mode == 0 ? g.tm_W : g.tm_Whi;
   cudaMemsetAsync(b.Pf, 0, sizeof(float) * 2 * kb * g.ldw, s);
-  cudaMemcpyAsync(b.gv, gvecs, sizeof(double) * 3 * kb, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(b.cs, h_cs.data(), sizeof(ColState) * kb, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(b.bs, &h_bs, sizeof(BatchState), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(b.X, 0, sizeof(double) * nvec, s);
-  brhs_kernel<<<(unsigned)((nvec + 255) / 256), 256, 0, s>>>(g.d_jptr, g.d_jrhs, N, b.gv, kb, b.R);
+  cudaMemcpyAsync(b.R, Rin, sizeof(double) * nvec, cudaMemcpyDeviceToDevice, s);
   const dim3 rgrid(BRED, kb);
   bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.R, N, kb, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, nL2), b.bs);
@@ -417,7 +524,7 @@ cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, 
   bupdate_p_kernel<<<kStrideBlocks, 256, 0, s>>>(b.P, b.Pf, g.ldw, b.Z, N, kb, b.cs, 1, b.bs);
   bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz), b.bs);
-  g.launches += 7;
+  g.launches += 6;
   // columns with zero data are finished before the first iteration
   if ((e = cudaMemcpyAsync(h_cs.data(), b.cs, sizeof(ColState) * kb, cudaMemcpyDeviceToHost, s)) !=
       cudaSuccess)
@@ -438,7 +545,7 @@ cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, 
   while (enq < maxit && !h_bs.all_done) {
     const int chunk = std::min(4, maxit - enq);
     for (int it = 0; it < chunk; ++it) {
-      launch_matvec(0, g.tm_W, tmP, N, kb, b.P, b.Q, b.part, &b.bs->all_done, &b.bs->err, s);
+      launch_matvec(mv_mode, tmW, tmP, N, kb, b.P, b.Q, b.part, &b.bs->all_done, &b.bs->err, s);
       breduce_kernel<<<kb, 256, 0, s>>>(b.part, (int)gemv_blocks, b.cs, offsetof(ColState, pq), b.bs);
       balpha_kernel<<<1, BK, 0, s>>>(b.cs, alpha_h, maxit, b.bs);
       bupdate_xr_kernel<<<rgrid, 256, 0, s>>>(b.X, b.R, b.P, b.Q, N, kb, b.cs, b.part, b.bs);
@@ -460,20 +567,8 @@ cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, 
   std::vector<double> h(hsz);
   cudaMemcpyAsync(h.data(), b.hist, sizeof(double) * hsz, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(h_cs.data(), b.cs, sizeof(ColState) * kb, cudaMemcpyDeviceToHost, s);
-  // densities, column c of X (row-major N x kb) -> X_out[c][i]
-  std::vector<double> xh;
-  if (X_out && out_on_device) {
-    btranspose_kernel<<<(unsigned)((nvec + 255) / 256), 256, 0, s>>>(b.X, N, kb, X_out);
-    ++g.launches;
-  } else if (X_out) {
-    xh.resize(nvec);
-    cudaMemcpyAsync(xh.data(), b.X, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s);
-  }
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   cudaFreeAsync(base, s);
-  if (X_out && !out_on_device)
-    for (int c = 0; c < kb; ++c)
-      for (int64_t i = 0; i < N; ++i) X_out[(size_t)c * N + i] = xh[(size_t)i * kb + c];
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   for (int c = 0; c < kb; ++c) {
     PcgOut& o = outs[c];
     const int it = h_cs[c].iter;
@@ -492,6 +587,179 @@ cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, 
                                   : MSBEM_OK;
   }
   return cudaSuccess;
+}
+
+// densities out: column c of X (row-major N x kb) -> X_out[c][i]
+static cudaError_t copy_out(DevGeom& g, const double* X, int64_t N, int kb, double* X_out, bool on_device,
+                            cudaStream_t s) {
+  if (!X_out) return cudaSuccess;
+  const size_t nvec = (size_t)N * kb;
+  if (on_device) {
+    btranspose_kernel<<<(unsigned)((nvec + 255) / 256), 256, 0, s>>>(X, N, kb, X_out);
+    ++g.launches;
+    return cudaStreamSynchronize(s);
+  }
+  std::vector<double> xh(nvec);
+  cudaMemcpyAsync(xh.data(), X, sizeof(double) * nvec, cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  for (int c = 0; c < kb; ++c)
+    for (int64_t i = 0; i < N; ++i) X_out[(size_t)c * N + i] = xh[(size_t)i * kb + c];
+  return cudaSuccess;
+}
+
+// L (N x kb) for the data g_c
+static cudaError_t batch_rhs(DevGeom& g, const double* gvecs, int kb, double* gv_dev, double* L, cudaStream_t s) {
+  const size_t nvec = (size_t)g.ndof * kb;
+  cudaMemcpyAsync(gv_dev, gvecs, sizeof(double) * 3 * kb, cudaMemcpyHostToDevice, s);
+  brhs_kernel<<<(unsigned)((nvec + 255) / 256), 256, 0, s>>>(g.d_jptr, g.d_jrhs, g.ndof, gv_dev, kb, L);
+  ++g.launches;
+  return cudaGetLastError();
+}
+
+cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, int fixed,
+                          int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
+                          cudaStream_t s) {
+  const int64_t N = g.ndof;
+  outs.assign(kb, PcgOut());
+  if (kb < 1 || kb > BK) return cudaErrorInvalidValue;
+  if (N == 0) {
+    for (auto& o : outs) { o.hist.push_back(0.0); o.status = MSBEM_OK; }
+    return cudaStreamSynchronize(s);
+  }
+  const size_t nvec = (size_t)N * kb;
+  char* base = nullptr;
+  cudaError_t e = pool_alloc((void**)&base, sizeof(double) * (2 * nvec + 3 * kb) + 64, g.pool, s);
+  if (e != cudaSuccess) return e;
+  Carver cv{base};
+  double* L = cv.take<double>(nvec);
+  double* X = cv.take<double>(nvec);
+  double* gv = cv.take<double>(3 * kb);
+  if ((e = batch_rhs(g, gvecs, kb, gv, L, s)) == cudaSuccess)
+    e = pcg_batch_core(g, kb, rtol, maxit, fixed, precondition, 0, L, X, outs, s);
+  if (e == cudaSuccess) e = copy_out(g, X, N, kb, X_out, out_on_device, s);
+  cudaFreeAsync(base, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  return e != cudaSuccess ? e : e2;
+}
+
+// Mixed precision (iterative refinement): the correction equation W D = R is
+// solved by the PCG above with FP32 products (hi plane of W) to the relative
+// tolerance inner_rtol, X += D, and the residual R = L - W X is recomputed
+// with the double-float product, until ||R_c|| <= rtol ||L_c|| for every
+// column.  Reported per column: the inner iterations summed, the true relative
+// residual after every refinement step (hist), and the Lanczos coefficients
+// of the first inner solve.
+cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, double inner_rtol,
+                         int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
+                         int* refinements, cudaStream_t s) {
+  const int64_t N = g.ndof;
+  outs.assign(kb, PcgOut());
+  if (refinements) *refinements = 0;
+  if (kb < 1 || kb > BK) return cudaErrorInvalidValue;
+  if (N == 0) {
+    for (auto& o : outs) { o.hist.push_back(0.0); o.status = MSBEM_OK; }
+    return cudaStreamSynchronize(s);
+  }
+  const unsigned gemv_blocks = matvec_blocks(N);
+  const size_t nvec = (size_t)N * kb;
+  const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, BRED);
+  const size_t bytes = sizeof(double) * (5 * nvec + nparts + 3 * kb + 2 * kb) + sizeof(float) * 2 * kb * g.ldw +
+                       sizeof(int) * kb + sizeof(BatchState) + 256;
+  char* base = nullptr;
+  cudaError_t e = pool_alloc((void**)&base, bytes, g.pool, s);
+  if (e != cudaSuccess) return e;
+  Carver cv{base};
+  double* L = cv.take<double>(nvec);
+  double* X = cv.take<double>(nvec);
+  double* R = cv.take<double>(nvec);
+  double* D = cv.take<double>(nvec);
+  double* Q = cv.take<double>(nvec);
+  double* part = cv.take<double>(nparts);
+  double* gv = cv.take<double>(3 * kb);
+  double* nrm = cv.take<double>(2 * kb);
+  float* Xf = cv.take<float>(2 * kb * g.ldw);
+  int* skip = cv.take<int>(kb);
+  BatchState* fl = cv.take<BatchState>(1);   // all_done = 0 throughout; err from the product
+  auto finish = [&](cudaError_t err) {
+    cudaFreeAsync(base, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    return err != cudaSuccess ? err : e2;
+  };
+  CUtensorMap tmX;
+  if ((e = encode_planes(&tmX, Xf, g.ldw, kb, kb * g.ldw, 2, kb)) != cudaSuccess) return finish(e);
+  BatchState h_fl{0, kb, 0, 0, 0.0, 0};
+  cudaMemcpyAsync(fl, &h_fl, sizeof(BatchState), cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(Xf, 0, sizeof(float) * 2 * kb * g.ldw, s);
+  cudaMemsetAsync(X, 0, sizeof(double) * nvec, s);
+  if ((e = batch_rhs(g, gvecs, kb, gv, L, s)) != cudaSuccess) return finish(e);
+  cudaMemcpyAsync(R, L, sizeof(double) * nvec, cudaMemcpyDeviceToDevice, s);
+  const dim3 rgrid(BRED, kb);
+  bdot_kernel<<<rgrid, 256, 0, s>>>(L, L, N, kb, part, fl);
+  bsum_kernel<<<kb, 256, 0, s>>>(part, BRED, nrm);
+  g.launches += 2;
+  std::vector<double> h_nrm(2 * kb);
+  std::vector<int> h_skip(kb, 0), inner_total(kb, 0), st(kb, MSBEM_OK);
+  std::vector<char> conv(kb, 0);
+  const int max_outer = 12;
+  int outer = 0;
+  for (;; ++outer) {
+    bdot_kernel<<<rgrid, 256, 0, s>>>(R, R, N, kb, part, fl);
+    bsum_kernel<<<kb, 256, 0, s>>>(part, BRED, nrm + kb);
+    g.launches += 2;
+    cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * 2 * kb, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return finish(e);
+    bool all = true;
+    for (int c = 0; c < kb; ++c) {
+      const double nl = h_nrm[c];
+      const double rel = nl > 0.0 ? std::sqrt(h_nrm[kb + c] / nl) : 0.0;
+      if (!conv[c]) outs[c].hist.push_back(rel);
+      if (!conv[c] && (nl == 0.0 || rel <= rtol)) conv[c] = 1;
+      if (!std::isfinite(rel)) { conv[c] = 1; st[c] = MSBEM_BREAKDOWN; }
+      all = all && conv[c];
+    }
+    if (all) break;
+    int budget = maxit;
+    for (int c = 0; c < kb; ++c)
+      if (!conv[c]) budget = std::min(budget, maxit - inner_total[c]);
+    if (outer >= max_outer || budget < 1) {
+      for (int c = 0; c < kb; ++c)
+        if (!conv[c]) st[c] = MSBEM_NOT_CONVERGED;
+      break;
+    }
+    for (int c = 0; c < kb; ++c) h_skip[c] = conv[c];
+    cudaMemcpyAsync(skip, h_skip.data(), sizeof(int) * kb, cudaMemcpyHostToDevice, s);
+    bmask_kernel<<<kStrideBlocks, 256, 0, s>>>(R, (int64_t)nvec, kb, skip, Q);
+    ++g.launches;
+    std::vector<PcgOut> in;
+    if ((e = pcg_batch_core(g, kb, inner_rtol, budget, 0, precondition, 1, Q, D, in, s)) != cudaSuccess)
+      return finish(e);
+    for (int c = 0; c < kb; ++c) {
+      if (conv[c]) continue;
+      inner_total[c] += in[c].iters;
+      if (outer == 0) {
+        outs[c].alpha = in[c].alpha;
+        outs[c].beta = in[c].beta;
+      }
+      if (in[c].status == MSBEM_DEVICE_TIMEOUT) st[c] = MSBEM_DEVICE_TIMEOUT;
+    }
+    baxpy_kernel<<<kStrideBlocks, 256, 0, s>>>(X, D, (int64_t)nvec);
+    bsplit_kernel<<<kStrideBlocks, 256, 0, s>>>(X, Xf, g.ldw, N, kb);
+    launch_matvec(0, g.tm_W, tmX, N, kb, X, Q, part, &fl->all_done, &fl->err, s);
+    bresid_kernel<<<kStrideBlocks, 256, 0, s>>>(L, Q, (int64_t)nvec, R);
+    g.launches += 4;
+    if ((e = cudaGetLastError()) != cudaSuccess) return finish(e);
+  }
+  cudaMemcpyAsync(&h_fl, fl, sizeof(BatchState), cudaMemcpyDeviceToHost, s);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return finish(e);
+  for (int c = 0; c < kb; ++c) {
+    outs[c].iters = inner_total[c];
+    outs[c].status = h_fl.err ? MSBEM_DEVICE_TIMEOUT : st[c];
+    if (h_nrm[c] == 0.0) outs[c].hist.assign(1, 0.0);
+  }
+  if (refinements) *refinements = outer;
+  e = copy_out(g, X, N, kb, X_out, out_on_device, s);
+  return finish(e);
 }
 
 }  // namespace msbem
