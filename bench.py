@@ -39,6 +39,17 @@ FP32_OPS_PER_FAR_PAIR = 36 * 82 + 6 * 45
 # the h=1/64 book by the number of triangle pairs (x16).  Valid for the kernel
 # as captured; reset to None when the kernel changes.
 FAR_DF_TRAFFIC_BOOK64 = 16 * (1.372672e6 + 257.199872e6)
+# double-float multiply-add on the FP32 pipe (df.cuh df_fma_acc)
+FP32_OPS_PER_DF_FMA = 13
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def parse():
@@ -50,6 +61,7 @@ def parse():
     ap.add_argument("--far-kernel", type=int, default=0, help="0 double-float (default), 1 native FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-modes", action="store_true", help="skip the solve-mode comparison")
     ap.add_argument("--workload", default="book64", choices=["book64", "book32", "flat"],
                     help="book64 is the measured workload; book32 (h=1/32) and flat are for profiling")
     return ap.parse_args()
@@ -286,6 +298,14 @@ def run_ours(args, world, rank, local, pg):
     achieved = ops / far_avg_s
     kernel = "far_df_kernel (double-float on FP32 pipe)" if args.far_kernel == 0 else "far_fp64_kernel"
 
+    # solve modes on the resident geometry (W and M already built by the last
+    # step): the plain FP64 comparator request by request, the double-float
+    # path, and the batched / mixed-precision forms on the same 16 requests
+    modes = None
+    if rank == 0 and not args.no_modes:
+        modes = solve_modes(S, geom, stream)
+    roof_mv = matvec_rooflines(S, N, stream) if rank == 0 and not args.no_modes else None
+
     # end to end through the C ABI with host buffers: upload (host topology +
     # H2D from pinned memory) + assemble + factor + solve + D2H of the density
     e2e = None
@@ -352,6 +372,8 @@ def run_ours(args, world, rank, local, pg):
                                      else None),
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (FP32-pipe ops/s)",
                          "ops_per_launch": ops, "launch_ms": far_avg_s * 1e3},
+            "roofline_matvec": roof_mv,
+            "solve_modes": modes,
             "clocks": ck,
             "gpu_launches": int(launches),
             "e2e": e2e,
@@ -359,6 +381,91 @@ def run_ours(args, world, rank, local, pg):
         }
         print(json.dumps(line), flush=True)
     S.close()
+
+
+def _events(stream, f):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    out = f()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b), out
+
+
+def solve_modes(S, geom, stream, nreq=16, seed=7):
+    """Solves/s and per-request latency of the solve forms on the same nreq
+    requests (seeded Neumann data, the first one the workload's g) on the
+    resident geometry.  The plain FP64 comparator runs request by request;
+    the batched forms take all nreq requests in one call.  Every result is
+    checked against the comparator's: its true relative residual (double-float
+    product) and its relative l2 difference."""
+    rng = np.random.default_rng(seed)
+    G = rng.uniform(-1.0, 1.0, (nreq, 3))
+    G[0] = geom.g
+    for prec in ("fp64", "df", "mixed"):          # warm-up (graphs, FP64 copy of W)
+        S.solve(G[0], precision=prec)
+    S.solve_batch(G, precision="mixed")
+    S.solve_batch(G, precision="df")
+    out = {"requests": nreq, "rtol": 1e-8, "data": "g_c uniform in [-1,1]^3 (seed 7), g_0 = workload g"}
+    ref = np.empty((nreq, S.n))
+    for name, prec in (("plain_fp64", "fp64"), ("df", "df"), ("mixed", "mixed")):
+        lat, it = [], []
+        for c in range(nreq):
+            ms, r = _events(stream, lambda: S.solve(G[c], rtol=1e-8, precision=prec))
+            lat.append(ms)
+            it.append(r["iters"])
+            if prec == "fp64":
+                ref[c] = r["density"]
+            else:
+                d = np.linalg.norm(r["density"] - ref[c]) / np.linalg.norm(ref[c])
+                out.setdefault(name + "_maxdiff_vs_fp64", 0.0)
+                out[name + "_maxdiff_vs_fp64"] = max(out[name + "_maxdiff_vs_fp64"], float(d))
+        lat.sort()
+        out[name] = {"solves_per_s": 1e3 * nreq / sum(lat), "p50_ms": lat[nreq // 2], "p99_ms": lat[-1],
+                     "iters": [int(min(it)), int(max(it))], "mode": "one request per call"}
+    for name, prec in (("df_batch", "df"), ("mixed_batch", "mixed")):
+        ms, r = _events(stream, lambda: S.solve_batch(G, rtol=1e-8, precision=prec))
+        diff = max(float(np.linalg.norm(r["density"][c] - ref[c]) / np.linalg.norm(ref[c])) for c in range(nreq))
+        # true residuals with the double-float product
+        Y, _ = S.apply(r["density"])
+        L = np.stack([S.rhs(G[c]) for c in range(nreq)])
+        rel = float(max(np.linalg.norm(L[c] - Y[c]) / np.linalg.norm(L[c]) for c in range(nreq)))
+        out[name] = {"solves_per_s": 1e3 * nreq / ms, "batch_ms": ms, "iters": [int(r["iters"].min()),
+                     int(r["iters"].max())], "max_true_relres": rel, "maxdiff_vs_fp64": diff,
+                     "mode": f"{nreq} requests in one call"}
+    base = out["plain_fp64"]["solves_per_s"]
+    out["speedup_vs_plain_fp64"] = {k: out[k]["solves_per_s"] / base
+                                    for k in ("df", "mixed", "df_batch", "mixed_batch")}
+    return out
+
+
+def matvec_rooflines(S, N, stream, reps=5):
+    """Device time of the matrix-vector product kernel (msbem_apply reports the
+    kernel's own CUDA-event time) against its bound: HBM for one vector
+    (double-float: 8 bytes per entry of W, FP32: 4), the FP32 pipe for 16
+    double-float vectors (13 FP32 operations per entry and vector)."""
+    hbm, src = measured_peaks()
+    fp32_peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6
+    rng = np.random.default_rng(3)
+    out = {}
+    for name, prec, k in (("df_k1", "df", 1), ("fp32_k1", "fp32", 1), ("df_k16", "df", 16), ("fp32_k16", "fp32", 16)):
+        X = rng.standard_normal((k, N))
+        S.apply(X, precision=prec)
+        ms = sorted(S.apply(X, precision=prec)[1] for _ in range(reps))[reps // 2]
+        if name == "df_k16":
+            ops = FP32_OPS_PER_DF_FMA * 16 * float(N) * N
+            ach = ops / (ms * 1e-3)
+            out[name] = {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                         "frac": ach / fp32_peak, "launch_ms": ms, "algorithmic": "13 x 16 x N^2 FP32 ops"}
+        else:
+            b = (8 if prec == "df" else 4) * float(N) * N
+            ach = b / (ms * 1e-3) / 1e9
+            out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "launch_ms": ms, "algorithmic": f"{8 if prec == 'df' else 4} B x N^2 (W read once)",
+                         "peak_source": src}
+    return out
 
 
 def main():

@@ -199,6 +199,17 @@ int msbem_solve(msbem_geom* g, const double gvec[3], const msbem_solve_opts* opt
 int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_solve_opts* opts,
                       double* densities, int* iters, double* relres, double* kappa_est);
 
+/* Y = W X: the Galerkin matrix applied to k <= 16 vectors at once (the
+ * matrix-vector product of PCG, Sec. 2.1), e.g. for energies Phi^T W Phi.
+ *   X[k*N], Y[k*N]  row c = vector c (host or device pointers, independently)
+ *   precision       0 double-float products (FP64-equivalent), 1 the plain
+ *                   FP64 copy of W (made on first use), 2 FP32 products with
+ *                   the hi plane of W (about 1e-7 relative)
+ *   kernel_ms       device time of the product kernel(s) alone (may be NULL)
+ * Errors: INVALID_ARG (k outside 1..16, bad precision), NOT_READY (no W),
+ * DEVICE_TIMEOUT, OOM, CUDA_ERROR. */
+int msbem_apply(msbem_geom* g, const double* X, int k, int precision, double* Y, double* kernel_ms);
+
 /* Timing of the last assemble / factor / solve on this geometry, in
  * milliseconds measured with CUDA events on the context's stream:
  * t[0] far field, t[1] near field, t[2] contraction to W, t[3] factor,

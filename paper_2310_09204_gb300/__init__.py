@@ -75,6 +75,7 @@ def lib():
         "msbem_counters": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
         "msbem_spd_inverse_noalloc": ([P, i64, P, P], i32),
         "msbem_solve_batch": ([P, P, i32, ctypes.POINTER(SolveOpts), P, P, P, P], i32),
+        "msbem_apply": ([P, P, i32, i32, P, P], i32),
         "msbem_mesh_dofs": ([P, i64, P, i64, ctypes.POINTER(i64), P, P, i64, ctypes.c_char_p, i32], i32),
     }
     for name, (args, res) in sig.items():
@@ -253,6 +254,18 @@ class Solver:
         o = PrecondOpts(wire_basket, use_coarse)
         _check(self.ctx, lib().msbem_factor(self.geom, ctypes.byref(o)))
         return self
+
+    def apply(self, X, precision="df", out=None):
+        """Y = W X for up to 16 vectors (rows of X); returns (Y, kernel_ms)."""
+        prec = {"df": 0, "fp64": 1, "fp32": 2}[precision]
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, np.float64).reshape(-1, self.n)
+        k = X.shape[0]
+        if out is None:
+            out = np.empty((k, self.n), np.float64)
+        ms = ctypes.c_double()
+        _check(self.ctx, lib().msbem_apply(self.geom, _ptr(X), k, prec, _ptr(out), ctypes.byref(ms)))
+        return out, float(ms.value)
 
     def solve_batch(self, G, rtol: float = 1e-8, maxit: int = 1000, fixed: bool = False,
                     precondition: bool = True, out=None, raise_on_status=True, precision="df",

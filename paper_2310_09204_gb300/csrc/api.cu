@@ -300,8 +300,8 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   if (N > 0) {
     chk(matvec_init());
     chk(cudaMemsetAsync(d.d_pfp, 0, sizeof(float) * 2 * d.ldw, s));
-    chk(encode_planes(&d.tm_W, d.d_Wh, d.ldw, N, N * d.ldw, 2, 16));
-    chk(encode_planes(&d.tm_Whi, d.d_Wh, d.ldw, N, N * d.ldw, 1, 16));
+    chk(encode_planes(&d.tm_W, d.d_Wh, d.ldw, N, N * d.ldw, 2, matvec_rows(0)));
+    chk(encode_planes(&d.tm_Whi, d.d_Wh, d.ldw, N, N * d.ldw, 1, matvec_rows(1)));
     chk(encode_planes(&d.tm_p, d.d_pfp, d.ldw, 1, d.ldw, 2, 1));
   }
   chk(dalloc(&d.d_rf, (size_t)N, c->pool, s));
@@ -612,6 +612,21 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
     return fail(c, worst, "msbem_solve_batch: a matrix copy did not complete in time");
   if (worst == MSBEM_BREAKDOWN) return fail(c, worst, "msbem_solve_batch: PCG breakdown");
   if (worst == MSBEM_NOT_CONVERGED) return fail(c, worst, "msbem_solve_batch: maxit reached");
+  return MSBEM_OK;
+}
+
+int msbem_apply(msbem_geom* g, const double* X, int k, int precision, double* Y, double* kernel_ms) {
+  if (!g || !X || !Y || k < 1 || k > 16 || precision < 0 || precision > 2) return MSBEM_INVALID_ARG;
+  msbem_ctx* c = g->ctx;
+  if (!g->dev.assembled) return fail(c, MSBEM_NOT_READY, "msbem_apply: not assembled");
+  cudaSetDevice(c->device);
+  // precision 0 -> kernel mode 0 (double-float), 1 -> plain FP64 copy, 2 -> FP32 hi plane
+  const int mode = precision == 0 ? 0 : precision == 1 ? 2 : 1;
+  float ms = 0.f;
+  cudaError_t e = apply_w(g->dev, X, is_device_ptr(X), k, mode, Y, is_device_ptr(Y), &ms, c->stream);
+  if (e == cudaErrorTimeout) return fail(c, MSBEM_DEVICE_TIMEOUT, "msbem_apply: a matrix copy did not complete");
+  if (e != cudaSuccess) return cuda_fail(c, e, "msbem_apply");
+  if (kernel_ms) *kernel_ms = ms;
   return MSBEM_OK;
 }
 

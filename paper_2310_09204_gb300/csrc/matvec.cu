@@ -5,11 +5,13 @@
 // W is held as two FP32 planes, hi and lo (W = hi + lo to ~2^-48 relative),
 // each N x ldw with ldw a multiple of 32 and zero padding; P is held the same
 // way, transposed: planes of k x ldp floats.  A CTA owns 16 rows (two per
-// warp) and walks the columns in chunks of 128:
+// warp; 32 rows, four per warp, in FP32) and walks the columns in chunks of
+// 128:
 //
-//   * one thread issues two TMA tensor copies per chunk (a 16 x 128 x planes
-//     box of W and a k x 128 x planes box of P) into a 3-stage shared-memory
-//     ring, completed through one mbarrier per stage;
+//   * one thread issues two TMA tensor copies per chunk (a rows x 128 x planes
+//     box of W and a KB x 128 x planes box of P, KB = k rounded up to a power
+//     of two, the extra rows zero-filled by the copy) into a shared-memory
+//     ring of 2-6 stages, completed through one mbarrier per stage;
 //   * lane l handles columns 4l .. 4l+3 of the chunk (float4 reads of both
 //     tiles, free of bank conflicts) and keeps, per row and right-hand side,
 //     a running sum;
@@ -29,6 +31,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -39,7 +42,6 @@ namespace msbem {
 
 #define MV_ROWS 16
 #define MV_KC 128
-#define MV_STAGES 3
 #define MV_MAXK 16
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -100,120 +102,154 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-template <int MODE>
-struct MvLayout {
+// Compile-time shape of one instantiation: MODE, KB (columns of P, the
+// caller's k rounded up to 1, 2, 4, 8 or 16; the TMA fills the extra rows with
+// zeros), rows per warp (2 in double-float, 4 in FP32, where the accumulators
+// are single floats), and as many pipeline stages as fit in ~100 KB so that
+// two CTAs share an SM.
+template <int MODE, int KB>
+struct MvCfg {
   static constexpr int NPL = MODE == 0 ? 2 : 1;
-  static constexpr int W_FLOATS = NPL * MV_ROWS * MV_KC;   // per stage
-  static constexpr int P_FLOATS = NPL * MV_MAXK * MV_KC;   // per stage
-  static constexpr size_t BYTES = 128 + sizeof(float) * MV_STAGES * (W_FLOATS + P_FLOATS) +
-                                  sizeof(uint64_t) * MV_STAGES + sizeof(double) * 8 * MV_MAXK;
+  static constexpr int RPW = MODE == 0 ? 2 : 4;
+  static constexpr int ROWS = 8 * RPW;
+  static constexpr int W_FLOATS = NPL * ROWS * MV_KC;      // per stage
+  static constexpr int P_FLOATS = NPL * KB * MV_KC;        // per stage
+  static constexpr int STAGE_BYTES = 4 * (W_FLOATS + P_FLOATS);
+  static constexpr int S0 = (100 * 1024) / STAGE_BYTES;
+  static constexpr int STAGES = S0 > 6 ? 6 : (S0 < 2 ? 2 : S0);
+  static constexpr size_t BYTES = 128 + (size_t)STAGES * STAGE_BYTES + sizeof(uint64_t) * STAGES +
+                                  sizeof(double) * 8 * KB;
 };
 
-template <int MODE>
+template <int MODE, int KB>
 __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ CUtensorMap tmW,
                                                         const __grid_constant__ CUtensorMap tmP,
-                                                        int N, int nchunks, int kb,
+                                                        int N, int nchunks_all, int cps, int kb,
                                                         const double* __restrict__ P,
                                                         double* __restrict__ Q,
                                                         double* __restrict__ part,
+                                                        float2* __restrict__ split_part,
                                                         const int* __restrict__ stop,
                                                         int* __restrict__ err) {
   if (*stop) return;
-  using L = MvLayout<MODE>;
+  using C = MvCfg<MODE, KB>;
+  // column split blockIdx.y covers chunks [chunk0, chunk0 + nchunks)
+  const int chunk0 = blockIdx.y * cps;
+  const int nchunks = min(nchunks_all - chunk0, cps);
+  constexpr int ST = C::STAGES, RPW = C::RPW;
   extern __shared__ unsigned char mv_raw[];
   float* sw = (float*)(((uintptr_t)mv_raw + 127) & ~(uintptr_t)127);
-  float* sp = sw + MV_STAGES * L::W_FLOATS;
-  uint64_t* bar = (uint64_t*)(sp + MV_STAGES * L::P_FLOATS);
-  double* spart = (double*)(bar + MV_STAGES);
+  float* sp = sw + ST * C::W_FLOATS;
+  uint64_t* bar = (uint64_t*)(sp + ST * C::P_FLOATS);
+  double* spart = (double*)(bar + ST);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int row0 = blockIdx.x * MV_ROWS;
-  const uint32_t tx_bytes = (uint32_t)(sizeof(float) * L::NPL * MV_KC * (MV_ROWS + kb));
+  const int row0 = blockIdx.x * C::ROWS;
+  const uint32_t tx_bytes = (uint32_t)C::STAGE_BYTES;
   if (tid == 0) {
-    for (int s = 0; s < MV_STAGES; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < ST; ++s) mbar_init(&bar[s], 1);
     mbar_fence_init();
   }
   __syncthreads();
   auto issue = [&](int stage, int chunk) {
     mbar_expect_tx(&bar[stage], tx_bytes);
-    tma_load_3d(sw + stage * L::W_FLOATS, &tmW, chunk * MV_KC, row0, 0, &bar[stage]);
-    tma_load_3d(sp + stage * L::P_FLOATS, &tmP, chunk * MV_KC, 0, 0, &bar[stage]);
+    tma_load_3d(sw + stage * C::W_FLOATS, &tmW, (chunk0 + chunk) * MV_KC, row0, 0, &bar[stage]);
+    tma_load_3d(sp + stage * C::P_FLOATS, &tmP, (chunk0 + chunk) * MV_KC, 0, 0, &bar[stage]);
   };
   if (tid == 0)
-    for (int s = 0; s < MV_STAGES && s < nchunks; ++s) issue(s, s);
+    for (int s = 0; s < ST && s < nchunks; ++s) issue(s, s);
 
-  float h[2][MV_MAXK], l[2][MV_MAXK];
+  float h[RPW][KB], l[MODE == 0 ? RPW : 1][KB];
 #pragma unroll
-  for (int r = 0; r < 2; ++r)
+  for (int r = 0; r < RPW; ++r)
 #pragma unroll
-    for (int c = 0; c < MV_MAXK; ++c) { h[r][c] = 0.f; l[r][c] = 0.f; }
+    for (int c = 0; c < KB; ++c) h[r][c] = 0.f;
+#pragma unroll
+  for (int r = 0; r < (MODE == 0 ? RPW : 1); ++r)
+#pragma unroll
+    for (int c = 0; c < KB; ++c) l[r][c] = 0.f;
 
   int failed_at = -1;
   for (int t = 0; t < nchunks; ++t) {
-    const int s = t % MV_STAGES;
-    const bool got = mbar_wait_bounded(&bar[s], (uint32_t)((t / MV_STAGES) & 1));
+    const int s = t % ST;
+    const bool got = mbar_wait_bounded(&bar[s], (uint32_t)((t / ST) & 1));
     // every thread has finished chunk t-1 once past this barrier
     if (__syncthreads_or(!got)) { failed_at = t; break; }
-    if (tid == 0 && t >= 1 && t - 1 + MV_STAGES < nchunks)
-      issue((t - 1) % MV_STAGES, t - 1 + MV_STAGES);
-    const float* ws = sw + s * L::W_FLOATS;
-    const float* ps = sp + s * L::P_FLOATS;
-    const float4 wh0 = *(const float4*)(ws + (2 * wid) * MV_KC + 4 * lane);
-    const float4 wh1 = *(const float4*)(ws + (2 * wid + 1) * MV_KC + 4 * lane);
-    if (MODE == 0) {
-      const float4 wl0 = *(const float4*)(ws + (MV_ROWS + 2 * wid) * MV_KC + 4 * lane);
-      const float4 wl1 = *(const float4*)(ws + (MV_ROWS + 2 * wid + 1) * MV_KC + 4 * lane);
+    if (tid == 0 && t >= 1 && t - 1 + ST < nchunks) issue((t - 1) % ST, t - 1 + ST);
+    const float* ws = sw + s * C::W_FLOATS;
+    const float* ps = sp + s * C::P_FLOATS;
+    float4 wh[RPW];
 #pragma unroll
-      for (int c = 0; c < MV_MAXK; ++c) {
-        if (c < kb) {
-          const float4 ph = *(const float4*)(ps + c * MV_KC + 4 * lane);
-          const float4 pl = *(const float4*)(ps + (kb + c) * MV_KC + 4 * lane);
-          df_fma_acc(wh0.x, wl0.x, ph.x, pl.x, h[0][c], l[0][c]);
-          df_fma_acc(wh1.x, wl1.x, ph.x, pl.x, h[1][c], l[1][c]);
-          df_fma_acc(wh0.y, wl0.y, ph.y, pl.y, h[0][c], l[0][c]);
-          df_fma_acc(wh1.y, wl1.y, ph.y, pl.y, h[1][c], l[1][c]);
-          df_fma_acc(wh0.z, wl0.z, ph.z, pl.z, h[0][c], l[0][c]);
-          df_fma_acc(wh1.z, wl1.z, ph.z, pl.z, h[1][c], l[1][c]);
-          df_fma_acc(wh0.w, wl0.w, ph.w, pl.w, h[0][c], l[0][c]);
-          df_fma_acc(wh1.w, wl1.w, ph.w, pl.w, h[1][c], l[1][c]);
+    for (int r = 0; r < RPW; ++r) wh[r] = *(const float4*)(ws + (RPW * wid + r) * MV_KC + 4 * lane);
+    if (MODE == 0) {
+      float4 wl[RPW];
+#pragma unroll
+      for (int r = 0; r < RPW; ++r)
+        wl[r] = *(const float4*)(ws + (C::ROWS + RPW * wid + r) * MV_KC + 4 * lane);
+#pragma unroll
+      for (int c = 0; c < KB; ++c) {
+        const float4 ph = *(const float4*)(ps + c * MV_KC + 4 * lane);
+        const float4 pl = *(const float4*)(ps + (KB + c) * MV_KC + 4 * lane);
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) {
+          df_fma_acc(wh[r].x, wl[r].x, ph.x, pl.x, h[r][c], l[r][c]);
+          df_fma_acc(wh[r].y, wl[r].y, ph.y, pl.y, h[r][c], l[r][c]);
+          df_fma_acc(wh[r].z, wl[r].z, ph.z, pl.z, h[r][c], l[r][c]);
+          df_fma_acc(wh[r].w, wl[r].w, ph.w, pl.w, h[r][c], l[r][c]);
         }
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < MV_MAXK; ++c) {
-        if (c < kb) {
-          const float4 ph = *(const float4*)(ps + c * MV_KC + 4 * lane);
-          h[0][c] = fmaf(wh0.x, ph.x, h[0][c]);
-          h[1][c] = fmaf(wh1.x, ph.x, h[1][c]);
-          l[0][c] = fmaf(wh0.y, ph.y, l[0][c]);
-          l[1][c] = fmaf(wh1.y, ph.y, l[1][c]);
-          h[0][c] = fmaf(wh0.z, ph.z, h[0][c]);
-          h[1][c] = fmaf(wh1.z, ph.z, h[1][c]);
-          l[0][c] = fmaf(wh0.w, ph.w, l[0][c]);
-          l[1][c] = fmaf(wh1.w, ph.w, l[1][c]);
+      for (int c = 0; c < KB; ++c) {
+        const float4 ph = *(const float4*)(ps + c * MV_KC + 4 * lane);
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) {
+          float a = h[r][c];
+          a = fmaf(wh[r].x, ph.x, a);
+          a = fmaf(wh[r].y, ph.y, a);
+          a = fmaf(wh[r].z, ph.z, a);
+          a = fmaf(wh[r].w, ph.w, a);
+          h[r][c] = a;
         }
       }
     }
   }
   if (failed_at >= 0) {
-    // drain the copies still in flight (chunks failed_at .. failed_at+STAGES-2)
+    // drain the copies still in flight (chunks failed_at .. failed_at+ST-2)
     if (tid == 0) {
-      for (int u = failed_at; u < nchunks && u <= failed_at + MV_STAGES - 2; ++u)
-        mbar_wait_bounded(&bar[u % MV_STAGES], (uint32_t)((u / MV_STAGES) & 1));
+      for (int u = failed_at; u < nchunks && u <= failed_at + ST - 2; ++u)
+        mbar_wait_bounded(&bar[u % ST], (uint32_t)((u / ST) & 1));
       atomicExch(err, 1);
     }
     return;
   }
 
-  double pq[MV_MAXK];
+  double pq[KB];
 #pragma unroll
-  for (int c = 0; c < MV_MAXK; ++c) pq[c] = 0.0;
+  for (int c = 0; c < KB; ++c) pq[c] = 0.0;
+  const bool split = gridDim.y > 1;
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int row = row0 + 2 * wid + r;
+  for (int r = 0; r < RPW; ++r) {
+    const int row = row0 + RPW * wid + r;
 #pragma unroll
-    for (int c = 0; c < MV_MAXK; ++c) {
-      if (c >= kb) break;
+    for (int c = 0; c < KB; ++c) {
       double q;
+      if (split) {
+        // this split's warp-reduced partial sum; matvec_combine_kernel adds them
+        float acch = h[r][c], accl = 0.f;
+        if constexpr (MODE == 0) accl = l[r][c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, acch, off);
+          const float ol = __shfl_xor_sync(0xffffffffu, accl, off);
+          float sh, se;
+          two_sum(acch, oh, sh, se);
+          acch = sh;
+          accl = accl + ol + se;
+        }
+        if (row < N && c < kb && lane == 0)
+          split_part[((int64_t)blockIdx.y * N + row) * kb + c] = make_float2(acch, accl);
+        continue;
+      }
       if (MODE == 0) {
         float acch = h[r][c], accl = l[r][c];
 #pragma unroll
@@ -227,26 +263,63 @@ __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ 
         }
         q = df_to_double(acch, accl);
       } else {
-        float acc = h[r][c] + l[r][c];
+        float acc = h[r][c];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         q = (double)acc;
       }
-      if (row < N) {
+      if (row < N && c < kb) {
         if (lane == 0) Q[(int64_t)row * kb + c] = q;
         pq[c] = fma(q, P[(int64_t)row * kb + c], pq[c]);
       }
     }
   }
+  if (split) return;
   if (lane == 0)
 #pragma unroll
-    for (int c = 0; c < MV_MAXK; ++c)
-      if (c < kb) spart[wid * MV_MAXK + c] = pq[c];
+    for (int c = 0; c < KB; ++c) spart[wid * KB + c] = pq[c];
   __syncthreads();
   if (tid < kb) {
     double sum = 0.0;
-    for (int w = 0; w < 8; ++w) sum += spart[w * MV_MAXK + tid];
+    for (int w = 0; w < 8; ++w) sum += spart[w * KB + tid];
     part[(int64_t)tid * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+// Sum of the column splits' partials in split order (double-float), Q and the
+// per-block partial sums of p_c . q_c with the same block layout as the
+// unsplit kernel (rows blocks of `rows`).
+__global__ void __launch_bounds__(256) matvec_combine_kernel(const float2* __restrict__ split_part, int S, int N,
+                                                             int kb, int rows, const double* __restrict__ P,
+                                                             double* __restrict__ Q, double* __restrict__ part,
+                                                             const int* __restrict__ stop) {
+  if (*stop) return;
+  __shared__ double sq[32 * MV_MAXK];
+  const int64_t row0 = (int64_t)blockIdx.x * rows;
+  for (int e = threadIdx.x; e < rows * kb; e += 256) {
+    const int r = e / kb, c = e - r * kb;
+    const int64_t row = row0 + r;
+    double pq = 0.0;
+    if (row < N) {
+      float h = 0.f, l = 0.f;
+      for (int sp = 0; sp < S; ++sp) {
+        const float2 v = split_part[((int64_t)sp * N + row) * kb + c];
+        float sh, se;
+        two_sum(h, v.x, sh, se);
+        h = sh;
+        l = l + v.y + se;
+      }
+      const double q = df_to_double(h, l);
+      Q[row * kb + c] = q;
+      pq = q * P[row * kb + c];
+    }
+    sq[e] = pq;
+  }
+  __syncthreads();
+  if (threadIdx.x < kb) {
+    double sum = 0.0;
+    for (int r = 0; r < rows; ++r) sum += sq[r * kb + threadIdx.x];
+    part[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = sum;
   }
 }
 
@@ -282,10 +355,21 @@ cudaError_t encode_planes(CUtensorMap* map, const float* base, int64_t ld, int64
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-unsigned matvec_blocks(int64_t N) { return (unsigned)((N + MV_ROWS - 1) / MV_ROWS); }
+int matvec_pad(int kb) { return kb <= 1 ? 1 : kb <= 2 ? 2 : kb <= 4 ? 4 : kb <= 8 ? 8 : 16; }
+int matvec_rows(int mode) { return mode == 0 ? MvCfg<0, 1>::ROWS : MvCfg<1, 1>::ROWS; }
+unsigned matvec_blocks(int64_t N, int mode) {
+  const int rows = matvec_rows(mode);
+  return (unsigned)((N + rows - 1) / rows);
+}
 
-// opt in to the dynamic shared memory of both modes (once per process and
-// device; called outside any stream capture)
+template <int MODE, int KB>
+static cudaError_t set_attr() {
+  return cudaFuncSetAttribute(matvec_kernel<MODE, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)MvCfg<MODE, KB>::BYTES);
+}
+
+// opt in to the dynamic shared memory of every instantiation (once per
+// process and device; called outside any stream capture)
 cudaError_t matvec_init() {
   static std::mutex mu;
   static std::vector<int> ready;
@@ -295,31 +379,70 @@ cudaError_t matvec_init() {
   std::lock_guard<std::mutex> lock(mu);
   for (int d : ready)
     if (d == dev) return cudaSuccess;
-  e = cudaFuncSetAttribute(matvec_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)MvLayout<0>::BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(matvec_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)MvLayout<1>::BYTES);
-  if (e == cudaSuccess) ready.push_back(dev);
-  return e;
+  cudaError_t r[10] = {set_attr<0, 1>(), set_attr<0, 2>(), set_attr<0, 4>(), set_attr<0, 8>(), set_attr<0, 16>(),
+                       set_attr<1, 1>(), set_attr<1, 2>(), set_attr<1, 4>(), set_attr<1, 8>(), set_attr<1, 16>()};
+  for (cudaError_t x : r)
+    if (x != cudaSuccess) return x;
+  ready.push_back(dev);
+  return cudaSuccess;
+}
+
+// Column splits for a matrix of order N: enough (row block x split) work
+// items for about four waves of two CTAs on each of the 152 SMs, at most 8,
+// and none for small matrices.  A function of N and the mode only, so a
+// vector's product never depends on how many vectors share the launch.
+int matvec_split(int64_t N, int mode) {
+  const int64_t nchunks = (N + MV_KC - 1) / MV_KC;
+  const int64_t blocks = matvec_blocks(N, mode);
+  if (nchunks < 16 || blocks >= 4 * 2 * 152) return 1;
+  int64_t S = (4 * 2 * 152 + blocks - 1) / blocks;
+  S = std::min<int64_t>(S, 8);
+  S = std::min<int64_t>(S, nchunks / 8);
+  // every split must own at least one chunk
+  while (S > 1 && (S - 1) * ((nchunks + S - 1) / S) >= nchunks) --S;
+  return (int)std::max<int64_t>(S, 1);
+}
+
+size_t matvec_scratch_bytes(int64_t N, int kb, int split) {
+  return split > 1 ? sizeof(float2) * (size_t)split * N * kb : 0;
+}
+
+template <int MODE, int KB>
+static cudaError_t launch_cfg(const CUtensorMap& tmW, const CUtensorMap& tmP, int64_t N, int kb, int split,
+                              const double* P, double* Q, double* part, float2* scratch, const int* stop,
+                              int* err, cudaStream_t s) {
+  const int nchunks = (int)((N + MV_KC - 1) / MV_KC);
+  const int cps = (nchunks + split - 1) / split;
+  const dim3 grid(matvec_blocks(N, MODE), split);
+  matvec_kernel<MODE, KB><<<grid, 256, MvCfg<MODE, KB>::BYTES, s>>>(tmW, tmP, (int)N, nchunks, cps, kb, P, Q,
+                                                                    part, scratch, stop, err);
+  if (split > 1)
+    matvec_combine_kernel<<<matvec_blocks(N, MODE), 256, 0, s>>>(scratch, split, (int)N, kb, MvCfg<MODE, KB>::ROWS,
+                                                                 P, Q, part, stop);
+  return cudaGetLastError();
 }
 
 template <int MODE>
-static cudaError_t launch_mode(const CUtensorMap& tmW, const CUtensorMap& tmP, int64_t N, int kb,
-                               const double* P, double* Q, double* part, const int* stop, int* err,
+static cudaError_t launch_mode(const CUtensorMap& tmW, const CUtensorMap& tmP, int64_t N, int kb, int split,
+                               const double* P, double* Q, double* part, float2* scr, const int* stop, int* err,
                                cudaStream_t s) {
-  const int nchunks = (int)((N + MV_KC - 1) / MV_KC);
-  matvec_kernel<MODE><<<matvec_blocks(N), 256, MvLayout<MODE>::BYTES, s>>>(tmW, tmP, (int)N, nchunks, kb,
-                                                                           P, Q, part, stop, err);
-  return cudaGetLastError();
+  switch (matvec_pad(kb)) {
+    case 1: return launch_cfg<MODE, 1>(tmW, tmP, N, kb, split, P, Q, part, scr, stop, err, s);
+    case 2: return launch_cfg<MODE, 2>(tmW, tmP, N, kb, split, P, Q, part, scr, stop, err, s);
+    case 4: return launch_cfg<MODE, 4>(tmW, tmP, N, kb, split, P, Q, part, scr, stop, err, s);
+    case 8: return launch_cfg<MODE, 8>(tmW, tmP, N, kb, split, P, Q, part, scr, stop, err, s);
+    default: return launch_cfg<MODE, 16>(tmW, tmP, N, kb, split, P, Q, part, scr, stop, err, s);
+  }
 }
 
 cudaError_t launch_matvec(int mode, const CUtensorMap& tmW, const CUtensorMap& tmP, int64_t N, int kb,
                           const double* P, double* Q, double* part, const int* stop, int* err,
-                          cudaStream_t s) {
-  if (N <= 0 || N > 0x7fffffff || kb < 1 || kb > MV_MAXK) return cudaErrorInvalidValue;
-  return mode == 0 ? launch_mode<0>(tmW, tmP, N, kb, P, Q, part, stop, err, s)
-                   : launch_mode<1>(tmW, tmP, N, kb, P, Q, part, stop, err, s);
+                          cudaStream_t s, int split, void* scratch) {
+  if (N <= 0 || N > 0x7fffffff || kb < 1 || kb > MV_MAXK || split < 1 || (split > 1 && !scratch))
+    return cudaErrorInvalidValue;
+  float2* scr = (float2*)scratch;
+  return mode == 0 ? launch_mode<0>(tmW, tmP, N, kb, split, P, Q, part, scr, stop, err, s)
+                   : launch_mode<1>(tmW, tmP, N, kb, split, P, Q, part, scr, stop, err, s);
 }
 
 }  // namespace msbem

@@ -108,7 +108,7 @@ struct DevGeom {
   float* d_Wh = nullptr;
   float* wlo() const { return d_Wh + ndof * ldw; }
   CUtensorMap tm_W;              // 16 x 128 x 2 boxes of both planes (matvec.cu)
-  CUtensorMap tm_Whi;            // 16 x 128 x 1 boxes of the hi plane
+  CUtensorMap tm_Whi;            // 32 x 128 x 1 boxes of the hi plane
   double* d_W64 = nullptr;       // FP64 copy of W for the plain comparator (made on first use)
   // preconditioner
   int64_t n_blocks = 0;
@@ -165,15 +165,21 @@ cudaError_t set_far_df_constants(const double w[6]);
 // Q = W P for kb <= 16 vectors (matvec.cu): mode 0 double-float on both W
 // planes (tmW over both), mode 1 FP32 on the hi plane (tmW over one plane);
 // tmP boxes are 128 x kb x planes.  Partial sums of p_c . q_c go to
-// part[c * matvec_blocks(N) + block].  The kernel returns at once when *stop
+// part[c * matvec_blocks(N, mode) + block].  The kernel returns at once when *stop
 // is non-zero and sets *err when a copy never completes.
 cudaError_t encode_planes(CUtensorMap* map, const float* base, int64_t ld, int64_t rows,
                           int64_t plane_stride, int nplanes, int box_rows);
-unsigned matvec_blocks(int64_t N);
+unsigned matvec_blocks(int64_t N, int mode);
+int matvec_pad(int kb);      // box rows of tmP for kb vectors (1, 2, 4, 8 or 16)
+int matvec_rows(int mode);   // box rows of tmW (16 double-float, 32 FP32)
 cudaError_t matvec_init();   // per device, before the first launch_matvec
+// split > 1 divides the columns among split CTAs per row block (scratch of
+// matvec_scratch_bytes; a second kernel adds the partials in split order).
 cudaError_t launch_matvec(int mode, const CUtensorMap& tmW, const CUtensorMap& tmP, int64_t N, int kb,
                           const double* P, double* Q, double* part, const int* stop, int* err,
-                          cudaStream_t s);
+                          cudaStream_t s, int split = 1, void* scratch = nullptr);
+int matvec_split(int64_t N, int mode);
+size_t matvec_scratch_bytes(int64_t N, int kb, int split);
 
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag,
                           cudaStream_t s, int* not_spd);
@@ -194,6 +200,11 @@ struct PcgOut {
 cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, int fixed,
                     int precondition, int precision, double* x_out_dev, PcgOut& out, cudaStream_t s);
 cudaError_t ensure_w64(DevGeom& g, cudaStream_t s);
+void launch_gemv64(const DevGeom& g, const double* p, double* q, double* part, const int* stop, cudaStream_t s);
+// Y = W X for kb <= 16 vectors (pcg_batch.cu); mode 0 double-float, 1 FP32 hi
+// plane, 2 plain FP64
+cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mode, double* Y_out, bool out_dev,
+                    float* kernel_ms, cudaStream_t s);
 void drop_pcg_graphs(DevGeom& g);
 // k <= 16 independent right-hand sides sharing the matrix-vector products
 // (pcg_batch.cu); X_out is k x N (row c = density of g_c)

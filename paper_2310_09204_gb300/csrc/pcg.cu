@@ -371,7 +371,7 @@ static void enqueue_iteration(DevGeom& g, int precondition, bool plain, double* 
   double* scal = g.d_scal;
   PcgState* st = (PcgState*)(scal + 8);
   double* part = scal + 16;
-  const unsigned gemv_blocks = matvec_blocks(N);
+  const unsigned gemv_blocks = matvec_blocks(N, 0);
   if (!s) {
     g.launches += 10 + 1 + ((precondition && !plain) ? 1 : 0) +
                   ((precondition && g.use_coarse && g.n_coarse > 0) ? 3 : 0);
@@ -402,6 +402,12 @@ void drop_pcg_graphs(DevGeom& g) {
       cudaGraphExecDestroy(ex);
       ex = nullptr;
     }
+}
+
+// q = W p with the FP64 copy of W (the comparator's product); stop as in PcgState.done
+void launch_gemv64(const DevGeom& g, const double* p, double* q, double* part, const int* stop, cudaStream_t s) {
+  gemv64_kernel<<<(unsigned)((g.ndof + 15) / 16), 256, 0, s>>>(g.d_W64, g.ndof, p, q, part,
+                                                                (const PcgState*)stop);
 }
 
 cudaError_t ensure_w64(DevGeom& g, cudaStream_t s) {

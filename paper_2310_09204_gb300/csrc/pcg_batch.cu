@@ -159,9 +159,11 @@ __global__ void bto_df_kernel(const double* __restrict__ X, float2* __restrict__
 // block's residual rows are gathered chunk by chunk (128 dofs x kb columns)
 // into shared memory, transposed and split into hi / lo planes, so each is
 // read from L2 once per tile instead of once per row; lane l takes the chunk's
-// dofs 4l .. 4l+3.
+// dofs 4l .. 4l+3.  F32: the hi parts of the inverses and of the residual
+// only, plain FP32 accumulation (inner solves of the iterative refinement).
 #define BA_KC 128
 #define BA_PAD 132   // row pitch of the staged planes (keeps float4 reads aligned, staging 2-way)
+template <bool F32>
 __global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restrict__ Ainv,
                                                           const int64_t* __restrict__ boff,
                                                           const int64_t* __restrict__ bptr,
@@ -207,19 +209,36 @@ __global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restri
       w0[q] = (ok0 && in) ? a0[j0 + jj] : make_float2(0.f, 0.f);
       w1[q] = (ok1 && in) ? a1[j0 + jj] : make_float2(0.f, 0.f);
     }
+    if (F32) {
 #pragma unroll
-    for (int c = 0; c < BK; ++c) {
-      if (c < kb) {
-        const float4 rh = *(const float4*)(sRh + c * BA_PAD + 4 * lane);
-        const float4 rl = *(const float4*)(sRl + c * BA_PAD + 4 * lane);
-        df_fma_acc(w0[0].x, w0[0].y, rh.x, rl.x, h[0][c], l[0][c]);
-        df_fma_acc(w1[0].x, w1[0].y, rh.x, rl.x, h[1][c], l[1][c]);
-        df_fma_acc(w0[1].x, w0[1].y, rh.y, rl.y, h[0][c], l[0][c]);
-        df_fma_acc(w1[1].x, w1[1].y, rh.y, rl.y, h[1][c], l[1][c]);
-        df_fma_acc(w0[2].x, w0[2].y, rh.z, rl.z, h[0][c], l[0][c]);
-        df_fma_acc(w1[2].x, w1[2].y, rh.z, rl.z, h[1][c], l[1][c]);
-        df_fma_acc(w0[3].x, w0[3].y, rh.w, rl.w, h[0][c], l[0][c]);
-        df_fma_acc(w1[3].x, w1[3].y, rh.w, rl.w, h[1][c], l[1][c]);
+      for (int c = 0; c < BK; ++c) {
+        if (c < kb) {
+          const float4 rh = *(const float4*)(sRh + c * BA_PAD + 4 * lane);
+          h[0][c] = fmaf(w0[0].x, rh.x, h[0][c]);
+          h[1][c] = fmaf(w1[0].x, rh.x, h[1][c]);
+          l[0][c] = fmaf(w0[1].x, rh.y, l[0][c]);
+          l[1][c] = fmaf(w1[1].x, rh.y, l[1][c]);
+          h[0][c] = fmaf(w0[2].x, rh.z, h[0][c]);
+          h[1][c] = fmaf(w1[2].x, rh.z, h[1][c]);
+          l[0][c] = fmaf(w0[3].x, rh.w, l[0][c]);
+          l[1][c] = fmaf(w1[3].x, rh.w, l[1][c]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < BK; ++c) {
+        if (c < kb) {
+          const float4 rh = *(const float4*)(sRh + c * BA_PAD + 4 * lane);
+          const float4 rl = *(const float4*)(sRl + c * BA_PAD + 4 * lane);
+          df_fma_acc(w0[0].x, w0[0].y, rh.x, rl.x, h[0][c], l[0][c]);
+          df_fma_acc(w1[0].x, w1[0].y, rh.x, rl.x, h[1][c], l[1][c]);
+          df_fma_acc(w0[1].x, w0[1].y, rh.y, rl.y, h[0][c], l[0][c]);
+          df_fma_acc(w1[1].x, w1[1].y, rh.y, rl.y, h[1][c], l[1][c]);
+          df_fma_acc(w0[2].x, w0[2].y, rh.z, rl.z, h[0][c], l[0][c]);
+          df_fma_acc(w1[2].x, w1[2].y, rh.z, rl.z, h[1][c], l[1][c]);
+          df_fma_acc(w0[3].x, w0[3].y, rh.w, rl.w, h[0][c], l[0][c]);
+          df_fma_acc(w1[3].x, w1[3].y, rh.w, rl.w, h[1][c], l[1][c]);
+        }
       }
     }
   }
@@ -230,6 +249,13 @@ __global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restri
 #pragma unroll
     for (int c = 0; c < BK; ++c) {
       if (c >= kb) break;
+      if (F32) {
+        float acc = h[r][c] + l[r][c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (ok && lane == 0) Z[(int64_t)d[i] * kb + c] = (double)acc;
+        continue;
+      }
       float acch = h[r][c], accl = l[r][c];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
@@ -376,7 +402,8 @@ struct BatchBuffers {
 };
 }  // namespace
 
-static void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precondition, cudaStream_t s) {
+static void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precondition, int f32,
+                          cudaStream_t s) {
   const int64_t N = g.ndof;
   if (!precondition) {
     bcopy_kernel<<<kStrideBlocks, 256, 0, s>>>(b.Z, b.R, N * kb, b.bs);
@@ -385,8 +412,12 @@ static void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precond
   }
   bto_df_kernel<<<kStrideBlocks, 256, 0, s>>>(b.R, b.Rf, N * kb, b.bs);
   if (g.n_btiles > 0) {
-    bblock_tile_kernel<<<(unsigned)g.n_btiles, 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
-                                                            g.d_btile, b.Rf, b.Z, kb, b.bs);
+    if (f32)
+      bblock_tile_kernel<true><<<(unsigned)g.n_btiles, 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
+                                                                    g.d_btile, b.Rf, b.Z, kb, b.bs);
+    else
+      bblock_tile_kernel<false><<<(unsigned)g.n_btiles, 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
+                                                                     g.d_btile, b.Rf, b.Z, kb, b.bs);
     ++g.launches;
   }
   ++g.launches;
@@ -473,13 +504,15 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   const int64_t N = g.ndof;
   outs.assign(kb, PcgOut());
   const int64_t NH = std::max<int64_t>(g.n_coarse, 1);
-  const unsigned gemv_blocks = matvec_blocks(N);
+  const unsigned gemv_blocks = matvec_blocks(N, mv_mode);
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, BRED);
   const size_t hsz = (size_t)kb * (maxit + 1) + 2 * (size_t)kb * maxit;
+  const int split = matvec_split(N, mv_mode);
+  const size_t scr_bytes = matvec_scratch_bytes(N, kb, split);
   const size_t bytes = sizeof(double) * (4 * nvec + 2 * NH * kb + nparts + hsz) +
                        sizeof(float) * 2 * kb * g.ldw + sizeof(float2) * nvec + sizeof(ColState) * kb +
-                       sizeof(BatchState) + 512;
+                       sizeof(BatchState) + scr_bytes + 512;
   char* base = nullptr;
   cudaError_t e = pool_alloc((void**)&base, bytes, g.pool, s);
   if (e != cudaSuccess) return e;
@@ -499,6 +532,7 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   b.Rf = cv.take<float2>(nvec);
   b.cs = cv.take<ColState>(kb);
   b.bs = cv.take<BatchState>(1);
+  char* scratch = cv.take<char>(scr_bytes);
   double* rel_h = b.hist;                                   // kb x (maxit+1)
   double* alpha_h = rel_h + (size_t)kb * (maxit + 1);       // kb x maxit
   double* beta_h = alpha_h + (size_t)kb * maxit;            // kb x maxit
@@ -507,7 +541,7 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   BatchState h_bs{0, kb, maxit, fixed, rtol, 0};
   CUtensorMap tmP;
   const int planes = mv_mode == 0 ? 2 : 1;
-  if ((e = encode_planes(&tmP, b.Pf, g.ldw, kb, kb * g.ldw, planes, kb)) != cudaSuccess) {
+  if ((e = encode_planes(&tmP, b.Pf, g.ldw, kb, kb * g.ldw, planes, matvec_pad(kb))) != cudaSuccess) {
     cudaFreeAsync(base, s);
     return e;
   }
@@ -520,7 +554,7 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   const dim3 rgrid(BRED, kb);
   bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.R, N, kb, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, nL2), b.bs);
-  apply_M_batch(g, b, kb, precondition, s);
+  apply_M_batch(g, b, kb, precondition, mv_mode, s);
   bupdate_p_kernel<<<kStrideBlocks, 256, 0, s>>>(b.P, b.Pf, g.ldw, b.Z, N, kb, b.cs, 1, b.bs);
   bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz), b.bs);
@@ -545,13 +579,13 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   while (enq < maxit && !h_bs.all_done) {
     const int chunk = std::min(4, maxit - enq);
     for (int it = 0; it < chunk; ++it) {
-      launch_matvec(mv_mode, tmW, tmP, N, kb, b.P, b.Q, b.part, &b.bs->all_done, &b.bs->err, s);
+      launch_matvec(mv_mode, tmW, tmP, N, kb, b.P, b.Q, b.part, &b.bs->all_done, &b.bs->err, s, split, scratch);
       breduce_kernel<<<kb, 256, 0, s>>>(b.part, (int)gemv_blocks, b.cs, offsetof(ColState, pq), b.bs);
       balpha_kernel<<<1, BK, 0, s>>>(b.cs, alpha_h, maxit, b.bs);
       bupdate_xr_kernel<<<rgrid, 256, 0, s>>>(b.X, b.R, b.P, b.Q, N, kb, b.cs, b.part, b.bs);
       breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rr), b.bs);
       bcheck_kernel<<<1, 32, 0, s>>>(b.cs, rel_h, maxit, b.bs);
-      apply_M_batch(g, b, kb, precondition, s);
+      apply_M_batch(g, b, kb, precondition, mv_mode, s);
       bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
       breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz_new), b.bs);
       bbeta_kernel<<<1, BK, 0, s>>>(b.cs, beta_h, maxit, b.bs);
@@ -661,11 +695,13 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
     for (auto& o : outs) { o.hist.push_back(0.0); o.status = MSBEM_OK; }
     return cudaStreamSynchronize(s);
   }
-  const unsigned gemv_blocks = matvec_blocks(N);
+  const unsigned gemv_blocks = matvec_blocks(N, 0);
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, BRED);
+  const int split = matvec_split(N, 0);
+  const size_t scr_bytes = matvec_scratch_bytes(N, kb, split);
   const size_t bytes = sizeof(double) * (5 * nvec + nparts + 3 * kb + 2 * kb) + sizeof(float) * 2 * kb * g.ldw +
-                       sizeof(int) * kb + sizeof(BatchState) + 256;
+                       sizeof(int) * kb + sizeof(BatchState) + scr_bytes + 256;
   char* base = nullptr;
   cudaError_t e = pool_alloc((void**)&base, bytes, g.pool, s);
   if (e != cudaSuccess) return e;
@@ -681,13 +717,14 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
   float* Xf = cv.take<float>(2 * kb * g.ldw);
   int* skip = cv.take<int>(kb);
   BatchState* fl = cv.take<BatchState>(1);   // all_done = 0 throughout; err from the product
+  char* scratch = cv.take<char>(scr_bytes);
   auto finish = [&](cudaError_t err) {
     cudaFreeAsync(base, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     return err != cudaSuccess ? err : e2;
   };
   CUtensorMap tmX;
-  if ((e = encode_planes(&tmX, Xf, g.ldw, kb, kb * g.ldw, 2, kb)) != cudaSuccess) return finish(e);
+  if ((e = encode_planes(&tmX, Xf, g.ldw, kb, kb * g.ldw, 2, matvec_pad(kb))) != cudaSuccess) return finish(e);
   BatchState h_fl{0, kb, 0, 0, 0.0, 0};
   cudaMemcpyAsync(fl, &h_fl, sizeof(BatchState), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(Xf, 0, sizeof(float) * 2 * kb * g.ldw, s);
@@ -745,7 +782,7 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
     }
     baxpy_kernel<<<kStrideBlocks, 256, 0, s>>>(X, D, (int64_t)nvec);
     bsplit_kernel<<<kStrideBlocks, 256, 0, s>>>(X, Xf, g.ldw, N, kb);
-    launch_matvec(0, g.tm_W, tmX, N, kb, X, Q, part, &fl->all_done, &fl->err, s);
+    launch_matvec(0, g.tm_W, tmX, N, kb, X, Q, part, &fl->all_done, &fl->err, s, split, scratch);
     bresid_kernel<<<kStrideBlocks, 256, 0, s>>>(L, Q, (int64_t)nvec, R);
     g.launches += 4;
     if ((e = cudaGetLastError()) != cudaSuccess) return finish(e);
@@ -760,6 +797,90 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
   if (refinements) *refinements = outer;
   e = copy_out(g, X, N, kb, X_out, out_on_device, s);
   return finish(e);
+}
+
+// X[i][c] = Xin[c][i]  (k x N  ->  N x k)
+__global__ void btranspose_in_kernel(const double* __restrict__ Xin, int64_t N, int kb, double* __restrict__ X) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * kb) return;
+  const int64_t i = e / kb;
+  const int c = (int)(e % kb);
+  X[e] = Xin[(int64_t)c * N + i];
+}
+
+// Y = W X for kb <= 16 vectors (rows of X_in, k x N, host or device); mode 0
+// double-float products, 1 FP32 products with the hi plane, 2 the plain FP64
+// copy (one vector at a time).  *kernel_ms receives the device time of the
+// product kernel(s) alone.
+cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mode, double* Y_out, bool out_dev,
+                    float* kernel_ms, cudaStream_t s) {
+  const int64_t N = g.ndof;
+  if (kb < 1 || kb > BK) return cudaErrorInvalidValue;
+  if (N == 0) return cudaSuccess;
+  cudaError_t e;
+  if (mode == 2 && (e = ensure_w64(g, s)) != cudaSuccess) return e;
+  const unsigned gemv_blocks = matvec_blocks(N, 0);
+  const size_t nvec = (size_t)N * kb;
+  const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, (unsigned)((N + 15) / 16));
+  const int split = mode == 2 ? 1 : matvec_split(N, mode);
+  const size_t scr_bytes = matvec_scratch_bytes(N, kb, split);
+  const size_t bytes = sizeof(double) * (3 * nvec + nparts) + sizeof(float) * 2 * kb * g.ldw +
+                       sizeof(BatchState) + scr_bytes + 256;
+  char* base = nullptr;
+  if ((e = pool_alloc((void**)&base, bytes, g.pool, s)) != cudaSuccess) return e;
+  Carver cv{base};
+  double* Xin = cv.take<double>(nvec);
+  double* X = cv.take<double>(nvec);
+  double* Q = cv.take<double>(nvec);
+  double* part = cv.take<double>(nparts);
+  float* Xf = cv.take<float>(2 * kb * g.ldw);
+  BatchState* fl = cv.take<BatchState>(1);
+  char* scratch = cv.take<char>(scr_bytes);
+  cudaEvent_t ev[2];
+  cudaEventCreate(&ev[0]);
+  cudaEventCreate(&ev[1]);
+  BatchState h_fl{0, kb, 0, 0, 0.0, 0};
+  cudaMemcpyAsync(fl, &h_fl, sizeof(BatchState), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(Xin, X_in, sizeof(double) * nvec, in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+  btranspose_in_kernel<<<(unsigned)((nvec + 255) / 256), 256, 0, s>>>(Xin, N, kb, X);
+  ++g.launches;
+  if (mode == 2) {
+    // plain FP64: column by column with the comparator's kernel (its layout is a
+    // contiguous vector), so the input stays k x N
+    cudaEventRecord(ev[0], s);
+    for (int c = 0; c < kb; ++c)
+      launch_gemv64(g, Xin + (size_t)c * N, Q + (size_t)c * N, part, &fl->all_done, s);
+    cudaEventRecord(ev[1], s);
+    g.launches += kb;
+    e = cudaMemcpyAsync(Y_out, Q, sizeof(double) * nvec, out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        s);
+  } else {
+    CUtensorMap tmX;
+    const int planes = mode == 0 ? 2 : 1;
+    e = encode_planes(&tmX, Xf, g.ldw, kb, kb * g.ldw, planes, matvec_pad(kb));
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(Xf, 0, sizeof(float) * 2 * kb * g.ldw, s);
+      bsplit_kernel<<<kStrideBlocks, 256, 0, s>>>(X, Xf, g.ldw, N, kb);
+      cudaEventRecord(ev[0], s);
+      e = launch_matvec(mode, mode == 0 ? g.tm_W : g.tm_Whi, tmX, N, kb, X, Q, part, &fl->all_done, &fl->err, s,
+                        split, scratch);
+      cudaEventRecord(ev[1], s);
+      g.launches += 2;
+    }
+    if (e == cudaSuccess) e = copy_out(g, Q, N, kb, Y_out, out_dev, s);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess && kernel_ms) cudaEventElapsedTime(kernel_ms, ev[0], ev[1]);
+  if (e == cudaSuccess) {
+    cudaMemcpy(&h_fl, fl, sizeof(BatchState), cudaMemcpyDeviceToHost);
+    if (h_fl.err) e = cudaErrorTimeout;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  cudaFreeAsync(base, s);
+  e2 = cudaStreamSynchronize(s);
+  return e != cudaSuccess ? e : e2;
 }
 
 }  // namespace msbem

@@ -146,3 +146,33 @@ def test_book_config_full_size_mixed():
         df = S.solve(geom.g, rtol=1e-8)
         assert abs(pl["iters"] - df["iters"]) <= 1
         assert np.linalg.norm(pl["density"] - df["density"]) <= 1e-7 * np.linalg.norm(df["density"])
+
+
+@pytest.mark.parametrize("geom", SMALL[:2], ids=lambda g: g.name)
+def test_apply_matches_oracle_W(geom):
+    """msbem_apply: Y = W X in the three product precisions against the
+    oracle's W; a vector's product does not depend on the others beside it."""
+    pb = problem(geom)
+    rng = np.random.default_rng(23)
+    X = rng.standard_normal((16, pb.ndof))
+    Yo = X @ pb.W                                   # W is symmetric
+    scale = np.abs(pb.W).max() * np.abs(X).sum(axis=1).max()
+    with M.Solver(geom) as S:
+        S.assemble()
+        for prec, tol in (("df", 1e-12), ("fp64", 1e-12), ("fp32", 1e-6)):
+            Y, ms = S.apply(X, precision=prec)
+            assert np.abs(Y - Yo).max() <= tol * scale, (prec, np.abs(Y - Yo).max() / scale)
+            assert ms > 0.0
+        Y16, _ = S.apply(X)
+        for c in (0, 5, 15):
+            Y1, _ = S.apply(X[c:c + 1])
+            assert np.array_equal(Y1[0], Y16[c])
+        import torch
+        Xd = torch.from_numpy(X[:3].copy()).cuda()
+        Yd = torch.empty_like(Xd)
+        S.apply(Xd, out=Yd)
+        torch.cuda.synchronize()
+        assert np.array_equal(Yd.cpu().numpy(), Y16[:3])
+        with pytest.raises(M.MsbemError) as e:
+            S.apply(np.zeros((17, pb.ndof)))
+        assert e.value.status == -1
