@@ -112,14 +112,63 @@ struct MvCfg {
   static constexpr int NPL = MODE == 0 ? 2 : 1;
   static constexpr int RPW = MODE == 0 ? 2 : 4;
   static constexpr int ROWS = 8 * RPW;
+  static constexpr int V = RPW * KB;                        // sums per lane
   static constexpr int W_FLOATS = NPL * ROWS * MV_KC;      // per stage
   static constexpr int P_FLOATS = NPL * KB * MV_KC;        // per stage
   static constexpr int STAGE_BYTES = 4 * (W_FLOATS + P_FLOATS);
   static constexpr int S0 = (100 * 1024) / STAGE_BYTES;
   static constexpr int STAGES = S0 > 6 ? 6 : (S0 < 2 ? 2 : S0);
   static constexpr size_t BYTES = 128 + (size_t)STAGES * STAGE_BYTES + sizeof(uint64_t) * STAGES +
-                                  sizeof(double) * 8 * KB;
+                                  sizeof(double) * 8 * V;
 };
+
+// Warp reduction of LEN sums per lane at once ("transposed" butterfly): at the
+// step of lane mask m, the lanes with that bit set keep the upper half of their
+// values and the others the lower half, each adding its partner's half, so
+// LEN values cost LEN - 1 shuffles instead of 5 LEN.  Every value is summed
+// over the same lane pairing as a plain xor butterfly, so the result of a sum
+// does not depend on how many others are reduced with it.  On return (LEN = V
+// at the start) lane L holds the sums of indices L * V/32 + j when V >= 32,
+// else index L >> log2(32/V).
+template <int LEN, int MASK, bool DF>
+__device__ __forceinline__ void warp_xreduce(float* h, float* l, int lane) {
+  if constexpr (MASK > 0) {
+    if constexpr (LEN >= 2) {
+      constexpr int HALF = LEN / 2;
+      const bool up = (lane & MASK) != 0;
+#pragma unroll
+      for (int i = 0; i < HALF; ++i) {
+        const float sh = up ? h[i] : h[HALF + i];
+        const float kh = up ? h[HALF + i] : h[i];
+        const float rh = __shfl_xor_sync(0xffffffffu, sh, MASK);
+        if constexpr (DF) {
+          const float sl = up ? l[i] : l[HALF + i];
+          const float kl = up ? l[HALF + i] : l[i];
+          const float rl = __shfl_xor_sync(0xffffffffu, sl, MASK);
+          float s, e;
+          two_sum(kh, rh, s, e);
+          h[i] = s;
+          l[i] = (kl + rl) + e;
+        } else {
+          h[i] = kh + rh;
+        }
+      }
+      warp_xreduce<HALF, MASK / 2, DF>(h, l, lane);
+    } else {
+      const float rh = __shfl_xor_sync(0xffffffffu, h[0], MASK);
+      if constexpr (DF) {
+        const float rl = __shfl_xor_sync(0xffffffffu, l[0], MASK);
+        float s, e;
+        two_sum(h[0], rh, s, e);
+        h[0] = s;
+        l[0] = (l[0] + rl) + e;
+      } else {
+        h[0] += rh;
+      }
+      warp_xreduce<1, MASK / 2, DF>(h, l, lane);
+    }
+  }
+}
 
 template <int MODE, int KB>
 __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ CUtensorMap tmW,
@@ -133,15 +182,15 @@ __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ 
                                                         int* __restrict__ err) {
   if (*stop) return;
   using C = MvCfg<MODE, KB>;
+  constexpr int ST = C::STAGES, RPW = C::RPW, V = C::V;
   // column split blockIdx.y covers chunks [chunk0, chunk0 + nchunks)
   const int chunk0 = blockIdx.y * cps;
   const int nchunks = min(nchunks_all - chunk0, cps);
-  constexpr int ST = C::STAGES, RPW = C::RPW;
   extern __shared__ unsigned char mv_raw[];
   float* sw = (float*)(((uintptr_t)mv_raw + 127) & ~(uintptr_t)127);
   float* sp = sw + ST * C::W_FLOATS;
   uint64_t* bar = (uint64_t*)(sp + ST * C::P_FLOATS);
-  double* spart = (double*)(bar + ST);
+  double* spq = (double*)(bar + ST);                        // [8 warps][V]
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int row0 = blockIdx.x * C::ROWS;
   const uint32_t tx_bytes = (uint32_t)C::STAGE_BYTES;
@@ -158,15 +207,12 @@ __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ 
   if (tid == 0)
     for (int s = 0; s < ST && s < nchunks; ++s) issue(s, s);
 
-  float h[RPW][KB], l[MODE == 0 ? RPW : 1][KB];
+  // running sums, index r * KB + c (row r of this warp, column c)
+  float h[V], l[MODE == 0 ? V : 1];
 #pragma unroll
-  for (int r = 0; r < RPW; ++r)
+  for (int i = 0; i < V; ++i) h[i] = 0.f;
 #pragma unroll
-    for (int c = 0; c < KB; ++c) h[r][c] = 0.f;
-#pragma unroll
-  for (int r = 0; r < (MODE == 0 ? RPW : 1); ++r)
-#pragma unroll
-    for (int c = 0; c < KB; ++c) l[r][c] = 0.f;
+  for (int i = 0; i < (MODE == 0 ? V : 1); ++i) l[i] = 0.f;
 
   int failed_at = -1;
   for (int t = 0; t < nchunks; ++t) {
@@ -180,7 +226,7 @@ __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ 
     float4 wh[RPW];
 #pragma unroll
     for (int r = 0; r < RPW; ++r) wh[r] = *(const float4*)(ws + (RPW * wid + r) * MV_KC + 4 * lane);
-    if (MODE == 0) {
+    if constexpr (MODE == 0) {
       float4 wl[RPW];
 #pragma unroll
       for (int r = 0; r < RPW; ++r)
@@ -191,10 +237,12 @@ __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ 
         const float4 pl = *(const float4*)(ps + (KB + c) * MV_KC + 4 * lane);
 #pragma unroll
         for (int r = 0; r < RPW; ++r) {
-          df_fma_acc(wh[r].x, wl[r].x, ph.x, pl.x, h[r][c], l[r][c]);
-          df_fma_acc(wh[r].y, wl[r].y, ph.y, pl.y, h[r][c], l[r][c]);
-          df_fma_acc(wh[r].z, wl[r].z, ph.z, pl.z, h[r][c], l[r][c]);
-          df_fma_acc(wh[r].w, wl[r].w, ph.w, pl.w, h[r][c], l[r][c]);
+          float& ah = h[r * KB + c];
+          float& al = l[r * KB + c];
+          df_fma_acc(wh[r].x, wl[r].x, ph.x, pl.x, ah, al);
+          df_fma_acc(wh[r].y, wl[r].y, ph.y, pl.y, ah, al);
+          df_fma_acc(wh[r].z, wl[r].z, ph.z, pl.z, ah, al);
+          df_fma_acc(wh[r].w, wl[r].w, ph.w, pl.w, ah, al);
         }
       }
     } else {
@@ -203,12 +251,12 @@ __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ 
         const float4 ph = *(const float4*)(ps + c * MV_KC + 4 * lane);
 #pragma unroll
         for (int r = 0; r < RPW; ++r) {
-          float a = h[r][c];
+          float a = h[r * KB + c];
           a = fmaf(wh[r].x, ph.x, a);
           a = fmaf(wh[r].y, ph.y, a);
           a = fmaf(wh[r].z, ph.z, a);
           a = fmaf(wh[r].w, ph.w, a);
-          h[r][c] = a;
+          h[r * KB + c] = a;
         }
       }
     }
@@ -223,65 +271,39 @@ __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ 
     return;
   }
 
-  double pq[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) pq[c] = 0.0;
+  warp_xreduce<V, 16, MODE == 0>(h, l, lane);
+  constexpr int F = V >= 32 ? V / 32 : 1;          // sums held per lane
+  constexpr int SH = V >= 32 ? 0 : (V == 16 ? 1 : V == 8 ? 2 : V == 4 ? 3 : V == 2 ? 4 : 5);
+  const bool writer = (lane & ((1 << SH) - 1)) == 0;
   const bool split = gridDim.y > 1;
 #pragma unroll
-  for (int r = 0; r < RPW; ++r) {
+  for (int j = 0; j < F; ++j) {
+    const int idx = V >= 32 ? lane * F + j : (lane >> SH);
+    const int r = idx / KB, c = idx - (idx / KB) * KB;
     const int row = row0 + RPW * wid + r;
-#pragma unroll
-    for (int c = 0; c < KB; ++c) {
-      double q;
-      if (split) {
-        // this split's warp-reduced partial sum; matvec_combine_kernel adds them
-        float acch = h[r][c], accl = 0.f;
-        if constexpr (MODE == 0) accl = l[r][c];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          const float oh = __shfl_xor_sync(0xffffffffu, acch, off);
-          const float ol = __shfl_xor_sync(0xffffffffu, accl, off);
-          float sh, se;
-          two_sum(acch, oh, sh, se);
-          acch = sh;
-          accl = accl + ol + se;
-        }
-        if (row < N && c < kb && lane == 0)
-          split_part[((int64_t)blockIdx.y * N + row) * kb + c] = make_float2(acch, accl);
-        continue;
+    const float sh = h[j];
+    float sl = 0.f;
+    if constexpr (MODE == 0) sl = l[j];
+    const bool valid = writer && row < N && c < kb;
+    if (split) {
+      // this split's partial sum; matvec_combine_kernel adds the splits
+      if (valid) split_part[((int64_t)blockIdx.y * N + row) * kb + c] = make_float2(sh, sl);
+    } else {
+      double pqv = 0.0;
+      if (valid) {
+        const double q = MODE == 0 ? df_to_double(sh, sl) : (double)sh;
+        Q[(int64_t)row * kb + c] = q;
+        pqv = q * P[(int64_t)row * kb + c];
       }
-      if (MODE == 0) {
-        float acch = h[r][c], accl = l[r][c];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          const float oh = __shfl_xor_sync(0xffffffffu, acch, off);
-          const float ol = __shfl_xor_sync(0xffffffffu, accl, off);
-          float sh, se;
-          two_sum(acch, oh, sh, se);
-          acch = sh;
-          accl = accl + ol + se;
-        }
-        q = df_to_double(acch, accl);
-      } else {
-        float acc = h[r][c];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        q = (double)acc;
-      }
-      if (row < N && c < kb) {
-        if (lane == 0) Q[(int64_t)row * kb + c] = q;
-        pq[c] = fma(q, P[(int64_t)row * kb + c], pq[c]);
-      }
+      if (writer) spq[wid * V + idx] = pqv;
     }
   }
   if (split) return;
-  if (lane == 0)
-#pragma unroll
-    for (int c = 0; c < KB; ++c) spart[wid * KB + c] = pq[c];
   __syncthreads();
   if (tid < kb) {
     double sum = 0.0;
-    for (int w = 0; w < 8; ++w) sum += spart[w * KB + tid];
+    for (int w = 0; w < 8; ++w)
+      for (int r = 0; r < RPW; ++r) sum += spq[w * V + r * KB + tid];
     part[(int64_t)tid * gridDim.x + blockIdx.x] = sum;
   }
 }

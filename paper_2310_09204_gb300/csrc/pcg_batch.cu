@@ -192,6 +192,15 @@ __global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restri
     for (int c = 0; c < BK; ++c) { h[r][c] = 0.f; l[r][c] = 0.f; }
   for (int64_t j0 = 0; j0 < n; j0 += BA_KC) {
     const int len = (int)((n - j0) < BA_KC ? (n - j0) : BA_KC);
+    // this chunk's inverse entries first, so their latency overlaps the staging
+    float2 w0[4], w1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int jj = 4 * lane + q;
+      const bool in = jj < len;
+      w0[q] = (ok0 && in) ? a0[j0 + jj] : make_float2(0.f, 0.f);
+      w1[q] = (ok1 && in) ? a1[j0 + jj] : make_float2(0.f, 0.f);
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < BA_KC * kb; e += 256) {
       const int jj = e / kb, c = e - jj * kb;
@@ -201,14 +210,6 @@ __global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restri
       sRl[c * BA_PAD + jj] = v.y;
     }
     __syncthreads();
-    float2 w0[4], w1[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int jj = 4 * lane + q;
-      const bool in = jj < len;
-      w0[q] = (ok0 && in) ? a0[j0 + jj] : make_float2(0.f, 0.f);
-      w1[q] = (ok1 && in) ? a1[j0 + jj] : make_float2(0.f, 0.f);
-    }
     if (F32) {
 #pragma unroll
       for (int c = 0; c < BK; ++c) {
