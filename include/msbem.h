@@ -248,6 +248,66 @@ int msbem_spd_inverse_noalloc(const double* A, int64_t n, double* Ainv, void* cu
  * Either pointer may be NULL. */
 int msbem_counters(const msbem_geom* g, int64_t* launches, int64_t* far_pairs);
 
+/* ------------------------------------------------------------------------
+ * Serving engine (no counterpart in the paper: it serves many solves of the
+ * paper's problem).  Geometries (mesh + partition) are registered under a
+ * key; solve requests (key, g) are queued, and msbem_server_progress admits
+ * geometries against an HBM budget (assembly + factorisation on first use,
+ * least-recently-used eviction of idle ones), runs a 16-slot multi-vector
+ * PCG per resident geometry on its own stream, and refills slots as requests
+ * finish (continuous batching).  A request's result does not depend on the
+ * other requests it shares a batch with (bit for bit).
+ * ------------------------------------------------------------------------ */
+typedef struct msbem_server msbem_server;
+
+typedef struct msbem_server_opts {
+  double hbm_budget_bytes;  /* admission limit for resident geometries (0: 80% of free) */
+  int precision;            /* 0 double-float PCG, 2 mixed (FP32 inner + refinement)   */
+  double rtol;              /* relative residual per request (0: 1e-8)                 */
+  double inner_rtol;        /* precision 2: inner tolerance (0: 1e-4)                  */
+  int maxit;                /* iterations per request (inner, summed; 0: 1000)         */
+  int chunk;                /* PCG iterations between scheduling points (0: 4)         */
+} msbem_server_opts;
+
+typedef struct msbem_server_stats {
+  int64_t submitted, completed, admissions, evictions;
+  double resident_bytes;
+  int resident_geometries;
+} msbem_server_stats;
+
+/* Create an engine on ctx (opts may be NULL).  Errors: INVALID_ARG, CUDA_ERROR. */
+int msbem_server_create(msbem_ctx* ctx, const msbem_server_opts* opts, msbem_server** out);
+/* Free every resident geometry and the engine. */
+int msbem_server_destroy(msbem_server* s);
+/* Register a geometry under `key` (arrays as msbem_upload; copied, nothing
+ * goes to the device yet).  Errors: INVALID_ARG (duplicate key), topology
+ * errors of msbem_upload. */
+int msbem_server_add_geometry(msbem_server* s, uint64_t key, const double* xyz, int64_t nv, const int32_t* tri,
+                              int64_t nt, const double* coarse_xyz, int64_t ncv, const int32_t* coarse_tri,
+                              int64_t nct, const int32_t* parent_coarse_tri, const int32_t* patch_of_tri);
+/* The engine's clock (seconds, monotonic) for arrival time stamps. */
+double msbem_server_now(void);
+/* Bytes the admission of a registered geometry asks of the budget (resident
+ * W, preconditioner and batch, plus the assembly's transient pair matrix);
+ * -1 for an unknown key. */
+double msbem_server_footprint(const msbem_server* s, uint64_t key);
+/* Queue a request; density (N doubles, host or device, may be NULL) receives
+ * Phi when it finishes.  t_arrival: arrival time on the engine's clock (<= 0:
+ * now); latency is measured from it.  *id identifies the request. */
+int msbem_server_submit(msbem_server* s, uint64_t key, const double gvec[3], double* density, double t_arrival,
+                        uint64_t* id);
+/* Admit, launch and harvest.  block = 0: one pass, returns at once; block = 1:
+ * until every queued request has finished.  *completed: requests finished in
+ * this call.  Returns the last admission error (OOM when a geometry never fits). */
+int msbem_server_progress(msbem_server* s, int block, int* completed);
+/* Result of a request: status (1 while pending, else a msbem status),
+ * iterations (inner iterations summed in precision 2), true relative
+ * residual, latency from arrival to the density being written, and the
+ * number of refinement steps (precision 2). */
+int msbem_server_result(msbem_server* s, uint64_t id, int* status, int* iters, double* relres, double* latency_ms,
+                        int* refinements);
+int msbem_server_stats_get(const msbem_server* s, msbem_server_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,17 @@ class SolveOpts(ctypes.Structure):
                 ("precondition", ctypes.c_int), ("precision", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("precision", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("inner_rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("chunk", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("admissions", ctypes.c_int64),
+                ("evictions", ctypes.c_int64), ("resident_bytes", ctypes.c_double),
+                ("resident_geometries", ctypes.c_int)]
+
+
 #: arithmetic of the solve's matrix-vector products (msbem_solve_opts.precision)
 PRECISION = {"df": 0, "fp64": 1, "mixed": 2}
 
@@ -76,6 +87,17 @@ def lib():
         "msbem_spd_inverse_noalloc": ([P, i64, P, P], i32),
         "msbem_solve_batch": ([P, P, i32, ctypes.POINTER(SolveOpts), P, P, P, P], i32),
         "msbem_apply": ([P, P, i32, i32, P, P], i32),
+        "msbem_server_create": ([P, ctypes.POINTER(ServerOpts), ctypes.POINTER(P)], i32),
+        "msbem_server_destroy": ([P], i32),
+        "msbem_server_add_geometry": ([P, ctypes.c_uint64, P, i64, P, i64, P, i64, P, i64, P, P], i32),
+        "msbem_server_now": ([], ctypes.c_double),
+        "msbem_server_footprint": ([P, ctypes.c_uint64], ctypes.c_double),
+        "msbem_server_submit": ([P, ctypes.c_uint64, P, P, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], i32),
+        "msbem_server_progress": ([P, i32, ctypes.POINTER(i32)], i32),
+        "msbem_server_result": ([P, ctypes.c_uint64, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(i32)], i32),
+        "msbem_server_stats_get": ([P, ctypes.POINTER(ServerStats)], i32),
         "msbem_mesh_dofs": ([P, i64, P, i64, ctypes.POINTER(i64), P, P, i64, ctypes.c_char_p, i32], i32),
     }
     for name, (args, res) in sig.items():
@@ -307,3 +329,82 @@ class Solver:
         nh = int(np.argmax(np.isnan(hist))) if np.isnan(hist).any() else hist_cap
         return {"density": out, "iters": n_it, "hist": hist[:nh].copy(),
                 "kappa": float(kap.value), "status": st}
+
+
+class Server:
+    """The serving engine (msbem_server_*): geometries registered by key stay
+    resident on the device once admitted; requests (key, g) are answered by a
+    continuously refilled 16-slot multi-vector PCG per geometry."""
+
+    def __init__(self, device: int = 0, stream=None, precision="mixed", rtol: float = 1e-8,
+                 inner_rtol: float = 0.0, hbm_budget: float = 0.0, maxit: int = 1000, chunk: int = 4):
+        self.ctx = msbem_create(device, stream)
+        o = ServerOpts(float(hbm_budget), PRECISION[precision], rtol, inner_rtol, maxit, chunk)
+        h = ctypes.c_void_p()
+        st = lib().msbem_server_create(self.ctx, ctypes.byref(o), ctypes.byref(h))
+        if st:
+            msbem_destroy(self.ctx)
+            raise MsbemError(st, "msbem_server_create failed")
+        self.h = h.value
+        self.ndof = {}
+
+    def add_geometry(self, key: int, geom) -> None:
+        xyz = np.ascontiguousarray(geom.xyz, np.float64)
+        tri = np.ascontiguousarray(geom.tri, np.int32)
+        cxyz = np.ascontiguousarray(geom.coarse_xyz, np.float64)
+        ctri = np.ascontiguousarray(geom.coarse_tri, np.int32)
+        par = np.ascontiguousarray(geom.parent, np.int32)
+        pat = np.ascontiguousarray(geom.patch, np.int32)
+        _check(self.ctx, lib().msbem_server_add_geometry(self.h, key, _ptr(xyz), len(xyz), _ptr(tri), len(tri),
+                                                         _ptr(cxyz), len(cxyz), _ptr(ctri), len(ctri),
+                                                         _ptr(par), _ptr(pat)))
+        self.ndof[key] = msbem_mesh_dofs(xyz, tri)[0]
+
+    def footprint(self, key: int) -> float:
+        """Bytes the admission of geometry `key` asks of the HBM budget."""
+        return float(lib().msbem_server_footprint(self.h, key))
+
+    @staticmethod
+    def now() -> float:
+        return float(lib().msbem_server_now())
+
+    def submit(self, key: int, g, out=None, t_arrival: float = 0.0) -> int:
+        gv = np.ascontiguousarray(g, np.float64)
+        rid = ctypes.c_uint64()
+        _check(self.ctx, lib().msbem_server_submit(self.h, key, _ptr(gv), None if out is None else _ptr(out),
+                                                   t_arrival, ctypes.byref(rid)))
+        return int(rid.value)
+
+    def progress(self, block: bool = False) -> int:
+        n = ctypes.c_int()
+        st = lib().msbem_server_progress(self.h, int(block), ctypes.byref(n))
+        if st:
+            raise MsbemError(st, "msbem_server_progress")
+        return int(n.value)
+
+    def result(self, rid: int) -> dict:
+        st, it, rf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rel, lat = ctypes.c_double(), ctypes.c_double()
+        _check(self.ctx, lib().msbem_server_result(self.h, rid, ctypes.byref(st), ctypes.byref(it),
+                                                   ctypes.byref(rel), ctypes.byref(lat), ctypes.byref(rf)))
+        return {"status": st.value, "iters": it.value, "relres": rel.value, "latency_ms": lat.value,
+                "refinements": rf.value}
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        lib().msbem_server_stats_get(self.h, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().msbem_server_destroy(self.h)
+            self.h = None
+        if getattr(self, "ctx", None):
+            msbem_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

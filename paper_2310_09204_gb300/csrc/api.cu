@@ -117,6 +117,11 @@ double tridiag_kappa(const std::vector<double>& alpha, const std::vector<double>
 
 }  // namespace
 
+namespace msbem {
+DevGeom& msbem_geom_dev(msbem_geom* g) { return g->dev; }
+int msbem_ctx_device(const msbem_ctx* c) { return c->device; }
+}  // namespace msbem
+
 extern "C" {
 
 int msbem_create(msbem_ctx** ctx, int device, void* stream) {

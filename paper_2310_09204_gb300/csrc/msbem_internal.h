@@ -217,4 +217,8 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
                          int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
                          int* refinements, cudaStream_t s);
 
+// accessors of the opaque handles (api.cu)
+DevGeom& msbem_geom_dev(msbem_geom* g);
+int msbem_ctx_device(const msbem_ctx* c);
+
 }  // namespace msbem

@@ -15,29 +15,10 @@
 #include <cstddef>
 #include <vector>
 
+#include "batch.cuh"
 #include "df.cuh"
-#include "msbem_internal.h"
 
 namespace msbem {
-
-#define BK 16                 // columns per pass
-#define BRED 128              // blocks of the column reductions
-static constexpr unsigned kStrideBlocks = 512;
-
-struct ColState {
-  double rz, pq, alpha, rr, rz_new, beta, nL2;
-  int done, iter, pad0, pad1;
-};
-struct BatchState {
-  int all_done;
-  int kb;
-  int maxit;
-  int fixed;
-  double rtol;
-  int err;      // set by the matrix-vector product when a copy never completed
-};
-
-__device__ __forceinline__ bool col_active(const ColState* cs, int c) { return cs[c].done == 0; }
 
 // per-column partial sums of a_c . b_c  (part: kb x BRED)
 __global__ void bdot_kernel(const double* __restrict__ A, const double* __restrict__ B, int64_t N,
@@ -393,18 +374,8 @@ __global__ void btranspose_kernel(const double* __restrict__ X, int64_t N, int k
   out[(int64_t)c * N + i] = X[e];
 }
 
-namespace {
-struct BatchBuffers {
-  double *X, *R, *Z, *P, *Q, *T, *U, *part, *gv, *hist;
-  float* Pf;     // [2][kb][ldw]
-  float2* Rf;
-  ColState* cs;
-  BatchState* bs;
-};
-}  // namespace
 
-static void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precondition, int f32,
-                          cudaStream_t s) {
+void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precondition, int f32, cudaStream_t s) {
   const int64_t N = g.ndof;
   if (!precondition) {
     bcopy_kernel<<<kStrideBlocks, 256, 0, s>>>(b.Z, b.R, N * kb, b.bs);
@@ -481,18 +452,28 @@ __global__ void bresid_kernel(const double* __restrict__ L, const double* __rest
     R[e] = L[e] - Q[e];
 }
 
-namespace {
-// carves one pool allocation into 16-byte aligned pieces
-struct Carver {
-  char* cur;
-  template <class T>
-  T* take(size_t n) {
-    T* p = (T*)cur;
-    cur += (sizeof(T) * n + 15) / 16 * 16;
-    return p;
-  }
-};
-}  // namespace
+
+void enqueue_batch_iteration(DevGeom& g, const BatchBuffers& b, int kb, int precondition, int mv_mode,
+                             const CUtensorMap& tmP, int split, void* scratch, int hcap, cudaStream_t s) {
+  const int64_t N = g.ndof;
+  const dim3 rgrid(BRED, kb);
+  double* rel_h = b.hist;
+  double* alpha_h = rel_h + (size_t)kb * (hcap + 1);
+  double* beta_h = alpha_h + (size_t)kb * hcap;
+  const CUtensorMap& tmW = mv_mode == 0 ? g.tm_W : g.tm_Whi;
+  launch_matvec(mv_mode, tmW, tmP, N, kb, b.P, b.Q, b.part, &b.bs->all_done, &b.bs->err, s, split, scratch);
+  breduce_kernel<<<kb, 256, 0, s>>>(b.part, (int)matvec_blocks(N, mv_mode), b.cs, offsetof(ColState, pq), b.bs);
+  balpha_kernel<<<1, BK, 0, s>>>(b.cs, alpha_h, hcap, b.bs);
+  bupdate_xr_kernel<<<rgrid, 256, 0, s>>>(b.X, b.R, b.P, b.Q, N, kb, b.cs, b.part, b.bs);
+  breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rr), b.bs);
+  bcheck_kernel<<<1, 32, 0, s>>>(b.cs, rel_h, hcap, b.bs);
+  apply_M_batch(g, b, kb, precondition, mv_mode, s);
+  bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
+  breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz_new), b.bs);
+  bbeta_kernel<<<1, BK, 0, s>>>(b.cs, beta_h, hcap, b.bs);
+  bupdate_p_kernel<<<kStrideBlocks, 256, 0, s>>>(b.P, b.Pf, g.ldw, b.Z, N, kb, b.cs, 0, b.bs);
+  g.launches += 10 + (split > 1 ? 1 : 0);
+}
 
 // PCG from X = 0 on the kb right-hand sides Rin (device, N x kb row-major);
 // the iterates are written to X (device, N x kb).  mv_mode 0: double-float
@@ -534,9 +515,6 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   b.cs = cv.take<ColState>(kb);
   b.bs = cv.take<BatchState>(1);
   char* scratch = cv.take<char>(scr_bytes);
-  double* rel_h = b.hist;                                   // kb x (maxit+1)
-  double* alpha_h = rel_h + (size_t)kb * (maxit + 1);       // kb x maxit
-  double* beta_h = alpha_h + (size_t)kb * maxit;            // kb x maxit
   std::vector<ColState> h_cs(kb);
   for (auto& c : h_cs) c = ColState{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   BatchState h_bs{0, kb, maxit, fixed, rtol, 0};
@@ -546,7 +524,6 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
     cudaFreeAsync(base, s);
     return e;
   }
-  const CUtensorMap& tmW = mv_mode == 0 ? g.tm_W : g.tm_Whi;
   cudaMemsetAsync(b.Pf, 0, sizeof(float) * 2 * kb * g.ldw, s);
   cudaMemcpyAsync(b.cs, h_cs.data(), sizeof(ColState) * kb, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(b.bs, &h_bs, sizeof(BatchState), cudaMemcpyHostToDevice, s);
@@ -579,20 +556,8 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   int enq = 0;
   while (enq < maxit && !h_bs.all_done) {
     const int chunk = std::min(4, maxit - enq);
-    for (int it = 0; it < chunk; ++it) {
-      launch_matvec(mv_mode, tmW, tmP, N, kb, b.P, b.Q, b.part, &b.bs->all_done, &b.bs->err, s, split, scratch);
-      breduce_kernel<<<kb, 256, 0, s>>>(b.part, (int)gemv_blocks, b.cs, offsetof(ColState, pq), b.bs);
-      balpha_kernel<<<1, BK, 0, s>>>(b.cs, alpha_h, maxit, b.bs);
-      bupdate_xr_kernel<<<rgrid, 256, 0, s>>>(b.X, b.R, b.P, b.Q, N, kb, b.cs, b.part, b.bs);
-      breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rr), b.bs);
-      bcheck_kernel<<<1, 32, 0, s>>>(b.cs, rel_h, maxit, b.bs);
-      apply_M_batch(g, b, kb, precondition, mv_mode, s);
-      bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
-      breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz_new), b.bs);
-      bbeta_kernel<<<1, BK, 0, s>>>(b.cs, beta_h, maxit, b.bs);
-      bupdate_p_kernel<<<kStrideBlocks, 256, 0, s>>>(b.P, b.Pf, g.ldw, b.Z, N, kb, b.cs, 0, b.bs);
-      g.launches += 10;
-    }
+    for (int it = 0; it < chunk; ++it)
+      enqueue_batch_iteration(g, b, kb, precondition, mv_mode, tmP, split, scratch, maxit, s);
     enq += chunk;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(&h_bs, b.bs, sizeof(BatchState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

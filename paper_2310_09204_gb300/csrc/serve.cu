@@ -1,0 +1,677 @@
+// Serving engine: solve requests (geometry key, Neumann data g) arriving over
+// time are answered from geometries kept resident on the device (W, the
+// factored preconditioner M(H;h) and a 16-slot batch of PCG vectors per
+// geometry), admitted against an HBM budget with least-recently-used
+// eviction of idle geometries.
+//
+// Continuous batching: every resident geometry runs its own multi-vector PCG
+// on its own CUDA stream, so the iterations of different geometries overlap
+// on the device.  Every `chunk` iterations the engine looks at the per-slot
+// states: finished slots are harvested and refilled at once from the
+// geometry's queue; a new request joins the running batch without disturbing
+// the other slots (every per-slot sum runs in the same order whatever the
+// batch holds, so each result is bit for bit the one it gets alone).
+//
+// precision 0: each slot runs the double-float PCG of msbem_solve_batch.
+// precision 2: each slot runs the iterative refinement of the mixed mode --
+// inner PCG with FP32 products to inner_rtol, then X += D and the true
+// residual R = L - W X with the double-float product; the slot finishes when
+// ||R|| <= rtol ||L||, else restarts its inner solve on R.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <unordered_map>
+#include <vector>
+
+#include "batch.cuh"
+#include "df.cuh"
+
+using namespace msbem;
+
+namespace msbem {
+
+// ---- column-masked kernels (mask[c] != 0 selects column c) -----------------
+__global__ void s_copy_cols(double* __restrict__ dst, const double* __restrict__ src, int64_t N, int kb,
+                            const int* __restrict__ mask) {
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < N * kb; e += (int64_t)gridDim.x * 256)
+    if (mask[e % kb]) dst[e] = src ? src[e] : 0.0;
+}
+
+__global__ void s_axpy_cols(double* __restrict__ X, const double* __restrict__ D, int64_t N, int kb,
+                            const int* __restrict__ mask) {
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < N * kb; e += (int64_t)gridDim.x * 256)
+    if (mask[e % kb]) X[e] += D[e];
+}
+
+__global__ void s_resid_cols(const double* __restrict__ L, const double* __restrict__ Q, double* __restrict__ R,
+                             int64_t N, int kb, const int* __restrict__ mask) {
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < N * kb; e += (int64_t)gridDim.x * 256)
+    if (mask[e % kb]) R[e] = L[e] - Q[e];
+}
+
+// R[i][c] = L_c[i] for the masked columns (constant data g_c)
+__global__ void s_rhs_cols(const int64_t* __restrict__ jptr, const double* __restrict__ jrhs, int64_t N,
+                           const double* __restrict__ gv, int kb, const int* __restrict__ mask,
+                           double* __restrict__ L) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * kb) return;
+  const int64_t i = e / kb;
+  const int c = (int)(e % kb);
+  if (!mask[c]) return;
+  double acc = 0.0;
+  for (int64_t k = jptr[i]; k < jptr[i + 1]; ++k)
+    acc += jrhs[3 * k] * gv[3 * c] + jrhs[3 * k + 1] * gv[3 * c + 1] + jrhs[3 * k + 2] * gv[3 * c + 2];
+  L[e] = acc;
+}
+
+// fixed-order sum of a masked column's partials into a ColState field
+__global__ void s_reduce_cols(const double* __restrict__ part, int nparts, ColState* cs, int field,
+                              const int* __restrict__ mask) {
+  __shared__ double sm[256];
+  const int c = blockIdx.x;
+  if (!mask[c]) return;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 256) acc += part[(int64_t)c * nparts + i];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *(double*)((char*)&cs[c] + field) = sm[0];
+}
+
+// P_c = Z_c (first search direction) and its float-pair planes, masked columns
+__global__ void s_setp_cols(double* __restrict__ P, float* __restrict__ Pf, int64_t ldp,
+                            const double* __restrict__ Z, int64_t N, int kb, const int* __restrict__ mask) {
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < N * kb; e += (int64_t)gridDim.x * 256) {
+    const int64_t i = e / kb;
+    const int c = (int)(e - i * kb);
+    if (!mask[c]) continue;
+    const double v = Z[e];
+    P[e] = v;
+    float h, l;
+    split_df(v, h, l);
+    Pf[(int64_t)c * ldp + i] = h;
+    Pf[(int64_t)(kb + c) * ldp + i] = l;
+  }
+}
+
+// masked columns start their recursion: iteration 0, running unless no data
+__global__ void s_start_cols(ColState* cs, int kb, const int* __restrict__ mask) {
+  const int c = threadIdx.x;
+  if (c >= kb || !mask[c]) return;
+  cs[c].iter = 0;
+  cs[c].done = cs[c].nL2 == 0.0 ? 4 : 0;
+}
+
+// out = column c of X (N x kb)
+__global__ void s_gather_col(const double* __restrict__ X, int64_t N, int kb, int c, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) out[i] = X[i * kb + c];
+}
+
+}  // namespace msbem
+
+// ---------------------------------------------------------------------------
+// host engine
+// ---------------------------------------------------------------------------
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+enum SlotPhase { IDLE = 0, INNER = 1 };
+
+struct Request {
+  uint64_t id = 0, key = 0;
+  double g[3] = {0, 0, 0};
+  double* out = nullptr;
+  double t_arrival = 0.0, t_done = -1.0;
+  int status = 1;          // 1 = pending (not finished yet)
+  int iters = 0;
+  int refinements = 0;
+  double relres = NAN;
+};
+
+struct Slot {
+  uint64_t req = 0;        // 0 = free
+  int phase = IDLE;
+  int inner_total = 0;
+  int refinements = 0;
+  double nL = 0.0;         // ||L_c||^2
+};
+
+struct Batch {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  char* base = nullptr;
+  size_t bytes = 0;
+  BatchBuffers b{};
+  double *L = nullptr, *Xo = nullptr, *Ro = nullptr, *nrm = nullptr, *out = nullptr;
+  float* Xf = nullptr;
+  int* mask = nullptr;
+  char* scratch = nullptr;
+  BatchState* fl = nullptr;        // all_done = 0 flags for the utility kernels
+  CUtensorMap tmP, tmX;
+  int split = 1;
+  ColState* h_cs = nullptr;        // pinned snapshots
+  double* h_nrm = nullptr;
+  int* h_mask = nullptr;
+  BatchState* h_bs = nullptr;
+  bool in_flight = false;
+  Slot slot[BK];
+};
+
+struct GeomEntry {
+  uint64_t key = 0;
+  std::vector<double> xyz, cxyz;
+  std::vector<int32_t> tri, ctri, parent, patch;
+  int64_t ndof = -1, nt = 0;
+  size_t footprint = 0;    // resident bytes (W, preconditioner, batch)
+  msbem_geom* geom = nullptr;
+  std::unique_ptr<Batch> batch;
+  std::deque<uint64_t> pending;
+  double last_used = 0.0;
+  int active = 0;          // busy slots
+};
+
+}  // namespace
+
+struct msbem_server {
+  msbem_ctx* ctx = nullptr;
+  msbem_server_opts opts{};
+  int device = 0;
+  std::unordered_map<uint64_t, std::unique_ptr<GeomEntry>> geoms;
+  std::unordered_map<uint64_t, Request> reqs;
+  std::deque<uint64_t> admit_queue;   // keys with pending requests that are not resident
+  uint64_t next_id = 1;
+  size_t resident = 0;
+  msbem_server_stats st{};
+};
+
+namespace {
+
+constexpr int kSlots = BK;
+
+size_t estimate_footprint(const GeomEntry& e) {
+  const size_t N = (size_t)std::max<int64_t>(e.ndof, 1);
+  const size_t ldw = (N + 31) / 32 * 32;
+  // W planes, FP64 + float-pair block inverses (faces of ~600 dofs at most plus
+  // a wire basket of ~sqrt(N) * 12 dofs, a bound), coarse scratch, batch vectors
+  const size_t wb = (size_t)(12.0 * std::sqrt((double)N)) + 64;
+  const size_t blocks = 16 * (N * 600 + wb * wb);
+  const size_t batch = sizeof(double) * N * kSlots * 12 + sizeof(float) * 4 * kSlots * ldw;
+  return 8 * N * ldw + blocks + 8 * N * 64 + batch + (2u << 20);
+}
+
+size_t transient_bytes(const GeomEntry& e) { return sizeof(float2) * (size_t)e.nt * e.nt; }
+
+void free_batch(Batch* B) {
+  if (!B) return;
+  if (B->s) cudaStreamSynchronize(B->s);
+  if (B->base) cudaFreeAsync(B->base, B->s);
+  if (B->s) cudaStreamSynchronize(B->s);
+  if (B->h_cs) cudaFreeHost(B->h_cs);
+  if (B->ev) cudaEventDestroy(B->ev);
+  if (B->s) cudaStreamDestroy(B->s);
+}
+
+int alloc_batch(msbem_server* S, GeomEntry& e) {
+  DevGeom& g = msbem_geom_dev(e.geom);
+  const int64_t N = g.ndof;
+  const int kb = kSlots;
+  auto B = std::make_unique<Batch>();
+  if (cudaStreamCreateWithFlags(&B->s, cudaStreamNonBlocking) != cudaSuccess) return MSBEM_CUDA_ERROR;
+  cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+  const int maxit = S->opts.maxit;
+  const int64_t NH = std::max<int64_t>(g.n_coarse, 1);
+  const size_t nvec = (size_t)N * kb;
+  const size_t nparts = (size_t)kb * std::max<unsigned>(matvec_blocks(N, 0), BRED);
+  const size_t hsz = (size_t)kb * (maxit + 1) + 2 * (size_t)kb * maxit;
+  B->split = std::max(matvec_split(N, 0), matvec_split(N, 1));
+  const size_t scr = matvec_scratch_bytes(N, kb, B->split);
+  B->bytes = sizeof(double) * (8 * nvec + 2 * NH * kb + nparts + hsz + 3 * kb + 2 * kb + N) +
+             sizeof(float) * 4 * kb * g.ldw + sizeof(float2) * nvec + sizeof(ColState) * kb +
+             2 * sizeof(BatchState) + sizeof(int) * kb + scr + 1024;
+  if (pool_alloc((void**)&B->base, B->bytes, g.pool, B->s) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(B.get());
+    return MSBEM_OOM;
+  }
+  Carver cv{B->base};
+  BatchBuffers& b = B->b;
+  b.X = cv.take<double>(nvec);      // inner iterate (the correction D in the mixed mode)
+  b.R = cv.take<double>(nvec);      // inner residual
+  b.Z = cv.take<double>(nvec);
+  b.P = cv.take<double>(nvec);
+  b.Q = cv.take<double>(nvec);
+  b.T = cv.take<double>(NH * kb);
+  b.U = cv.take<double>(NH * kb);
+  b.part = cv.take<double>(nparts);
+  b.hist = cv.take<double>(hsz);
+  b.gv = cv.take<double>(3 * kb);
+  b.Pf = cv.take<float>(2 * kb * g.ldw);
+  b.Rf = cv.take<float2>(nvec);
+  b.cs = cv.take<ColState>(kb);
+  b.bs = cv.take<BatchState>(1);
+  B->L = cv.take<double>(nvec);
+  B->Xo = cv.take<double>(nvec);
+  B->Ro = cv.take<double>(nvec);
+  B->nrm = cv.take<double>(2 * kb);
+  B->out = cv.take<double>(N);
+  B->Xf = cv.take<float>(2 * kb * g.ldw);
+  B->mask = cv.take<int>(kb);
+  B->fl = cv.take<BatchState>(1);
+  B->scratch = cv.take<char>(scr);
+  cudaError_t ce = encode_planes(&B->tmP, b.Pf, g.ldw, kb, kb * g.ldw, S->opts.precision == 2 ? 1 : 2,
+                                 matvec_pad(kb));
+  if (ce == cudaSuccess) ce = encode_planes(&B->tmX, B->Xf, g.ldw, kb, kb * g.ldw, 2, matvec_pad(kb));
+  // pinned snapshots: ColState[kb], nrm[2kb], mask[kb], BatchState
+  void* pin = nullptr;
+  if (ce == cudaSuccess)
+    ce = cudaMallocHost(&pin, sizeof(ColState) * kb + sizeof(double) * 2 * kb + sizeof(int) * kb +
+                                  sizeof(BatchState) + 64);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(B.get());
+    return MSBEM_CUDA_ERROR;
+  }
+  B->h_cs = (ColState*)pin;
+  B->h_nrm = (double*)(B->h_cs + kb);
+  B->h_mask = (int*)(B->h_nrm + 2 * kb);
+  B->h_bs = (BatchState*)(B->h_mask + kb);
+  for (int c = 0; c < kb; ++c) B->h_cs[c] = ColState{0, 0, 0, 0, 0, 0, 0, 6, 0, 0, 0};
+  const double inner = S->opts.precision == 2 ? S->opts.inner_rtol : S->opts.rtol;
+  *B->h_bs = BatchState{1, kb, maxit, 0, inner, 0};
+  cudaMemsetAsync(B->base, 0, B->bytes, B->s);
+  cudaMemcpyAsync(b.cs, B->h_cs, sizeof(ColState) * kb, cudaMemcpyHostToDevice, B->s);
+  cudaMemcpyAsync(b.bs, B->h_bs, sizeof(BatchState), cudaMemcpyHostToDevice, B->s);
+  if (cudaStreamSynchronize(B->s) != cudaSuccess) {
+    free_batch(B.get());
+    return MSBEM_CUDA_ERROR;
+  }
+  e.batch = std::move(B);
+  return MSBEM_OK;
+}
+
+void evict(msbem_server* S, GeomEntry& e) {
+  free_batch(e.batch.get());
+  e.batch.reset();
+  if (e.geom) msbem_geom_free(e.geom);
+  e.geom = nullptr;
+  S->resident -= std::min(S->resident, e.footprint);
+  e.footprint = 0;
+  ++S->st.evictions;
+}
+
+// make room for `need` bytes by evicting idle geometries, least recently used first
+bool make_room(msbem_server* S, size_t need, uint64_t keep) {
+  while (S->resident + need > (size_t)S->opts.hbm_budget_bytes) {
+    GeomEntry* victim = nullptr;
+    for (auto& kv : S->geoms) {
+      GeomEntry& e = *kv.second;
+      if (!e.geom || e.key == keep || e.active > 0 || !e.pending.empty()) continue;
+      if (!victim || e.last_used < victim->last_used) victim = &e;
+    }
+    if (!victim) return false;
+    evict(S, *victim);
+  }
+  return true;
+}
+
+int admit(msbem_server* S, GeomEntry& e) {
+  const size_t need = estimate_footprint(e) + transient_bytes(e);
+  if (!make_room(S, need, e.key)) return MSBEM_OOM;
+  msbem_geom* g = nullptr;
+  int st = msbem_upload(S->ctx, e.xyz.data(), (int64_t)e.xyz.size() / 3, e.tri.data(), (int64_t)e.tri.size() / 3,
+                        e.cxyz.data(), (int64_t)e.cxyz.size() / 3, e.ctri.data(), (int64_t)e.ctri.size() / 3,
+                        e.parent.data(), e.patch.data(), &g);
+  if (st) return st;
+  if ((st = msbem_assemble(g, nullptr)) || (st = msbem_factor(g, nullptr))) {
+    msbem_geom_free(g);
+    return st;
+  }
+  e.geom = g;
+  if ((st = alloc_batch(S, e))) {
+    msbem_geom_free(g);
+    e.geom = nullptr;
+    return st;
+  }
+  {
+    DevGeom& d = msbem_geom_dev(g);
+    const size_t NH = (size_t)std::max<int64_t>(d.n_coarse, 1);
+    e.footprint = sizeof(float) * 2 * (size_t)d.ndof * d.ldw + (sizeof(double) + sizeof(float2)) * d.binv_size +
+                  sizeof(double) * (NH * d.ndof + 8 * (size_t)d.ndof) + e.batch->bytes;
+  }
+  S->resident += e.footprint;
+  ++S->st.admissions;
+  return MSBEM_OK;
+}
+
+void finish(msbem_server* S, GeomEntry& e, int c, int status, int iters, double relres, const double* src_cols) {
+  Batch& B = *e.batch;
+  Slot& sl = B.slot[c];
+  Request& r = S->reqs[sl.req];
+  DevGeom& g = msbem_geom_dev(e.geom);
+  const int64_t N = g.ndof;
+  s_gather_col<<<(unsigned)((N + 255) / 256), 256, 0, B.s>>>(src_cols, N, kSlots, c, B.out);
+  if (r.out) cudaMemcpyAsync(r.out, B.out, sizeof(double) * N, cudaMemcpyDefault, B.s);
+  cudaStreamSynchronize(B.s);
+  r.status = status;
+  r.iters = iters;
+  r.relres = relres;
+  r.refinements = sl.refinements;
+  r.t_done = now_s();
+  sl = Slot();
+  B.h_cs[c].done = 6;
+  --e.active;
+  ++S->st.completed;
+}
+
+// one scheduling point of a resident geometry whose batch is not in flight
+void schedule(msbem_server* S, GeomEntry& e) {
+  Batch& B = *e.batch;
+  DevGeom& g = msbem_geom_dev(e.geom);
+  const int64_t N = g.ndof;
+  const int kb = kSlots;
+  const bool mixed = S->opts.precision == 2;
+  const unsigned grid = kStrideBlocks;
+  const dim3 rgrid(BRED, kb);
+  cudaStream_t s = B.s;
+  // 1. slots whose inner recursion stopped
+  std::vector<int> refine;
+  for (int c = 0; c < kb; ++c) {
+    Slot& sl = B.slot[c];
+    if (sl.phase != INNER) continue;
+    const ColState& cs = B.h_cs[c];
+    if (cs.done == 0) continue;
+    sl.inner_total += cs.iter;
+    const double rel = cs.nL2 > 0.0 ? std::sqrt(cs.rr / cs.nL2) : 0.0;
+    if (!mixed) {
+      const int status = cs.done == 1 || cs.done == 4 ? MSBEM_OK
+                       : cs.done == 2 ? MSBEM_BREAKDOWN
+                       : cs.done == 5 ? MSBEM_DEVICE_TIMEOUT
+                                      : MSBEM_NOT_CONVERGED;
+      finish(S, e, c, status, sl.inner_total, cs.done == 4 ? 0.0 : rel, B.b.X);
+    } else if (cs.done == 2 || cs.done == 5) {
+      finish(S, e, c, cs.done == 2 ? MSBEM_BREAKDOWN : MSBEM_DEVICE_TIMEOUT, sl.inner_total, NAN, B.Xo);
+    } else {
+      refine.push_back(c);
+    }
+  }
+  std::vector<int> start;   // columns whose inner recursion (re)starts on Ro
+  if (!refine.empty()) {
+    // X += D and the true residual R = L - W X (double-float product)
+    for (int c = 0; c < kb; ++c) B.h_mask[c] = 0;
+    for (int c : refine) B.h_mask[c] = 1;
+    cudaMemcpyAsync(B.mask, B.h_mask, sizeof(int) * kb, cudaMemcpyHostToDevice, s);
+    s_axpy_cols<<<grid, 256, 0, s>>>(B.Xo, B.b.X, N, kb, B.mask);
+    bsplit_kernel<<<grid, 256, 0, s>>>(B.Xo, B.Xf, g.ldw, N, kb);
+    launch_matvec(0, g.tm_W, B.tmX, N, kb, B.Xo, B.b.Q, B.b.part, &B.fl->all_done, &B.fl->err, s,
+                  matvec_split(N, 0), B.scratch);
+    s_resid_cols<<<grid, 256, 0, s>>>(B.L, B.b.Q, B.Ro, N, kb, B.mask);
+    bdot_kernel<<<rgrid, 256, 0, s>>>(B.Ro, B.Ro, N, kb, B.b.part, B.fl);
+    bsum_kernel<<<kb, 256, 0, s>>>(B.b.part, BRED, B.nrm);
+    cudaMemcpyAsync(B.h_nrm, B.nrm, sizeof(double) * kb, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    g.launches += 6;
+    for (int c : refine) {
+      Slot& sl = B.slot[c];
+      ++sl.refinements;
+      const double rel = sl.nL > 0.0 ? std::sqrt(B.h_nrm[c] / sl.nL) : 0.0;
+      if (rel <= S->opts.rtol)
+        finish(S, e, c, MSBEM_OK, sl.inner_total, rel, B.Xo);
+      else if (sl.inner_total >= S->opts.maxit || sl.refinements >= 12)
+        finish(S, e, c, MSBEM_NOT_CONVERGED, sl.inner_total, rel, B.Xo);
+      else
+        start.push_back(c);
+    }
+  }
+  // 2. free slots take queued requests
+  std::vector<int> fresh;
+  for (int c = 0; c < kb && !e.pending.empty(); ++c) {
+    if (B.slot[c].req) continue;
+    const uint64_t id = e.pending.front();
+    e.pending.pop_front();
+    Slot& sl = B.slot[c];
+    sl = Slot();
+    sl.req = id;
+    sl.phase = INNER;
+    ++e.active;
+    fresh.push_back(c);
+  }
+  if (!fresh.empty()) {
+    double gv[3 * BK];
+    for (int c = 0; c < kb; ++c) {
+      B.h_mask[c] = 0;
+      for (int k = 0; k < 3; ++k) gv[3 * c + k] = 0.0;
+    }
+    for (int c : fresh) {
+      B.h_mask[c] = 1;
+      const Request& r = S->reqs[B.slot[c].req];
+      for (int k = 0; k < 3; ++k) gv[3 * c + k] = r.g[k];
+    }
+    cudaMemcpyAsync(B.mask, B.h_mask, sizeof(int) * kb, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(B.b.gv, gv, sizeof(double) * 3 * kb, cudaMemcpyHostToDevice, s);
+    s_rhs_cols<<<(unsigned)((N * kb + 255) / 256), 256, 0, s>>>(g.d_jptr, g.d_jrhs, N, B.b.gv, kb, B.mask, B.L);
+    s_copy_cols<<<grid, 256, 0, s>>>(B.Ro, B.L, N, kb, B.mask);
+    s_copy_cols<<<grid, 256, 0, s>>>(B.Xo, nullptr, N, kb, B.mask);
+    bdot_kernel<<<rgrid, 256, 0, s>>>(B.L, B.L, N, kb, B.b.part, B.fl);
+    bsum_kernel<<<kb, 256, 0, s>>>(B.b.part, BRED, B.nrm);
+    cudaMemcpyAsync(B.h_nrm, B.nrm, sizeof(double) * kb, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    g.launches += 6;
+    for (int c : fresh) {
+      B.slot[c].nL = B.h_nrm[c];
+      start.push_back(c);
+    }
+  }
+  // 3. (re)start the inner recursion of the selected columns on Ro
+  if (!start.empty()) {
+    for (int c = 0; c < kb; ++c) B.h_mask[c] = 0;
+    for (int c : start) {
+      B.h_mask[c] = 1;
+      B.slot[c].phase = INNER;
+    }
+    cudaMemcpyAsync(B.mask, B.h_mask, sizeof(int) * kb, cudaMemcpyHostToDevice, s);
+    B.h_bs->all_done = 0;
+    cudaMemcpyAsync(B.b.bs, B.h_bs, sizeof(BatchState), cudaMemcpyHostToDevice, s);
+    const int f32 = mixed ? 1 : 0;
+    s_copy_cols<<<grid, 256, 0, s>>>(B.b.R, B.Ro, N, kb, B.mask);
+    s_copy_cols<<<grid, 256, 0, s>>>(B.b.X, nullptr, N, kb, B.mask);
+    bdot_kernel<<<rgrid, 256, 0, s>>>(B.b.R, B.b.R, N, kb, B.b.part, B.fl);
+    s_reduce_cols<<<kb, 256, 0, s>>>(B.b.part, BRED, B.b.cs, offsetof(ColState, nL2), B.mask);
+    apply_M_batch(g, B.b, kb, 1, f32, s);
+    s_setp_cols<<<grid, 256, 0, s>>>(B.b.P, B.b.Pf, g.ldw, B.b.Z, N, kb, B.mask);
+    bdot_kernel<<<rgrid, 256, 0, s>>>(B.b.R, B.b.Z, N, kb, B.b.part, B.fl);
+    s_reduce_cols<<<kb, 256, 0, s>>>(B.b.part, BRED, B.b.cs, offsetof(ColState, rz), B.mask);
+    s_start_cols<<<1, BK, 0, s>>>(B.b.cs, kb, B.mask);
+    g.launches += 9;
+  }
+  // 4. iterate the running slots
+  if (e.active > 0) {
+    const int mv_mode = mixed ? 1 : 0;
+    const int split = matvec_split(N, mv_mode);
+    for (int it = 0; it < S->opts.chunk; ++it)
+      enqueue_batch_iteration(g, B.b, kb, 1, mv_mode, B.tmP, split, B.scratch, S->opts.maxit, s);
+    cudaMemcpyAsync(B.h_cs, B.b.cs, sizeof(ColState) * kb, cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(B.ev, s);
+    B.in_flight = true;
+    e.last_used = now_s();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int msbem_server_create(msbem_ctx* ctx, const msbem_server_opts* opts, msbem_server** out) {
+  if (!ctx || !out) return MSBEM_INVALID_ARG;
+  *out = nullptr;
+  auto S = std::make_unique<msbem_server>();
+  S->ctx = ctx;
+  msbem_server_opts o{};
+  if (opts) o = *opts;
+  if (o.rtol <= 0.0) o.rtol = 1e-8;
+  if (o.inner_rtol <= 0.0) o.inner_rtol = 1e-4;
+  if (o.maxit <= 0) o.maxit = 1000;
+  if (o.chunk <= 0) o.chunk = 4;
+  if (o.precision != 0 && o.precision != 2) return MSBEM_INVALID_ARG;
+  if (!(o.inner_rtol < 1.0)) return MSBEM_INVALID_ARG;
+  if (o.hbm_budget_bytes <= 0.0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return MSBEM_CUDA_ERROR;
+    o.hbm_budget_bytes = 0.8 * (double)fr;
+  }
+  S->opts = o;
+  *out = S.release();
+  return MSBEM_OK;
+}
+
+int msbem_server_destroy(msbem_server* S) {
+  if (!S) return MSBEM_INVALID_ARG;
+  for (auto& kv : S->geoms)
+    if (kv.second->geom) evict(S, *kv.second);
+  delete S;
+  return MSBEM_OK;
+}
+
+int msbem_server_add_geometry(msbem_server* S, uint64_t key, const double* xyz, int64_t nv, const int32_t* tri,
+                              int64_t nt, const double* cxyz, int64_t ncv, const int32_t* ctri, int64_t nct,
+                              const int32_t* parent, const int32_t* patch) {
+  if (!S || !xyz || !tri || !cxyz || !ctri || !parent || !patch || nv <= 0 || nt <= 0 || ncv <= 0 || nct <= 0)
+    return MSBEM_INVALID_ARG;
+  if (S->geoms.count(key)) return MSBEM_INVALID_ARG;
+  auto e = std::make_unique<GeomEntry>();
+  e->key = key;
+  e->xyz.assign(xyz, xyz + 3 * nv);
+  e->tri.assign(tri, tri + 3 * nt);
+  e->cxyz.assign(cxyz, cxyz + 3 * ncv);
+  e->ctri.assign(ctri, ctri + 3 * nct);
+  e->parent.assign(parent, parent + nt);
+  e->patch.assign(patch, patch + nt);
+  e->nt = nt;
+  int64_t n = 0;
+  const int st = msbem_mesh_dofs(xyz, nv, tri, nt, &n, nullptr, nullptr, 0, nullptr, 0);
+  if (st) return st;
+  e->ndof = n;
+  S->geoms[key] = std::move(e);
+  return MSBEM_OK;
+}
+
+double msbem_server_now(void) { return now_s(); }
+
+double msbem_server_footprint(const msbem_server* S, uint64_t key) {
+  if (!S) return -1.0;
+  auto it = S->geoms.find(key);
+  if (it == S->geoms.end()) return -1.0;
+  return (double)(estimate_footprint(*it->second) + transient_bytes(*it->second));
+}
+
+int msbem_server_submit(msbem_server* S, uint64_t key, const double g[3], double* density, double t_arrival,
+                        uint64_t* id) {
+  if (!S || !g || !id) return MSBEM_INVALID_ARG;
+  auto it = S->geoms.find(key);
+  if (it == S->geoms.end()) return MSBEM_INVALID_ARG;
+  Request r;
+  r.id = S->next_id++;
+  r.key = key;
+  for (int k = 0; k < 3; ++k) r.g[k] = g[k];
+  r.out = density;
+  r.t_arrival = t_arrival > 0.0 ? t_arrival : now_s();
+  S->reqs[r.id] = r;
+  GeomEntry& e = *it->second;
+  e.pending.push_back(r.id);
+  *id = r.id;
+  ++S->st.submitted;
+  return MSBEM_OK;
+}
+
+int msbem_server_progress(msbem_server* S, int block, int* completed) {
+  if (!S) return MSBEM_INVALID_ARG;
+  cudaSetDevice(msbem_ctx_device(S->ctx));
+  const int64_t before = S->st.completed;
+  int status = MSBEM_OK;
+  for (;;) {
+    bool busy = false;
+    // admissions: geometries with queued requests that are not resident
+    for (auto& kv : S->geoms) {
+      GeomEntry& e = *kv.second;
+      if (e.geom || e.pending.empty()) continue;
+      const int st = admit(S, e);
+      // resident geometries with work will go idle and become evictable
+      bool others_busy = false;
+      for (auto& kv2 : S->geoms) {
+        const GeomEntry& o = *kv2.second;
+        others_busy = others_busy || (o.geom && (o.active > 0 || !o.pending.empty()));
+      }
+      if (st == MSBEM_OOM && others_busy) {
+        busy = true;           // wait until running geometries go idle
+        continue;
+      }
+      if (st) {                // the geometry cannot be served: fail its requests
+        for (uint64_t id : e.pending) {
+          Request& r = S->reqs[id];
+          r.status = st;
+          r.t_done = now_s();
+          ++S->st.completed;
+        }
+        e.pending.clear();
+        status = st;
+      }
+    }
+    for (auto& kv : S->geoms) {
+      GeomEntry& e = *kv.second;
+      if (!e.geom) continue;
+      Batch& B = *e.batch;
+      if (B.in_flight) {
+        const cudaError_t q = cudaEventQuery(B.ev);
+        if (q == cudaErrorNotReady) {
+          busy = true;
+          continue;
+        }
+        B.in_flight = false;
+        if (q != cudaSuccess) return MSBEM_CUDA_ERROR;
+      }
+      if (e.active > 0 || !e.pending.empty()) {
+        schedule(S, e);
+        busy = busy || B.in_flight || e.active > 0 || !e.pending.empty();
+      }
+    }
+    if (!block || !busy) break;
+  }
+  if (completed) *completed = (int)(S->st.completed - before);
+  S->st.resident_bytes = (double)S->resident;
+  int nres = 0;
+  for (auto& kv : S->geoms) nres += kv.second->geom != nullptr;
+  S->st.resident_geometries = nres;
+  return status;
+}
+
+int msbem_server_result(msbem_server* S, uint64_t id, int* status, int* iters, double* relres, double* latency_ms,
+                        int* refinements) {
+  if (!S) return MSBEM_INVALID_ARG;
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return MSBEM_INVALID_ARG;
+  const Request& r = it->second;
+  if (status) *status = r.status;
+  if (iters) *iters = r.iters;
+  if (relres) *relres = r.relres;
+  if (latency_ms) *latency_ms = r.t_done >= 0 ? 1e3 * (r.t_done - r.t_arrival) : -1.0;
+  if (refinements) *refinements = r.refinements;
+  return MSBEM_OK;
+}
+
+int msbem_server_stats_get(const msbem_server* S, msbem_server_stats* out) {
+  if (!S || !out) return MSBEM_INVALID_ARG;
+  *out = S->st;
+  return MSBEM_OK;
+}
+
+}  // extern "C"
