@@ -317,6 +317,113 @@ def bowtie(n: int = 8, n_coarse: int = 2, g=(1.0, 0.5, 0.25)) -> Geometry:
                     {"family": "bowtie", "n": n, "n_coarse": n_coarse})
 
 
+def _square_points(origin, eu, ev, m: int = 13) -> np.ndarray:
+    t = np.linspace(0.0, 1.0, m)
+    U, V = np.meshgrid(t, t, indexing="ij")
+    return (np.asarray(origin)[None, :] + U.reshape(-1, 1) * np.asarray(eu)[None, :]
+            + V.reshape(-1, 1) * np.asarray(ev)[None, :])
+
+
+def _min_dist(a: np.ndarray, b: np.ndarray) -> float:
+    d = a[:, None, :] - b[None, :, :]
+    return float(np.sqrt(np.min(np.einsum("ijk,ijk->ij", d, d))))
+
+
+def panels(seed: int, n: int | None = None, n_panels: int | None = None, g=None,
+           max_tries: int = 200, angle_range=(30.0, 180.0), n_coarse: int | None = None) -> Geometry:
+    """Multiscreen of 2-6 unit squares joined at shared edges with seeded
+    random dihedral angles (the 'batched + mixed precision' workload family).
+
+    The first square is [0,1]^2 in z = 0; every further square hinges on a
+    random edge of a square already placed, at a dihedral angle drawn from
+    U[30, 180] degrees (180: coplanar continuation; ``angle_range`` changes
+    the interval), folded to a random side.
+    A draw is rejected when two squares that share no hinge come closer than h
+    (points of each square kept 3h away from the points they share), or two
+    squares on the same hinge make an angle below 30 degrees; so the screen has
+    no closed cells and no point contacts.  h = 1/n with n drawn from
+    {24, 32, 48} unless given, H chosen so (H/h - 1)^2 lies in [150, 600]
+    (n = 24: H = 1; 32, 48: H = 1/2; ``n_coarse`` overrides).  Patches: the
+    coarse squares of every panel.  g: uniform in [-1, 1]^3 unless given."""
+    rng = np.random.default_rng(seed)
+    if n is None:
+        n = int(rng.choice([24, 32, 48]))
+    if n_coarse is None:
+        n_coarse = {24: 1, 32: 2, 48: 2}.get(n, max(1, n // 24))
+    if n % n_coarse:
+        raise ValueError("n must be a multiple of n_coarse")
+    if n_panels is None:
+        n_panels = int(rng.integers(2, 7))
+    h = 1.0 / n
+    sq = [(np.zeros(3), np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0]))]
+    hinge_dirs: dict = {}   # hinge (sorted end points) -> directions of the squares on it
+    tries = 0
+    while len(sq) < n_panels:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("panels: no admissible placement found")
+        k = int(rng.integers(len(sq)))
+        o, eu, ev = sq[k]
+        corners = [o, o + eu, o + eu + ev, o + ev]
+        e = int(rng.integers(4))
+        a, b = corners[e], corners[(e + 1) % 4]
+        w = o + 0.5 * (eu + ev) - 0.5 * (a + b)
+        w /= np.linalg.norm(w)                  # in square k's plane, into it
+        nrm = np.cross(eu, ev)
+        nrm /= np.linalg.norm(nrm)
+        th = math.radians(float(rng.uniform(*angle_range)))
+        side = 1.0 if rng.random() < 0.5 else -1.0
+        d = math.cos(th) * w + side * math.sin(th) * nrm
+        d /= np.linalg.norm(d)
+        new = (a.copy(), b - a, d)
+        hkey = tuple(sorted((tuple(np.round(a, 9)), tuple(np.round(b, 9)))))
+        dirs = hinge_dirs.get(hkey, [w])
+        ok = all(math.degrees(math.acos(float(np.clip(np.dot(dj, d), -1.0, 1.0)))) >= angle_range[0]
+                 for dj in dirs)
+        if ok:
+            pn = _square_points(*new)
+            for j, (oj, euj, evj) in enumerate(sq):
+                if j == k:
+                    continue
+                pj = _square_points(oj, euj, evj)
+                # points both squares share (hinges, corners) and their neighbourhood
+                shared = [p for p in pn if np.min(np.linalg.norm(pj - p, axis=1)) < 1e-9]
+                A, Bp = pn, pj
+                if shared:
+                    S = np.array(shared)
+                    A = pn[np.min(np.linalg.norm(pn[:, None, :] - S[None], axis=2), axis=1) > 3 * h]
+                    Bp = pj[np.min(np.linalg.norm(pj[:, None, :] - S[None], axis=2), axis=1) > 3 * h]
+                if A.size and Bp.size and _min_dist(A, Bp) < h:
+                    ok = False
+                    break
+        if not ok:
+            continue
+        sq.append(new)
+        hinge_dirs[hkey] = dirs + [d]
+    mb = _MeshBuilder()
+    cb = _MeshBuilder()
+    tags = []
+    for k, (o, eu, ev) in enumerate(sq):
+        def tag(i, j, t, k=k):
+            return (k * n_coarse + (j * n_coarse) // n) * n_coarse + (i * n_coarse) // n
+        _grid_panel(mb, o, eu, ev, n, n, tags, tag)
+        _grid_panel(cb, o, eu, ev, n_coarse, n_coarse)
+    xyz, tri = mb.arrays()
+    cxyz, ctri = cb.arrays()
+    parent = _locate_parents(xyz, tri, cxyz, ctri)
+    if g is None:
+        g = rng.uniform(-1.0, 1.0, 3)
+    return Geometry(f"panels{len(sq)}_s{seed}_h1/{n}", xyz, tri, cxyz, ctri, parent,
+                    np.array(tags, dtype=np.int32), np.asarray(g, float), h, 1.0 / n_coarse,
+                    {"family": "panels", "seed": seed, "n": n, "n_coarse": n_coarse, "panels": len(sq),
+                     "hinges": sorted(len(v) for v in hinge_dirs.values())})
+
+
+def panels_config(instances: int = 16) -> list:
+    """Sixteen seeded panel multiscreens (instance seeds 0..15)."""
+    return [panels(seed) for seed in range(instances)]
+
+
 def flat_config() -> Geometry:
     """Plain FP64 flat-screen workload: unit square h = 1/16 (225 interior
     dofs), 2 x 2 substructuring (H = 1/2) plus the coarse space, g = (0,0,1)."""

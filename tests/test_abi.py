@@ -30,6 +30,7 @@ def test_exports_every_declared_symbol(L):
 
 
 @pytest.mark.parametrize("geom", [WL.flat_config(), WL.book(8, 2), WL.disk(5, fin=True), WL.bowtie(6, 2),
+                                  WL.panels(7, n=6), WL.panels(5, n=6),
                                   WL.book_config()], ids=lambda g: g.name)
 def test_dof_map_matches_oracle(L, geom):
     n, v, s = M.msbem_mesh_dofs(geom.xyz, geom.tri)

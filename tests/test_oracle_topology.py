@@ -88,8 +88,11 @@ def _same_partition(lab_a, lab_b):
 
 
 @pytest.mark.parametrize("geom", [WL.book(4, 2, jitter=False), WL.disk(3, fin=True), WL.bowtie(4, 2),
-                                  WL.unit_square(4, 2)], ids=lambda g: g.name)
+                                  WL.unit_square(4, 2), WL.panels(7, n=2, angle_range=(60.0, 180.0)),
+                                  WL.panels(5, n=2, angle_range=(60.0, 180.0))], ids=lambda g: g.name)
 def test_sectors_match_sphere_flood_fill(geom):
+    # (the probe directions of the geometric count need wedges of some width:
+    # the panel screens here keep >= 60 degrees between squares on a hinge)
     top = Topology(geom.xyz, geom.tri)
     for v in range(top.nv):
         geo = sphere_sectors(top, v)
@@ -159,3 +162,17 @@ def test_rejects_point_contact_and_duplicates():
         Topology(xyz, np.array([[0, 1, 2], [1, 2, 0]]))
     with pytest.raises(MeshError):
         Topology(np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0]], float), np.array([[0, 1, 2]]))
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_panels_dof_count(seed):
+    """Squares hinged at arbitrary dihedral angles: every interior vertex of a
+    square has 2 sectors (1 dof), a vertex inside a hinge shared by m squares
+    has m sectors (m - 1 dofs), square corners have 1; so
+    N = sum over squares (n-1)^2 + sum over hinges (m-1)(n-1)."""
+    n = 4
+    g = WL.panels(seed, n=n)
+    top = Topology(g.xyz, g.tri)
+    expected = g.meta["panels"] * (n - 1) ** 2 + sum((m - 1) * (n - 1) for m in g.meta["hinges"])
+    assert top.ndof == expected
+    assert int(np.max(top.q)) == max(g.meta["hinges"])
