@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the solve-mode comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving simulation")
+    ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--workload", default="book64", choices=["book64", "book32", "flat"],
                     help="book64 is the measured workload; book32 (h=1/32) and flat are for profiling")
     return ap.parse_args()
@@ -306,6 +308,10 @@ def run_ours(args, world, rank, local, pg):
         modes = solve_modes(S, geom, stream)
     roof_mv = matvec_rooflines(S, N, stream) if rank == 0 and not args.no_modes else None
 
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = serve_bench(args.serve_requests, local, stream)
+
     # end to end through the C ABI with host buffers: upload (host topology +
     # H2D from pinned memory) + assemble + factor + solve + D2H of the density
     e2e = None
@@ -374,6 +380,7 @@ def run_ours(args, world, rank, local, pg):
                          "ops_per_launch": ops, "launch_ms": far_avg_s * 1e3},
             "roofline_matvec": roof_mv,
             "solve_modes": modes,
+            "serving": serving,
             "clocks": ck,
             "gpu_launches": int(launches),
             "e2e": e2e,
@@ -466,6 +473,122 @@ def matvec_rooflines(S, N, stream, reps=5):
                          "launch_ms": ms, "algorithmic": f"{8 if prec == 'df' else 4} B x N^2 (W read once)",
                          "peak_source": src}
     return out
+
+
+def serving_workload(R: int, seed: int = 0, new_fraction: float = 0.3):
+    """Seeded request stream: each request names a geometry and constant
+    Neumann data g in [-1,1]^3; with probability new_fraction (always for the
+    first) the geometry is a new one -- the next of a seeded sequence drawn
+    from the square (h = 1/24 .. 1/96), three-page book (h = 1/32, 1/48) and
+    panel families (500 - 13.5k dofs) -- else one used before."""
+    from paper_2310_09204_gb300 import workloads as WL
+    rng = np.random.default_rng(seed)
+    geoms, reqs = {}, []
+
+    def new_geom(k):
+        f = k % 4
+        if f == 0:
+            n = int(rng.choice([24, 32, 40, 48, 56, 64, 80, 96]))
+            return WL.unit_square(n, 2, "square")
+        if f == 1:
+            n = int(rng.choice([32, 48]))
+            return WL.book(n, 4, jitter=True, seed=int(rng.integers(1 << 30)))
+        return WL.panels(1000 + k)
+
+    for i in range(R):
+        if i == 0 or rng.random() < new_fraction:
+            key = len(geoms) + 1
+            geoms[key] = new_geom(key)
+        else:
+            key = int(rng.integers(1, len(geoms) + 1))
+        reqs.append((key, rng.uniform(-1.0, 1.0, 3)))
+    return geoms, reqs
+
+
+def serve_bench(R: int, device: int, stream, load: float = 1.5):
+    """Serving: the plain FP64 comparator (one request at a time in arrival
+    order, geometries cached once assembled) against the serving engine in
+    mixed precision (continuous batching), on the same seeded requests.
+
+    The comparator runs its requests back to back: that gives its capacity
+    and every request's service time; requests then arrive as a Poisson
+    stream at `load` x that capacity, and the comparator's latencies follow
+    from the FIFO recurrence done_i = max(arrival_i, done_{i-1}) + service_i
+    (exact for a one-at-a-time server).  The engine serves the same arrivals
+    in real time; a second, saturated run (every request queued at once)
+    measures its capacity.  Every engine density is checked against the
+    comparator's."""
+    import torch
+    import paper_2310_09204_gb300 as M
+    geoms, reqs = serving_workload(R)
+    # -- plain comparator, back to back
+    cache, ref, service = {}, [], []
+    for key, g in reqs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if key not in cache:
+            gm = geoms[key]
+            S = M.Solver(gm, device=device)
+            S.assemble().factor()
+            cache[key] = S
+        out = cache[key].solve(g, rtol=1e-8, precision="fp64")
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+        ref.append(out["density"].copy())
+    for S in cache.values():
+        S.close()
+    del cache
+    cap_plain = R / sum(service)
+    rate = load * cap_plain
+    rng = np.random.default_rng(1)
+    arr = np.cumsum(rng.exponential(1.0 / rate, R))
+    done, lat_plain = 0.0, []
+    for a, sv in zip(arr, service):
+        done = max(a, done) + sv
+        lat_plain.append(done - a)
+    makespan_plain = done - arr[0]
+
+    def run_engine(arrivals):
+        with M.Server(device=device, precision="mixed") as E:
+            for key, gm in geoms.items():
+                E.add_geometry(key, gm)
+            outs = [np.empty(E.ndof[k]) for k, _ in reqs]
+            ids = [0] * R
+            t0 = E.now() + 0.01
+            i, completed = 0, 0
+            while completed < R:
+                now = E.now()
+                while i < R and t0 + arrivals[i] <= now:
+                    ids[i] = E.submit(reqs[i][0], reqs[i][1], outs[i], t_arrival=t0 + arrivals[i])
+                    i += 1
+                completed += E.progress(block=False)
+                if completed == i and i < R:
+                    time.sleep(max(0.0, t0 + arrivals[i] - E.now()))
+            t_end = E.now()
+            res = [E.result(x) for x in ids]
+            st = E.stats()
+        lat = sorted(r["latency_ms"] for r in res)
+        diff = max(float(np.linalg.norm(o - r) / max(np.linalg.norm(r), 1e-300)) for o, r in zip(outs, ref))
+        return {"solves_per_s": R / (t_end - t0 - arrivals[0]), "p50_ms": lat[R // 2],
+                "p99_ms": lat[min(R - 1, int(0.99 * R))], "max_relres": max(r["relres"] for r in res),
+                "all_ok": all(r["status"] == 0 for r in res), "maxdiff_vs_plain_fp64": diff,
+                "admissions": st["admissions"], "evictions": st["evictions"]}
+
+    eng = run_engine(arr)
+    sat = run_engine(np.zeros(R))
+    lp = sorted(lat_plain)
+    return {
+        "requests": R, "distinct_geometries": len(geoms), "new_geometry_fraction": len(geoms) / R,
+        "families": "squares h=1/24..1/96, three-page books h=1/32,1/48, panel screens (500-13.5k dofs)",
+        "arrivals": f"Poisson, rate {rate:.1f}/s = {load} x plain capacity (seed 1)",
+        "plain_fp64": {"capacity_solves_per_s": cap_plain, "solves_per_s": R / makespan_plain,
+                       "p50_ms": 1e3 * lp[R // 2], "p99_ms": 1e3 * lp[min(R - 1, int(0.99 * R))],
+                       "mode": "one request at a time, FIFO, geometry cache; latencies by the FIFO recurrence"},
+        "engine_mixed": eng,
+        "engine_mixed_saturated": {"capacity_solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"],
+                                   "p99_ms": sat["p99_ms"], "all_ok": sat["all_ok"]},
+        "capacity_vs_plain": sat["solves_per_s"] / cap_plain,
+    }
 
 
 def main():

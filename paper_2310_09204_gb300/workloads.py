@@ -62,21 +62,30 @@ class _MeshBuilder:
 
     def __init__(self, decimals: int = 10):
         self.decimals = decimals
+        self.scale = 10.0 ** decimals
         self.key_to_id: dict = {}
         self.pts: list = []
         self.tris: list = []
 
     def vid(self, p) -> int:
-        key = tuple(np.round(np.asarray(p, dtype=np.float64), self.decimals) + 0.0)
+        # key: the coordinates rounded to `decimals` places, as integers
+        # (rint(x * 10^decimals), ties to even)
+        x, y, z = float(p[0]), float(p[1]), float(p[2])
+        s = self.scale
+        key = (round(x * s), round(y * s), round(z * s))
         i = self.key_to_id.get(key)
         if i is None:
             i = len(self.pts)
             self.key_to_id[key] = i
-            self.pts.append(np.asarray(p, dtype=np.float64))
+            self.pts.append((x, y, z))
         return i
 
     def add(self, a, b, c) -> int:
         self.tris.append((self.vid(a), self.vid(b), self.vid(c)))
+        return len(self.tris) - 1
+
+    def add_ids(self, a: int, b: int, c: int) -> int:
+        self.tris.append((a, b, c))
         return len(self.tris) - 1
 
     def arrays(self):
@@ -91,14 +100,24 @@ def _grid_panel(mb: _MeshBuilder, origin, eu, ev, nu: int, nv: int, tags=None, t
     eu = np.asarray(eu, float)
     ev = np.asarray(ev, float)
 
-    def P(i, j):
-        return origin + (i / nu) * eu + (j / nv) * ev
+    I, J = np.meshgrid(np.arange(nu + 1) / nu, np.arange(nv + 1) / nv, indexing="ij")
+    pts = (origin[None, None, :] + I[:, :, None] * eu[None, None, :] + J[:, :, None] * ev[None, None, :]).tolist()
+    ids: dict = {}
+
+    def V(i, j):   # vertex id of grid point (i, j), in order of first use
+        k = ids.get((i, j))
+        if k is None:
+            k = ids[(i, j)] = mb.vid(pts[i][j])
+        return k
 
     for j in range(nv):
         for i in range(nu):
-            p00, p10, p11, p01 = P(i, j), P(i + 1, j), P(i + 1, j + 1), P(i, j + 1)
-            t0 = mb.add(p00, p10, p11)
-            t1 = mb.add(p00, p11, p01)
+            v00 = V(i, j)
+            v10 = V(i + 1, j)
+            v11 = V(i + 1, j + 1)
+            mb.add_ids(v00, v10, v11)
+            v01 = V(i, j + 1)
+            mb.add_ids(v00, v11, v01)
             if tags is not None:
                 tags.append(tag_fn(i, j, 0))
                 tags.append(tag_fn(i, j, 1))
