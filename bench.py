@@ -64,8 +64,11 @@ def parse():
     ap.add_argument("--no-modes", action="store_true", help="skip the solve-mode comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving simulation")
     ap.add_argument("--serve-requests", type=int, default=300)
-    ap.add_argument("--workload", default="book64", choices=["book64", "book32", "flat"],
-                    help="book64 is the measured workload; book32 (h=1/32) and flat are for profiling")
+    ap.add_argument("--workload", default="book64", choices=["book64", "book48", "book32", "flat"],
+                    help="book64 is the measured workload; book48, book32 and flat are for profiling")
+    ap.add_argument("--matvec", type=int, default=0,
+                    help="microbenchmark only: time the product kernel on K vectors (msbem_apply)")
+    ap.add_argument("--matvec-precision", default="df", choices=["df", "fp32", "fp64"])
     return ap.parse_args()
 
 
@@ -75,6 +78,8 @@ def make_workload(name):
         return WL.book_config()
     if name == "book32":
         return WL.book(32, 4, jitter=True, seed=0)
+    if name == "book48":
+        return WL.book(48, 4, jitter=True, seed=0)
     return WL.flat_config()
 
 
@@ -591,8 +596,41 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5):
     }
 
 
+def run_matvec(args):
+    """Product-kernel microbenchmark: assemble the workload, then apply W to
+    K seeded vectors `steps` times (after `warmup` untimed applications); one
+    JSON line with the kernel's median device time and its roofline fraction."""
+    import paper_2310_09204_gb300 as M
+    from paper_2310_09204_gb300 import build as B
+    B.build()
+    geom = make_workload(args.workload)
+    k = args.matvec
+    with M.Solver(geom) as S:
+        S.assemble()
+        X = np.random.default_rng(0).standard_normal((k, S.n))
+        for _ in range(args.warmup):
+            S.apply(X, precision=args.matvec_precision)
+        ms = sorted(S.apply(X, precision=args.matvec_precision)[1] for _ in range(max(args.steps, 1)))
+        t = ms[len(ms) // 2]
+        N = float(S.n)
+    hbm, src = measured_peaks()
+    if args.matvec_precision == "df" and k > 1:
+        ops = FP32_OPS_PER_DF_FMA * k * N * N
+        roof = {"bound": "alu", "achieved": ops / (t * 1e-3) / 1e12, "peak": SM_COUNT * FP32_LANES * SM_MAX_MHZ / 1e6,
+                "unit": "TFLOP/s"}
+    else:
+        b = (8 if args.matvec_precision in ("df", "fp64") else 4) * N * N
+        roof = {"bound": "hbm", "achieved": b / (t * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s", "peak_source": src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    print(json.dumps({"matvec": {"workload": args.workload, "N": int(N), "k": k,
+                                 "precision": args.matvec_precision, "kernel_ms": t, "roofline": roof}}), flush=True)
+
+
 def main():
     args = parse()
+    if args.matvec:
+        run_matvec(args)
+        return
     world, rank, local, pg = dist_setup(args)
     try:
         if args.impl == "reference":
