@@ -526,32 +526,40 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5):
     import torch
     import paper_2310_09204_gb300 as M
     geoms, reqs = serving_workload(R)
-    # -- plain comparator, back to back
-    cache, ref, service = {}, [], []
-    for key, g in reqs:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        if key not in cache:
-            gm = geoms[key]
-            S = M.Solver(gm, device=device)
-            S.assemble().factor()
-            cache[key] = S
-        out = cache[key].solve(g, rtol=1e-8, precision="fp64")
-        torch.cuda.synchronize()
-        service.append(time.perf_counter() - t0)
-        ref.append(out["density"].copy())
-    for S in cache.values():
-        S.close()
-    del cache
+
+    def plain(far_kernel):
+        """The comparator, back to back: (service times, densities)."""
+        cache, ref, service = {}, [], []
+        for key, g in reqs:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if key not in cache:
+                S = M.Solver(geoms[key], device=device)
+                S.assemble(far_kernel=far_kernel).factor()
+                cache[key] = S
+            out = cache[key].solve(g, rtol=1e-8, precision="fp64")
+            torch.cuda.synchronize()
+            service.append(time.perf_counter() - t0)
+            ref.append(out["density"].copy())
+        for S in cache.values():
+            S.close()
+        return service, ref
+
+    def fifo(service, arr):
+        done, lat = 0.0, []
+        for a, sv in zip(arr, service):
+            done = max(a, done) + sv
+            lat.append(done - a)
+        lat.sort()
+        return {"capacity_solves_per_s": R / sum(service), "solves_per_s": R / (done - arr[0]),
+                "p50_ms": 1e3 * lat[R // 2], "p99_ms": 1e3 * lat[min(R - 1, int(0.99 * R))]}
+
+    service, ref = plain(1)            # FP64 pair integrals, FP64 W copy, FP64 PCG
+    service_df, _ = plain(0)           # the same with the double-float assembly
     cap_plain = R / sum(service)
     rate = load * cap_plain
     rng = np.random.default_rng(1)
     arr = np.cumsum(rng.exponential(1.0 / rate, R))
-    done, lat_plain = 0.0, []
-    for a, sv in zip(arr, service):
-        done = max(a, done) + sv
-        lat_plain.append(done - a)
-    makespan_plain = done - arr[0]
 
     def run_engine(arrivals):
         with M.Server(device=device, precision="mixed") as E:
@@ -581,49 +589,23 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5):
 
     eng = run_engine(arr)
     sat = run_engine(np.zeros(R))
-    lp = sorted(lat_plain)
+    pl = fifo(service, arr)
+    pl["mode"] = ("FP64 pair integrals (far_kernel 1), FP64 copy of W, FP64 PCG; one request at a time, FIFO, "
+                  "geometry cache; latencies by the FIFO recurrence")
+    pld = fifo(service_df, arr)
+    pld["mode"] = "as plain_fp64 but with the double-float assembly of W"
     return {
         "requests": R, "distinct_geometries": len(geoms), "new_geometry_fraction": len(geoms) / R,
         "families": "squares h=1/24..1/96, three-page books h=1/32,1/48, panel screens (500-13.5k dofs)",
-        "arrivals": f"Poisson, rate {rate:.1f}/s = {load} x plain capacity (seed 1)",
-        "plain_fp64": {"capacity_solves_per_s": cap_plain, "solves_per_s": R / makespan_plain,
-                       "p50_ms": 1e3 * lp[R // 2], "p99_ms": 1e3 * lp[min(R - 1, int(0.99 * R))],
-                       "mode": "one request at a time, FIFO, geometry cache; latencies by the FIFO recurrence"},
+        "arrivals": f"Poisson, rate {rate:.1f}/s = {load} x plain FP64 capacity (seed 1)",
+        "plain_fp64": pl,
+        "plain_fp64_df_assembly": pld,
         "engine_mixed": eng,
         "engine_mixed_saturated": {"capacity_solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"],
                                    "p99_ms": sat["p99_ms"], "all_ok": sat["all_ok"]},
-        "capacity_vs_plain": sat["solves_per_s"] / cap_plain,
+        "capacity_vs_plain_fp64": sat["solves_per_s"] / cap_plain,
+        "capacity_vs_plain_df_assembly": sat["solves_per_s"] * sum(service_df) / R,
     }
-
-
-def run_matvec(args):
-    """Product-kernel microbenchmark: assemble the workload, then apply W to
-    K seeded vectors `steps` times (after `warmup` untimed applications); one
-    JSON line with the kernel's median device time and its roofline fraction."""
-    import paper_2310_09204_gb300 as M
-    from paper_2310_09204_gb300 import build as B
-    B.build()
-    geom = make_workload(args.workload)
-    k = args.matvec
-    with M.Solver(geom) as S:
-        S.assemble()
-        X = np.random.default_rng(0).standard_normal((k, S.n))
-        for _ in range(args.warmup):
-            S.apply(X, precision=args.matvec_precision)
-        ms = sorted(S.apply(X, precision=args.matvec_precision)[1] for _ in range(max(args.steps, 1)))
-        t = ms[len(ms) // 2]
-        N = float(S.n)
-    hbm, src = measured_peaks()
-    if args.matvec_precision == "df" and k > 1:
-        ops = FP32_OPS_PER_DF_FMA * k * N * N
-        roof = {"bound": "alu", "achieved": ops / (t * 1e-3) / 1e12, "peak": SM_COUNT * FP32_LANES * SM_MAX_MHZ / 1e6,
-                "unit": "TFLOP/s"}
-    else:
-        b = (8 if args.matvec_precision in ("df", "fp64") else 4) * N * N
-        roof = {"bound": "hbm", "achieved": b / (t * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s", "peak_source": src}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    print(json.dumps({"matvec": {"workload": args.workload, "N": int(N), "k": k,
-                                 "precision": args.matvec_precision, "kernel_ms": t, "roofline": roof}}), flush=True)
 
 
 def main():

@@ -267,6 +267,8 @@ typedef struct msbem_server_opts {
   double inner_rtol;        /* precision 2: inner tolerance (0: 1e-4)                  */
   int maxit;                /* iterations per request (inner, summed; 0: 1000)         */
   int chunk;                /* PCG iterations between scheduling points (0: 4)         */
+  int admission_threads;    /* host threads admitting new geometries, each with its   */
+                            /* own context and stream (0: 2; at most 8)                */
 } msbem_server_opts;
 
 typedef struct msbem_server_stats {

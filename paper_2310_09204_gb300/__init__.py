@@ -45,7 +45,8 @@ class SolveOpts(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("precision", ctypes.c_int), ("rtol", ctypes.c_double),
-                ("inner_rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("chunk", ctypes.c_int)]
+                ("inner_rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("admission_threads", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -337,9 +338,10 @@ class Server:
     continuously refilled 16-slot multi-vector PCG per geometry."""
 
     def __init__(self, device: int = 0, stream=None, precision="mixed", rtol: float = 1e-8,
-                 inner_rtol: float = 0.0, hbm_budget: float = 0.0, maxit: int = 1000, chunk: int = 4):
+                 inner_rtol: float = 0.0, hbm_budget: float = 0.0, maxit: int = 1000, chunk: int = 4,
+                 admission_threads: int = 0):
         self.ctx = msbem_create(device, stream)
-        o = ServerOpts(float(hbm_budget), PRECISION[precision], rtol, inner_rtol, maxit, chunk)
+        o = ServerOpts(float(hbm_budget), PRECISION[precision], rtol, inner_rtol, maxit, chunk, admission_threads)
         h = ctypes.c_void_p()
         st = lib().msbem_server_create(self.ctx, ctypes.byref(o), ctypes.byref(h))
         if st:

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -393,8 +394,19 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   double bary[6][3], w6[6], glx[16], glw[16];
   six_point_rule(bary, w6);
   gauss_legendre01(n, glx, glw);
-  cudaError_t e = set_far_constants(bary, w6);
-  if (e == cudaSuccess) e = set_far_df_constants(w6);
+  // the 6-point rule is fixed: its weights go to the device's constant memory
+  // once (assemblies of other contexts may be running on other threads)
+  cudaError_t e = cudaSuccess;
+  {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), c->device) == done.end()) {
+      e = set_far_constants(bary, w6);
+      if (e == cudaSuccess) e = set_far_df_constants(w6);
+      if (e == cudaSuccess) done.push_back(c->device);
+    }
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "far constants");
   // V (nt^2 float pairs) is scratch of the assembly only: taken from the pool
   // here and returned once W is formed, so a resident geometry holds W alone

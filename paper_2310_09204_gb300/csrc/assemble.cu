@@ -129,7 +129,13 @@ cudaError_t launch_far_fp64(const DevGeom& g, cudaStream_t s) {
 // Near field
 // ---------------------------------------------------------------------------
 #define NEAR_MAXN 16
-__constant__ double c_gl_x[NEAR_MAXN], c_gl_w[NEAR_MAXN];
+// Gauss-Legendre nodes and weights on [0,1] of the singular rules, FP64 and
+// as float pairs; passed by value to the near-field kernels (so contexts that
+// assemble concurrently with different orders do not share a table)
+struct GLTable {
+  double x[NEAR_MAXN], w[NEAR_MAXN];
+  float2 xf[NEAR_MAXN], wf[NEAR_MAXN];
+};
 
 __device__ __forceinline__ double inv_norm3(double a, double b, double c) {
   return rsqrt(fma(c, c, fma(b, b, a * a)));
@@ -142,7 +148,8 @@ __device__ __forceinline__ double tri_area_d(const double* P) {
   return 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
 }
 
-__global__ void __launch_bounds__(256) near_kernel(const NearPair* __restrict__ pairs, int64_t npairs,
+__global__ void __launch_bounds__(256) near_kernel(const __grid_constant__ GLTable gl,
+                                                   const NearPair* __restrict__ pairs, int64_t npairs,
                                                    const double* __restrict__ xyz, int n, int64_t ldv,
                                                    float2* __restrict__ V) {
   const int lane = threadIdx.x & 31;
@@ -165,12 +172,12 @@ __global__ void __launch_bounds__(256) near_kernel(const NearPair* __restrict__ 
     const double e2[3] = {P[6] - P[3], P[7] - P[4], P[8] - P[5]};
     for (int idx = lane; idx < 3 * n; idx += 32) {
       int s = idx / n, j = idx % n;
-      double et = c_gl_x[j];
+      double et = gl.x[j];
       double a0, a1;  // J w = a0 e1 + a1 e2
       if (s == 0) { a0 = 1.0; a1 = et; }
       else if (s == 1) { a0 = 1.0 - et; a1 = 1.0; }
       else { a0 = -et; a1 = 1.0 - et; }
-      sum += c_gl_w[j] * inv_norm3(a0 * e1[0] + a1 * e2[0], a0 * e1[1] + a1 * e2[1],
+      sum += gl.w[j] * inv_norm3(a0 * e1[0] + a1 * e2[0], a0 * e1[1] + a1 * e2[1],
                                    a0 * e1[2] + a1 * e2[2]);
     }
     pref = aT * aT / (3.0 * M_PI);
@@ -182,7 +189,7 @@ __global__ void __launch_bounds__(256) near_kernel(const NearPair* __restrict__ 
     const int nn = n * n;
     for (int idx = lane; idx < 4 * nn; idx += 32) {
       int reg = idx / nn, rem = idx % nn, i1 = rem / n, i2 = rem % n;
-      double sg = c_gl_x[i1], ta = c_gl_x[i2], wq = c_gl_w[i1] * c_gl_w[i2];
+      double sg = gl.x[i1], ta = gl.x[i2], wq = gl.w[i1] * gl.w[i2];
       double fu, fv, fw, J;
       if (reg == 0) { fu = sg; fv = 1.0 - sg; fw = ta; J = 1.0; }
       else if (reg == 1) { fu = sg * (1.0 - ta); fv = sg * ta; fw = 1.0; J = sg; }
@@ -204,8 +211,8 @@ __global__ void __launch_bounds__(256) near_kernel(const NearPair* __restrict__ 
     for (int idx = lane; idx < 2 * nnn; idx += 32) {
       int reg = idx / nnn, rem = idx % nnn;
       int i1 = rem / (n * n), i2 = (rem / n) % n, i3 = rem % n;
-      double a1 = c_gl_x[i1], a2 = c_gl_x[i2], a3 = c_gl_x[i3];
-      double wq = c_gl_w[i1] * c_gl_w[i2] * c_gl_w[i3] * a2;
+      double a1 = gl.x[i1], a2 = gl.x[i2], a3 = gl.x[i3];
+      double wq = gl.w[i1] * gl.w[i2] * gl.w[i3] * a2;
       double s1, s2, t1, t2;
       if (reg == 0) { s1 = 1.0; s2 = a1; t1 = a2; t2 = a2 * a3; }
       else { t1 = 1.0; t2 = a1; s1 = a2; s2 = a2 * a3; }
@@ -230,7 +237,6 @@ __global__ void __launch_bounds__(256) near_kernel(const NearPair* __restrict__ 
 // pair the edge vectors are formed in FP64 and split into float pairs; per
 // evaluation the direction vector g, 1/|g| and the weighted sum use float pairs
 // (Gauss-Legendre nodes and weights as (hi, lo) pairs in constant memory).
-__constant__ float2 c_glx_df[NEAR_MAXN], c_glw_df[NEAR_MAXN];
 
 __device__ __forceinline__ void split3(const double* v, float2* o) {
 #pragma unroll
@@ -247,7 +253,8 @@ __device__ __forceinline__ void axpy3(float ch, float cl, const float2* v, float
   for (int k = 0; k < 3; ++k) df_fma_acc(ch, cl, v[k].x, v[k].y, acc[k].x, acc[k].y);
 }
 
-__global__ void __launch_bounds__(256) near_df_kernel(const NearPair* __restrict__ pairs,
+__global__ void __launch_bounds__(256) near_df_kernel(const __grid_constant__ GLTable gl,
+                                                      const NearPair* __restrict__ pairs,
                                                       int64_t npairs, const double* __restrict__ xyz,
                                                       int n, int64_t ldv, float2* __restrict__ V) {
   const int lane = threadIdx.x & 31;
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(256) near_df_kernel(const NearPair* __restrict
   if (pr.cls == 3) {
     for (int idx = lane; idx < 3 * n; idx += 32) {
       const int sct = idx / n, j = idx % n;
-      const float2 et = c_glx_df[j];
+      const float2 et = gl.xf[j];
       float2 om;  // 1 - eta
       df_add(1.f, 0.f, -et.x, -et.y, om.x, om.y);
       float2 a0, a1;
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(256) near_df_kernel(const NearPair* __restrict
       axpy3(a1.x, a1.y, v1, g);
       float y, corr;
       df_rsqrt3(g[0].x, g[0].y, g[1].x, g[1].y, g[2].x, g[2].y, y, corr);
-      const float2 wq = c_glw_df[j];
+      const float2 wq = gl.wf[j];
       df_fma_acc(wq.x, wq.y, y, corr, acch, accl);
     }
     pref = aT * aT / (3.0 * M_PI);
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(256) near_df_kernel(const NearPair* __restrict
     const int nn = n * n;
     for (int idx = lane; idx < 4 * nn; idx += 32) {
       const int reg = idx / nn, rem = idx % nn, i1 = rem / n, i2 = rem % n;
-      const float2 sg = c_glx_df[i1], ta = c_glx_df[i2];
+      const float2 sg = gl.xf[i1], ta = gl.xf[i2];
       float2 omt, oms, sgta, sgomt;
       df_add(1.f, 0.f, -ta.x, -ta.y, omt.x, omt.y);
       df_add(1.f, 0.f, -sg.x, -sg.y, oms.x, oms.y);
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(256) near_df_kernel(const NearPair* __restrict
       float y, corr;
       df_rsqrt3(g[0].x, g[0].y, g[1].x, g[1].y, g[2].x, g[2].y, y, corr);
       float2 wq, wJ;
-      df_mul(c_glw_df[i1].x, c_glw_df[i1].y, c_glw_df[i2].x, c_glw_df[i2].y, wq.x, wq.y);
+      df_mul(gl.wf[i1].x, gl.wf[i1].y, gl.wf[i2].x, gl.wf[i2].y, wq.x, wq.y);
       df_mul(wq.x, wq.y, J.x, J.y, wJ.x, wJ.y);
       df_fma_acc(wJ.x, wJ.y, y, corr, acch, accl);
     }
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(256) near_df_kernel(const NearPair* __restrict
     for (int idx = lane; idx < 2 * nnn; idx += 32) {
       const int reg = idx / nnn, rem = idx % nnn;
       const int i1 = rem / (n * n), i2 = (rem / n) % n, i3 = rem % n;
-      const float2 a1 = c_glx_df[i1], a2 = c_glx_df[i2], a3 = c_glx_df[i3];
+      const float2 a1 = gl.xf[i1], a2 = gl.xf[i2], a3 = gl.xf[i3];
       float2 a23;
       df_mul(a2.x, a2.y, a3.x, a3.y, a23.x, a23.y);
       float2 s1, s2, t1, t2;
@@ -346,8 +353,8 @@ __global__ void __launch_bounds__(256) near_df_kernel(const NearPair* __restrict
       float y, corr;
       df_rsqrt3(g[0].x, g[0].y, g[1].x, g[1].y, g[2].x, g[2].y, y, corr);
       float2 w12, w123, wq;
-      df_mul(c_glw_df[i1].x, c_glw_df[i1].y, c_glw_df[i2].x, c_glw_df[i2].y, w12.x, w12.y);
-      df_mul(w12.x, w12.y, c_glw_df[i3].x, c_glw_df[i3].y, w123.x, w123.y);
+      df_mul(gl.wf[i1].x, gl.wf[i1].y, gl.wf[i2].x, gl.wf[i2].y, w12.x, w12.y);
+      df_mul(w12.x, w12.y, gl.wf[i3].x, gl.wf[i3].y, w123.x, w123.y);
       df_mul(w123.x, w123.y, a2.x, a2.y, wq.x, wq.y);
       df_fma_acc(wq.x, wq.y, y, corr, acch, accl);
     }
@@ -373,27 +380,20 @@ __global__ void __launch_bounds__(256) near_df_kernel(const NearPair* __restrict
 cudaError_t launch_near(const DevGeom& g, int n, const double* gl_x, const double* gl_w,
                         int fp64, cudaStream_t s) {
   if (n < 2 || n > NEAR_MAXN) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemcpyToSymbolAsync(c_gl_x, gl_x, sizeof(double) * n, 0,
-                                          cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyToSymbolAsync(c_gl_w, gl_w, sizeof(double) * n, 0, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
-  float2 xf[NEAR_MAXN], wf[NEAR_MAXN];
+  GLTable gl{};
   for (int j = 0; j < n; ++j) {
+    gl.x[j] = gl_x[j];
+    gl.w[j] = gl_w[j];
     float xh = (float)gl_x[j], wh = (float)gl_w[j];
-    xf[j] = make_float2(xh, (float)(gl_x[j] - (double)xh));
-    wf[j] = make_float2(wh, (float)(gl_w[j] - (double)wh));
+    gl.xf[j] = make_float2(xh, (float)(gl_x[j] - (double)xh));
+    gl.wf[j] = make_float2(wh, (float)(gl_w[j] - (double)wh));
   }
-  e = cudaMemcpyToSymbolAsync(c_glx_df, xf, sizeof(float2) * n, 0, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyToSymbolAsync(c_glw_df, wf, sizeof(float2) * n, 0, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
   if (g.n_near == 0) return cudaSuccess;
   int64_t blocks = (g.n_near + 7) / 8;
   if (fp64)
-    near_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
+    near_kernel<<<(unsigned)blocks, 256, 0, s>>>(gl, g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
   else
-    near_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
+    near_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(gl, g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
   return cudaGetLastError();
 }
 

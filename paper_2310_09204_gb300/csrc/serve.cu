@@ -18,11 +18,15 @@
 // residual R = L - W X with the double-float product; the slot finishes when
 // ||R|| <= rtol ||L||, else restarts its inner solve on R.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cmath>
 #include <cstring>
 #include <deque>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -168,8 +172,15 @@ struct Batch {
   Slot slot[BK];
 };
 
+// life cycle of a geometry in the engine
+enum GeomState { G_OUT = 0, G_ADMITTING = 1, G_READY = 2, G_FAILED = 3, G_EVICTING = 4 };
+
 struct GeomEntry {
   uint64_t key = 0;
+  std::atomic<int> state{G_OUT};   // written by the admission thread, read by progress()
+  int admit_status = 0;
+  size_t reserved = 0;             // budget bytes held while admitting
+  int owner = -1;                  // admission thread (context) holding the geometry
   std::vector<double> xyz, cxyz;
   std::vector<int32_t> tri, ctri, parent, patch;
   int64_t ndof = -1, nt = 0;
@@ -189,10 +200,24 @@ struct msbem_server {
   int device = 0;
   std::unordered_map<uint64_t, std::unique_ptr<GeomEntry>> geoms;
   std::unordered_map<uint64_t, Request> reqs;
-  std::deque<uint64_t> admit_queue;   // keys with pending requests that are not resident
   uint64_t next_id = 1;
-  size_t resident = 0;
+  size_t resident = 0;             // bytes of resident + admitting geometries
   msbem_server_stats st{};
+  // admission threads: each uploads, assembles and factors new geometries (and
+  // frees the evicted ones it admitted) on its own context and stream, so the
+  // PCG iterations of the resident geometries keep running meanwhile and the
+  // host topology of one geometry overlaps the GPU assembly of another
+  struct Worker {
+    msbem_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    std::thread th;
+    std::deque<std::pair<int, GeomEntry*>> tasks;   // (1 admit | 2 evict, entry)
+    int queued_admissions = 0;
+  };
+  std::vector<std::unique_ptr<Worker>> workers;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
 };
 
 namespace {
@@ -300,36 +325,17 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
   return MSBEM_OK;
 }
 
-void evict(msbem_server* S, GeomEntry& e) {
+// on the admission thread
+void release_geometry(GeomEntry& e) {
   free_batch(e.batch.get());
   e.batch.reset();
   if (e.geom) msbem_geom_free(e.geom);
   e.geom = nullptr;
-  S->resident -= std::min(S->resident, e.footprint);
-  e.footprint = 0;
-  ++S->st.evictions;
 }
 
-// make room for `need` bytes by evicting idle geometries, least recently used first
-bool make_room(msbem_server* S, size_t need, uint64_t keep) {
-  while (S->resident + need > (size_t)S->opts.hbm_budget_bytes) {
-    GeomEntry* victim = nullptr;
-    for (auto& kv : S->geoms) {
-      GeomEntry& e = *kv.second;
-      if (!e.geom || e.key == keep || e.active > 0 || !e.pending.empty()) continue;
-      if (!victim || e.last_used < victim->last_used) victim = &e;
-    }
-    if (!victim) return false;
-    evict(S, *victim);
-  }
-  return true;
-}
-
-int admit(msbem_server* S, GeomEntry& e) {
-  const size_t need = estimate_footprint(e) + transient_bytes(e);
-  if (!make_room(S, need, e.key)) return MSBEM_OOM;
+int admit_now(msbem_server* S, msbem_ctx* actx, GeomEntry& e) {
   msbem_geom* g = nullptr;
-  int st = msbem_upload(S->ctx, e.xyz.data(), (int64_t)e.xyz.size() / 3, e.tri.data(), (int64_t)e.tri.size() / 3,
+  int st = msbem_upload(actx, e.xyz.data(), (int64_t)e.xyz.size() / 3, e.tri.data(), (int64_t)e.tri.size() / 3,
                         e.cxyz.data(), (int64_t)e.cxyz.size() / 3, e.ctri.data(), (int64_t)e.ctri.size() / 3,
                         e.parent.data(), e.patch.data(), &g);
   if (st) return st;
@@ -343,15 +349,77 @@ int admit(msbem_server* S, GeomEntry& e) {
     e.geom = nullptr;
     return st;
   }
-  {
-    DevGeom& d = msbem_geom_dev(g);
-    const size_t NH = (size_t)std::max<int64_t>(d.n_coarse, 1);
-    e.footprint = sizeof(float) * 2 * (size_t)d.ndof * d.ldw + (sizeof(double) + sizeof(float2)) * d.binv_size +
-                  sizeof(double) * (NH * d.ndof + 8 * (size_t)d.ndof) + e.batch->bytes;
-  }
-  S->resident += e.footprint;
-  ++S->st.admissions;
+  DevGeom& d = msbem_geom_dev(g);
+  const size_t NH = (size_t)std::max<int64_t>(d.n_coarse, 1);
+  e.footprint = sizeof(float) * 2 * (size_t)d.ndof * d.ldw + (sizeof(double) + sizeof(float2)) * d.binv_size +
+                sizeof(double) * (NH * d.ndof + 8 * (size_t)d.ndof) + e.batch->bytes;
   return MSBEM_OK;
+}
+
+void admission_thread(msbem_server* S, int w) {
+  cudaSetDevice(S->device);
+  msbem_server::Worker& W = *S->workers[w];
+  for (;;) {
+    std::pair<int, GeomEntry*> t;
+    {
+      std::unique_lock<std::mutex> lock(S->mu);
+      S->cv.wait(lock, [S, &W] { return S->stop || !W.tasks.empty(); });
+      if (W.tasks.empty()) return;          // stop requested and nothing left
+      t = W.tasks.front();
+      W.tasks.pop_front();
+    }
+    GeomEntry& e = *t.second;
+    if (t.first == 2) {
+      release_geometry(e);
+      e.state.store(G_OUT);
+    } else {
+      const int st = admit_now(S, W.ctx, e);
+      e.admit_status = st;
+      {
+        std::lock_guard<std::mutex> lock(S->mu);
+        --W.queued_admissions;
+      }
+      e.state.store(st == MSBEM_OK ? G_READY : G_FAILED);
+    }
+  }
+}
+
+// admissions go to the thread with the fewest queued, evictions to the thread
+// that owns the geometry
+void post(msbem_server* S, int kind, GeomEntry* e) {
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    int w = e->owner;
+    if (kind == 1) {
+      w = 0;
+      for (int i = 1; i < (int)S->workers.size(); ++i)
+        if (S->workers[i]->queued_admissions < S->workers[w]->queued_admissions) w = i;
+      e->owner = w;
+      ++S->workers[w]->queued_admissions;
+    }
+    S->workers[w]->tasks.emplace_back(kind, e);
+  }
+  S->cv.notify_all();
+}
+
+// make room for `need` bytes by evicting idle resident geometries, least
+// recently used first (the frees run on the admission thread, queued before
+// the admission that needs the room)
+bool make_room(msbem_server* S, size_t need) {
+  while (S->resident + need > (size_t)S->opts.hbm_budget_bytes) {
+    GeomEntry* victim = nullptr;
+    for (auto& kv : S->geoms) {
+      GeomEntry& e = *kv.second;
+      if (e.state.load() != G_READY || e.active > 0 || !e.pending.empty()) continue;
+      if (!victim || e.last_used < victim->last_used) victim = &e;
+    }
+    if (!victim) return false;
+    victim->state.store(G_EVICTING);
+    S->resident -= std::min(S->resident, victim->footprint);
+    ++S->st.evictions;
+    post(S, 2, victim);
+  }
+  return true;
 }
 
 void finish(msbem_server* S, GeomEntry& e, int c, int status, int iters, double relres, const double* src_cols) {
@@ -530,14 +598,44 @@ int msbem_server_create(msbem_ctx* ctx, const msbem_server_opts* opts, msbem_ser
     o.hbm_budget_bytes = 0.8 * (double)fr;
   }
   S->opts = o;
-  *out = S.release();
+  S->device = msbem_ctx_device(ctx);
+  cudaSetDevice(S->device);
+  const int nw = o.admission_threads > 0 ? std::min(o.admission_threads, 8) : 2;
+  for (int i = 0; i < nw; ++i) {
+    auto W = std::make_unique<msbem_server::Worker>();
+    if (cudaStreamCreateWithFlags(&W->stream, cudaStreamNonBlocking) != cudaSuccess) return MSBEM_CUDA_ERROR;
+    const int st = msbem_create(&W->ctx, S->device, W->stream);
+    if (st) {
+      cudaStreamDestroy(W->stream);
+      for (auto& w : S->workers) {
+        msbem_destroy(w->ctx);
+        cudaStreamDestroy(w->stream);
+      }
+      return st;
+    }
+    S->workers.push_back(std::move(W));
+  }
+  msbem_server* raw = S.release();
+  for (int i = 0; i < nw; ++i) raw->workers[i]->th = std::thread(admission_thread, raw, i);
+  *out = raw;
   return MSBEM_OK;
 }
 
 int msbem_server_destroy(msbem_server* S) {
   if (!S) return MSBEM_INVALID_ARG;
-  for (auto& kv : S->geoms)
-    if (kv.second->geom) evict(S, *kv.second);
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  for (auto& w : S->workers)
+    if (w->th.joinable()) w->th.join();
+  cudaSetDevice(S->device);
+  for (auto& kv : S->geoms) release_geometry(*kv.second);
+  for (auto& w : S->workers) {
+    msbem_destroy(w->ctx);
+    cudaStreamDestroy(w->stream);
+  }
   delete S;
   return MSBEM_OK;
 }
@@ -603,32 +701,60 @@ int msbem_server_progress(msbem_server* S, int block, int* completed) {
     // admissions: geometries with queued requests that are not resident
     for (auto& kv : S->geoms) {
       GeomEntry& e = *kv.second;
-      if (e.geom || e.pending.empty()) continue;
-      const int st = admit(S, e);
-      // resident geometries with work will go idle and become evictable
-      bool others_busy = false;
-      for (auto& kv2 : S->geoms) {
-        const GeomEntry& o = *kv2.second;
-        others_busy = others_busy || (o.geom && (o.active > 0 || !o.pending.empty()));
-      }
-      if (st == MSBEM_OOM && others_busy) {
-        busy = true;           // wait until running geometries go idle
+      const int gs = e.state.load();
+      if (gs == G_ADMITTING || gs == G_EVICTING) {
+        busy = true;
         continue;
       }
-      if (st) {                // the geometry cannot be served: fail its requests
+      if (gs == G_FAILED) {                  // the geometry cannot be served
         for (uint64_t id : e.pending) {
           Request& r = S->reqs[id];
-          r.status = st;
+          r.status = e.admit_status;
           r.t_done = now_s();
           ++S->st.completed;
         }
         e.pending.clear();
-        status = st;
+        S->resident -= std::min(S->resident, e.reserved);
+        e.reserved = 0;
+        status = e.admit_status;
+        e.state.store(G_OUT);
+        continue;
       }
+      if (gs != G_OUT || e.pending.empty()) continue;
+      const size_t need = estimate_footprint(e) + transient_bytes(e);
+      if (!make_room(S, need)) {
+        // wait while other geometries have work and will go idle; a geometry
+        // that can never fit fails its requests
+        bool others = false;
+        for (auto& kv2 : S->geoms) {
+          const GeomEntry& o = *kv2.second;
+          const int os = o.state.load();
+          others = others || os == G_ADMITTING || os == G_EVICTING ||
+                   (os == G_READY && (o.active > 0 || !o.pending.empty()));
+        }
+        if (others) {
+          busy = true;
+          continue;
+        }
+        e.admit_status = MSBEM_OOM;
+        e.state.store(G_FAILED);
+        busy = true;
+        continue;
+      }
+      S->resident += need;
+      e.reserved = need;
+      e.state.store(G_ADMITTING);
+      ++S->st.admissions;
+      post(S, 1, &e);
+      busy = true;
     }
     for (auto& kv : S->geoms) {
       GeomEntry& e = *kv.second;
-      if (!e.geom) continue;
+      if (e.state.load() != G_READY) continue;
+      if (e.reserved) {                     // admission finished: book the actual bytes
+        S->resident = S->resident - std::min(S->resident, e.reserved) + e.footprint;
+        e.reserved = 0;
+      }
       Batch& B = *e.batch;
       if (B.in_flight) {
         const cudaError_t q = cudaEventQuery(B.ev);
@@ -649,7 +775,7 @@ int msbem_server_progress(msbem_server* S, int block, int* completed) {
   if (completed) *completed = (int)(S->st.completed - before);
   S->st.resident_bytes = (double)S->resident;
   int nres = 0;
-  for (auto& kv : S->geoms) nres += kv.second->geom != nullptr;
+  for (auto& kv : S->geoms) nres += kv.second->state.load() == G_READY;
   S->st.resident_geometries = nres;
   return status;
 }

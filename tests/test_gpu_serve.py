@@ -113,3 +113,33 @@ def test_errors():
         S.progress(block=True)
         r = S.result(rid)
         assert r["status"] == 0 and r["iters"] == 0
+
+
+def test_concurrent_contexts_assemble_independently():
+    """Two contexts assembling at the same time on two host threads, with
+    different singular orders: each W is bit for bit its sequential one
+    (the quadrature tables travel with each launch)."""
+    import threading
+    jobs = [(GEOMS[2], 3), (GEOMS[3], 8), (GEOMS[1], 5)]
+    seq = []
+    for geom, order in jobs:
+        with M.Solver(geom) as S:
+            S.assemble(ss_order=order)
+            seq.append(S.matrix())
+    for _ in range(3):
+        out = [None] * len(jobs)
+
+        def work(i):
+            geom, order = jobs[i]
+            with M.Solver(geom) as S:
+                for _ in range(3):
+                    S.assemble(ss_order=order)
+                out[i] = S.matrix()
+
+        th = [threading.Thread(target=work, args=(i,)) for i in range(len(jobs))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for a, b in zip(out, seq):
+            assert np.array_equal(a, b)
