@@ -199,6 +199,22 @@ int msbem_solve(msbem_geom* g, const double gvec[3], const msbem_solve_opts* opt
 int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_solve_opts* opts,
                       double* densities, int* iters, double* relres, double* kappa_est);
 
+/* Closed cells.  When the screen encloses bounded regions of R^3 (the cube
+ * with its mid-planes encloses eight), the indicators of those cells have
+ * vanishing surface curls and span the kernel of the hypersingular form; the
+ * paper's connectedness assumption fails.  Reading used: msbem_assemble then
+ * stores W + rho Z Z^T, rho = mean diag(W), Z = the psi-coordinates of the
+ * cells' indicators (value [sector j in K] minus its mean over the q_i sectors
+ * of the vertex); for constant g, Z^T L = 0 and the solution is the one with
+ * Z^T Phi = 0.  Cells are the components of R^3 minus the screen found from the
+ * sectors whose flux sum |T| (x_T . n) / 3 is negative (bounded, divergence
+ * theorem).  Outputs: *ncells; Z[N * ncells] row-major (host, may be NULL);
+ * *rho (valid after msbem_assemble). */
+int msbem_cells(const msbem_geom* g, int* ncells, double* Z, double* rho);
+/* The same, host only, from a mesh (no device): Z written when cap >= N * ncells. */
+int msbem_mesh_cells(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int* ncells, double* Z,
+                     int64_t cap);
+
 /* Y = W X: the Galerkin matrix applied to k <= 16 vectors at once (the
  * matrix-vector product of PCG, Sec. 2.1), e.g. for energies Phi^T W Phi.
  *   X[k*N], Y[k*N]  row c = vector c (host or device pointers, independently)

@@ -174,6 +174,18 @@ def lanczos_kappa(alphas, betas) -> float:
     return float(ev.max() / ev.min())
 
 
+def augment_cells(top: Topology, W: np.ndarray):
+    """A screen enclosing cells has the cells' indicators in the kernel of W
+    (their jumps are constant on every triangle, so their surface curls
+    vanish).  Reading of the paper's connectedness assumption: solve with
+    W + rho Z Z^T, Z the psi-coordinates of the indicators (Topology.cells),
+    rho the mean of diag(W); for constant g, Z^T L = 0, and the solution is
+    the one with Z^T Phi = 0.  Returns (W, Z, rho); W unchanged."""
+    Z = top.cells()
+    rho = float(np.mean(np.diag(W))) if W.size else 0.0
+    return W, Z, rho
+
+
 class Problem:
     """Everything the oracle knows about one geometry."""
 
@@ -196,6 +208,9 @@ class Problem:
     def assemble(self):
         self.V = core.assemble_V(self.geom.xyz, self.geom.tri, self.far_order, self.ss_order)
         self.W = assemble_W(self.top, self.V)
+        self.W0, self.Z, self.rho = augment_cells(self.top, self.W)
+        if self.Z.shape[1]:
+            self.W = self.W0 + self.rho * (self.Z @ self.Z.T)
         return self.W
 
     def rhs(self, g=None) -> np.ndarray:

@@ -204,6 +204,70 @@ class Topology:
         self.s_coef = np.array([e[3] for e in entries], dtype=np.float64)
 
     # ------------------------------------------------------------------
+    def cells(self) -> np.ndarray:
+        """Closed cells of the screen and the psi-coordinates of their
+        indicators, Z (ndof x ncells).
+
+        The oriented triangles (T, s) that share a sector at some vertex lie
+        in the same connected region of R^3 minus the screen; the regions are
+        the components of that relation.  A region is bounded exactly when
+        the flux of x through its sides, sum |T| (x_T . n_(T,s)) / 3 with
+        n_(T,s) pointing into the region, is minus its volume (negative); the
+        unbounded one has zero or positive flux (divergence theorem).  For a
+        cell K, the function that is 1 in K and 0 outside has, at vertex i,
+        the value [sector j in K] on sector j; modulo the continuous
+        functions its coordinate on psi_(i,j) is [sector j in K] - (number of
+        sectors of i in K) / q_i (the coefficients minus their mean, Sec. 4.2).
+        """
+        nt = self.nt
+        dsu = _DSU(2 * nt)
+        first_node = {}
+        for T in range(nt):
+            for a in range(3):
+                v = int(self.tri[T, a])
+                for s in (0, 1):
+                    key = (v, int(self.sector[T, s, a]))
+                    node = 2 * T + s
+                    if key in first_node:
+                        dsu.union(first_node[key], node)
+                    else:
+                        first_node[key] = node
+        roots = np.array([dsu.find(k) for k in range(2 * nt)])
+        cen = self.xyz[self.tri].mean(axis=1)
+        flux_T = self.area * np.einsum("ij,ij->i", cen, self.normal) / 3.0   # side +; side - has the opposite
+        flux = {}
+        for k in range(2 * nt):
+            T, s = divmod(k, 2)
+            flux[roots[k]] = flux.get(roots[k], 0.0) + (flux_T[T] if s == 0 else -flux_T[T])
+        scale = float(self.area.sum() * np.abs(self.xyz).max() + 1e-300)
+        cell_roots = sorted(r for r, f in flux.items() if f < -1e-9 * scale)
+        cid = {r: c for c, r in enumerate(cell_roots)}
+        Z = np.zeros((self.ndof, len(cell_roots)))
+        # sectors of each vertex -> cell (every side in a sector is in one region)
+        sec_cell = {}
+        for T in range(nt):
+            for a in range(3):
+                v = int(self.tri[T, a])
+                for s in (0, 1):
+                    r = roots[2 * T + s]
+                    sec_cell[(v, int(self.sector[T, s, a]))] = cid.get(r, -1)
+        for v in range(self.nv):
+            q = int(self.q[v])
+            if q < 2:
+                continue
+            cnt = np.zeros(len(cell_roots))
+            for j in range(q):
+                c = sec_cell[(v, j)]
+                if c >= 0:
+                    cnt[c] += 1
+            for j in range(q - 1):
+                row = int(self.first_dof[v]) + j
+                c = sec_cell[(v, j)]
+                Z[row] = -cnt / q
+                if c >= 0:
+                    Z[row, c] += 1.0
+        return Z
+
     def curl_vectors(self) -> np.ndarray:
         """s_{T,nu} for every curl-list entry: coef (x_{a+1} - x_{a+2}) / (2|T|)."""
         T, a = self.s_tri, self.s_loc

@@ -88,6 +88,8 @@ def lib():
         "msbem_spd_inverse_noalloc": ([P, i64, P, P], i32),
         "msbem_solve_batch": ([P, P, i32, ctypes.POINTER(SolveOpts), P, P, P, P], i32),
         "msbem_apply": ([P, P, i32, i32, P, P], i32),
+        "msbem_cells": ([P, ctypes.POINTER(i32), P, ctypes.POINTER(ctypes.c_double)], i32),
+        "msbem_mesh_cells": ([P, i64, P, i64, ctypes.POINTER(i32), P, i64], i32),
         "msbem_server_create": ([P, ctypes.POINTER(ServerOpts), ctypes.POINTER(P)], i32),
         "msbem_server_destroy": ([P], i32),
         "msbem_server_add_geometry": ([P, ctypes.c_uint64, P, i64, P, i64, P, i64, P, i64, P, P], i32),
@@ -148,6 +150,21 @@ def msbem_upload(ctx, xyz, tri, coarse_xyz, coarse_tri, parent, patch):
                             ctypes.byref(g))
     _check(ctx, st)
     return g
+
+
+def msbem_mesh_cells(xyz, tri):
+    """Host-only closed cells of a mesh: Z (N x ncells), the cells' indicators in the psi basis."""
+    xyz = np.ascontiguousarray(xyz, np.float64)
+    tri = np.ascontiguousarray(tri, np.int32)
+    n = msbem_mesh_dofs(xyz, tri)[0]
+    nc = ctypes.c_int()
+    st = lib().msbem_mesh_cells(_ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0], ctypes.byref(nc), None, 0)
+    if st != MSBEM_OK:
+        raise MsbemError(st, "msbem_mesh_cells")
+    Z = np.zeros((n, nc.value))
+    if nc.value:
+        lib().msbem_mesh_cells(_ptr(xyz), xyz.shape[0], _ptr(tri), tri.shape[0], ctypes.byref(nc), _ptr(Z), Z.size)
+    return Z
 
 
 def msbem_mesh_dofs(xyz, tri):
@@ -277,6 +294,17 @@ class Solver:
         o = PrecondOpts(wire_basket, use_coarse)
         _check(self.ctx, lib().msbem_factor(self.geom, ctypes.byref(o)))
         return self
+
+    def cells(self):
+        """(Z, rho): the closed cells' indicators in the psi basis (N x ncells)
+        and the augmentation weight (after assemble)."""
+        nc = ctypes.c_int()
+        rho = ctypes.c_double()
+        _check(self.ctx, lib().msbem_cells(self.geom, ctypes.byref(nc), None, ctypes.byref(rho)))
+        Z = np.zeros((self.n, nc.value))
+        if nc.value:
+            _check(self.ctx, lib().msbem_cells(self.geom, None, _ptr(Z), None))
+        return Z, rho.value
 
     def apply(self, X, precision="df", out=None):
         """Y = W X for up to 16 vectors (rows of X); returns (Y, kernel_ms)."""

@@ -70,7 +70,7 @@ void free_dev(DevGeom& d, cudaStream_t s) {
   void* ptrs[] = {d.d_hist, d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
                   d.d_jptr, d.d_jtri, d.d_jvec, d.d_jvecf, d.d_jrhs, d.d_Wh, d.d_bptr, d.d_bdofs, d.d_boff,
                   d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pfp, d.d_rf, d.d_binvf,
-                  d.d_btile, d.d_W64, d.d_WP, d.d_vec, d.d_scal};
+                  d.d_btile, d.d_W64, d.d_cellZ, d.d_WP, d.d_vec, d.d_scal};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
@@ -187,6 +187,7 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   std::string err;
   int st = build_topology(xyz, nv, tri, nt, g->fine, err);
   if (st) return fail(c, st, "fine mesh: " + err);
+  build_cells(g->fine);
   st = build_topology(cxyz, ncv, ctri, nct, g->coarse, err);
   if (st) return fail(c, st, "coarse mesh: " + err);
   st = build_split(g->fine, g->coarse, parent, patch, g->split, err);
@@ -297,6 +298,8 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
     chk(dput(&d.d_cvalf, cvalf, c->pool, s));
   }
   const int64_t N = f.ndof;
+  d.ncells = f.ncells;
+  if (f.ncells) chk(dput(&d.d_cellZ, f.cellZ, c->pool, s));
   d.ldw = (N + 31) / 32 * 32;
   chk(dalloc(&d.d_Wh, (size_t)2 * N * d.ldw, c->pool, s));
   if (N > 0) chk(cudaMemsetAsync(d.d_Wh, 0, sizeof(float) * 2 * N * d.ldw, s));
@@ -344,6 +347,20 @@ int msbem_mesh_dofs(const double* xyz, int64_t nv, const int32_t* tri, int64_t n
     if (vertex_of_dof) std::memcpy(vertex_of_dof, t.dof_vertex.data(), sizeof(int32_t) * t.ndof);
     if (sector_of_dof) std::memcpy(sector_of_dof, t.dof_sector.data(), sizeof(int32_t) * t.ndof);
   }
+  return MSBEM_OK;
+}
+
+int msbem_mesh_cells(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, int* ncells, double* Z,
+                     int64_t cap) {
+  if (!ncells) return MSBEM_INVALID_ARG;
+  Topo t;
+  std::string err;
+  int st = build_topology(xyz, nv, tri, nt, t, err);
+  if (st) return st;
+  build_cells(t);
+  *ncells = t.ncells;
+  if (Z && cap >= (int64_t)t.cellZ.size() && !t.cellZ.empty())
+    std::memcpy(Z, t.cellZ.data(), sizeof(double) * t.cellZ.size());
   return MSBEM_OK;
 }
 
@@ -431,6 +448,22 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   cudaEventRecord(c->ev[2], s);
   e = launch_contract(d, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+  if (d.ncells > 0 && d.ndof > 0) {
+    // closed cells: W + rho Z Z^T, rho = mean diag(W) (summed in dof order)
+    std::vector<double> diag(d.ndof);
+    double* dd = nullptr;
+    e = pool_alloc((void**)&dd, sizeof(double) * d.ndof, d.pool, s);
+    if (e == cudaSuccess) e = copy_diagonal(d, dd, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(diag.data(), dd, sizeof(double) * d.ndof, cudaMemcpyDeviceToHost, s);
+    if (dd) cudaFreeAsync(dd, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cells");
+    double sum = 0.0;
+    for (double x : diag) sum += x;
+    d.rho = sum / (double)d.ndof;
+    if ((e = launch_augment(d, d.rho, s)) != cudaSuccess) return cuda_fail(c, e, "cells");
+    ++d.launches;
+  }
   cudaEventRecord(c->ev[3], s);
   d.launches += 1 + (d.n_near > 0) + (d.ndof > 0);
   cudaFreeAsync(d.d_V, s);
@@ -644,6 +677,14 @@ int msbem_apply(msbem_geom* g, const double* X, int k, int precision, double* Y,
   if (e == cudaErrorTimeout) return fail(c, MSBEM_DEVICE_TIMEOUT, "msbem_apply: a matrix copy did not complete");
   if (e != cudaSuccess) return cuda_fail(c, e, "msbem_apply");
   if (kernel_ms) *kernel_ms = ms;
+  return MSBEM_OK;
+}
+
+int msbem_cells(const msbem_geom* g, int* ncells, double* Z, double* rho) {
+  if (!g) return MSBEM_INVALID_ARG;
+  if (ncells) *ncells = g->fine.ncells;
+  if (Z && !g->fine.cellZ.empty()) std::memcpy(Z, g->fine.cellZ.data(), sizeof(double) * g->fine.cellZ.size());
+  if (rho) *rho = g->dev.rho;
   return MSBEM_OK;
 }
 

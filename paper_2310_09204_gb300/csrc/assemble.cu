@@ -546,6 +546,45 @@ cudaError_t copy_rows_to_double(const DevGeom& g, int64_t row0, int64_t nrows, d
   return cudaGetLastError();
 }
 
+// diag(W) in FP64
+__global__ void diag_kernel(const float* __restrict__ Wh, const float* __restrict__ Wl, int64_t ldw, int64_t N,
+                            double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) out[i] = df_to_double(Wh[i * ldw + i], Wl[i * ldw + i]);
+}
+
+cudaError_t copy_diagonal(const DevGeom& g, double* out, cudaStream_t s) {
+  if (g.ndof == 0) return cudaSuccess;
+  diag_kernel<<<(unsigned)((g.ndof + 255) / 256), 256, 0, s>>>(g.d_Wh, g.wlo(), g.ldw, g.ndof, out);
+  return cudaGetLastError();
+}
+
+// W += rho Z Z^T for a screen with closed cells (Z: N x nc, the cells'
+// indicators); the correction is summed in FP64 and added to the float pair
+__global__ void augment_kernel(float* __restrict__ Wh, float* __restrict__ Wl, int64_t ldw, int64_t N,
+                               const double* __restrict__ Z, int nc, double rho) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N, j = e - (e / N) * N;
+    double corr = 0.0;
+    for (int k = 0; k < nc; ++k) corr = fma(Z[i * nc + k], Z[j * nc + k], corr);
+    if (corr == 0.0) continue;
+    const int64_t o = i * ldw + j;
+    float h, l;
+    split_df(df_to_double(Wh[o], Wl[o]) + rho * corr, h, l);
+    Wh[o] = h;
+    Wl[o] = l;
+  }
+}
+
+cudaError_t launch_augment(const DevGeom& g, double rho, cudaStream_t s) {
+  if (g.ndof == 0 || g.ncells == 0) return cudaSuccess;
+  const int64_t n2 = g.ndof * g.ndof;
+  const int64_t blocks = std::min<int64_t>((n2 + 255) / 256, 152 * 64);
+  augment_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_Wh, g.wlo(), g.ldw, g.ndof, g.d_cellZ, g.ncells, rho);
+  return cudaGetLastError();
+}
+
 __global__ void rhs_kernel(const int64_t* __restrict__ jptr, const double* __restrict__ jrhs,
                            int64_t N, double gx, double gy, double gz, double* __restrict__ L) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

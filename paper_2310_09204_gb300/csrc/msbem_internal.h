@@ -34,11 +34,18 @@ struct Topo {
   std::vector<int64_t> jptr;
   std::vector<int32_t> jtri, jloc;
   std::vector<double> jcoef;
+  // closed cells (bounded regions of R^3 minus the screen) and the
+  // psi-coordinates of their indicators, cellZ[nu * ncells + c]
+  int ncells = 0;
+  std::vector<double> cellZ;
 };
 
 // Builds the topology; returns MSBEM_OK or an error status with a message.
 int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, Topo& out,
                    std::string& err);
+
+// Closed cells of the screen (fills Topo::ncells and Topo::cellZ; topology.cpp).
+void build_cells(Topo& t);
 
 // Near pairs (pairs sharing at least one vertex, including T = T), with the
 // canonical local vertex orderings used by the singular rules:
@@ -110,6 +117,9 @@ struct DevGeom {
   CUtensorMap tm_W;              // 16 x 128 x 2 boxes of both planes (matvec.cu)
   CUtensorMap tm_Whi;            // 32 x 128 x 1 boxes of the hi plane
   double* d_W64 = nullptr;       // FP64 copy of W for the plain comparator (made on first use)
+  int ncells = 0;                // closed cells: W holds W + rho Z Z^T (Z: [N][ncells])
+  double* d_cellZ = nullptr;
+  double rho = 0.0;
   // preconditioner
   int64_t n_blocks = 0;
   int64_t* d_bptr = nullptr;     // n_blocks+1
@@ -159,6 +169,9 @@ cudaError_t launch_contract(const DevGeom& g, cudaStream_t s);
 cudaError_t launch_rhs(const DevGeom& g, const double gvec[3], double* out, cudaStream_t s);
 cudaError_t copy_rows_to_double(const DevGeom& g, int64_t row0, int64_t nrows, double* out,
                                 cudaStream_t s);
+// diag(W) as FP64 (N values) and the rank-ncells update W += rho Z Z^T
+cudaError_t copy_diagonal(const DevGeom& g, double* out, cudaStream_t s);
+cudaError_t launch_augment(const DevGeom& g, double rho, cudaStream_t s);
 cudaError_t set_far_constants(const double bary[6][3], const double w[6]);
 cudaError_t set_far_df_constants(const double w[6]);
 

@@ -267,6 +267,72 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
   return MSBEM_OK;
 }
 
+// Regions of R^3 minus the screen: oriented triangles (T, s) that share a
+// sector at a vertex lie in the same region (components of that relation).
+// A region is bounded when the flux of x through its sides (normals into the
+// region), sum |T| (c_T . n_(T,s)) / 3, is negative: minus its volume by the
+// divergence theorem; the unbounded region's flux is zero or positive.  The
+// indicator of a bounded cell K takes the value [sector j in K] on sector j of
+// vertex i; modulo continuous functions its coordinate on psi_(i,j) is that
+// value minus its mean over the q_i sectors.
+void build_cells(Topo& t) {
+  const int64_t nt = t.nt, nv = t.nv;
+  std::vector<int64_t> sbase(nv + 1, 0);
+  for (int64_t v = 0; v < nv; ++v) sbase[v + 1] = sbase[v] + t.q[v];
+  std::vector<int64_t> rep(sbase[nv], -1);
+  Dsu dsu(2 * nt);
+  for (int64_t T = 0; T < nt; ++T)
+    for (int a = 0; a < 3; ++a) {
+      const int32_t v = t.tri[3 * T + a];
+      for (int s = 0; s < 2; ++s) {
+        const int64_t key = sbase[v] + t.sector[(2 * T + s) * 3 + a];
+        const int64_t node = 2 * T + s;
+        if (rep[key] < 0) rep[key] = node; else dsu.unite(rep[key], node);
+      }
+    }
+  std::vector<double> flux(2 * nt, 0.0);
+  double area_sum = 0.0, xmax = 0.0;
+  for (int64_t i = 0; i < 3 * nv; ++i) xmax = std::max(xmax, std::fabs(t.xyz[i]));
+  for (int64_t T = 0; T < nt; ++T) {
+    double c[3];
+    for (int k = 0; k < 3; ++k)
+      c[k] = (t.xyz[3 * t.tri[3 * T] + k] + t.xyz[3 * t.tri[3 * T + 1] + k] + t.xyz[3 * t.tri[3 * T + 2] + k]) / 3.0;
+    const double f = t.area[T] * (c[0] * t.normal[3 * T] + c[1] * t.normal[3 * T + 1] + c[2] * t.normal[3 * T + 2]) / 3.0;
+    flux[dsu.find(2 * T)] += f;
+    flux[dsu.find(2 * T + 1)] -= f;
+    area_sum += t.area[T];
+  }
+  const double tol = 1e-9 * (area_sum * xmax + 1e-300);
+  std::vector<int> cell_of_root(2 * nt, -1);
+  int nc = 0;
+  for (int64_t r = 0; r < 2 * nt; ++r)
+    if (dsu.find(r) == r && flux[r] < -tol) cell_of_root[r] = nc++;
+  t.ncells = nc;
+  t.cellZ.assign((size_t)t.ndof * nc, 0.0);
+  if (!nc) return;
+  std::vector<int> sec_cell(sbase[nv], -1);
+  for (int64_t T = 0; T < nt; ++T)
+    for (int a = 0; a < 3; ++a) {
+      const int32_t v = t.tri[3 * T + a];
+      for (int s = 0; s < 2; ++s)
+        sec_cell[sbase[v] + t.sector[(2 * T + s) * 3 + a]] = cell_of_root[dsu.find(2 * T + s)];
+    }
+  std::vector<double> cnt(nc);
+  for (int64_t v = 0; v < nv; ++v) {
+    const int q = t.q[v];
+    if (q < 2) continue;
+    std::fill(cnt.begin(), cnt.end(), 0.0);
+    for (int j = 0; j < q; ++j)
+      if (sec_cell[sbase[v] + j] >= 0) cnt[sec_cell[sbase[v] + j]] += 1.0;
+    for (int j = 0; j + 1 < q; ++j) {
+      double* z = &t.cellZ[(size_t)(t.first_dof[v] + j) * nc];
+      for (int c = 0; c < nc; ++c) z[c] = -cnt[c] / q;
+      const int c = sec_cell[sbase[v] + j];
+      if (c >= 0) z[c] += 1.0;
+    }
+  }
+}
+
 void build_near_pairs(const Topo& t, std::vector<NearPair>& out) {
   out.clear();
   const int64_t nt = t.nt, nv = t.nv;

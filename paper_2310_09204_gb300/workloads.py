@@ -443,6 +443,50 @@ def panels_config(instances: int = 16) -> list:
     return [panels(seed) for seed in range(instances)]
 
 
+def cube_midplanes(n: int = 24, n_coarse: int = 6, g=None, seed: int = 0) -> Geometry:
+    """Surface of the unit cube [0,1]^3 with its three interior mid-planes
+    x = 1/2, y = 1/2, z = 1/2 (nine unit squares; non-manifold junction lines
+    where a mid-plane meets a face or another mid-plane, and a junction point
+    at the centre).  The screen encloses the eight octant cells, so the
+    hypersingular operator has an eight-dimensional kernel (the cells'
+    indicators).
+
+    h = 1/n (n even), H = 1/n_coarse (n_coarse even, dividing n); every square
+    carries the nested "/"-split grids; patches are the coarse grid squares of
+    every face and mid-plane quarter.  g: uniform in [-1, 1]^3 (seeded) unless
+    given."""
+    if n % 2 or n_coarse % 2 or n % n_coarse:
+        raise ValueError("n and n_coarse must be even, n a multiple of n_coarse")
+    mb = _MeshBuilder()
+    cb = _MeshBuilder()
+    tags = []
+    sheets = []
+    e = np.eye(3)
+    for ax in range(3):
+        u, v = e[(ax + 1) % 3], e[(ax + 2) % 3]
+        for off in (0.0, 0.5, 1.0):            # two faces and the mid-plane
+            sheets.append((off * e[ax], u, v))
+    for k, (o, u, v) in enumerate(sheets):
+        def tag(i, j, t, k=k):
+            return (k * n_coarse + (j * n_coarse) // n) * n_coarse + (i * n_coarse) // n
+        _grid_panel(mb, o, u, v, n, n, tags, tag)
+        _grid_panel(cb, o, u, v, n_coarse, n_coarse)
+    xyz, tri = mb.arrays()
+    cxyz, ctri = cb.arrays()
+    parent = _locate_parents(xyz, tri, cxyz, ctri)
+    if g is None:
+        g = np.random.default_rng(seed).uniform(-1.0, 1.0, 3)
+    return Geometry(f"cube_midplanes_h1/{n}_H1/{n_coarse}", xyz, tri, cxyz, ctri, parent,
+                    np.array(tags, dtype=np.int32), np.asarray(g, float), 1.0 / n, 1.0 / n_coarse,
+                    {"family": "cube", "n": n, "n_coarse": n_coarse, "cells": 8})
+
+
+def cube_config() -> Geometry:
+    """Cube with mid-planes at h = 1/96 (83,817 dofs, 165,888 triangles), the
+    coarse squares of H = 1/6 as patches (324 of them), g seeded (seed 0)."""
+    return cube_midplanes(96, 6, seed=0)
+
+
 def flat_config() -> Geometry:
     """Plain FP64 flat-screen workload: unit square h = 1/16 (225 interior
     dofs), 2 x 2 substructuring (H = 1/2) plus the coarse space, g = (0,0,1)."""

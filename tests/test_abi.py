@@ -59,3 +59,14 @@ def test_rejects_bad_meshes(L):
 def test_single_triangle_has_no_dofs(L):
     n, v, s = M.msbem_mesh_dofs(np.eye(3), np.array([[0, 1, 2]]))
     assert n == 0
+
+
+@pytest.mark.parametrize("geom", [WL.cube_midplanes(4, 2), WL.cube_midplanes(6, 2), WL.book(4, 2),
+                                  WL.panels(7, n=4)], ids=lambda g: g.name)
+def test_cells_match_oracle(L, geom):
+    """The library's closed cells (its own C++ code) equal the oracle's bit for bit."""
+    from oracle.topology import Topology
+    Zg = M.msbem_mesh_cells(geom.xyz, geom.tri)
+    Zo = Topology(geom.xyz, geom.tri).cells()
+    assert Zg.shape == Zo.shape
+    assert np.array_equal(Zg, Zo)
