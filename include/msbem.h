@@ -116,6 +116,12 @@ typedef struct msbem_assemble_opts {
                    /* (Sauter-Schwab-type) rules, 1..16; default 5            */
   int far_kernel;  /* pair integrals: 0 = double-float arithmetic on the FP32 */
                    /* pipe (default), 1 = native FP64 (far and near field)    */
+  int64_t panel_rows; /* 0 (default): V (nt x nt float pairs) in one piece    */
+                   /* when it fits in free device memory, else in row panels  */
+                   /* sized to fit; > 0: panels of that many triangle rows    */
+                   /* (a multiple of 64).  Panels need far_kernel 0; W is     */
+                   /* then summed panel by panel (equal to rounding, not bit  */
+                   /* for bit symmetric).                                     */
 } msbem_assemble_opts;
 
 /* Assemble W[nu,nu'] = a(psi~_nu, psi~_nu') (Sec. 4.3 eq. eval_a_phiij with
@@ -203,10 +209,11 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
  * with its mid-planes encloses eight), the indicators of those cells have
  * vanishing surface curls and span the kernel of the hypersingular form; the
  * paper's connectedness assumption fails.  Reading used: msbem_assemble then
- * stores W + rho Z Z^T, rho = mean diag(W), Z = the psi-coordinates of the
- * cells' indicators (value [sector j in K] minus its mean over the q_i sectors
- * of the vertex); for constant g, Z^T L = 0 and the solution is the one with
- * Z^T Phi = 0.  Cells are the components of R^3 minus the screen found from the
+ * stores W + rho Q Q^T, rho = mean diag(W), Q = Z L^-T (Z^T Z = L L^T) an
+ * orthonormal basis of the span of Z, the psi-coordinates of the cells'
+ * indicators (value [sector j in K] minus its mean over the q_i sectors of the
+ * vertex): the kernel directions take the eigenvalue rho; for constant g,
+ * Z^T L = 0 and the solution is the one with Z^T Phi = 0.  Cells are the components of R^3 minus the screen found from the
  * sectors whose flux sum |T| (x_T . n) / 3 is negative (bounded, divergence
  * theorem).  Outputs: *ncells; Z[N * ncells] row-major (host, may be NULL);
  * *rho (valid after msbem_assemble). */

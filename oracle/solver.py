@@ -178,12 +178,19 @@ def augment_cells(top: Topology, W: np.ndarray):
     """A screen enclosing cells has the cells' indicators in the kernel of W
     (their jumps are constant on every triangle, so their surface curls
     vanish).  Reading of the paper's connectedness assumption: solve with
-    W + rho Z Z^T, Z the psi-coordinates of the indicators (Topology.cells),
-    rho the mean of diag(W); for constant g, Z^T L = 0, and the solution is
-    the one with Z^T Phi = 0.  Returns (W, Z, rho); W unchanged."""
+    W + rho Q Q^T, rho the mean of diag(W) and Q = Z L^-T (Z^T Z = L L^T) an
+    orthonormal basis of the span of the indicators' psi-coordinates Z
+    (Topology.cells): rho times the orthogonal projector onto the kernel, so
+    the kernel directions take the eigenvalue rho, inside the spectrum of W.
+    For constant g, Z^T L = 0, and the solution is the one with Z^T Phi = 0.
+    Returns (W, Z, rho, Q); W unchanged."""
     Z = top.cells()
     rho = float(np.mean(np.diag(W))) if W.size else 0.0
-    return W, Z, rho
+    Q = Z
+    if Z.shape[1]:
+        Lc = np.linalg.cholesky(Z.T @ Z)
+        Q = sla.solve_triangular(Lc, Z.T, lower=True).T
+    return W, Z, rho, Q
 
 
 class Problem:
@@ -208,9 +215,9 @@ class Problem:
     def assemble(self):
         self.V = core.assemble_V(self.geom.xyz, self.geom.tri, self.far_order, self.ss_order)
         self.W = assemble_W(self.top, self.V)
-        self.W0, self.Z, self.rho = augment_cells(self.top, self.W)
+        self.W0, self.Z, self.rho, self.Q = augment_cells(self.top, self.W)
         if self.Z.shape[1]:
-            self.W = self.W0 + self.rho * (self.Z @ self.Z.T)
+            self.W = self.W0 + self.rho * (self.Q @ self.Q.T)
         return self.W
 
     def rhs(self, g=None) -> np.ndarray:

@@ -31,7 +31,7 @@ class MsbemError(RuntimeError):
 
 
 class AssembleOpts(ctypes.Structure):
-    _fields_ = [("ss_order", ctypes.c_int), ("far_kernel", ctypes.c_int)]
+    _fields_ = [("ss_order", ctypes.c_int), ("far_kernel", ctypes.c_int), ("panel_rows", ctypes.c_int64)]
 
 
 class PrecondOpts(ctypes.Structure):
@@ -271,8 +271,10 @@ class Solver:
         return dict(zip(("far_ms", "near_ms", "contract_ms", "factor_ms", "solve_ms"), t.tolist()))
 
     # --- the hot path
-    def assemble(self, ss_order: int = 5, far_kernel: int = 0):
-        o = AssembleOpts(ss_order, far_kernel)
+    def assemble(self, ss_order: int = 5, far_kernel: int = 0, panel_rows: int = 0):
+        """W; panel_rows > 0 forces the pair matrix V into row panels of that
+        many triangles (0: in one piece when it fits)."""
+        o = AssembleOpts(ss_order, far_kernel, panel_rows)
         _check(self.ctx, lib().msbem_assemble(self.geom, ctypes.byref(o)))
         return self
 

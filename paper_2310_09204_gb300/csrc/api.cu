@@ -299,7 +299,7 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   }
   const int64_t N = f.ndof;
   d.ncells = f.ncells;
-  if (f.ncells) chk(dput(&d.d_cellZ, f.cellZ, c->pool, s));
+  if (f.ncells) chk(dput(&d.d_cellZ, f.cellQ, c->pool, s));
   d.ldw = (N + 31) / 32 * 32;
   chk(dalloc(&d.d_Wh, (size_t)2 * N * d.ldw, c->pool, s));
   if (N > 0) chk(cudaMemsetAsync(d.d_Wh, 0, sizeof(float) * 2 * N * d.ldw, s));
@@ -432,24 +432,89 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
     cudaFreeAsync(d.d_W64, s);
     d.d_W64 = nullptr;
   }
+  // V in one piece when it fits, else in row panels of triangles (a multiple
+  // of 64 rows) computed and contracted one after the other
+  int64_t panel = opts ? opts->panel_rows : 0;
+  const int64_t nt_pad = d.nt_pad;
+  if (panel <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    uint64_t reserved = 0, used = 0;
+    if (d.pool) {
+      cudaMemPoolGetAttribute(d.pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+      cudaMemPoolGetAttribute(d.pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    }
+    const double avail = (double)fr + (double)(reserved > used ? reserved - used : 0);
+    const double full = (double)sizeof(float2) * d.nt * d.nt;
+    if (full > 0.8 * avail)
+      panel = std::max<int64_t>(64, (int64_t)(0.6 * avail / (sizeof(float2) * (double)d.nt)) / 64 * 64);
+  }
+  const bool panels = panel > 0 && panel < nt_pad;
+  if (panel % 64) return fail(c, MSBEM_INVALID_ARG, "panel_rows must be a multiple of 64");
+  if (panels && far_kernel == 1)
+    return fail(c, MSBEM_INVALID_ARG, "panel assembly uses the double-float pair kernel (far_kernel 0)");
+  const int64_t vrows = panels ? panel : d.nt;
   if (!d.d_V) {
-    e = pool_alloc((void**)&d.d_V, sizeof(float2) * std::max<int64_t>(1, d.nt * d.nt), d.pool, s);
+    e = pool_alloc((void**)&d.d_V, sizeof(float2) * std::max<int64_t>(1, vrows * d.nt), d.pool, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(c, MSBEM_OOM, "assemble: no room for the pair matrix V");
     }
   }
-  cudaEventRecord(c->ev[0], s);
-  e = (far_kernel == 1) ? launch_far_fp64(d, s) : launch_far_df(d, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "far field");
-  cudaEventRecord(c->ev[1], s);
-  e = launch_near(d, n, glx, glw, far_kernel == 1, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "near field");
-  cudaEventRecord(c->ev[2], s);
-  e = launch_contract(d, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+  float t_far = 0.f, t_near = 0.f, t_con = 0.f;
+  if (!panels) {
+    cudaEventRecord(c->ev[0], s);
+    e = (far_kernel == 1) ? launch_far_fp64(d, s) : launch_far_df(d, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "far field");
+    cudaEventRecord(c->ev[1], s);
+    e = launch_near(d, n, glx, glw, far_kernel == 1, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "near field");
+    cudaEventRecord(c->ev[2], s);
+    e = launch_contract(d, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "contraction");
+    cudaEventRecord(c->ev[3], s);
+    d.launches += 1 + (d.n_near > 0) + (d.ndof > 0);
+  } else {
+    // dof rows each panel touches: the dofs of the vertices of its triangles
+    const Topo& f = g->fine;
+    const int64_t np = (d.nt + panel - 1) / panel;
+    std::vector<int> rt0(np, INT32_MAX), rt1(np, -1);
+    for (int64_t T = 0; T < d.nt; ++T) {
+      const int64_t p = T / panel;
+      for (int a = 0; a < 3; ++a) {
+        const int32_t v = f.tri[3 * T + a];
+        if (f.first_dof[v + 1] > f.first_dof[v]) {
+          rt0[p] = std::min<int>(rt0[p], (int)(f.first_dof[v] / 32));
+          rt1[p] = std::max<int>(rt1[p], (int)((f.first_dof[v + 1] - 1) / 32));
+        }
+      }
+    }
+    if (d.ndof > 0) e = cudaMemsetAsync(d.d_Wh, 0, sizeof(float) * 2 * d.ndof * d.ldw, s);
+    std::vector<cudaEvent_t> evs(4 * np);
+    for (auto& x : evs) cudaEventCreate(&x);
+    for (int64_t p = 0; p < np && e == cudaSuccess; ++p) {
+      const int64_t t0 = p * panel, t1 = std::min<int64_t>(d.nt, t0 + panel);
+      cudaEventRecord(evs[4 * p], s);
+      e = launch_far_df_panel(d, (int)(t0 / 64), (int)((std::min<int64_t>(nt_pad, t0 + panel) - t0) / 64), s);
+      cudaEventRecord(evs[4 * p + 1], s);
+      if (e == cudaSuccess) e = launch_near(d, n, glx, glw, 0, s, t0, t1);
+      cudaEventRecord(evs[4 * p + 2], s);
+      if (e == cudaSuccess && rt1[p] >= rt0[p]) e = launch_contract_panel(d, t0, t1, rt0[p], rt1[p] - rt0[p] + 1, s);
+      cudaEventRecord(evs[4 * p + 3], s);
+      d.launches += 3;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int64_t p = 0; p < np && e == cudaSuccess; ++p) {
+      float t;
+      cudaEventElapsedTime(&t, evs[4 * p], evs[4 * p + 1]); t_far += t;
+      cudaEventElapsedTime(&t, evs[4 * p + 1], evs[4 * p + 2]); t_near += t;
+      cudaEventElapsedTime(&t, evs[4 * p + 2], evs[4 * p + 3]); t_con += t;
+    }
+    for (auto& x : evs) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(c, e, "panel assembly");
+  }
   if (d.ncells > 0 && d.ndof > 0) {
-    // closed cells: W + rho Z Z^T, rho = mean diag(W) (summed in dof order)
+    // closed cells: W + rho Q Q^T, rho = mean diag(W) (summed in dof order)
     std::vector<double> diag(d.ndof);
     double* dd = nullptr;
     e = pool_alloc((void**)&dd, sizeof(double) * d.ndof, d.pool, s);
@@ -464,16 +529,19 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
     if ((e = launch_augment(d, d.rho, s)) != cudaSuccess) return cuda_fail(c, e, "cells");
     ++d.launches;
   }
-  cudaEventRecord(c->ev[3], s);
-  d.launches += 1 + (d.n_near > 0) + (d.ndof > 0);
   cudaFreeAsync(d.d_V, s);
   d.d_V = nullptr;
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "assemble");
-  float t;
-  cudaEventElapsedTime(&t, c->ev[0], c->ev[1]); d.times[0] = t;
-  cudaEventElapsedTime(&t, c->ev[1], c->ev[2]); d.times[1] = t;
-  cudaEventElapsedTime(&t, c->ev[2], c->ev[3]); d.times[2] = t;
+  if (!panels) {
+    cudaEventElapsedTime(&t_far, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&t_near, c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&t_con, c->ev[2], c->ev[3]);
+  }
+  d.times[0] = t_far;
+  d.times[1] = t_near;
+  d.times[2] = t_con;
+  d.panel_rows = panels ? panel : 0;
   d.assembled = 1;
   d.factored = 0;
   return MSBEM_OK;

@@ -151,7 +151,7 @@ __device__ __forceinline__ double tri_area_d(const double* P) {
 __global__ void __launch_bounds__(256) near_kernel(const __grid_constant__ GLTable gl,
                                                    const NearPair* __restrict__ pairs, int64_t npairs,
                                                    const double* __restrict__ xyz, int n, int64_t ldv,
-                                                   float2* __restrict__ V) {
+                                                   float2* __restrict__ V, int64_t t0, int64_t t1) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= npairs) return;
@@ -228,8 +228,9 @@ __global__ void __launch_bounds__(256) near_kernel(const __grid_constant__ GLTab
   if (lane == 0) {
     float h, l;
     split_df(pref * sum, h, l);
-    V[(int64_t)pr.T * ldv + pr.S] = make_float2(h, l);
-    V[(int64_t)pr.S * ldv + pr.T] = make_float2(h, l);
+    // rows t0 .. t1-1 of V are held (all of them outside panel mode)
+    if (pr.T >= t0 && pr.T < t1) V[(int64_t)(pr.T - t0) * ldv + pr.S] = make_float2(h, l);
+    if (pr.S >= t0 && pr.S < t1) V[(int64_t)(pr.S - t0) * ldv + pr.T] = make_float2(h, l);
   }
 }
 
@@ -256,7 +257,8 @@ __device__ __forceinline__ void axpy3(float ch, float cl, const float2* v, float
 __global__ void __launch_bounds__(256) near_df_kernel(const __grid_constant__ GLTable gl,
                                                       const NearPair* __restrict__ pairs,
                                                       int64_t npairs, const double* __restrict__ xyz,
-                                                      int n, int64_t ldv, float2* __restrict__ V) {
+                                                      int n, int64_t ldv, float2* __restrict__ V,
+                                                      int64_t t0, int64_t t1) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= npairs) return;
@@ -372,13 +374,15 @@ __global__ void __launch_bounds__(256) near_df_kernel(const __grid_constant__ GL
   if (lane == 0) {
     float h, l;
     split_df(pref * df_to_double(acch, accl), h, l);
-    V[(int64_t)pr.T * ldv + pr.S] = make_float2(h, l);
-    V[(int64_t)pr.S * ldv + pr.T] = make_float2(h, l);
+    // rows t0 .. t1-1 of V are held (all of them outside panel mode)
+    if (pr.T >= t0 && pr.T < t1) V[(int64_t)(pr.T - t0) * ldv + pr.S] = make_float2(h, l);
+    if (pr.S >= t0 && pr.S < t1) V[(int64_t)(pr.S - t0) * ldv + pr.T] = make_float2(h, l);
   }
 }
 
 cudaError_t launch_near(const DevGeom& g, int n, const double* gl_x, const double* gl_w,
-                        int fp64, cudaStream_t s) {
+                        int fp64, cudaStream_t s, int64_t t0, int64_t t1) {
+  if (t1 < 0) t1 = g.nt;
   if (n < 2 || n > NEAR_MAXN) return cudaErrorInvalidValue;
   GLTable gl{};
   for (int j = 0; j < n; ++j) {
@@ -391,9 +395,9 @@ cudaError_t launch_near(const DevGeom& g, int n, const double* gl_x, const doubl
   if (g.n_near == 0) return cudaSuccess;
   int64_t blocks = (g.n_near + 7) / 8;
   if (fp64)
-    near_kernel<<<(unsigned)blocks, 256, 0, s>>>(gl, g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
+    near_kernel<<<(unsigned)blocks, 256, 0, s>>>(gl, g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V, t0, t1);
   else
-    near_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(gl, g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V);
+    near_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(gl, g.d_near, g.n_near, g.d_xyz, n, g.nt, g.d_V, t0, t1);
   return cudaGetLastError();
 }
 
@@ -412,13 +416,15 @@ cudaError_t launch_near(const DevGeom& g, int n, const double* gl_x, const doubl
 // Diagonal tiles mirror their upper half so W is exactly symmetric.
 // One W entry: sum over the row's curl entries [ka,kz) and the column's
 // [ma,mz) (lists in shared memory when STAGED, else in global memory).
-template <bool STAGED>
+template <bool STAGED, bool PANEL = false>
 __device__ __forceinline__ void contract_entry(const float2* __restrict__ V, int64_t ldv, int ka,
                                                int kz, int ma, int mz, const int32_t* rtri,
                                                const float2* rvec, const int32_t* ctri,
-                                               const float2* cvec, float& acch, float& accl) {
+                                               const float2* cvec, float& acch, float& accl,
+                                               int64_t t0 = 0, int64_t t1 = 0) {
   for (int k = ka; k < kz; ++k) {
-    const float2* vrow = V + (int64_t)rtri[k] * ldv;
+    if (PANEL && (rtri[k] < t0 || rtri[k] >= t1)) continue;   // row of V not in this panel
+    const float2* vrow = V + (int64_t)(rtri[k] - t0) * ldv;
     const float2 sk[3] = {rvec[3 * k], rvec[3 * k + 1], rvec[3 * k + 2]};
     int m = ma;
     for (; m + CT_BATCH <= mz; m += CT_BATCH) {
@@ -524,6 +530,77 @@ cudaError_t launch_contract(const DevGeom& g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Panel mode: V holds the rows t0 .. t1-1 only.  W[nu, nu'] += the part of
+// sum_{k in J(nu)} sum_{m in J(nu')} V[T_k, T_m] s_k . s_m with T_k in the
+// panel, for the row tiles rt0 .. rt0+nrt-1 (the dofs the panel touches) and
+// every column tile; W starts at zero and the panels add up (double-float).
+__global__ void __launch_bounds__(256) contract_panel_kernel(const float2* __restrict__ V, int64_t ldv,
+                                                             int64_t t0, int64_t t1,
+                                                             const int64_t* __restrict__ jptr,
+                                                             const int32_t* __restrict__ jtri,
+                                                             const float2* __restrict__ jvec, int64_t N,
+                                                             int nbt, int rt0, float* __restrict__ Wh,
+                                                             float* __restrict__ Wl, int64_t ldw) {
+  __shared__ int32_t s_rtri[CT_CAP], s_ctri[CT_CAP];
+  __shared__ float2 s_rvec[3 * CT_CAP], s_cvec[3 * CT_CAP];
+  __shared__ int32_t s_rptr[CT + 1], s_cptr[CT + 1];
+  const int bi = rt0 + (int)(blockIdx.x / nbt), bj = (int)(blockIdx.x % nbt);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t r0 = (int64_t)bi * CT, c0 = (int64_t)bj * CT;
+  const int64_t rl = (N - r0 < CT) ? N - r0 : CT, cl = (N - c0 < CT) ? N - c0 : CT;
+  if (rl <= 0 || cl <= 0) return;
+  const int64_t rbase = jptr[r0], cbase = jptr[c0];
+  const int64_t rcount = jptr[r0 + rl] - rbase, ccount = jptr[c0 + cl] - cbase;
+  const bool staged = rcount <= CT_CAP && ccount <= CT_CAP;
+  if (threadIdx.x <= CT) {
+    const int i = threadIdx.x;
+    s_rptr[i] = (int32_t)(jptr[r0 + (i < rl ? i : rl)] - rbase);
+    s_cptr[i] = (int32_t)(jptr[c0 + (i < cl ? i : cl)] - cbase);
+  }
+  if (staged) {
+    for (int64_t e = threadIdx.x; e < rcount; e += blockDim.x) {
+      s_rtri[e] = jtri[rbase + e];
+      s_rvec[3 * e] = jvec[3 * (rbase + e)];
+      s_rvec[3 * e + 1] = jvec[3 * (rbase + e) + 1];
+      s_rvec[3 * e + 2] = jvec[3 * (rbase + e) + 2];
+    }
+    for (int64_t e = threadIdx.x; e < ccount; e += blockDim.x) {
+      s_ctri[e] = jtri[cbase + e];
+      s_cvec[3 * e] = jvec[3 * (cbase + e)];
+      s_cvec[3 * e + 1] = jvec[3 * (cbase + e) + 1];
+      s_cvec[3 * e + 2] = jvec[3 * (cbase + e) + 2];
+    }
+  }
+  __syncthreads();
+  for (int rr = ty; rr < CT; rr += 8) {
+    if (rr >= rl || tx >= cl) continue;
+    float acch = 0.f, accl = 0.f;
+    if (staged)
+      contract_entry<true, true>(V, ldv, s_rptr[rr], s_rptr[rr + 1], s_cptr[tx], s_cptr[tx + 1], s_rtri, s_rvec,
+                                 s_ctri, s_cvec, acch, accl, t0, t1);
+    else
+      contract_entry<false, true>(V, ldv, s_rptr[rr], s_rptr[rr + 1], s_cptr[tx], s_cptr[tx + 1], jtri + rbase,
+                                  jvec + 3 * rbase, jtri + cbase, jvec + 3 * cbase, acch, accl, t0, t1);
+    if (acch == 0.f && accl == 0.f) continue;
+    const int64_t o = (r0 + rr) * ldw + c0 + tx;
+    float h, l;
+    df_add(Wh[o], Wl[o], acch, accl, h, l);
+    two_sum(h, l, h, l);
+    Wh[o] = h;
+    Wl[o] = l;
+  }
+}
+
+cudaError_t launch_contract_panel(const DevGeom& g, int64_t t0, int64_t t1, int rt0, int nrt, cudaStream_t s) {
+  const int nbt = (int)((g.ndof + CT - 1) / CT);
+  const int64_t blocks = (int64_t)nrt * nbt;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  contract_panel_kernel<<<(unsigned)blocks, 256, 0, s>>>(g.d_V, g.nt, t0, t1, g.d_jptr, g.d_jtri, g.d_jvecf,
+                                                         g.ndof, nbt, rt0, g.d_Wh, g.wlo(), g.ldw);
+  return cudaGetLastError();
+}
+
 // rows row0 .. row0+nrows-1 of W as dense FP64 rows of length N
 __global__ void w_to_double_kernel(const float* __restrict__ Wh, const float* __restrict__ Wl,
                                    int64_t ldw, int64_t N, int64_t row0, int64_t nrows,
@@ -559,8 +636,9 @@ cudaError_t copy_diagonal(const DevGeom& g, double* out, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// W += rho Z Z^T for a screen with closed cells (Z: N x nc, the cells'
-// indicators); the correction is summed in FP64 and added to the float pair
+// W += rho Q Q^T for a screen with closed cells (Q: N x nc, an orthonormal
+// basis of the cells' indicators); the correction is summed in FP64 and added
+// to the float pair
 __global__ void augment_kernel(float* __restrict__ Wh, float* __restrict__ Wl, int64_t ldw, int64_t N,
                                const double* __restrict__ Z, int nc, double rho) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * N;

@@ -24,12 +24,15 @@ namespace msbem {
 #define DF_TILE 64
 __constant__ float c_wdf[12];   // rule weights as (hi, lo) pairs
 
+// PANEL: rows of tiles tb0 .. (V holds triangle rows tb0*64 ..), every column
+// tile, no mirrored write; otherwise the upper triangle of tiles, mirrored.
+template <bool PANEL>
 __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ cen,
                                                      const float* __restrict__ qoff,
                                                      const double* __restrict__ area,
                                                      const int32_t* __restrict__ tri, int nb,
                                                      int64_t nt, int64_t ldv,
-                                                     float2* __restrict__ V) {
+                                                     float2* __restrict__ V, int tb0) {
   __shared__ float s_off[DF_TILE * 36];
   __shared__ double s_cen[DF_TILE * 3];
   __shared__ double s_area[DF_TILE];
@@ -37,7 +40,10 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
   __shared__ float2 s_out[DF_TILE][DF_TILE + 1];
   // upper-triangle tile coordinates
   int bi, bj;
-  {
+  if (PANEL) {
+    bi = tb0 + (int)(blockIdx.x / nb);
+    bj = (int)(blockIdx.x % nb);
+  } else {
     const int64_t t = blockIdx.x;
     double disc = (2.0 * nb + 1.0) * (2.0 * nb + 1.0) - 8.0 * (double)t;
     int r = (int)floor(((2.0 * nb + 1.0) - sqrt(disc)) * 0.5);
@@ -129,9 +135,9 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
   for (int i = tid; i < DF_TILE * DF_TILE; i += blockDim.x) {
     int rr = i / DF_TILE, c = i % DF_TILE;
     int64_t R = row0 + rr, C = col0 + c;
-    if (R < nt && C < nt) V[R * ldv + C] = s_out[rr][c];
+    if (R < nt && C < nt) V[(R - (int64_t)tb0 * DF_TILE) * ldv + C] = s_out[rr][c];
   }
-  if (bi != bj) {
+  if (!PANEL && bi != bj) {
     for (int i = tid; i < DF_TILE * DF_TILE; i += blockDim.x) {
       int c = i / DF_TILE, rr = i % DF_TILE;
       int64_t R = row0 + rr, C = col0 + c;
@@ -154,8 +160,19 @@ cudaError_t launch_far_df(const DevGeom& g, cudaStream_t s) {
   int nb = (int)(g.nt_pad / DF_TILE);
   int64_t tiles = (int64_t)nb * (nb + 1) / 2;
   if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
-  far_df_kernel<<<(unsigned)tiles, 256, 0, s>>>(g.d_cen, g.d_qoff, g.d_area, g.d_tri, nb, g.nt, g.nt,
-                                                g.d_V);
+  far_df_kernel<false><<<(unsigned)tiles, 256, 0, s>>>(g.d_cen, g.d_qoff, g.d_area, g.d_tri, nb, g.nt, g.nt,
+                                                       g.d_V, 0);
+  return cudaGetLastError();
+}
+
+// rows [tb0*64, (tb0+ntb)*64) of V into a panel buffer of ntb*64 rows
+cudaError_t launch_far_df_panel(const DevGeom& g, int tb0, int ntb, cudaStream_t s) {
+  int nb = (int)(g.nt_pad / DF_TILE);
+  int64_t tiles = (int64_t)ntb * nb;
+  if (tiles <= 0) return cudaSuccess;
+  if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
+  far_df_kernel<true><<<(unsigned)tiles, 256, 0, s>>>(g.d_cen, g.d_qoff, g.d_area, g.d_tri, nb, g.nt, g.nt,
+                                                      g.d_V, tb0);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ struct Topo {
   // psi-coordinates of their indicators, cellZ[nu * ncells + c]
   int ncells = 0;
   std::vector<double> cellZ;
+  std::vector<double> cellQ;    // orthonormal basis Z L^-T of their span (Z^T Z = L L^T)
 };
 
 // Builds the topology; returns MSBEM_OK or an error status with a message.
@@ -117,8 +118,9 @@ struct DevGeom {
   CUtensorMap tm_W;              // 16 x 128 x 2 boxes of both planes (matvec.cu)
   CUtensorMap tm_Whi;            // 32 x 128 x 1 boxes of the hi plane
   double* d_W64 = nullptr;       // FP64 copy of W for the plain comparator (made on first use)
-  int ncells = 0;                // closed cells: W holds W + rho Z Z^T (Z: [N][ncells])
-  double* d_cellZ = nullptr;
+  int64_t panel_rows = 0;        // rows of V per panel in the last assembly (0: V in one piece)
+  int ncells = 0;                // closed cells: W holds W + rho Q Q^T (Q: [N][ncells], orthonormal)
+  double* d_cellZ = nullptr;     // Q
   double rho = 0.0;
   // preconditioner
   int64_t n_blocks = 0;
@@ -163,13 +165,17 @@ struct DevGeom {
 // launch wrappers (assemble.cu, factor.cu, pcg.cu); all return cudaError_t
 cudaError_t launch_far_fp64(const DevGeom& g, cudaStream_t s);
 cudaError_t launch_far_df(const DevGeom& g, cudaStream_t s);
+// t0, t1: the rows of V held (panel mode); t1 < 0: all rows
 cudaError_t launch_near(const DevGeom& g, int ss_order, const double* gl_x, const double* gl_w,
-                        int fp64, cudaStream_t s);
+                        int fp64, cudaStream_t s, int64_t t0 = 0, int64_t t1 = -1);
 cudaError_t launch_contract(const DevGeom& g, cudaStream_t s);
+// panel mode (V holds triangle rows tb0*64 .. (tb0+ntb)*64 - 1)
+cudaError_t launch_far_df_panel(const DevGeom& g, int tb0, int ntb, cudaStream_t s);
+cudaError_t launch_contract_panel(const DevGeom& g, int64_t t0, int64_t t1, int rt0, int nrt, cudaStream_t s);
 cudaError_t launch_rhs(const DevGeom& g, const double gvec[3], double* out, cudaStream_t s);
 cudaError_t copy_rows_to_double(const DevGeom& g, int64_t row0, int64_t nrows, double* out,
                                 cudaStream_t s);
-// diag(W) as FP64 (N values) and the rank-ncells update W += rho Z Z^T
+// diag(W) as FP64 (N values) and the rank-ncells update W += rho Q Q^T
 cudaError_t copy_diagonal(const DevGeom& g, double* out, cudaStream_t s);
 cudaError_t launch_augment(const DevGeom& g, double rho, cudaStream_t s);
 cudaError_t set_far_constants(const double bary[6][3], const double w[6]);

@@ -331,6 +331,30 @@ void build_cells(Topo& t) {
       if (c >= 0) z[c] += 1.0;
     }
   }
+  // orthonormal basis Q = Z L^-T of the kernel (Z^T Z = L L^T, Cholesky)
+  std::vector<double> G((size_t)nc * nc, 0.0), Lc((size_t)nc * nc, 0.0);
+  for (int64_t r = 0; r < t.ndof; ++r) {
+    const double* z = &t.cellZ[(size_t)r * nc];
+    for (int a = 0; a < nc; ++a)
+      for (int b = 0; b < nc; ++b) G[(size_t)a * nc + b] += z[a] * z[b];
+  }
+  for (int a = 0; a < nc; ++a) {
+    for (int b = 0; b <= a; ++b) {
+      double sum = G[(size_t)a * nc + b];
+      for (int k = 0; k < b; ++k) sum -= Lc[(size_t)a * nc + k] * Lc[(size_t)b * nc + k];
+      Lc[(size_t)a * nc + b] = (a == b) ? std::sqrt(sum) : sum / Lc[(size_t)b * nc + b];
+    }
+  }
+  t.cellQ.assign(t.cellZ.size(), 0.0);
+  for (int64_t r = 0; r < t.ndof; ++r) {
+    const double* z = &t.cellZ[(size_t)r * nc];
+    double* qv = &t.cellQ[(size_t)r * nc];
+    for (int a = 0; a < nc; ++a) {   // L q = z (forward substitution)
+      double sum = z[a];
+      for (int k = 0; k < a; ++k) sum -= Lc[(size_t)a * nc + k] * qv[k];
+      qv[a] = sum / Lc[(size_t)a * nc + a];
+    }
+  }
 }
 
 void build_near_pairs(const Topo& t, std::vector<NearPair>& out) {

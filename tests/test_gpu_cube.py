@@ -54,3 +54,37 @@ def test_cube_against_oracle(n):
             assert np.linalg.norm(L - pb.W @ mx["density"]) <= 1.05e-8 * np.linalg.norm(L)
             # the augmented solution solves the original singular system
             assert np.linalg.norm(L - pb.W0 @ out["density"]) <= 1e-7 * np.linalg.norm(L)
+
+
+@pytest.mark.parametrize("geom,rows", [(WL.book(8, 2, jitter=True, seed=3), 64), (WL.cube_midplanes(6, 2), 128),
+                                       (WL.panels(7, n=8, n_coarse=2), 192)], ids=lambda x: getattr(x, "name", x))
+def test_panel_assembly(geom, rows):
+    """V in row panels: W equals the one-piece assembly to rounding and the
+    oracle to the parity bar; the solves agree."""
+    pb = solver.Problem(geom)
+    with M.Solver(geom) as S:
+        S.assemble()
+        W1 = S.matrix()
+        S.assemble(panel_rows=rows)
+        Wp = S.matrix()
+        scale = np.abs(W1).max()
+        # another summation order of the same double-float terms (each entry sums
+        # ~100 terms with cancellation at 2^-48 per operation), and the panels
+        # sum W[nu, nu'] and W[nu', nu] in different orders: both at rounding
+        # level, ten times below the parity bar
+        assert np.abs(Wp - W1).max() <= 1e-13 * scale
+        assert np.abs(Wp - Wp.T).max() <= 1e-13 * scale
+        assert np.abs(Wp - pb.W).max() <= 1e-12 * scale
+        d = np.abs(np.diag(Wp) - np.diag(pb.W)) / np.abs(np.diag(pb.W))
+        assert d.max() <= 1e-12
+        S.factor()
+        out = S.solve(geom.g, rtol=1e-8)
+        pb.factor()
+        ref = pb.solve(geom.g, rtol=1e-8)
+        assert abs(out["iters"] - ref.iters) <= 1
+        with pytest.raises(M.MsbemError) as e:
+            S.assemble(panel_rows=100)
+        assert e.value.status == -1
+        with pytest.raises(M.MsbemError) as e:
+            S.assemble(panel_rows=64, far_kernel=1)
+        assert e.value.status == -1

@@ -97,3 +97,23 @@ def test_augmented_solve():
         r = pb.solve(gv, rtol=1e-10)
         assert np.abs(pb.Z.T @ r.x).max() <= 1e-8 * np.linalg.norm(r.x)
         assert np.linalg.norm(L - pb.W0 @ r.x) <= 1e-9 * np.linalg.norm(L)
+
+
+def test_projector_augmentation():
+    """W + rho Q Q^T with Q an orthonormal basis of span Z: Q^T Q = I, the
+    kernel directions get the eigenvalue rho exactly (W Q = 0), and the
+    preconditioned condition number stays small and bounded in h (the
+    additive Schwarz bound of Thm. main with H fixed)."""
+    kap = []
+    for n in (4, 8):
+        g = WL.cube_midplanes(n, 2)
+        pb = solver.Problem(g)
+        Q, Z = pb.Q, pb.Z
+        assert np.abs(Q.T @ Q - np.eye(8)).max() <= 1e-13
+        # span Q = span Z
+        assert np.linalg.norm(Z - Q @ (Q.T @ Z)) <= 1e-12 * np.linalg.norm(Z)
+        assert np.linalg.norm(pb.W @ Q - pb.rho * Q) <= 1e-13 * np.linalg.norm(pb.W) * 8
+        pb.factor()
+        r = pb.solve(g.g, rtol=1e-10)
+        kap.append(r.kappa)
+    assert max(kap) < 6.0
