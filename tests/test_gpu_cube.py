@@ -88,3 +88,84 @@ def test_panel_assembly(geom, rows):
         with pytest.raises(M.MsbemError) as e:
             S.assemble(panel_rows=64, far_kernel=1)
         assert e.value.status == -1
+
+
+def _oracle_rows(top, xyz, tri, rows, Q, rho):
+    """Rows of W + rho Q Q^T from the oracle's pair integrals: for dof nu,
+    W[nu, :] = sum_{k in J(nu)} s_k . (V[T_k, :] S), S the curl matrices."""
+    from oracle import core
+    s = top.curl_vectors()
+    S = top.S_matrices()
+    starts = np.searchsorted(top.s_dof, np.arange(top.ndof + 1))
+    out = []
+    for nu in rows:
+        ks = np.arange(starts[nu], starts[nu + 1])
+        R = np.repeat(top.s_tri[ks], top.nt)
+        C = np.tile(np.arange(top.nt), len(ks))
+        Vr = core.V_entries(xyz, tri, R, C).reshape(len(ks), top.nt)
+        row = np.zeros(top.ndof)
+        for c in range(3):
+            row += S[c].T @ (s[ks, c] @ Vr)
+        out.append(row + rho * (Q @ Q[nu]))
+    return np.array(out)
+
+
+def _oracle_diag(top, xyz, tri):
+    """diag(W) from the oracle's pair integrals (each distinct near pair once)."""
+    from oracle import core
+    s = top.curl_vectors()
+    starts = np.searchsorted(top.s_dof, np.arange(top.ndof + 1))
+    cnt = np.diff(starts)
+    owner = np.repeat(np.arange(top.ndof), cnt * cnt)
+    off = np.arange(owner.size) - np.repeat(np.cumsum(cnt * cnt) - cnt * cnt, cnt * cnt)
+    a = starts[owner] + off // cnt[owner]
+    b = starts[owner] + off % cnt[owner]
+    ta, tb = top.s_tri[a], top.s_tri[b]
+    key = np.minimum(ta, tb) * top.nt + np.maximum(ta, tb)
+    uk, inv = np.unique(key, return_inverse=True)
+    v = core.V_entries(xyz, tri, uk // top.nt, uk % top.nt)[inv]
+    d = np.zeros(top.ndof)
+    np.add.at(d, owner, v * np.einsum("ij,ij->i", s[a], s[b]))
+    return d
+
+
+def test_cube_config_full_size():
+    """The cube with mid-planes at h = 1/96 (N = 83,817, W 56 GB, V assembled in
+    panels): Z and rho against the oracle (rho from all 83,817 FP64 diagonal
+    entries), three sampled rows of W + rho Q Q^T, and the solves (true
+    residual, the plain FP64 comparator's iteration count, mixed precision)."""
+    from oracle.topology import Topology
+    geom = WL.cube_config()
+    top = Topology(geom.xyz, geom.tri)
+    Zo = top.cells()
+    xyz, tri = geom.xyz, geom.tri.astype(np.int32)
+    diag_o = _oracle_diag(top, xyz, tri)
+    rho_o = float(np.mean(diag_o))
+    Lc = np.linalg.cholesky(Zo.T @ Zo)
+    import scipy.linalg as sla
+    Qo = sla.solve_triangular(Lc, Zo.T, lower=True).T
+    with M.Solver(geom) as S:
+        S.assemble()
+        Z, rho = S.cells()
+        assert np.array_equal(Z, Zo)
+        # rho is the mean of 83,817 diagonal entries, each held to the 1e-12 bar
+        assert abs(rho - rho_o) <= 1e-11 * rho_o
+        rows = [0, 40000, S.n - 1]
+        Wo = _oracle_rows(top, xyz, tri, rows, Qo, rho_o)
+        scale = float(np.max(diag_o)) + rho_o
+        for r, wo in zip(rows, Wo):
+            wg = S.matrix(r, 1)[0]
+            print("row", r, "max |dW| / scale", np.abs(wg - wo).max() / scale, "diag rel", abs(wg[r] - wo[r]) / abs(wo[r]))
+            assert np.abs(wg - wo).max() <= 1e-12 * scale
+            assert abs(wg[r] - wo[r]) <= 1e-12 * abs(wo[r])
+        S.factor()
+        df = S.solve(geom.g, rtol=1e-8)
+        assert df["iters"] < 60
+        Y, _ = S.apply(df["density"][None, :])
+        L = S.rhs(geom.g)
+        assert np.linalg.norm(L - Y[0]) <= 1.05e-8 * np.linalg.norm(L)
+        assert np.abs(Z.T @ df["density"]).max() <= 1e-7 * np.linalg.norm(df["density"])
+        pl = S.solve(geom.g, rtol=1e-8, precision="fp64")
+        assert abs(pl["iters"] - df["iters"]) <= 1
+        mx = S.solve(geom.g, rtol=1e-8, precision="mixed")
+        assert np.linalg.norm(mx["density"] - df["density"]) <= 1e-7 * np.linalg.norm(df["density"])
