@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-modes", action="store_true", help="skip the solve-mode comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving simulation")
     ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--no-cube", action="store_true", help="skip the cube-with-mid-planes section")
     ap.add_argument("--workload", default="book64", choices=["book64", "book48", "book32", "flat"],
                     help="book64 is the measured workload; book48, book32 and flat are for profiling")
     ap.add_argument("--matvec", type=int, default=0,
@@ -316,6 +317,9 @@ def run_ours(args, world, rank, local, pg):
     serving = None
     if rank == 0 and not args.no_serve:
         serving = serve_bench(args.serve_requests, local, stream)
+    cube = None
+    if rank == 0 and not args.no_cube:
+        cube = cube_bench(local, stream)
 
     # end to end through the C ABI with host buffers: upload (host topology +
     # H2D from pinned memory) + assemble + factor + solve + D2H of the density
@@ -386,6 +390,7 @@ def run_ours(args, world, rank, local, pg):
             "roofline_matvec": roof_mv,
             "solve_modes": modes,
             "serving": serving,
+            "cube": cube,
             "clocks": ck,
             "gpu_launches": int(launches),
             "e2e": e2e,
@@ -477,6 +482,73 @@ def matvec_rooflines(S, N, stream, reps=5):
             out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                          "launch_ms": ms, "algorithmic": f"{8 if prec == 'df' else 4} B x N^2 (W read once)",
                          "peak_source": src}
+    return out
+
+
+def cube_bench(device, stream, reps: int = 3):
+    """The cube with its three mid-planes at h = 1/96 (N = 83,817; W 56 GB as
+    two FP32 planes; V, 220 GB, assembled in row panels; eight closed cells):
+    set-up phases, solves per form (median of `reps`), and the product
+    kernel's rooflines at this size (W far larger than L2)."""
+    import torch
+    import paper_2310_09204_gb300 as M
+    from paper_2310_09204_gb300 import workloads as WL
+    geom = WL.cube_config()
+    out = {"workload": "cube + 3 mid-planes, h=1/96, N=83817, N_T=165888, 324 patches, coarse 387, 8 cells, "
+                       "g seeded"}
+    with M.Solver(None, device=device) as S:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.upload(geom.xyz, geom.tri, geom.coarse_xyz, geom.coarse_tri, geom.parent, geom.patch)
+        torch.cuda.synchronize()
+        out["upload_s"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        S.assemble()
+        torch.cuda.synchronize()
+        out["assemble_s"] = time.perf_counter() - t0
+        t = S.timings()
+        out["phases_ms"] = {k: t[k] for k in ("far_ms", "near_ms", "contract_ms")}
+        t0 = time.perf_counter()
+        S.factor()
+        torch.cuda.synchronize()
+        out["factor_s"] = time.perf_counter() - t0
+        out["split"] = S.split_info()
+        rng = np.random.default_rng(0)
+        G = rng.uniform(-1.0, 1.0, (16, 3))
+        G[0] = geom.g
+        S.solve(G[0], precision="fp64")              # makes the FP64 copy of W
+        forms = {}
+        for name, prec in (("plain_fp64", "fp64"), ("df", "df"), ("mixed", "mixed")):
+            ms, it = [], 0
+            for r in range(reps):
+                m, o = _events(stream, lambda: S.solve(G[r], rtol=1e-8, precision=prec))
+                ms.append(m)
+                it = o["iters"]
+            forms[name] = {"solves_per_s": 1e3 / sorted(ms)[reps // 2], "iters": it}
+        m, o = _events(stream, lambda: S.solve_batch(G, rtol=1e-8, precision="mixed"))
+        forms["mixed_batch16"] = {"solves_per_s": 16e3 / m, "iters": int(o["iters"].max())}
+        base = forms["plain_fp64"]["solves_per_s"]
+        for v in forms.values():
+            v["vs_plain_fp64"] = v["solves_per_s"] / base
+        out["solves"] = forms
+        hbm, src = measured_peaks()
+        N = float(S.n)
+        roof = {}
+        for name, prec, k in (("df_k1", "df", 1), ("fp32_k1", "fp32", 1), ("df_k16", "df", 16),
+                              ("fp32_k16", "fp32", 16)):
+            X = rng.standard_normal((k, S.n))
+            S.apply(X, precision=prec)
+            ms = sorted(S.apply(X, precision=prec)[1] for _ in range(reps))[reps // 2]
+            if name == "df_k16":
+                a = FP32_OPS_PER_DF_FMA * 16 * N * N / (ms * 1e-3)
+                pk = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6
+                roof[name] = {"bound": "alu", "achieved": a / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s",
+                              "frac": a / pk, "launch_ms": ms}
+            else:
+                b = (8 if prec == "df" else 4) * N * N / (ms * 1e-3) / 1e9
+                roof[name] = {"bound": "hbm", "achieved": b, "peak": hbm, "unit": "GB/s", "frac": b / hbm,
+                              "launch_ms": ms, "peak_source": src}
+        out["roofline_matvec"] = roof
     return out
 
 

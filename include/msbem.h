@@ -291,7 +291,7 @@ typedef struct msbem_server_opts {
   int maxit;                /* iterations per request (inner, summed; 0: 1000)         */
   int chunk;                /* PCG iterations between scheduling points (0: 4)         */
   int admission_threads;    /* host threads admitting new geometries, each with its   */
-                            /* own context and stream (0: 2; at most 8)                */
+                            /* own context and stream (0: 4; at most 8)                */
 } msbem_server_opts;
 
 typedef struct msbem_server_stats {

@@ -600,7 +600,7 @@ int msbem_server_create(msbem_ctx* ctx, const msbem_server_opts* opts, msbem_ser
   S->opts = o;
   S->device = msbem_ctx_device(ctx);
   cudaSetDevice(S->device);
-  const int nw = o.admission_threads > 0 ? std::min(o.admission_threads, 8) : 2;
+  const int nw = o.admission_threads > 0 ? std::min(o.admission_threads, 8) : 4;
   for (int i = 0; i < nw; ++i) {
     auto W = std::make_unique<msbem_server::Worker>();
     if (cudaStreamCreateWithFlags(&W->stream, cudaStreamNonBlocking) != cudaSuccess) return MSBEM_CUDA_ERROR;
