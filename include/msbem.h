@@ -233,6 +233,20 @@ int msbem_mesh_cells(const double* xyz, int64_t nv, const int32_t* tri, int64_t 
  * DEVICE_TIMEOUT, OOM, CUDA_ERROR. */
 int msbem_apply(msbem_geom* g, const double* X, int k, int precision, double* Y, double* kernel_ms);
 
+/* The field U = DL Phi off the screen (Lemma lemrepDL, eq. formulaDL): for
+ * targets x_m off Gamma,
+ *   U(x) = sum_T sum_a J_{T,a} int_T n_T.(y - x) lambda_a(y) / (4 pi |x-y|^3) dy,
+ *   J_{T,a} = sum_nu Phi_nu (c_+ - c_-)(T, a, nu)  (the jump of the density),
+ * each triangle integrated by the 6-point rule on its 4^refine congruent
+ * sub-triangles (refine 0..4; raise it for targets within a few h of Gamma).
+ *   density[N]      Phi, e.g. from msbem_solve (host or device)
+ *   targets[3*M]    target points, xyz triples (host or device)
+ *   out[M]          U(x_m) (host or device)
+ *   kernel_ms       device time of the evaluation kernel (may be NULL)
+ * FP64 throughout.  Errors: INVALID_ARG, OOM, CUDA_ERROR. */
+int msbem_dl_potential(msbem_geom* g, const double* density, const double* targets, int64_t M, int refine,
+                       double* out, double* kernel_ms);
+
 /* Timing of the last assemble / factor / solve on this geometry, in
  * milliseconds measured with CUDA events on the context's stream:
  * t[0] far field, t[1] near field, t[2] contraction to W, t[3] factor,

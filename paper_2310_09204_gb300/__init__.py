@@ -89,6 +89,7 @@ def lib():
         "msbem_solve_batch": ([P, P, i32, ctypes.POINTER(SolveOpts), P, P, P, P], i32),
         "msbem_apply": ([P, P, i32, i32, P, P], i32),
         "msbem_cells": ([P, ctypes.POINTER(i32), P, ctypes.POINTER(ctypes.c_double)], i32),
+        "msbem_dl_potential": ([P, P, P, i64, i32, P, P], i32),
         "msbem_mesh_cells": ([P, i64, P, i64, ctypes.POINTER(i32), P, i64], i32),
         "msbem_server_create": ([P, ctypes.POINTER(ServerOpts), ctypes.POINTER(P)], i32),
         "msbem_server_destroy": ([P], i32),
@@ -296,6 +297,20 @@ class Solver:
         o = PrecondOpts(wire_basket, use_coarse)
         _check(self.ctx, lib().msbem_factor(self.geom, ctypes.byref(o)))
         return self
+
+    def potential(self, density, targets, refine: int = 0, out=None):
+        """U = DL Phi at target points (M x 3); returns (U, kernel_ms)."""
+        if isinstance(density, np.ndarray):
+            density = np.ascontiguousarray(density, np.float64)
+        if isinstance(targets, np.ndarray):
+            targets = np.ascontiguousarray(targets, np.float64).reshape(-1, 3)
+        M = targets.shape[0]
+        if out is None:
+            out = np.empty(M, np.float64)
+        ms = ctypes.c_double()
+        _check(self.ctx, lib().msbem_dl_potential(self.geom, _ptr(density), _ptr(targets), M, refine, _ptr(out),
+                                                  ctypes.byref(ms)))
+        return out, float(ms.value)
 
     def cells(self):
         """(Z, rho): the closed cells' indicators in the psi basis (N x ncells)

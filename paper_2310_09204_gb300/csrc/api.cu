@@ -756,6 +756,39 @@ int msbem_cells(const msbem_geom* g, int* ncells, double* Z, double* rho) {
   return MSBEM_OK;
 }
 
+int msbem_dl_potential(msbem_geom* g, const double* density, const double* targets, int64_t M, int refine,
+                       double* out, double* kernel_ms) {
+  if (!g || !density || !targets || !out || M < 0 || refine < 0 || refine > 4) return MSBEM_INVALID_ARG;
+  msbem_ctx* c = g->ctx;
+  cudaSetDevice(c->device);
+  const Topo& f = g->fine;
+  const int64_t N = f.ndof;
+  cudaStream_t s = c->stream;
+  std::vector<double> phi(N);
+  cudaError_t e = cudaMemcpy(phi.data(), density, sizeof(double) * N, cudaMemcpyDefault);
+  if (e != cudaSuccess) return cuda_fail(c, e, "msbem_dl_potential density");
+  // jump values J[T][a] from the curl lists, summed in list order
+  std::vector<double> J(3 * f.nt, 0.0);
+  for (int64_t nu = 0; nu < N; ++nu)
+    for (int64_t k = f.jptr[nu]; k < f.jptr[nu + 1]; ++k) J[3 * f.jtri[k] + f.jloc[k]] += phi[nu] * f.jcoef[k];
+  const bool xdev = is_device_ptr(targets), odev = is_device_ptr(out);
+  double *dx = nullptr, *dout = nullptr;
+  if (!xdev && (e = pool_alloc((void**)&dx, sizeof(double) * std::max<int64_t>(1, 3 * M), c->pool, s)) != cudaSuccess)
+    return cuda_fail(c, e, "msbem_dl_potential");
+  if (!odev && (e = pool_alloc((void**)&dout, sizeof(double) * std::max<int64_t>(1, M), c->pool, s)) != cudaSuccess)
+    return cuda_fail(c, e, "msbem_dl_potential");
+  if (!xdev) cudaMemcpyAsync(dx, targets, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, s);
+  float ms = 0.f;
+  e = dl_potential(g->dev, J, xdev ? targets : dx, M, refine, odev ? out : dout, &ms, s);
+  if (e == cudaSuccess && !odev) e = cudaMemcpyAsync(out, dout, sizeof(double) * M, cudaMemcpyDeviceToHost, s);
+  if (dx) cudaFreeAsync(dx, s);
+  if (dout) cudaFreeAsync(dout, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "msbem_dl_potential");
+  if (kernel_ms) *kernel_ms = ms;
+  return MSBEM_OK;
+}
+
 int msbem_last_timings(const msbem_geom* g, double t[5]) {
   if (!g || !t) return MSBEM_INVALID_ARG;
   for (int i = 0; i < 5; ++i) t[i] = g->dev.times[i];

@@ -236,6 +236,11 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
                          int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
                          int* refinements, cudaStream_t s);
 
+// double-layer potential at M targets (device arrays) from the jump values
+// J[T][a] (host, 3 per triangle); refine: 4^refine sub-triangles (potential.cu)
+cudaError_t dl_potential(DevGeom& g, const std::vector<double>& J, const double* X_dev, int64_t M, int refine,
+                         double* out_dev, float* kernel_ms, cudaStream_t s);
+
 // accessors of the opaque handles (api.cu)
 DevGeom& msbem_geom_dev(msbem_geom* g);
 int msbem_ctx_device(const msbem_ctx* c);
