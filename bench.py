@@ -32,13 +32,13 @@ METRIC = "PCG solves/s and p50/p99 latency at rel. residual 1e-8 vs plain FP64 G
 UNIT = "solves/s"
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # double-float far-field kernel: FP32-pipe operations per unordered pair
-# (36 evaluations x 82 + 6 x 45 per-point updates), counted from far_df.cu
-FP32_OPS_PER_FAR_PAIR = 36 * 82 + 6 * 45
+# (36 evaluations x 76 + 6 x 36 per-point updates), counted from far_df.cu
+FP32_OPS_PER_FAR_PAIR = 36 * 76 + 6 * 36
 # DRAM bytes (read + write) of one far_df_kernel launch, from an ncu capture of
 # the h=1/32 book (6,144 triangles: 1.37 MB read + 257.2 MB written), scaled to
 # the h=1/64 book by the number of triangle pairs (x16).  Valid for the kernel
 # as captured; reset to None when the kernel changes.
-FAR_DF_TRAFFIC_BOOK64 = 16 * (1.372672e6 + 257.199872e6)
+FAR_DF_TRAFFIC_BOOK64 = None   # recapture after the kernel change (was 16 x (1.37 + 257.2) MB)
 # double-float multiply-add on the FP32 pipe (df.cuh df_fma_acc)
 FP32_OPS_PER_DF_FMA = 13
 

@@ -10,7 +10,8 @@
 //   * per pair the centroid difference D = c_T - c_T' is formed once in FP64
 //     (exact to 2^-53 |D|) and split into a float pair by integer bit
 //     operations, so no FP64<->FP32 conversion instruction is issued;
-//   * per evaluation d = (a_p + D) - b_q is formed with error-free two-sums,
+//   * per evaluation d = (a_p + D) - b_q is formed with error-free two-sums
+//     (kept as unnormalised pairs),
 //     r^2 with FMA-exact squares, 1/r from the FP32 reciprocal square root
 //     followed by one second-order correction computed in double-float, and
 //     the weighted sums are accumulated as float pairs.
@@ -23,6 +24,14 @@ namespace msbem {
 
 #define DF_TILE 64
 __constant__ float c_wdf[12];   // rule weights as (hi, lo) pairs
+
+// a + b as an unnormalised pair (s, e): s + e = a + b to ~2^-48 relative and
+// |e| <= ulp(s) + |al + bl|; the consumers (df_rsqrt3, the next addition) only
+// need the sum, not a canonical split, so the renormalisation is left out
+__device__ __forceinline__ void df_add_raw(float ah, float al, float bh, float bl, float& s, float& e) {
+  two_sum(ah, bh, s, e);
+  e += al + bl;
+}
 
 // PANEL: rows of tiles tb0 .. (V holds triangle rows tb0*64 ..), every column
 // tile, no mirrored write; otherwise the upper triangle of tiles, mirrored.
@@ -91,16 +100,16 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
 #pragma unroll 1
       for (int p = 0; p < 6; ++p) {
         float uxh, uxl, uyh, uyl, uzh, uzl;   // u = a_p + D
-        df_add(a[6 * p + 0], a[6 * p + 1], Dxh, Dxl, uxh, uxl);
-        df_add(a[6 * p + 2], a[6 * p + 3], Dyh, Dyl, uyh, uyl);
-        df_add(a[6 * p + 4], a[6 * p + 5], Dzh, Dzl, uzh, uzl);
+        df_add_raw(a[6 * p + 0], a[6 * p + 1], Dxh, Dxl, uxh, uxl);
+        df_add_raw(a[6 * p + 2], a[6 * p + 3], Dyh, Dyl, uyh, uyl);
+        df_add_raw(a[6 * p + 4], a[6 * p + 5], Dzh, Dzl, uzh, uzl);
         float ih = 0.0f, il = 0.0f;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           float dxh, dxl, dyh, dyl, dzh, dzl;  // d = u - b_q
-          df_add(uxh, uxl, -bq[6 * q + 0], -bq[6 * q + 1], dxh, dxl);
-          df_add(uyh, uyl, -bq[6 * q + 2], -bq[6 * q + 3], dyh, dyl);
-          df_add(uzh, uzl, -bq[6 * q + 4], -bq[6 * q + 5], dzh, dzl);
+          df_add_raw(uxh, uxl, -bq[6 * q + 0], -bq[6 * q + 1], dxh, dxl);
+          df_add_raw(uyh, uyl, -bq[6 * q + 2], -bq[6 * q + 3], dyh, dyl);
+          df_add_raw(uzh, uzl, -bq[6 * q + 4], -bq[6 * q + 5], dzh, dzl);
           float y, corr;
           df_rsqrt3(dxh, dxl, dyh, dyl, dzh, dzl, y, corr);
           // inner += w_q * (y + corr)
