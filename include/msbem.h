@@ -227,7 +227,11 @@ int msbem_mesh_cells(const double* xyz, int64_t nv, const int32_t* tri, int64_t 
  *   X[k*N], Y[k*N]  row c = vector c (host or device pointers, independently)
  *   precision       0 double-float products (FP64-equivalent), 1 the plain
  *                   FP64 copy of W (made on first use), 2 FP32 products with
- *                   the hi plane of W (about 1e-7 relative)
+ *                   the hi plane of W (about 1e-7 relative), 3 double-float
+ *                   accuracy on the tensor cores: W and X cut into six exact
+ *                   8-bit integer slices (bf16), slice products summed exactly
+ *                   in FP32 accumulators (the slices of W, 12 bytes per entry,
+ *                   are made on first use and kept until the next assembly)
  *   kernel_ms       device time of the product kernel(s) alone (may be NULL)
  * Errors: INVALID_ARG (k outside 1..16, bad precision), NOT_READY (no W),
  * DEVICE_TIMEOUT, OOM, CUDA_ERROR. */

@@ -70,7 +70,7 @@ void free_dev(DevGeom& d, cudaStream_t s) {
   void* ptrs[] = {d.d_hist, d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
                   d.d_jptr, d.d_jtri, d.d_jvec, d.d_jvecf, d.d_jrhs, d.d_Wh, d.d_bptr, d.d_bdofs, d.d_boff,
                   d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pfp, d.d_rf, d.d_binvf,
-                  d.d_btile, d.d_W64, d.d_cellZ, d.d_WP, d.d_vec, d.d_scal};
+                  d.d_btile, d.d_W64, d.d_wsl, d.d_cellZ, d.d_WP, d.d_vec, d.d_scal};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
@@ -428,10 +428,11 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   // V (nt^2 float pairs) is scratch of the assembly only: taken from the pool
   // here and returned once W is formed, so a resident geometry holds W alone
   drop_pcg_graphs(d);
-  if (d.d_W64) {  // the FP64 copy follows W
+  if (d.d_W64) {  // the FP64 copy and the slices follow W
     cudaFreeAsync(d.d_W64, s);
     d.d_W64 = nullptr;
   }
+  drop_w_slices(d, s);
   // V in one piece when it fits, else in row panels of triangles (a multiple
   // of 64 rows) computed and contracted one after the other
   int64_t panel = opts ? opts->panel_rows : 0;
@@ -734,12 +735,13 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
 }
 
 int msbem_apply(msbem_geom* g, const double* X, int k, int precision, double* Y, double* kernel_ms) {
-  if (!g || !X || !Y || k < 1 || k > 16 || precision < 0 || precision > 2) return MSBEM_INVALID_ARG;
+  if (!g || !X || !Y || k < 1 || k > 16 || precision < 0 || precision > 3) return MSBEM_INVALID_ARG;
   msbem_ctx* c = g->ctx;
   if (!g->dev.assembled) return fail(c, MSBEM_NOT_READY, "msbem_apply: not assembled");
   cudaSetDevice(c->device);
-  // precision 0 -> kernel mode 0 (double-float), 1 -> plain FP64 copy, 2 -> FP32 hi plane
-  const int mode = precision == 0 ? 0 : precision == 1 ? 2 : 1;
+  // precision 0 -> kernel mode 0 (double-float), 1 -> plain FP64 copy, 2 -> FP32 hi plane,
+  // 3 -> double-float from integer slices on the tensor cores
+  const int mode = precision == 0 ? 0 : precision == 1 ? 2 : precision == 2 ? 1 : 3;
   float ms = 0.f;
   cudaError_t e = apply_w(g->dev, X, is_device_ptr(X), k, mode, Y, is_device_ptr(Y), &ms, c->stream);
   if (e == cudaErrorTimeout) return fail(c, MSBEM_DEVICE_TIMEOUT, "msbem_apply: a matrix copy did not complete");

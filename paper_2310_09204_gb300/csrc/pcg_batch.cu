@@ -776,7 +776,8 @@ __global__ void btranspose_in_kernel(const double* __restrict__ Xin, int64_t N, 
 
 // Y = W X for kb <= 16 vectors (rows of X_in, k x N, host or device); mode 0
 // double-float products, 1 FP32 products with the hi plane, 2 the plain FP64
-// copy (one vector at a time).  *kernel_ms receives the device time of the
+// copy (one vector at a time), 3 double-float from integer slices on the
+// tensor cores.  *kernel_ms receives the device time of the
 // product kernel(s) alone.
 cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mode, double* Y_out, bool out_dev,
                     float* kernel_ms, cudaStream_t s) {
@@ -785,11 +786,12 @@ cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mod
   if (N == 0) return cudaSuccess;
   cudaError_t e;
   if (mode == 2 && (e = ensure_w64(g, s)) != cudaSuccess) return e;
+  if (mode == 3 && (e = ensure_w_slices(g, s)) != cudaSuccess) return e;
   const unsigned gemv_blocks = matvec_blocks(N, 0);
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, (unsigned)((N + 15) / 16));
-  const int split = mode == 2 ? 1 : matvec_split(N, mode);
-  const size_t scr_bytes = matvec_scratch_bytes(N, kb, split);
+  const int split = mode >= 2 ? 1 : matvec_split(N, mode);
+  const size_t scr_bytes = mode == 3 ? tc_work_bytes(g) : matvec_scratch_bytes(N, kb, split);
   const size_t bytes = sizeof(double) * (3 * nvec + nparts) + sizeof(float) * 2 * kb * g.ldw +
                        sizeof(BatchState) + scr_bytes + 256;
   char* base = nullptr;
@@ -820,6 +822,11 @@ cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mod
     g.launches += kb;
     e = cudaMemcpyAsync(Y_out, Q, sizeof(double) * nvec, out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         s);
+  } else if (mode == 3) {
+    cudaEventRecord(ev[0], s);
+    e = launch_matvec_tc(g, kb, X, Q, part, &fl->all_done, &fl->err, scratch, s);
+    cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess) e = copy_out(g, Q, N, kb, Y_out, out_dev, s);
   } else {
     CUtensorMap tmX;
     const int planes = mode == 0 ? 2 : 1;
