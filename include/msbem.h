@@ -175,8 +175,18 @@ typedef struct msbem_solve_opts {
                       /*    is solved by PCG with FP32 products (hi plane of   */
                       /*    W) to inner_rtol; iters counts inner iterations,   */
                       /*    resid_hist holds the true relative residual after  */
-                      /*    each refinement step; fixed_iters is not allowed   */
-  double inner_rtol;  /* precision 2: inner tolerance (<= 0: default 1e-4)     */
+                      /*    each refinement step; fixed_iters is not allowed;  */
+                      /*  3 tensor cores, double-float: as 0 with the products */
+                      /*    formed by tcgen05 MMAs from six exact 8-bit        */
+                      /*    integer slices of W and of the vectors (W's slices */
+                      /*    take N*N*12 more bytes, made on first use);        */
+                      /*  4 mixed, tensor-core residual: as 2 with the         */
+                      /*    residual products as in 3;                         */
+                      /*  5 mixed, scaled FP16: as 4 with the inner products   */
+                      /*    on the tensor cores from an fp16 copy of W scaled  */
+                      /*    by a power of two per row (each entry to 2^-11 of  */
+                      /*    itself; N*N*2 more bytes)                          */
+  double inner_rtol;  /* precision 2, 4, 5: inner tolerance (<= 0: 1e-4)       */
 } msbem_solve_opts;
 
 /* Solve W Phi = L for constant Neumann data g by PCG from Phi_0 = 0
@@ -231,7 +241,10 @@ int msbem_mesh_cells(const double* xyz, int64_t nv, const int32_t* tri, int64_t 
  *                   accuracy on the tensor cores: W and X cut into six exact
  *                   8-bit integer slices (bf16), slice products summed exactly
  *                   in FP32 accumulators (the slices of W, 12 bytes per entry,
- *                   are made on first use and kept until the next assembly)
+ *                   are made on first use and kept until the next assembly),
+ *                   4 scaled FP16 on the tensor cores (an fp16 copy of W
+ *                   scaled by a power of two per row: each entry to 2^-11 of
+ *                   itself; the vectors as two fp16 terms; FP32 accumulation)
  *   kernel_ms       device time of the product kernel(s) alone (may be NULL)
  * Errors: INVALID_ARG (k outside 1..16, bad precision), NOT_READY (no W),
  * DEVICE_TIMEOUT, OOM, CUDA_ERROR. */
@@ -303,9 +316,11 @@ typedef struct msbem_server msbem_server;
 
 typedef struct msbem_server_opts {
   double hbm_budget_bytes;  /* admission limit for resident geometries (0: 80% of free) */
-  int precision;            /* 0 double-float PCG, 2 mixed (FP32 inner + refinement)   */
+  int precision;            /* as msbem_solve_opts.precision, except 1: 0 double-float */
+                            /* PCG, 2 mixed (FP32 inner + refinement), 3, 4, 5 their   */
+                            /* tensor-core forms                                        */
   double rtol;              /* relative residual per request (0: 1e-8)                 */
-  double inner_rtol;        /* precision 2: inner tolerance (0: 1e-4)                  */
+  double inner_rtol;        /* mixed precisions: inner tolerance (0: 1e-4)             */
   int maxit;                /* iterations per request (inner, summed; 0: 1000)         */
   int chunk;                /* PCG iterations between scheduling points (0: 4)         */
   int admission_threads;    /* host threads admitting new geometries, each with its   */

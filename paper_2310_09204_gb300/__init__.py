@@ -56,7 +56,7 @@ class ServerStats(ctypes.Structure):
 
 
 #: arithmetic of the solve's matrix-vector products (msbem_solve_opts.precision)
-PRECISION = {"df": 0, "fp64": 1, "mixed": 2}
+PRECISION = {"df": 0, "fp64": 1, "mixed": 2, "tc": 3, "mixed-tc": 4, "mixed-fp16": 5}
 
 
 def lib():
@@ -325,7 +325,7 @@ class Solver:
 
     def apply(self, X, precision="df", out=None):
         """Y = W X for up to 16 vectors (rows of X); returns (Y, kernel_ms)."""
-        prec = {"df": 0, "fp64": 1, "fp32": 2, "tc": 3}[precision]
+        prec = {"df": 0, "fp64": 1, "fp32": 2, "tc": 3, "fp16-tc": 4}[precision]
         if isinstance(X, np.ndarray):
             X = np.ascontiguousarray(X, np.float64).reshape(-1, self.n)
         k = X.shape[0]

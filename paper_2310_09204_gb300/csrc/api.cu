@@ -70,7 +70,7 @@ void free_dev(DevGeom& d, cudaStream_t s) {
   void* ptrs[] = {d.d_hist, d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
                   d.d_jptr, d.d_jtri, d.d_jvec, d.d_jvecf, d.d_jrhs, d.d_Wh, d.d_bptr, d.d_bdofs, d.d_boff,
                   d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pfp, d.d_rf, d.d_binvf,
-                  d.d_btile, d.d_W64, d.d_wsl, d.d_cellZ, d.d_WP, d.d_vec, d.d_scal};
+                  d.d_btile, d.d_W64, d.d_wsl, d.d_wf16, d.d_wexp, d.d_cellZ, d.d_WP, d.d_vec, d.d_scal};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
@@ -626,9 +626,9 @@ int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts,
   const int precision = opts ? opts->precision : 0;
   const double inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-4;
   if (!(rtol >= 0.0) || maxit < 1) return fail(c, MSBEM_INVALID_ARG, "rtol >= 0 and maxit >= 1 required");
-  if (precision < 0 || precision > 2) return fail(c, MSBEM_INVALID_ARG, "precision must be 0, 1 or 2");
-  if (precision == 2 && (fixed || !(inner < 1.0)))
-    return fail(c, MSBEM_INVALID_ARG, "precision 2: no fixed_iters, inner_rtol < 1");
+  if (precision < 0 || precision > 5) return fail(c, MSBEM_INVALID_ARG, "precision must be 0 .. 5");
+  if ((precision == 2 || precision >= 4) && (fixed || !(inner < 1.0)))
+    return fail(c, MSBEM_INVALID_ARG, "mixed precision: no fixed_iters, inner_rtol < 1");
   if (!d.assembled) return fail(c, MSBEM_NOT_READY, "msbem_solve: not assembled");
   if (prec && !d.factored) return fail(c, MSBEM_NOT_READY, "msbem_solve: call msbem_factor first");
   cudaSetDevice(c->device);
@@ -637,9 +637,14 @@ int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts,
   PcgOut po;
   cudaEventRecord(c->ev[6], c->stream);
   cudaError_t e;
-  if (precision == 2) {
+  if (precision == 2 || precision >= 4) {
     std::vector<PcgOut> outs;
-    e = run_ir_batch(d, gv, 1, rtol, maxit, inner, prec, d.d_vec, true, outs, nullptr, c->stream);
+    e = run_ir_batch(d, gv, 1, rtol, maxit, inner, prec, d.d_vec, true, outs, nullptr, c->stream, precision >= 4,
+                     precision == 5);
+    if (e == cudaSuccess) po = outs[0];
+  } else if (precision == 3) {
+    std::vector<PcgOut> outs;
+    e = run_pcg_batch(d, gv, 1, rtol, maxit, fixed, prec, d.d_vec, true, outs, c->stream, 1);
     if (e == cudaSuccess) po = outs[0];
   } else {
     e = run_pcg(d, gv, rtol, maxit, fixed, prec, precision, d.d_vec, po, c->stream);
@@ -683,9 +688,9 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
   const int precision = opts ? opts->precision : 0;
   const double inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-4;
   if (!(rtol >= 0.0) || maxit < 1) return fail(c, MSBEM_INVALID_ARG, "rtol >= 0 and maxit >= 1 required");
-  if (precision < 0 || precision > 2) return fail(c, MSBEM_INVALID_ARG, "precision must be 0, 1 or 2");
-  if (precision == 2 && (fixed || !(inner < 1.0)))
-    return fail(c, MSBEM_INVALID_ARG, "precision 2: no fixed_iters, inner_rtol < 1");
+  if (precision < 0 || precision > 5) return fail(c, MSBEM_INVALID_ARG, "precision must be 0 .. 5");
+  if ((precision == 2 || precision >= 4) && (fixed || !(inner < 1.0)))
+    return fail(c, MSBEM_INVALID_ARG, "mixed precision: no fixed_iters, inner_rtol < 1");
   if (!d.assembled) return fail(c, MSBEM_NOT_READY, "msbem_solve_batch: not assembled");
   if (prec && !d.factored) return fail(c, MSBEM_NOT_READY, "msbem_solve_batch: call msbem_factor first");
   cudaSetDevice(c->device);
@@ -704,12 +709,12 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
         e = cudaMemcpyAsync(density + (size_t)c0 * N, d.d_vec, sizeof(double) * N,
                             dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    } else if (precision == 2) {
+    } else if (precision == 2 || precision >= 4) {
       e = run_ir_batch(d, gvecs + 3 * c0, kb, rtol, maxit, inner, prec, density + (size_t)c0 * N, dev_out,
-                       outs, nullptr, c->stream);
+                       outs, nullptr, c->stream, precision >= 4, precision == 5);
     } else {
       e = run_pcg_batch(d, gvecs + 3 * c0, kb, rtol, maxit, fixed, prec, density + (size_t)c0 * N, dev_out,
-                        outs, c->stream);
+                        outs, c->stream, precision == 3);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "msbem_solve_batch");
     for (int j = 0; j < kb; ++j) {
@@ -735,13 +740,13 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
 }
 
 int msbem_apply(msbem_geom* g, const double* X, int k, int precision, double* Y, double* kernel_ms) {
-  if (!g || !X || !Y || k < 1 || k > 16 || precision < 0 || precision > 3) return MSBEM_INVALID_ARG;
+  if (!g || !X || !Y || k < 1 || k > 16 || precision < 0 || precision > 4) return MSBEM_INVALID_ARG;
   msbem_ctx* c = g->ctx;
   if (!g->dev.assembled) return fail(c, MSBEM_NOT_READY, "msbem_apply: not assembled");
   cudaSetDevice(c->device);
   // precision 0 -> kernel mode 0 (double-float), 1 -> plain FP64 copy, 2 -> FP32 hi plane,
-  // 3 -> double-float from integer slices on the tensor cores
-  const int mode = precision == 0 ? 0 : precision == 1 ? 2 : precision == 2 ? 1 : 3;
+  // 3 -> double-float from integer slices on the tensor cores, 4 -> scaled FP16 on the tensor cores
+  const int mode = precision == 0 ? 0 : precision == 1 ? 2 : precision == 2 ? 1 : precision;
   float ms = 0.f;
   cudaError_t e = apply_w(g->dev, X, is_device_ptr(X), k, mode, Y, is_device_ptr(Y), &ms, c->stream);
   if (e == cudaErrorTimeout) return fail(c, MSBEM_DEVICE_TIMEOUT, "msbem_apply: a matrix copy did not complete");

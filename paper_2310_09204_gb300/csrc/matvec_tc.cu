@@ -1,36 +1,48 @@
-// Q = W P in double-float accuracy on the tensor cores (tcgen05), for up to
-// 16 vectors: exact integer slicing of both operands.
+// Q = W P on the tensor cores (tcgen05) for up to 16 vectors, from integer
+// slices of both operands: double-float accuracy, or a scaled-FP16 product
+// for the inner solves of the iterative refinement.
 //
 // Every row i of W is scaled by 2^-e_i so that its entries lie in (-1/2, 1/2)
-// and written as six signed 8-bit digits, W_ij = 2^e_i sum_s a_s[i,j] 2^-8s
-// (+ a remainder below 2^-49 of 2^e_i), each digit rounded to nearest so that
-// |a_s| <= 128: an integer that bf16 holds exactly.  The vectors P are sliced
-// the same way per column (exponent f_c, digits b_t).  Then
+// and written in base 2^B as W_ij = 2^e_i sum_s a_s[i,j] 2^-Bs (+ remainder),
+// each digit rounded to nearest so that |a_s| <= 2^(B-1): an integer that the
+// MMA's 16-bit type holds exactly.  The vectors P are sliced the same way per
+// column (exponent f_c, digits b_t).  Then
 //
-//   (W P)_ic = 2^(e_i + f_c) sum_l 2^-8l sum_{s+t=l} sum_j a_s[i,j] b_t[j,c],
+//   (W P)_ic = 2^(e_i + f_c) sum_l 2^-Bl sum_{s+t=l} sum_j a_s[i,j] b_t[j,c],
 //
-// and every inner sum over j is a product of bf16 integer matrices: the tensor
-// core forms it with FP32 accumulation, exactly, as long as the partial sums
-// stay below 2^24.  Every slice pair (s, t) has its own accumulator; products
-// are below 2^14, so a window of 512 columns (sums below 2^23) is folded from
-// TMEM into double-float registers before the next one starts.  Levels above
-// 8 are left out: they add less than 2^-46 of the row and column scales.
+// and every inner sum over j is a product of integer matrices that the tensor
+// core forms with FP32 accumulation.
 //
-// One CTA: 128 rows (M = 128), all vectors padded to 16, a range of 32-column
-// chunks; TMA brings the six W slices (128 x 32 x 6 bf16, 64-byte swizzle)
-// and the six P slices (16 x 32 x 6) of a chunk into a four-stage ring.  The P
-// slices lie side by side in shared memory, so one MMA per W slice s and K
-// step (N = 16 x the slices u with s + u <= 8) forms all its pair sums at once
-// into TMEM (416 columns); all four warps fold them every 512 columns.  Warp 5
-// issues the copies, warp 4 the MMAs, warps 0-3 fold.  Waits are bounded;
-// TMEM is always freed.
+// * Double-float (TcDF): B = 8, six slices of W and of P in bf16, the slice
+//   pairs with s + t <= 8.  Products are below 2^14, so the pair sums of a
+//   window of 512 columns stay below 2^23 and are exact; they are folded from
+//   TMEM into double-float registers before the next window starts.  The
+//   levels left out and the remainders (2^-49 of the scales) keep the error
+//   below 2^-44 max_j |W_ij| sum_j |P_jc|.
+// * Scaled FP16 (TcF16): no digits but floating-point fp16 values: W_ij 2^(14-e_i)
+//   rounded to fp16 (2 bytes an entry; each entry to 2^-11 of itself, its
+//   own exponent within fp16's range below the row's largest entry), and the
+//   vectors as P_jc 2^(14-f_c) = hi + lo, two fp16 values; the two products
+//   accumulate in FP32 and (W P)_ic = 2^(e_i + f_c - 28) (W P_hi + W P_lo)_ic.
+//
+// The slices of W are kept in a blocked layout: tiles of 8 rows x 64 columns
+// (128-byte rows), the slices of a tile side by side, tiles by column chunk
+// within a row group, so that one copy of 128 rows x 64 columns reads 16
+// contiguous runs.  One CTA: 128 rows (M = 128), the vectors padded to 16, a
+// range of 64-column chunks.  Warp 5 issues the TMA copies (W slices with a
+// 128-byte swizzle, P slices side by side) into a ring of stages, warp 4
+// issues one MMA per W slice and K step with B = all the P slices paired with
+// it (N = 16 x their count), and warps 0-3 fold the accumulators every 512
+// columns.  Waits are bounded; TMEM is always freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "df.cuh"
@@ -38,25 +50,38 @@
 
 namespace msbem {
 
-#define TC_NSL 6          // slices per operand
-#define TC_LMAX 8         // highest level kept (s + t)
-#ifndef TC_ROWB
-#define TC_ROWB 128       // bytes of a chunk row: the swizzle span (32, 64 or 128)
-#endif
-#define TC_KC (TC_ROWB / 2)   // columns per chunk
-#define TC_WIN (512 / TC_KC)  // chunks per fold window (512 columns: pair sums below 2^23)
+#define TC_ROWB 128           // bytes of a chunk row (the 128-byte swizzle span)
+#define TC_KC 64              // columns per chunk
+#define TC_WIN (512 / TC_KC)  // chunks per fold window (512 columns)
 #define TC_ROWS 128
-#define TC_NV 16          // vectors (MMA N)
-#ifndef TC_STAGES
-#define TC_STAGES (256 / TC_ROWB)
-#endif
-#ifndef TC_PROMO
-#define TC_PROMO CU_TENSOR_MAP_L2_PROMOTION_L2_256B
-#endif
-#define TC_W_BYTES (TC_NSL * TC_ROWS * TC_KC * 2)   // 48 KB
-#define TC_P_BYTES (TC_NSL * TC_NV * TC_KC * 2)     // 6 KB
-#define TC_STAGE_BYTES (TC_W_BYTES + TC_P_BYTES)
-#define TC_SMEM (1024 + TC_STAGES * TC_STAGE_BYTES + 256)   // + barriers and flags (< 256 B)
+#define TC_NV 16              // vectors (16 columns per slice in the MMA's N)
+#define TC_NSTORE 6           // bf16 slices stored per entry of W
+#define TC_SMEM_RING (216 * 1024)
+
+// a slicing of the product: W slices read, P slices, highest level kept,
+// digit bits (0: floating-point fp16 values scaled by 2^14 instead of
+// integer digits), fp16 (else bf16) operands
+template <int NW_, int NP_, int LMAX_, int BITS_, bool F16_>
+struct TcCfg {
+  static constexpr int NW = NW_, NP = NP_, LMAX = LMAX_, BITS = BITS_;
+  static constexpr bool F16 = F16_;
+  static constexpr bool FLOATING = BITS_ == 0;
+  static constexpr int FSHIFT = 14;   // the floating values' scale 2^14 (per operand)
+  static constexpr int STAGE_W = NW * TC_ROWS * TC_ROWB;
+  static constexpr int STAGE_P = NP * TC_NV * TC_ROWB;
+  static constexpr int STAGE = STAGE_W + STAGE_P;
+  static constexpr int STAGES = TC_SMEM_RING / STAGE < 8 ? TC_SMEM_RING / STAGE : 8;
+  static constexpr int SMEM = 1024 + STAGES * STAGE + 256;   // + barriers and flags (< 256 B)
+  // P slices paired with W slice s, and the TMEM column where its pair sums start
+  __host__ __device__ static constexpr int nu(int s) { return LMAX - s < NP ? LMAX - s : NP; }
+  __host__ __device__ static constexpr int off(int s) { return s <= 1 ? 0 : off(s - 1) + TC_NV * nu(s - 1); }
+  static constexpr int COLS = off(NW + 1);
+  static constexpr int TMEM = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
+  static_assert(COLS <= 512, "accumulators exceed TMEM");
+  static_assert(STAGES >= 2, "ring too shallow");
+};
+using TcDF = TcCfg<6, 6, 8, 8, false>;     // 96 + 96 + 80 + 64 + 48 + 32 = 416 columns
+using TcF16 = TcCfg<1, 2, 3, 0, true>;     // 32 columns: W P_hi, W P_lo
 
 __device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t tc_ns() {
@@ -78,12 +103,11 @@ __device__ __noinline__ bool tc_wait(uint64_t* bar, uint32_t parity, const volat
   }
   return false;
 }
-// shared-memory matrix descriptor: K-major, rows of TC_ROWB bytes under the
-// swizzle of that span (layout 2: 128 B, 4: 64 B, 6: 32 B), 8-row groups
-// group_stride bytes apart
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t group_stride = 8 * TC_ROWB) {
+// shared-memory matrix descriptor: K-major, 128-byte rows under the 128-byte
+// swizzle (layout 2), 8-row groups group_stride bytes apart
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t group_stride) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(group_stride >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)(TC_ROWB == 128 ? 2 : TC_ROWB == 64 ? 4 : 6) << 61);
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
 // ---- slicing ---------------------------------------------------------------
@@ -107,76 +131,105 @@ __global__ void tc_row_exp_kernel(const float* __restrict__ Wh, const float* __r
   }
 }
 
-// six signed 8-bit digits of x in (-1/2, 1/2): x = sum_s d_s 256^-s + r
-__device__ __forceinline__ void tc_digits(double x, __nv_bfloat16* d, int64_t stride) {
-#pragma unroll
-  for (int s = 0; s < TC_NSL; ++s) {
-    x *= 256.0;
+// n digits of x in (-1/2, 1/2) in base 2^bits, rounded to nearest:
+// x = sum_s d_s 2^-(bits s) + r, |d_s| <= 2^(bits-1)
+template <typename T>
+__device__ __forceinline__ void tc_digits(double x, int n, int bits, T* d, int64_t stride) {
+  const double base = ldexp(1.0, bits);
+  for (int s = 0; s < n; ++s) {
+    x *= base;
     const double a = rint(x);
     x -= a;
-    d[s * stride] = __float2bfloat16((float)a);
+    if constexpr (std::is_same<T, __half>::value)
+      d[s * stride] = __float2half_rn((float)a);
+    else
+      d[s * stride] = __float2bfloat16((float)a);
   }
 }
 
-// Blocked layout of the W slices: tiles of 8 rows x TC_KC columns, the six
-// slices of a tile side by side, tiles by chunk within a row group:
-//   element (s, i, j) at (((i / 8) * nch + j / TC_KC) * 6 + s) * 8 * TC_KC + (i % 8) * TC_KC + j % TC_KC,
-// so that the copy of 128 rows x one chunk reads 16 runs of 6 tiles; rows
-// and columns past N hold zeros.
-__host__ __device__ inline int64_t tc_wsl_index(int s, int64_t i, int64_t j, int64_t nch) {
-  return (((i >> 3) * nch + j / TC_KC) * TC_NSL + s) * (8 * TC_KC) + (i & 7) * TC_KC + j % TC_KC;
+// x 2^shift (x in (-1/2, 1/2)) as n fp16 values: x 2^shift = d_0 + d_1 + ...,
+// each the fp16 rounding of what the previous left
+__device__ __forceinline__ void tc_fp16_split(double x, int n, int shift, __half* d, int64_t stride) {
+  x = ldexp(x, shift);
+  for (int s = 0; s < n; ++s) {
+    const __half h = __double2half(x);
+    d[s * stride] = h;
+    x -= (double)__half2float(h);
+  }
 }
+
+// Blocked layout of nsl slices of W: element (s, i, j) at
+//   (((i / 8) * nch + j / 64) * nsl + s) * 512 + (i % 8) * 64 + j % 64;
+// rows and columns past N hold zeros.
+__host__ __device__ inline int64_t tc_wsl_index(int s, int64_t i, int64_t j, int64_t nch, int nsl) {
+  return (((i >> 3) * nch + j / TC_KC) * nsl + s) * (8 * TC_KC) + (i & 7) * TC_KC + j % TC_KC;
+}
+template <typename T>
 __global__ void tc_slice_w_kernel(const float* __restrict__ Wh, const float* __restrict__ Wl, int64_t ldw, int64_t N,
-                                  int64_t nch, int64_t ngroups, const int* __restrict__ ex,
-                                  __nv_bfloat16* __restrict__ S) {
+                                  int64_t nch, int64_t ngroups, int nsl, int bits, const int* __restrict__ ex,
+                                  T* __restrict__ S) {
   const int64_t cols = nch * TC_KC;
   const int64_t n = ngroups * 8 * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / cols, j = e - i * cols;
     const double w = (i < N && j < N) ? ldexp(df_to_double(Wh[i * ldw + j], Wl[i * ldw + j]), -ex[i]) : 0.0;
-    __nv_bfloat16* d = S + tc_wsl_index(0, i, j, nch);
-    tc_digits(w, d, 8 * TC_KC);
+    if constexpr (std::is_same<T, __half>::value)
+      tc_fp16_split(w, nsl, bits, S + tc_wsl_index(0, i, j, nch, nsl), 8 * TC_KC);   // bits: the shift
+    else
+      tc_digits(w, nsl, bits, S + tc_wsl_index(0, i, j, nch, nsl), 8 * TC_KC);
   }
 }
 
-// column exponents of P (N x kb row-major): f_c as for the rows of W
-__global__ void tc_col_exp_kernel(const double* __restrict__ P, int64_t N, int kb, int* __restrict__ fx) {
-  __shared__ double sm[256];
-  const int c = blockIdx.x;
-  double m = 0.0;
-  for (int64_t i = threadIdx.x; i < N; i += 256) m = fmax(m, fabs(P[i * kb + c]));
+// column maxima of |P| (N x kb row-major): per-block maxima combined by an
+// atomic maximum on their bit patterns (the order of non-negative doubles)
+__global__ void tc_col_max_kernel(const double* __restrict__ P, int64_t N, int kb,
+                                  unsigned long long* __restrict__ mx) {
+  __shared__ unsigned long long sm[256];
+  const int64_t n = N * kb;
+  unsigned long long m = 0;
+  // a stride that is a multiple of kb keeps each thread on one column
+  const int64_t stride = (int64_t)gridDim.x * 256 / kb * kb;
+  const int64_t start = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (start < stride)
+    for (int64_t e = start; e < n; e += stride) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(P[e]));
+      m = b > m ? b : m;
+    }
   sm[threadIdx.x] = m;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    int e = 0;
-    if (sm[0] > 0.0) frexp(sm[0], &e);
-    fx[c] = sm[0] > 0.0 ? e + 1 : 0;
+  if (threadIdx.x < kb) {
+    // column c gathers the threads t with (block offset + t) = c mod kb
+    const int shift = (int)(((int64_t)blockIdx.x * 256) % kb);
+    unsigned long long r = 0;
+    for (int t = 0; t < 256; ++t)
+      if ((shift + t) % kb == (int)threadIdx.x) r = sm[t] > r ? sm[t] : r;
+    atomicMax(&mx[threadIdx.x], r);
   }
 }
 
-// P slices by chunk: element (u, c, j) at ((j / TC_KC * 6 + u) * 16 + c) * TC_KC + j % TC_KC
-// (vectors c >= kb and entries j >= N stay zero)
-__global__ void tc_slice_p_kernel(const double* __restrict__ P, int64_t N, int kb, const int* __restrict__ fx,
-                                  __nv_bfloat16* __restrict__ S) {
+// P slices by chunk: element (u, c, j) at ((j / 64 * np + u) * 16 + c) * 64 + j % 64
+// (vectors c >= kb and entries j >= N stay zero); column exponents f_c from
+// the maxima as for the rows of W
+template <typename T>
+__global__ void tc_slice_p_kernel(const double* __restrict__ P, int64_t N, int kb, int np, int bits,
+                                  const unsigned long long* __restrict__ mx, int* __restrict__ fx,
+                                  T* __restrict__ S) {
   const int64_t n = N * kb;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / kb;
     const int c = (int)(e - j * kb);
-    tc_digits(ldexp(P[e], -fx[c]), S + ((j / TC_KC) * TC_NSL * TC_NV + c) * TC_KC + j % TC_KC, TC_NV * TC_KC);
+    const double m = __longlong_as_double((long long)mx[c]);
+    int f = 0;
+    if (m > 0.0) frexp(m, &f);
+    f = m > 0.0 ? f + 1 : 0;
+    if (j == 0) fx[c] = f;
+    T* d = S + ((j / TC_KC) * np * TC_NV + c) * TC_KC + j % TC_KC;
+    if constexpr (std::is_same<T, __half>::value)
+      tc_fp16_split(ldexp(P[e], -f), np, bits, d, TC_NV * TC_KC);   // bits: the shift
+    else
+      tc_digits(ldexp(P[e], -f), np, bits, d, TC_NV * TC_KC);
   }
 }
-
-// ---- the product -------------------------------------------------------------
-// P slices paired with W slice s (levels s + u <= 8) and the TMEM column where
-// its accumulators start: 96 + 96 + 80 + 64 + 48 + 32 = 416 columns
-__host__ __device__ constexpr int tc_nu(int s) { return TC_LMAX - s < TC_NSL ? TC_LMAX - s : TC_NSL; }
-__host__ __device__ constexpr int tc_off(int s) { return s <= 1 ? 0 : tc_off(s - 1) + TC_NV * tc_nu(s - 1); }
-static_assert(tc_off(TC_NSL + 1) <= 512, "accumulators exceed TMEM");
-#define TC_TMEM_COLS 512
 
 // 16 consecutive accumulator columns of this warp's 32 lanes; the wait names
 // the registers so that no use is scheduled before the data has arrived
@@ -190,19 +243,23 @@ __device__ __forceinline__ void tc_ld16(uint32_t addr, uint32_t* r) {
                  "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
                :: "memory");
 }
+
+// ---- the product -------------------------------------------------------------
+template <class C>
 __global__ void __launch_bounds__(192, 1) tc_matvec_kernel(const __grid_constant__ CUtensorMap tmW,
                                                            const __grid_constant__ CUtensorMap tmP, int N,
                                                            int nchunks_all, int cps, int kb,
                                                            const int* __restrict__ ex, const int* __restrict__ fx,
                                                            double* __restrict__ split_part,
                                                            const int* __restrict__ stop, int* __restrict__ err) {
+  constexpr int ST = C::STAGES;
   if (*stop) return;
   extern __shared__ unsigned char tc_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(base + TC_STAGES * TC_STAGE_BYTES);   // copy landed
-  uint64_t* empty = full + TC_STAGES;                                  // its MMAs done
-  uint64_t* accfull = empty + TC_STAGES;                               // a window's sums final
-  uint64_t* accempty = accfull + 1;                                    // a window's sums read
+  uint64_t* full = (uint64_t*)(base + ST * C::STAGE);   // copy landed
+  uint64_t* empty = full + ST;                          // its MMAs done
+  uint64_t* accfull = empty + ST;                       // a window's sums final
+  uint64_t* accempty = accfull + 1;                     // a window's sums read
   uint32_t* tbase = (uint32_t*)(accempty + 1);
   volatile int* s_fail = (volatile int*)(tbase + 1);
   volatile int* s_issued = s_fail + 1;   // chunks whose copy was issued
@@ -214,11 +271,11 @@ __global__ void __launch_bounds__(192, 1) tc_matvec_kernel(const __grid_constant
   const int nwin = (nchunks + TC_WIN - 1) / TC_WIN;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(tbase)),
-                 "r"(TC_TMEM_COLS) : "memory");
+                 "r"(C::TMEM) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int st = 0; st < TC_STAGES; ++st) {
+    for (int st = 0; st < ST; ++st) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&full[st])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&empty[st])) : "memory");
     }
@@ -240,24 +297,24 @@ __global__ void __launch_bounds__(192, 1) tc_matvec_kernel(const __grid_constant
   for (int c = 0; c < TC_NV; ++c) { acch[c] = 0.f; accl[c] = 0.f; }
 
   if (warp == 5) {
-    // ---- producer: the copies of chunk t once the MMAs of chunk t - STAGES are done
+    // ---- producer: the copies of chunk t once the MMAs of chunk t - ST are done
     if (lane == 0) {
       for (int t = 0; t < nchunks; ++t) {
-        const int st = t % TC_STAGES;
-        if (t >= TC_STAGES && !tc_wait(&empty[st], (uint32_t)((t / TC_STAGES - 1) & 1), s_fail)) {
+        const int st = t % ST;
+        if (t >= ST && !tc_wait(&empty[st], (uint32_t)((t / ST - 1) & 1), s_fail)) {
           *s_fail = 1;
           break;
         }
-        unsigned char* sw = base + st * TC_STAGE_BYTES;
+        unsigned char* sw = base + st * C::STAGE;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem(&full[st])),
-                     "r"(TC_STAGE_BYTES) : "memory");
+                     "r"(C::STAGE) : "memory");
         asm volatile(
             "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
             ::"r"(tc_smem(sw)), "l"((uint64_t)&tmW), "r"(0), "r"(0), "r"(0), "r"(chunk0 + t), "r"(row0 >> 3),
             "r"(tc_smem(&full[st])) : "memory");
         asm volatile(
             "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-            ::"r"(tc_smem(sw + TC_W_BYTES)), "l"((uint64_t)&tmP), "r"(0), "r"(0), "r"(0), "r"(chunk0 + t),
+            ::"r"(tc_smem(sw + C::STAGE_W)), "l"((uint64_t)&tmP), "r"(0), "r"(0), "r"(0), "r"(chunk0 + t),
             "r"(tc_smem(&full[st])) : "memory");
         *s_issued = t + 1;
       }
@@ -266,29 +323,30 @@ __global__ void __launch_bounds__(192, 1) tc_matvec_kernel(const __grid_constant
     // ---- MMA issuer: one MMA per W slice and K step, B = the P slices paired with it
     if (lane == 0) {
       for (int t = 0; t < nchunks; ++t) {
-        const int st = t % TC_STAGES;
+        const int st = t % ST;
         const int w = t / TC_WIN;
         const bool first = t % TC_WIN == 0;
-        if (!tc_wait(&full[st], (uint32_t)((t / TC_STAGES) & 1), s_fail) ||
+        if (!tc_wait(&full[st], (uint32_t)((t / ST) & 1), s_fail) ||
             (first && w > 0 && !tc_wait(accempty, (uint32_t)((w - 1) & 1), s_fail))) {
           *s_fail = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sw = tc_smem(base + st * TC_STAGE_BYTES);
-        const uint32_t sp = sw + TC_W_BYTES;
+        const uint32_t sw = tc_smem(base + st * C::STAGE);
+        const uint32_t sp = sw + C::STAGE_W;
         for (int k = 0; k < TC_KC / 16; ++k)
 #pragma unroll
-          for (int sl = 1; sl <= TC_NSL; ++sl) {
-            // slice s of the copied tiles: one 8-row group every six tiles
-            const uint64_t ad = tc_desc(sw + (uint32_t)((sl - 1) * 8 * TC_ROWB) + 32u * k, TC_NSL * 8 * TC_ROWB);
-            const uint64_t bd = tc_desc(sp + 32u * k);
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                                   ((uint32_t)(TC_NV * tc_nu(sl) >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+          for (int sl = 1; sl <= C::NW; ++sl) {
+            // slice s of the copied tiles: one 8-row group every NW tiles
+            const uint64_t ad = tc_desc(sw + (uint32_t)((sl - 1) * 8 * TC_ROWB) + 32u * k, C::NW * 8 * TC_ROWB);
+            const uint64_t bd = tc_desc(sp + 32u * k, 8 * TC_ROWB);
+            const uint32_t ty = C::F16 ? 0u : 1u;   // operand type: 0 fp16, 1 bf16 (A and B alike)
+            const uint32_t idesc = (1u << 4) | (ty << 7) | (ty << 10) | ((uint32_t)(TC_NV * C::nu(sl) >> 3) << 17) |
+                                   ((uint32_t)(TC_ROWS >> 4) << 24);
             const uint32_t en = (first && k == 0) ? 0u : 1u;
             asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                         ::"r"(taddr + (uint32_t)tc_off(sl)), "l"(ad), "l"(bd), "r"(idesc), "r"(en) : "memory");
+                         ::"r"(taddr + (uint32_t)C::off(sl)), "l"(ad), "l"(bd), "r"(idesc), "r"(en) : "memory");
           }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      ::"r"(tc_smem(&empty[st])) : "memory");
@@ -307,28 +365,43 @@ __global__ void __launch_bounds__(192, 1) tc_matvec_kernel(const __grid_constant
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // level by level: the pair sums (exact integers below 2^23) add exactly
-      // in 32-bit integers; the sum v (below 2^26) enters the double-float
-      // accumulator as its FP32 rounding plus the (at most 2) that it missed
+      if constexpr (C::FLOATING) {
+        // floating values at one scale: the sums W P_u add into the double-float sums
 #pragma unroll
-      for (int l = 2; l <= TC_LMAX; ++l) {
+        for (int u = 1; u <= C::NP; ++u) {
+          uint32_t r[16];
+          tc_ld16(taddr + lanes + (uint32_t)(TC_NV * (u - 1)), r);
+#pragma unroll
+          for (int c = 0; c < TC_NV; ++c) {
+            float sh, e;
+            two_sum(acch[c], __uint_as_float(r[c]), sh, e);
+            acch[c] = sh;
+            accl[c] += e;
+          }
+        }
+      }
+      // level by level: the pair sums (integers below 2^30) add exactly in
+      // 32-bit integers; the sum v enters the double-float accumulator as its
+      // FP32 rounding plus what that missed
+#pragma unroll
+      for (int l = 2; l <= (C::FLOATING ? 1 : C::LMAX); ++l) {
         int lv[TC_NV];
 #pragma unroll
         for (int c = 0; c < TC_NV; ++c) lv[c] = 0;
 #pragma unroll
-        for (int sl = 1; sl <= TC_NSL; ++sl) {
+        for (int sl = 1; sl <= C::NW; ++sl) {
           const int u = l - sl;
-          if (u < 1 || u > tc_nu(sl)) continue;
+          if (u < 1 || u > C::nu(sl)) continue;
           uint32_t r[16];
-          tc_ld16(taddr + lanes + (uint32_t)(tc_off(sl) + TC_NV * (u - 1)), r);
+          tc_ld16(taddr + lanes + (uint32_t)(C::off(sl) + TC_NV * (u - 1)), r);
 #pragma unroll
           for (int c = 0; c < TC_NV; ++c) lv[c] += __float2int_rn(__uint_as_float(r[c]));
         }
-        const float sc = ldexpf(1.0f, -8 * l);
+        const float sc = ldexpf(1.0f, -C::BITS * l);
 #pragma unroll
         for (int c = 0; c < TC_NV; ++c) {
           const float hi = __int2float_rn(lv[c]);
-          const int lo = lv[c] - __float2int_rn(hi);   // |lo| <= 2: v is below 2^26
+          const int lo = lv[c] - __float2int_rn(hi);
           float sh, e;
           two_sum(acch[c], hi * sc, sh, e);
           acch[c] = sh;
@@ -351,7 +424,7 @@ __global__ void __launch_bounds__(192, 1) tc_matvec_kernel(const __grid_constant
           if (c >= kb) break;
           // scaled in FP64, so that no vector's range is limited by FP32's
           split_part[((int64_t)blockIdx.y * N + row) * kb + c] =
-              ldexp((double)acch[c] + (double)accl[c], e + fx[c]);
+              ldexp((double)acch[c] + (double)accl[c], e + fx[c] - (C::FLOATING ? 2 * C::FSHIFT : 0));
         }
       }
     }
@@ -359,15 +432,14 @@ __global__ void __launch_bounds__(192, 1) tc_matvec_kernel(const __grid_constant
     // let the copies and the MMAs still in flight finish (bounded) before the
     // shared memory and the accumulators are given back
     const int taken = *s_taken, issued = *s_issued;
-    for (int u = taken; u < issued; ++u)
-      tc_wait(&full[u % TC_STAGES], (uint32_t)((u / TC_STAGES) & 1), nullptr);
-    if (taken > 0) tc_wait(&empty[(taken - 1) % TC_STAGES], (uint32_t)(((taken - 1) / TC_STAGES) & 1), nullptr);
+    for (int u = taken; u < issued; ++u) tc_wait(&full[u % ST], (uint32_t)((u / ST) & 1), nullptr);
+    if (taken > 0) tc_wait(&empty[(taken - 1) % ST], (uint32_t)(((taken - 1) / ST) & 1), nullptr);
     atomicExch(err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(C::TMEM) : "memory");
 }
 
 // Q = the sum of the S splits' partials (in split order, FP64) and the
@@ -414,57 +486,93 @@ static PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
   return fn;
 }
 
-// bf16 tensor of `rank` dims (dims[0] innermost), byte strides of dims 1.., one box
-static cudaError_t encode_bf16(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
-                               const cuuint64_t* strides, const cuuint32_t* box) {
+// 16-bit tensor of `rank` dims (dims[0] innermost), byte strides of dims 1.., one box
+static cudaError_t encode16(CUtensorMap* map, bool f16, const void* base, int rank, const cuuint64_t* dims,
+                            const cuuint64_t* strides, const cuuint32_t* box) {
   auto fn = tc_encode_fn();
   if (!fn) return cudaErrorNotSupported;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, (void*)base, dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  TC_ROWB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
-                                 : TC_ROWB == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
-                  TC_PROMO, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, (void*)base,
+                  dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 static int64_t tc_nch(int64_t N) { return (N + TC_KC - 1) / TC_KC; }
 static int64_t tc_ngroups(int64_t N) { return (N + 7) / 8; }
-static size_t tc_wsl_elems(int64_t N) { return (size_t)tc_ngroups(N) * 8 * tc_nch(N) * TC_KC * TC_NSL; }
-static size_t tc_psl_elems(int64_t N) { return (size_t)tc_nch(N) * TC_NSL * TC_NV * TC_KC; }
+static size_t tc_wsl_elems(int64_t N, int nsl) { return (size_t)tc_ngroups(N) * 8 * tc_nch(N) * TC_KC * nsl; }
+static size_t tc_psl_elems(int64_t N, int np) { return (size_t)tc_nch(N) * np * TC_NV * TC_KC; }
 
-size_t tc_slices_bytes(const DevGeom& g) { return tc_wsl_elems(g.ndof) * 2 + sizeof(int) * g.ndof; }
+// W slices, nsl stored per tile; boxes of the first nw of them x 16 row groups
+static cudaError_t encode_w_slices(CUtensorMap* map, bool f16, const void* base, int64_t N, int nsl, int nw) {
+  const int64_t nch = tc_nch(N), ngr = tc_ngroups(N);
+  // (column in chunk, row in group, slice, chunk, row group)
+  const cuuint64_t dims[5] = {TC_KC, 8, (cuuint64_t)nsl, (cuuint64_t)nch, (cuuint64_t)ngr};
+  const cuuint64_t strides[4] = {TC_ROWB, 8 * TC_ROWB, (cuuint64_t)nsl * 8 * TC_ROWB,
+                                 (cuuint64_t)nch * nsl * 8 * TC_ROWB};
+  const cuuint32_t box[5] = {TC_KC, 8, (cuuint32_t)nw, 1, TC_ROWS / 8};
+  return encode16(map, f16, base, 5, dims, strides, box);
+}
 
-cudaError_t ensure_w_slices(DevGeom& g, cudaStream_t s) {
-  if (g.d_wsl || g.ndof == 0) return cudaSuccess;
+template <class C>
+static cudaError_t tc_set_attr() {
+  return cudaFuncSetAttribute(tc_matvec_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+}
+
+// per device, once: the shared memory of both products (outside any capture)
+static cudaError_t tc_init_device() {
   static std::mutex mu;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    static std::vector<int> ready;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (std::find(ready.begin(), ready.end(), dev) == ready.end()) {
-      cudaError_t e = cudaFuncSetAttribute(tc_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-      if (e != cudaSuccess) return e;
-      ready.push_back(dev);
-    }
-  }
-  cudaError_t e = pool_alloc((void**)&g.d_wsl, tc_slices_bytes(g), g.pool, s);
+  static std::vector<int> ready;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (std::find(ready.begin(), ready.end(), dev) != ready.end()) return cudaSuccess;
+  cudaError_t e = tc_set_attr<TcDF>();
+  if (e == cudaSuccess) e = tc_set_attr<TcF16>();
+  if (e == cudaSuccess) ready.push_back(dev);
+  return e;
+}
+
+size_t tc_slices_bytes(const DevGeom& g, int prec) {
+  return (prec == 0 ? tc_wsl_elems(g.ndof, TC_NSTORE) : tc_wsl_elems(g.ndof, 1)) * 2 + sizeof(int) * g.ndof;
+}
+
+// the row exponents (shared by both slicings) and the slices of one precision
+cudaError_t ensure_w_slices(DevGeom& g, int prec, cudaStream_t s) {
+  if (g.ndof == 0) return cudaSuccess;
+  if ((prec == 0 && g.d_wsl) || (prec == 1 && g.d_wf16)) return cudaSuccess;
+  cudaError_t e = tc_init_device();
   if (e != cudaSuccess) return e;
   const int64_t N = g.ndof, nch = tc_nch(N), ngr = tc_ngroups(N);
-  g.d_wexp = (int*)((char*)g.d_wsl + tc_wsl_elems(N) * 2);
-  tc_row_exp_kernel<<<(unsigned)N, 256, 0, s>>>(g.d_Wh, g.wlo(), g.ldw, N, g.d_wexp);
   const int64_t n = ngr * 8 * nch * TC_KC;
-  tc_slice_w_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64), 256, 0, s>>>(
-      g.d_Wh, g.wlo(), g.ldw, N, nch, ngr, g.d_wexp, (__nv_bfloat16*)g.d_wsl);
-  g.launches += 2;
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64);
+  if (!g.d_wexp) {
+    if ((e = pool_alloc((void**)&g.d_wexp, sizeof(int) * N, g.pool, s)) != cudaSuccess) return e;
+    tc_row_exp_kernel<<<(unsigned)N, 256, 0, s>>>(g.d_Wh, g.wlo(), g.ldw, N, g.d_wexp);
+    ++g.launches;
+  }
+  if (prec == 0) {
+    if ((e = pool_alloc((void**)&g.d_wsl, tc_wsl_elems(N, TC_NSTORE) * 2, g.pool, s)) != cudaSuccess) return e;
+    tc_slice_w_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(g.d_Wh, g.wlo(), g.ldw, N, nch, ngr, TC_NSTORE,
+                                                            TcDF::BITS, g.d_wexp, (__nv_bfloat16*)g.d_wsl);
+    ++g.launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return encode_w_slices(&g.tm_wsl, false, g.d_wsl, N, TC_NSTORE, TcDF::NW);
+  }
+  if ((e = pool_alloc((void**)&g.d_wf16, tc_wsl_elems(N, 1) * 2, g.pool, s)) != cudaSuccess) return e;
+  tc_slice_w_kernel<__half><<<blocks, 256, 0, s>>>(g.d_Wh, g.wlo(), g.ldw, N, nch, ngr, 1, TcF16::FSHIFT,
+                                                   g.d_wexp, (__half*)g.d_wf16);
+  ++g.launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // (column in chunk, row in group, slice, chunk, row group); boxes of 16 row groups
-  const cuuint64_t dims[5] = {TC_KC, 8, TC_NSL, (cuuint64_t)nch, (cuuint64_t)ngr};
-  const cuuint64_t strides[4] = {TC_KC * 2, 8 * TC_KC * 2, TC_NSL * 8 * TC_KC * 2,
-                                 (cuuint64_t)nch * TC_NSL * 8 * TC_KC * 2};
-  const cuuint32_t box[5] = {TC_KC, 8, TC_NSL, 1, TC_ROWS / 8};
-  return encode_bf16(&g.tm_wsl, g.d_wsl, 5, dims, strides, box);
+  return encode_w_slices(&g.tm_wf16, true, g.d_wf16, N, 1, 1);
+}
+
+void drop_w_slices(DevGeom& g, cudaStream_t s) {
+  for (void* p : {(void*)g.d_wsl, (void*)g.d_wf16, (void*)g.d_wexp})
+    if (p) cudaFreeAsync(p, s);
+  g.d_wsl = nullptr;
+  g.d_wf16 = nullptr;
+  g.d_wexp = nullptr;
 }
 
 // Column splits for order N (a function of N only, so that a vector's product
@@ -472,7 +580,7 @@ cudaError_t ensure_w_slices(DevGeom& g, cudaStream_t s) {
 // (row block x split) CTAs best, one CTA per SM on 152 SMs, with a slight
 // preference for fewer splits; every split keeps at least two fold windows.
 static int tc_split(int64_t N) {
-  const int64_t nchunks = (N + TC_KC - 1) / TC_KC;
+  const int64_t nchunks = tc_nch(N);
   const int64_t blocks = (N + TC_ROWS - 1) / TC_ROWS;
   const int64_t smax = std::min<int64_t>(64, std::max<int64_t>(1, nchunks / (2 * TC_WIN)));
   int best = 1;
@@ -492,52 +600,62 @@ static int tc_split(int64_t N) {
 }
 
 size_t tc_work_bytes(const DevGeom& g) {
-  return tc_psl_elems(g.ndof) * 2 + sizeof(double) * (size_t)tc_split(g.ndof) * g.ndof * TC_NV + 1024;
+  return tc_psl_elems(g.ndof, TcDF::NP) * 2 + sizeof(double) * (size_t)tc_split(g.ndof) * g.ndof * TC_NV + 1024;
 }
 
-void drop_w_slices(DevGeom& g, cudaStream_t s) {
-  if (g.d_wsl) cudaFreeAsync(g.d_wsl, s);
-  g.d_wsl = nullptr;
-  g.d_wexp = nullptr;
-}
-
-// Q (N x kb) and the partial sums of p.q (layout of launch_matvec) from P
-// (N x kb, row-major double); work: tc_work_bytes(g) of scratch.
-cudaError_t launch_matvec_tc(DevGeom& g, int kb, const double* P, double* Q, double* part, const int* stop, int* err,
-                             void* work, cudaStream_t s) {
+template <class C>
+static cudaError_t launch_cfg(DevGeom& g, const CUtensorMap& tmW, int kb, const double* P, double* Q, double* part,
+                              const int* stop, int* err, void* work, cudaStream_t s) {
   const int64_t N = g.ndof;
-  if (N <= 0 || kb < 1 || kb > TC_NV || !g.d_wsl) return cudaErrorInvalidValue;
   const int split = tc_split(N);
   char* cur = (char*)(((uintptr_t)work + 255) & ~(uintptr_t)255);
-  __nv_bfloat16* ps = (__nv_bfloat16*)cur;
-  const size_t pbytes = tc_psl_elems(N) * 2;
+  void* ps = cur;
+  const size_t pbytes = tc_psl_elems(N, C::NP) * 2;
   cur += (pbytes + 255) / 256 * 256;
-  int* fx = (int*)cur;
+  unsigned long long* mx = (unsigned long long*)cur;   // 16 maxima, then 16 exponents
+  int* fx = (int*)(cur + 128);
   cur += 256;
   double* sp = (double*)cur;
   CUtensorMap tmP;
   // (column in chunk, vector, slice, chunk); one chunk per box
-  const cuuint64_t dims[4] = {TC_KC, TC_NV, TC_NSL, (cuuint64_t)tc_nch(N)};
-  const cuuint64_t strides[3] = {TC_KC * 2, TC_NV * TC_KC * 2, TC_NSL * TC_NV * TC_KC * 2};
-  const cuuint32_t box[4] = {TC_KC, TC_NV, TC_NSL, 1};
-  cudaError_t e = encode_bf16(&tmP, ps, 4, dims, strides, box);
+  const cuuint64_t dims[4] = {TC_KC, TC_NV, (cuuint64_t)C::NP, (cuuint64_t)tc_nch(N)};
+  const cuuint64_t strides[3] = {TC_ROWB, TC_NV * TC_ROWB, (cuuint64_t)C::NP * TC_NV * TC_ROWB};
+  const cuuint32_t box[4] = {TC_KC, TC_NV, (cuuint32_t)C::NP, 1};
+  cudaError_t e = encode16(&tmP, C::F16, ps, 4, dims, strides, box);
   if (e != cudaSuccess) return e;
   cudaMemsetAsync(ps, 0, pbytes, s);
-  cudaMemsetAsync(fx, 0, sizeof(int) * TC_NV, s);
-  tc_col_exp_kernel<<<kb, 256, 0, s>>>(P, N, kb, fx);
-  tc_slice_p_kernel<<<(unsigned)std::min<int64_t>((N * kb + 255) / 256, 152 * 16), 256, 0, s>>>(P, N, kb, fx, ps);
-  const int nchunks = (int)((N + TC_KC - 1) / TC_KC);
+  cudaMemsetAsync(mx, 0, 256, s);
+  const unsigned pblocks = (unsigned)std::min<int64_t>((N * kb + 255) / 256, 152 * 16);
+  tc_col_max_kernel<<<pblocks, 256, 0, s>>>(P, N, kb, mx);
+  if constexpr (C::F16)
+    tc_slice_p_kernel<__half><<<pblocks, 256, 0, s>>>(P, N, kb, C::NP, C::FSHIFT, mx, fx, (__half*)ps);
+  else
+    tc_slice_p_kernel<__nv_bfloat16><<<pblocks, 256, 0, s>>>(P, N, kb, C::NP, C::BITS, mx, fx, (__nv_bfloat16*)ps);
+  const int nchunks = (int)tc_nch(N);
   const int cps = (nchunks + split - 1) / split;
   const int nsplit = (nchunks + cps - 1) / cps;
   const dim3 grid((unsigned)((N + TC_ROWS - 1) / TC_ROWS), (unsigned)nsplit);
-  tc_matvec_kernel<<<grid, 192, TC_SMEM, s>>>(g.tm_wsl, tmP, (int)N, nchunks, cps, kb, g.d_wexp, fx, sp, stop, err);
-  g.launches += 4;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // the reduction blocks must match those of the double-float product
+  tc_matvec_kernel<C><<<grid, 192, C::SMEM, s>>>(tmW, tmP, (int)N, nchunks, cps, kb, g.d_wexp, fx, sp, stop, err);
   static_assert(TC_PART_ROWS == 16, "blocks of the p.q partial sums");
   tc_combine_kernel<<<(unsigned)((N + TC_PART_ROWS - 1) / TC_PART_ROWS), 256, 0, s>>>(sp, nsplit, (int)N, kb, P, Q,
                                                                                       part, stop);
+  g.launches += 4;
   return cudaGetLastError();
+}
+
+// Q (N x kb) and the partial sums of p.q (layout of launch_matvec) from P
+// (N x kb, row-major double); prec 0 double-float, 1 scaled FP16; work:
+// tc_work_bytes(g) of scratch; the slices of that precision must exist.
+cudaError_t launch_matvec_tc(DevGeom& g, int prec, int kb, const double* P, double* Q, double* part,
+                             const int* stop, int* err, void* work, cudaStream_t s) {
+  const int64_t N = g.ndof;
+  if (N <= 0 || N > 0x7fffffff || kb < 1 || kb > TC_NV || !g.d_wexp) return cudaErrorInvalidValue;
+  if (prec == 0) {
+    if (!g.d_wsl) return cudaErrorInvalidValue;
+    return launch_cfg<TcDF>(g, g.tm_wsl, kb, P, Q, part, stop, err, work, s);
+  }
+  if (!g.d_wf16) return cudaErrorInvalidValue;
+  return launch_cfg<TcF16>(g, g.tm_wf16, kb, P, Q, part, stop, err, work, s);
 }
 
 }  // namespace msbem

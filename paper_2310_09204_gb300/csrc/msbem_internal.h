@@ -118,9 +118,13 @@ struct DevGeom {
   CUtensorMap tm_W;              // 16 x 128 x 2 boxes of both planes (matvec.cu)
   CUtensorMap tm_Whi;            // 32 x 128 x 1 boxes of the hi plane
   double* d_W64 = nullptr;       // FP64 copy of W for the plain comparator (made on first use)
-  void* d_wsl = nullptr;         // W as six bf16 integer slices [6][N][ldw] + row exponents (matvec_tc.cu)
-  int* d_wexp = nullptr;         //   (made on first use; follows W)
-  CUtensorMap tm_wsl;            // 64 x 128 x 6 boxes of the slices (128-byte swizzle)
+  // integer slices of W for the tensor-core products (matvec_tc.cu; made on
+  // first use, dropped with W): six bf16 8-bit slices, one fp16 11-bit slice,
+  // the row exponents they share, and their tensor maps
+  void* d_wsl = nullptr;
+  void* d_wf16 = nullptr;
+  int* d_wexp = nullptr;
+  CUtensorMap tm_wsl, tm_wf16;
   int64_t panel_rows = 0;        // rows of V per panel in the last assembly (0: V in one piece)
   int ncells = 0;                // closed cells: W holds W + rho Q Q^T (Q: [N][ncells], orthonormal)
   double* d_cellZ = nullptr;     // Q
@@ -203,16 +207,17 @@ cudaError_t launch_matvec(int mode, const CUtensorMap& tmW, const CUtensorMap& t
 int matvec_split(int64_t N, int mode);
 size_t matvec_scratch_bytes(int64_t N, int kb, int split);
 
-// Q = W P in double-float accuracy on the tensor cores from exact integer
-// slices of W and P (matvec_tc.cu); same outputs and part layout as mode 0 of
-// launch_matvec.  ensure_w_slices makes the slices of W (once per assembly);
-// work holds tc_work_bytes(g) of scratch.
-cudaError_t ensure_w_slices(DevGeom& g, cudaStream_t s);
+// Q = W P on the tensor cores from integer slices of W and P (matvec_tc.cu);
+// prec 0 double-float accuracy, 1 scaled FP16 (W to 11 bits under its row
+// scale); same outputs and part layout as mode 0 of launch_matvec.
+// ensure_w_slices makes the slices of W of that precision (once per
+// assembly); work holds tc_work_bytes(g) of scratch.
+cudaError_t ensure_w_slices(DevGeom& g, int prec, cudaStream_t s);
 void drop_w_slices(DevGeom& g, cudaStream_t s);
-size_t tc_slices_bytes(const DevGeom& g);
+size_t tc_slices_bytes(const DevGeom& g, int prec);
 size_t tc_work_bytes(const DevGeom& g);
-cudaError_t launch_matvec_tc(DevGeom& g, int kb, const double* P, double* Q, double* part, const int* stop, int* err,
-                             void* work, cudaStream_t s);
+cudaError_t launch_matvec_tc(DevGeom& g, int prec, int kb, const double* P, double* Q, double* part,
+                             const int* stop, int* err, void* work, cudaStream_t s);
 
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag,
                           cudaStream_t s, int* not_spd);
@@ -235,20 +240,22 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
 cudaError_t ensure_w64(DevGeom& g, cudaStream_t s);
 void launch_gemv64(const DevGeom& g, const double* p, double* q, double* part, const int* stop, cudaStream_t s);
 // Y = W X for kb <= 16 vectors (pcg_batch.cu); mode 0 double-float, 1 FP32 hi
-// plane, 2 plain FP64, 3 double-float from integer slices on the tensor cores
+// plane, 2 plain FP64, 3 double-float from integer slices on the tensor cores,
+// 4 scaled FP16 on the tensor cores
 cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mode, double* Y_out, bool out_dev,
                     float* kernel_ms, cudaStream_t s);
 void drop_pcg_graphs(DevGeom& g);
 // k <= 16 independent right-hand sides sharing the matrix-vector products
 // (pcg_batch.cu); X_out is k x N (row c = density of g_c)
+// (tensor: double-float products on the tensor cores)
 cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, int fixed,
                           int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
-                          cudaStream_t s);
+                          cudaStream_t s, int tensor = 0);
 // mixed precision: FP32 inner PCG inside double-float iterative refinement
 // (pcg_batch.cu); *refinements receives the number of refinement steps
 cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, double inner_rtol,
                          int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
-                         int* refinements, cudaStream_t s);
+                         int* refinements, cudaStream_t s, int tensor = 0, int inner_fp16 = 0);
 
 // double-layer potential at M targets (device arrays) from the jump values
 // J[T][a] (host, 3 per triangle); refine: 4^refine sub-triangles (potential.cu)

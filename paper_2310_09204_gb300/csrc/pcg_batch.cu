@@ -460,44 +460,53 @@ void enqueue_batch_iteration(DevGeom& g, const BatchBuffers& b, int kb, int prec
   double* rel_h = b.hist;
   double* alpha_h = rel_h + (size_t)kb * (hcap + 1);
   double* beta_h = alpha_h + (size_t)kb * hcap;
-  const CUtensorMap& tmW = mv_mode == 0 ? g.tm_W : g.tm_Whi;
-  launch_matvec(mv_mode, tmW, tmP, N, kb, b.P, b.Q, b.part, &b.bs->all_done, &b.bs->err, s, split, scratch);
-  breduce_kernel<<<kb, 256, 0, s>>>(b.part, (int)matvec_blocks(N, mv_mode), b.cs, offsetof(ColState, pq), b.bs);
+  if (mv_mode >= 3) {
+    launch_matvec_tc(g, mv_mode - 3, kb, b.P, b.Q, b.part, &b.bs->all_done, &b.bs->err, scratch, s);
+  } else {
+    const CUtensorMap& tmW = mv_mode == 0 ? g.tm_W : g.tm_Whi;
+    launch_matvec(mv_mode, tmW, tmP, N, kb, b.P, b.Q, b.part, &b.bs->all_done, &b.bs->err, s, split, scratch);
+  }
+  breduce_kernel<<<kb, 256, 0, s>>>(b.part, (int)matvec_blocks(N, mv_mode == 1 ? 1 : 0), b.cs,
+                                    offsetof(ColState, pq), b.bs);
   balpha_kernel<<<1, BK, 0, s>>>(b.cs, alpha_h, hcap, b.bs);
   bupdate_xr_kernel<<<rgrid, 256, 0, s>>>(b.X, b.R, b.P, b.Q, N, kb, b.cs, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rr), b.bs);
   bcheck_kernel<<<1, 32, 0, s>>>(b.cs, rel_h, hcap, b.bs);
-  apply_M_batch(g, b, kb, precondition, mv_mode, s);
+  apply_M_batch(g, b, kb, precondition, mv_mode == 1 || mv_mode == 4, s);
   bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz_new), b.bs);
   bbeta_kernel<<<1, BK, 0, s>>>(b.cs, beta_h, hcap, b.bs);
   bupdate_p_kernel<<<kStrideBlocks, 256, 0, s>>>(b.P, b.Pf, g.ldw, b.Z, N, kb, b.cs, 0, b.bs);
-  g.launches += 10 + (split > 1 ? 1 : 0);
+  g.launches += mv_mode >= 3 ? 9 : 10 + (split > 1 ? 1 : 0);   // (the tensor-core product counts its own)
 }
 
 // PCG from X = 0 on the kb right-hand sides Rin (device, N x kb row-major);
 // the iterates are written to X (device, N x kb).  mv_mode 0: double-float
 // products with W; 1: FP32 products with the hi plane (inner solves of the
-// iterative refinement).  Each column's relative residual is measured against
-// its own ||Rin_c||.
+// iterative refinement); 3: double-float products on the tensor cores; 4:
+// scaled-FP16 products on the tensor cores (inner solves).  The block inverses
+// are applied in FP32 with modes 1 and 4, in double-float otherwise.  Each
+// column's relative residual is measured against its own ||Rin_c||.
 static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, int fixed, int precondition,
                                   int mv_mode, const double* Rin, double* X, std::vector<PcgOut>& outs,
                                   cudaStream_t s) {
   const int64_t N = g.ndof;
   outs.assign(kb, PcgOut());
   const int64_t NH = std::max<int64_t>(g.n_coarse, 1);
-  const unsigned gemv_blocks = matvec_blocks(N, mv_mode);
+  const bool tc = mv_mode >= 3;
+  cudaError_t e;
+  if (tc && (e = ensure_w_slices(g, mv_mode - 3, s)) != cudaSuccess) return e;
+  const unsigned gemv_blocks = matvec_blocks(N, mv_mode == 1 ? 1 : 0);
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, BRED);
   const size_t hsz = (size_t)kb * (maxit + 1) + 2 * (size_t)kb * maxit;
-  const int split = matvec_split(N, mv_mode);
-  const size_t scr_bytes = matvec_scratch_bytes(N, kb, split);
+  const int split = tc ? 1 : matvec_split(N, mv_mode);
+  const size_t scr_bytes = tc ? tc_work_bytes(g) : matvec_scratch_bytes(N, kb, split);
   const size_t bytes = sizeof(double) * (4 * nvec + 2 * NH * kb + nparts + hsz) +
                        sizeof(float) * 2 * kb * g.ldw + sizeof(float2) * nvec + sizeof(ColState) * kb +
                        sizeof(BatchState) + scr_bytes + 512;
   char* base = nullptr;
-  cudaError_t e = pool_alloc((void**)&base, bytes, g.pool, s);
-  if (e != cudaSuccess) return e;
+  if ((e = pool_alloc((void**)&base, bytes, g.pool, s)) != cudaSuccess) return e;
   Carver cv{base};
   BatchBuffers b;
   b.X = X;
@@ -518,8 +527,8 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   std::vector<ColState> h_cs(kb);
   for (auto& c : h_cs) c = ColState{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   BatchState h_bs{0, kb, maxit, fixed, rtol, 0};
-  CUtensorMap tmP;
-  const int planes = mv_mode == 0 ? 2 : 1;
+  CUtensorMap tmP;   // the FP32 planes of P read by the CUDA-core products
+  const int planes = mv_mode == 1 ? 1 : 2;
   if ((e = encode_planes(&tmP, b.Pf, g.ldw, kb, kb * g.ldw, planes, matvec_pad(kb))) != cudaSuccess) {
     cudaFreeAsync(base, s);
     return e;
@@ -532,7 +541,7 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   const dim3 rgrid(BRED, kb);
   bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.R, N, kb, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, nL2), b.bs);
-  apply_M_batch(g, b, kb, precondition, mv_mode, s);
+  apply_M_batch(g, b, kb, precondition, mv_mode == 1 || mv_mode == 4, s);
   bupdate_p_kernel<<<kStrideBlocks, 256, 0, s>>>(b.P, b.Pf, g.ldw, b.Z, N, kb, b.cs, 1, b.bs);
   bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz), b.bs);
@@ -619,7 +628,7 @@ static cudaError_t batch_rhs(DevGeom& g, const double* gvecs, int kb, double* gv
 
 cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, int fixed,
                           int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
-                          cudaStream_t s) {
+                          cudaStream_t s, int tensor) {
   const int64_t N = g.ndof;
   outs.assign(kb, PcgOut());
   if (kb < 1 || kb > BK) return cudaErrorInvalidValue;
@@ -636,7 +645,7 @@ cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, 
   double* X = cv.take<double>(nvec);
   double* gv = cv.take<double>(3 * kb);
   if ((e = batch_rhs(g, gvecs, kb, gv, L, s)) == cudaSuccess)
-    e = pcg_batch_core(g, kb, rtol, maxit, fixed, precondition, 0, L, X, outs, s);
+    e = pcg_batch_core(g, kb, rtol, maxit, fixed, precondition, tensor ? 3 : 0, L, X, outs, s);
   if (e == cudaSuccess) e = copy_out(g, X, N, kb, X_out, out_on_device, s);
   cudaFreeAsync(base, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
@@ -647,12 +656,13 @@ cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, 
 // solved by the PCG above with FP32 products (hi plane of W) to the relative
 // tolerance inner_rtol, X += D, and the residual R = L - W X is recomputed
 // with the double-float product, until ||R_c|| <= rtol ||L_c|| for every
-// column.  Reported per column: the inner iterations summed, the true relative
+// column.  tensor: the residual's double-float product on the tensor cores;
+// inner_fp16: the inner products in scaled FP16 on the tensor cores.  Reported per column: the inner iterations summed, the true relative
 // residual after every refinement step (hist), and the Lanczos coefficients
 // of the first inner solve.
 cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, double inner_rtol,
                          int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
-                         int* refinements, cudaStream_t s) {
+                         int* refinements, cudaStream_t s, int tensor, int inner_fp16) {
   const int64_t N = g.ndof;
   outs.assign(kb, PcgOut());
   if (refinements) *refinements = 0;
@@ -661,16 +671,17 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
     for (auto& o : outs) { o.hist.push_back(0.0); o.status = MSBEM_OK; }
     return cudaStreamSynchronize(s);
   }
+  cudaError_t e;
+  if (tensor && (e = ensure_w_slices(g, 0, s)) != cudaSuccess) return e;
   const unsigned gemv_blocks = matvec_blocks(N, 0);
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, BRED);
-  const int split = matvec_split(N, 0);
-  const size_t scr_bytes = matvec_scratch_bytes(N, kb, split);
+  const int split = tensor ? 1 : matvec_split(N, 0);
+  const size_t scr_bytes = tensor ? tc_work_bytes(g) : matvec_scratch_bytes(N, kb, split);
   const size_t bytes = sizeof(double) * (5 * nvec + nparts + 3 * kb + 2 * kb) + sizeof(float) * 2 * kb * g.ldw +
                        sizeof(int) * kb + sizeof(BatchState) + scr_bytes + 256;
   char* base = nullptr;
-  cudaError_t e = pool_alloc((void**)&base, bytes, g.pool, s);
-  if (e != cudaSuccess) return e;
+  if ((e = pool_alloc((void**)&base, bytes, g.pool, s)) != cudaSuccess) return e;
   Carver cv{base};
   double* L = cv.take<double>(nvec);
   double* X = cv.take<double>(nvec);
@@ -735,7 +746,8 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
     bmask_kernel<<<kStrideBlocks, 256, 0, s>>>(R, (int64_t)nvec, kb, skip, Q);
     ++g.launches;
     std::vector<PcgOut> in;
-    if ((e = pcg_batch_core(g, kb, inner_rtol, budget, 0, precondition, 1, Q, D, in, s)) != cudaSuccess)
+    if ((e = pcg_batch_core(g, kb, inner_rtol, budget, 0, precondition, inner_fp16 ? 4 : 1, Q, D, in, s)) !=
+        cudaSuccess)
       return finish(e);
     for (int c = 0; c < kb; ++c) {
       if (conv[c]) continue;
@@ -747,10 +759,15 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
       if (in[c].status == MSBEM_DEVICE_TIMEOUT) st[c] = MSBEM_DEVICE_TIMEOUT;
     }
     baxpy_kernel<<<kStrideBlocks, 256, 0, s>>>(X, D, (int64_t)nvec);
-    bsplit_kernel<<<kStrideBlocks, 256, 0, s>>>(X, Xf, g.ldw, N, kb);
-    launch_matvec(0, g.tm_W, tmX, N, kb, X, Q, part, &fl->all_done, &fl->err, s, split, scratch);
+    if (tensor) {
+      launch_matvec_tc(g, 0, kb, X, Q, part, &fl->all_done, &fl->err, scratch, s);
+    } else {
+      bsplit_kernel<<<kStrideBlocks, 256, 0, s>>>(X, Xf, g.ldw, N, kb);
+      launch_matvec(0, g.tm_W, tmX, N, kb, X, Q, part, &fl->all_done, &fl->err, s, split, scratch);
+      g.launches += 2;
+    }
     bresid_kernel<<<kStrideBlocks, 256, 0, s>>>(L, Q, (int64_t)nvec, R);
-    g.launches += 4;
+    g.launches += 2;
     if ((e = cudaGetLastError()) != cudaSuccess) return finish(e);
   }
   cudaMemcpyAsync(&h_fl, fl, sizeof(BatchState), cudaMemcpyDeviceToHost, s);
@@ -777,7 +794,7 @@ __global__ void btranspose_in_kernel(const double* __restrict__ Xin, int64_t N, 
 // Y = W X for kb <= 16 vectors (rows of X_in, k x N, host or device); mode 0
 // double-float products, 1 FP32 products with the hi plane, 2 the plain FP64
 // copy (one vector at a time), 3 double-float from integer slices on the
-// tensor cores.  *kernel_ms receives the device time of the
+// tensor cores, 4 scaled FP16 on the tensor cores.  *kernel_ms receives the device time of the
 // product kernel(s) alone.
 cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mode, double* Y_out, bool out_dev,
                     float* kernel_ms, cudaStream_t s) {
@@ -786,12 +803,12 @@ cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mod
   if (N == 0) return cudaSuccess;
   cudaError_t e;
   if (mode == 2 && (e = ensure_w64(g, s)) != cudaSuccess) return e;
-  if (mode == 3 && (e = ensure_w_slices(g, s)) != cudaSuccess) return e;
+  if (mode >= 3 && (e = ensure_w_slices(g, mode - 3, s)) != cudaSuccess) return e;
   const unsigned gemv_blocks = matvec_blocks(N, 0);
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, (unsigned)((N + 15) / 16));
   const int split = mode >= 2 ? 1 : matvec_split(N, mode);
-  const size_t scr_bytes = mode == 3 ? tc_work_bytes(g) : matvec_scratch_bytes(N, kb, split);
+  const size_t scr_bytes = mode >= 3 ? tc_work_bytes(g) : matvec_scratch_bytes(N, kb, split);
   const size_t bytes = sizeof(double) * (3 * nvec + nparts) + sizeof(float) * 2 * kb * g.ldw +
                        sizeof(BatchState) + scr_bytes + 256;
   char* base = nullptr;
@@ -822,9 +839,9 @@ cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mod
     g.launches += kb;
     e = cudaMemcpyAsync(Y_out, Q, sizeof(double) * nvec, out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         s);
-  } else if (mode == 3) {
+  } else if (mode >= 3) {
     cudaEventRecord(ev[0], s);
-    e = launch_matvec_tc(g, kb, X, Q, part, &fl->all_done, &fl->err, scratch, s);
+    e = launch_matvec_tc(g, mode - 3, kb, X, Q, part, &fl->all_done, &fl->err, scratch, s);
     cudaEventRecord(ev[1], s);
     if (e == cudaSuccess) e = copy_out(g, Q, N, kb, Y_out, out_dev, s);
   } else {

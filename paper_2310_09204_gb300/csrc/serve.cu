@@ -12,10 +12,12 @@
 // the other slots (every per-slot sum runs in the same order whatever the
 // batch holds, so each result is bit for bit the one it gets alone).
 //
-// precision 0: each slot runs the double-float PCG of msbem_solve_batch.
-// precision 2: each slot runs the iterative refinement of the mixed mode --
-// inner PCG with FP32 products to inner_rtol, then X += D and the true
-// residual R = L - W X with the double-float product; the slot finishes when
+// precision 0 (3): each slot runs the double-float PCG of msbem_solve_batch
+// (with the tensor-core products).
+// precision 2 (4, 5): each slot runs the iterative refinement of the mixed
+// mode -- inner PCG with FP32 products (FP32, scaled FP16 on the tensor
+// cores) to inner_rtol, then X += D and the true residual R = L - W X with
+// the double-float product (on the tensor cores); the slot finishes when
 // ||R|| <= rtol ||L||, else restarts its inner solve on R.
 #include <algorithm>
 #include <atomic>
@@ -224,7 +226,14 @@ namespace {
 
 constexpr int kSlots = BK;
 
-size_t estimate_footprint(const GeomEntry& e) {
+bool is_mixed(int precision) { return precision == 2 || precision == 4 || precision == 5; }
+bool tc_residual(int precision) { return precision >= 3; }   // double-float products on the tensor cores
+// the product mode of the slots' PCG iterations (enqueue_batch_iteration)
+int inner_mode(int precision) {
+  return precision == 0 ? 0 : precision == 3 ? 3 : precision == 5 ? 4 : 1;
+}
+
+size_t estimate_footprint(const GeomEntry& e, int precision) {
   const size_t N = (size_t)std::max<int64_t>(e.ndof, 1);
   const size_t ldw = (N + 31) / 32 * 32;
   // W planes, FP64 + float-pair block inverses (faces of ~600 dofs at most plus
@@ -232,7 +241,11 @@ size_t estimate_footprint(const GeomEntry& e) {
   const size_t wb = (size_t)(12.0 * std::sqrt((double)N)) + 64;
   const size_t blocks = 16 * (N * 600 + wb * wb);
   const size_t batch = sizeof(double) * N * kSlots * 12 + sizeof(float) * 4 * kSlots * ldw;
-  return 8 * N * ldw + blocks + 8 * N * 64 + batch + (2u << 20);
+  // integer slices of W for the tensor-core products (bf16: 12 bytes an
+  // entry, fp16: 2), on padded 8 x 64 tiles
+  const size_t tiles = ((N + 7) / 8 * 8) * ((N + 63) / 64 * 64);
+  const size_t slices = (tc_residual(precision) ? 12 * tiles + 4 * N : 0) + (precision == 5 ? 2 * tiles : 0);
+  return 8 * N * ldw + blocks + 8 * N * 64 + batch + slices + (2u << 20);
 }
 
 size_t transient_bytes(const GeomEntry& e) { return sizeof(float2) * (size_t)e.nt * e.nt; }
@@ -260,7 +273,20 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
   const size_t nparts = (size_t)kb * std::max<unsigned>(matvec_blocks(N, 0), BRED);
   const size_t hsz = (size_t)kb * (maxit + 1) + 2 * (size_t)kb * maxit;
   B->split = std::max(matvec_split(N, 0), matvec_split(N, 1));
-  const size_t scr = matvec_scratch_bytes(N, kb, B->split);
+  const int prec = S->opts.precision;
+  size_t scr = matvec_scratch_bytes(N, kb, B->split);
+  if (tc_residual(prec)) {
+    // the slices of W, made here on the admission thread's context
+    cudaError_t ce = ensure_w_slices(g, 0, B->s);
+    if (ce == cudaSuccess && prec == 5) ce = ensure_w_slices(g, 1, B->s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(B->s);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(B.get());
+      return ce == cudaErrorMemoryAllocation ? MSBEM_OOM : MSBEM_CUDA_ERROR;
+    }
+    scr = std::max(scr, tc_work_bytes(g));
+  }
   B->bytes = sizeof(double) * (8 * nvec + 2 * NH * kb + nparts + hsz + 3 * kb + 2 * kb + N) +
              sizeof(float) * 4 * kb * g.ldw + sizeof(float2) * nvec + sizeof(ColState) * kb +
              2 * sizeof(BatchState) + sizeof(int) * kb + scr + 1024;
@@ -294,7 +320,7 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
   B->mask = cv.take<int>(kb);
   B->fl = cv.take<BatchState>(1);
   B->scratch = cv.take<char>(scr);
-  cudaError_t ce = encode_planes(&B->tmP, b.Pf, g.ldw, kb, kb * g.ldw, S->opts.precision == 2 ? 1 : 2,
+  cudaError_t ce = encode_planes(&B->tmP, b.Pf, g.ldw, kb, kb * g.ldw, inner_mode(prec) == 1 ? 1 : 2,
                                  matvec_pad(kb));
   if (ce == cudaSuccess) ce = encode_planes(&B->tmX, B->Xf, g.ldw, kb, kb * g.ldw, 2, matvec_pad(kb));
   // pinned snapshots: ColState[kb], nrm[2kb], mask[kb], BatchState
@@ -312,7 +338,7 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
   B->h_mask = (int*)(B->h_nrm + 2 * kb);
   B->h_bs = (BatchState*)(B->h_mask + kb);
   for (int c = 0; c < kb; ++c) B->h_cs[c] = ColState{0, 0, 0, 0, 0, 0, 0, 6, 0, 0, 0};
-  const double inner = S->opts.precision == 2 ? S->opts.inner_rtol : S->opts.rtol;
+  const double inner = is_mixed(prec) ? S->opts.inner_rtol : S->opts.rtol;
   *B->h_bs = BatchState{1, kb, maxit, 0, inner, 0};
   cudaMemsetAsync(B->base, 0, B->bytes, B->s);
   cudaMemcpyAsync(b.cs, B->h_cs, sizeof(ColState) * kb, cudaMemcpyHostToDevice, B->s);
@@ -351,8 +377,10 @@ int admit_now(msbem_server* S, msbem_ctx* actx, GeomEntry& e) {
   }
   DevGeom& d = msbem_geom_dev(g);
   const size_t NH = (size_t)std::max<int64_t>(d.n_coarse, 1);
+  const int prec = S->opts.precision;
   e.footprint = sizeof(float) * 2 * (size_t)d.ndof * d.ldw + (sizeof(double) + sizeof(float2)) * d.binv_size +
-                sizeof(double) * (NH * d.ndof + 8 * (size_t)d.ndof) + e.batch->bytes;
+                sizeof(double) * (NH * d.ndof + 8 * (size_t)d.ndof) + e.batch->bytes +
+                (tc_residual(prec) ? tc_slices_bytes(d, 0) : 0) + (prec == 5 ? tc_slices_bytes(d, 1) : 0);
   return MSBEM_OK;
 }
 
@@ -448,7 +476,8 @@ void schedule(msbem_server* S, GeomEntry& e) {
   DevGeom& g = msbem_geom_dev(e.geom);
   const int64_t N = g.ndof;
   const int kb = kSlots;
-  const bool mixed = S->opts.precision == 2;
+  const int prec = S->opts.precision;
+  const bool mixed = is_mixed(prec);
   const unsigned grid = kStrideBlocks;
   const dim3 rgrid(BRED, kb);
   cudaStream_t s = B.s;
@@ -480,9 +509,13 @@ void schedule(msbem_server* S, GeomEntry& e) {
     for (int c : refine) B.h_mask[c] = 1;
     cudaMemcpyAsync(B.mask, B.h_mask, sizeof(int) * kb, cudaMemcpyHostToDevice, s);
     s_axpy_cols<<<grid, 256, 0, s>>>(B.Xo, B.b.X, N, kb, B.mask);
-    bsplit_kernel<<<grid, 256, 0, s>>>(B.Xo, B.Xf, g.ldw, N, kb);
-    launch_matvec(0, g.tm_W, B.tmX, N, kb, B.Xo, B.b.Q, B.b.part, &B.fl->all_done, &B.fl->err, s,
-                  matvec_split(N, 0), B.scratch);
+    if (tc_residual(prec)) {
+      launch_matvec_tc(g, 0, kb, B.Xo, B.b.Q, B.b.part, &B.fl->all_done, &B.fl->err, B.scratch, s);
+    } else {
+      bsplit_kernel<<<grid, 256, 0, s>>>(B.Xo, B.Xf, g.ldw, N, kb);
+      launch_matvec(0, g.tm_W, B.tmX, N, kb, B.Xo, B.b.Q, B.b.part, &B.fl->all_done, &B.fl->err, s,
+                    matvec_split(N, 0), B.scratch);
+    }
     s_resid_cols<<<grid, 256, 0, s>>>(B.L, B.b.Q, B.Ro, N, kb, B.mask);
     bdot_kernel<<<rgrid, 256, 0, s>>>(B.Ro, B.Ro, N, kb, B.b.part, B.fl);
     bsum_kernel<<<kb, 256, 0, s>>>(B.b.part, BRED, B.nrm);
@@ -550,7 +583,7 @@ void schedule(msbem_server* S, GeomEntry& e) {
     cudaMemcpyAsync(B.mask, B.h_mask, sizeof(int) * kb, cudaMemcpyHostToDevice, s);
     B.h_bs->all_done = 0;
     cudaMemcpyAsync(B.b.bs, B.h_bs, sizeof(BatchState), cudaMemcpyHostToDevice, s);
-    const int f32 = mixed ? 1 : 0;
+    const int f32 = inner_mode(prec) == 1 || inner_mode(prec) == 4 ? 1 : 0;
     s_copy_cols<<<grid, 256, 0, s>>>(B.b.R, B.Ro, N, kb, B.mask);
     s_copy_cols<<<grid, 256, 0, s>>>(B.b.X, nullptr, N, kb, B.mask);
     bdot_kernel<<<rgrid, 256, 0, s>>>(B.b.R, B.b.R, N, kb, B.b.part, B.fl);
@@ -564,8 +597,8 @@ void schedule(msbem_server* S, GeomEntry& e) {
   }
   // 4. iterate the running slots
   if (e.active > 0) {
-    const int mv_mode = mixed ? 1 : 0;
-    const int split = matvec_split(N, mv_mode);
+    const int mv_mode = inner_mode(prec);
+    const int split = mv_mode >= 3 ? 1 : matvec_split(N, mv_mode);
     for (int it = 0; it < S->opts.chunk; ++it)
       enqueue_batch_iteration(g, B.b, kb, 1, mv_mode, B.tmP, split, B.scratch, S->opts.maxit, s);
     cudaMemcpyAsync(B.h_cs, B.b.cs, sizeof(ColState) * kb, cudaMemcpyDeviceToHost, s);
@@ -590,7 +623,7 @@ int msbem_server_create(msbem_ctx* ctx, const msbem_server_opts* opts, msbem_ser
   if (o.inner_rtol <= 0.0) o.inner_rtol = 1e-4;
   if (o.maxit <= 0) o.maxit = 1000;
   if (o.chunk <= 0) o.chunk = 4;
-  if (o.precision != 0 && o.precision != 2) return MSBEM_INVALID_ARG;
+  if (o.precision < 0 || o.precision > 5 || o.precision == 1) return MSBEM_INVALID_ARG;
   if (!(o.inner_rtol < 1.0)) return MSBEM_INVALID_ARG;
   if (o.hbm_budget_bytes <= 0.0) {
     size_t fr = 0, tot = 0;
@@ -669,7 +702,7 @@ double msbem_server_footprint(const msbem_server* S, uint64_t key) {
   if (!S) return -1.0;
   auto it = S->geoms.find(key);
   if (it == S->geoms.end()) return -1.0;
-  return (double)(estimate_footprint(*it->second) + transient_bytes(*it->second));
+  return (double)(estimate_footprint(*it->second, S->opts.precision) + transient_bytes(*it->second));
 }
 
 int msbem_server_submit(msbem_server* S, uint64_t key, const double g[3], double* density, double t_arrival,
@@ -721,7 +754,7 @@ int msbem_server_progress(msbem_server* S, int block, int* completed) {
         continue;
       }
       if (gs != G_OUT || e.pending.empty()) continue;
-      const size_t need = estimate_footprint(e) + transient_bytes(e);
+      const size_t need = estimate_footprint(e, S->opts.precision) + transient_bytes(e);
       if (!make_room(S, need)) {
         // wait while other geometries have work and will go idle; a geometry
         // that can never fit fails its requests

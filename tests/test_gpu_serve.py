@@ -50,7 +50,7 @@ def _serve(reqs, precision, interleave=False, budget=0.0):
         return outs, res, S.stats()
 
 
-@pytest.mark.parametrize("precision", ["df", "mixed"])
+@pytest.mark.parametrize("precision", ["df", "mixed", "tc", "mixed-tc", "mixed-fp16"])
 def test_alone_and_in_the_mix(precision):
     reqs = _requests(40, 31)       # > 16 on some geometry: slots are refilled
     mix, res, st = _serve(reqs, precision, interleave=True)
@@ -64,7 +64,7 @@ def test_alone_and_in_the_mix(precision):
         assert r["status"] == 0 and r["relres"] <= 1e-8 and r["latency_ms"] >= 0.0
 
 
-@pytest.mark.parametrize("precision", ["df", "mixed"])
+@pytest.mark.parametrize("precision", ["df", "mixed", "tc", "mixed-tc", "mixed-fp16"])
 def test_matches_batch_solve_and_oracle(precision):
     reqs = _requests(12, 32)
     outs, res, _ = _serve(reqs, precision)

@@ -148,3 +148,125 @@ def test_tc_product_full_size_book():
         scale = np.abs(W).max(axis=1)[None, :] * np.abs(X).sum(axis=1)[:, None]
         assert np.all(np.abs(Ytc - Ydf) <= 2 * BOUND * scale)
         print(f"book N={n}: tc {ms_tc:.3f} ms, df {ms_df:.3f} ms (16 vectors)")
+
+
+@pytest.mark.parametrize("geom", [WL.book(8, 2, jitter=True, seed=3), WL.panels(7, n=6)], ids=lambda g: g.name)
+def test_fp16_product_bound(geom):
+    """Scaled FP16 on the tensor cores: W rounded to 11 bits under its row's
+    power-of-two scale (at most 2^-10 of the row's largest entry), the vectors
+    to 22 bits, FP32 accumulation: within 2^-9 max_j |W_ij| sum_j |X_cj|."""
+    rng = np.random.default_rng(42)
+    with M.Solver(geom) as S:
+        S.assemble()
+        W = S.matrix()
+        X = rng.standard_normal((16, S.n))
+        X[2] *= 1e-150
+        X[5] *= 1e150
+        Y, ms = S.apply(X, precision="fp16-tc")
+        assert ms > 0.0
+        Ye = _exact_rows(W, X, np.arange(S.n))
+        scale = np.abs(W).max(axis=1)[:, None] * np.abs(X).sum(axis=1)[None, :]
+        err = np.abs(Y.T - Ye) / scale
+        assert err.max() <= 2.0 ** -9, err.max()
+        assert err.max() >= 2.0 ** -40            # it is the low-precision product
+        Y1, _ = S.apply(X[4:5], precision="fp16-tc")
+        assert np.array_equal(Y1[0], Y[4])
+
+
+SMALL = [WL.flat_config(), WL.book(8, 2, jitter=True, seed=3), WL.bowtie(6, 2)]
+
+
+@pytest.mark.parametrize("geom", SMALL, ids=lambda g: g.name)
+def test_tc_solve_against_oracle(geom):
+    """Double-float PCG with the tensor-core products: the parity bar of the
+    default path (iterations within +-1, densities to 1e-8 at a fixed count)."""
+    from oracle import solver
+    pb = solver.Problem(geom)
+    pb.factor()
+    ref = pb.solve(rtol=1e-8)
+    with M.Solver(geom) as S:
+        S.assemble().factor()
+        out = S.solve(geom.g, rtol=1e-8, precision="tc")
+        assert abs(out["iters"] - ref.iters) <= 1
+        fx = S.solve(geom.g, rtol=0.0, maxit=ref.iters, fixed=True, precision="tc")
+        assert np.linalg.norm(fx["density"] - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+        df = S.solve(geom.g, rtol=0.0, maxit=ref.iters, fixed=True)
+        assert np.linalg.norm(fx["density"] - df["density"]) <= 1e-11 * np.linalg.norm(df["density"])
+
+
+def test_tc_batch_column_independent():
+    geom = WL.book(8, 2, jitter=True, seed=3)
+    G = np.random.default_rng(12).uniform(-1, 1, (19, 3))
+    with M.Solver(geom) as S:
+        S.assemble().factor()
+        full = S.solve_batch(G, rtol=1e-9, precision="tc")
+        for c in (0, 9, 17):
+            alone = S.solve_batch(G[c:c + 1], rtol=1e-9, precision="tc")
+            assert alone["iters"][0] == full["iters"][c]
+            assert np.array_equal(alone["density"][0], full["density"][c])
+        one = S.solve(G[4], rtol=1e-9, precision="tc")
+        assert np.array_equal(one["density"], full["density"][4])
+        df = S.solve_batch(G[:16], rtol=1e-9)
+        assert np.abs(df["iters"] - full["iters"][:16]).max() <= 1
+        assert np.linalg.norm(df["density"] - full["density"][:16]) <= 1e-8 * np.linalg.norm(df["density"])
+
+
+@pytest.mark.parametrize("prec", ["mixed-tc", "mixed-fp16"])
+@pytest.mark.parametrize("geom", SMALL, ids=lambda g: g.name)
+def test_mixed_tc_reaches_true_residual(geom, prec):
+    """Mixed precision with the refinement residual on the tensor cores
+    (double-float product), the inner PCG in FP32 on the CUDA cores or in
+    scaled FP16 on the tensor cores; the TRUE residual with the oracle's W
+    meets the tolerance."""
+    from oracle import solver
+    pb = solver.Problem(geom)
+    rng = np.random.default_rng(21)
+    with M.Solver(geom) as S:
+        S.assemble().factor()
+        for g in (geom.g, rng.uniform(-1, 1, 3)):
+            L = pb.rhs(g)
+            out = S.solve(g, rtol=1e-8, precision=prec)
+            rel = np.linalg.norm(L - pb.W @ out["density"]) / np.linalg.norm(L)
+            assert rel <= 1.05e-8, rel
+            assert out["hist"][-1] <= 1e-8 and len(out["hist"]) >= 2
+            assert np.all(np.diff(out["hist"]) < 0)
+
+
+@pytest.mark.parametrize("prec", ["mixed-tc", "mixed-fp16"])
+def test_mixed_tc_batch_alone_and_in_the_mix(prec):
+    geom = WL.book(8, 2, jitter=True, seed=3)
+    from oracle import solver
+    pb = solver.Problem(geom)
+    G = np.random.default_rng(22).uniform(-1, 1, (6, 3))
+    G[3] = 0.0
+    with M.Solver(geom) as S:
+        S.assemble().factor()
+        bt = S.solve_batch(G, rtol=1e-8, precision=prec)
+        for c in range(len(G)):
+            if c == 3:
+                assert bt["iters"][c] == 0 and np.all(bt["density"][c] == 0.0)
+                continue
+            L = pb.rhs(G[c])
+            assert np.linalg.norm(L - pb.W @ bt["density"][c]) <= 1.05e-8 * np.linalg.norm(L)
+        alone = S.solve_batch(G[1:2], rtol=1e-8, precision=prec)
+        assert np.array_equal(alone["density"][0], bt["density"][1])
+
+
+def test_tensor_modes_full_size_book():
+    """The full-size book: 16 right-hand sides in the tensor-core modes;
+    true residuals with the device's own W, densities against the default
+    double-float batch."""
+    geom = WL.book_config()
+    G = np.random.default_rng(31).uniform(-1, 1, (16, 3))
+    with M.Solver(geom) as S:
+        S.assemble().factor()
+        ref = S.solve_batch(G, rtol=1e-8)
+        W = S.matrix()
+        L = np.stack([S.rhs(g) for g in G])
+        for prec in ("tc", "mixed-tc", "mixed-fp16"):
+            out = S.solve_batch(G, rtol=1e-8, precision=prec)
+            R = L - out["density"] @ W
+            rel = np.linalg.norm(R, axis=1) / np.linalg.norm(L, axis=1)
+            assert rel.max() <= 1.05e-8, (prec, rel.max())
+            d = np.linalg.norm(out["density"] - ref["density"], axis=1) / np.linalg.norm(ref["density"], axis=1)
+            assert d.max() <= 1e-6, (prec, d.max())
