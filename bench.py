@@ -64,12 +64,13 @@ def parse():
     ap.add_argument("--no-modes", action="store_true", help="skip the solve-mode comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving simulation")
     ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-precision", default="mixed", choices=["mixed", "mixed-tc", "mixed-fp16", "df", "tc"])
     ap.add_argument("--no-cube", action="store_true", help="skip the cube-with-mid-planes section")
     ap.add_argument("--workload", default="book64", choices=["book64", "book48", "book32", "flat"],
                     help="book64 is the measured workload; book48, book32 and flat are for profiling")
     ap.add_argument("--matvec", type=int, default=0,
                     help="microbenchmark only: time the product kernel on K vectors (msbem_apply)")
-    ap.add_argument("--matvec-precision", default="df", choices=["df", "fp32", "fp64"])
+    ap.add_argument("--matvec-precision", default="df", choices=["df", "fp32", "fp64", "tc", "fp16-tc"])
     return ap.parse_args()
 
 
@@ -316,7 +317,7 @@ def run_ours(args, world, rank, local, pg):
 
     serving = None
     if rank == 0 and not args.no_serve:
-        serving = serve_bench(args.serve_requests, local, stream)
+        serving = serve_bench(args.serve_requests, local, stream, precision=args.serve_precision)
     cube = None
     if rank == 0 and not args.no_cube:
         cube = cube_bench(local, stream)
@@ -421,13 +422,20 @@ def solve_modes(S, geom, stream, nreq=16, seed=7):
     rng = np.random.default_rng(seed)
     G = rng.uniform(-1.0, 1.0, (nreq, 3))
     G[0] = geom.g
-    for prec in ("fp64", "df", "mixed"):          # warm-up (graphs, FP64 copy of W)
+    batch_forms = (("df_batch", "df"), ("mixed_batch", "mixed"), ("tc_batch", "tc"), ("mixed_tc_batch", "mixed-tc"),
+                   ("mixed_fp16_batch", "mixed-fp16"))
+    for prec in ("fp64", "df", "mixed", "tc", "mixed-tc"):   # warm-up (graphs, FP64 copy and slices of W)
         S.solve(G[0], precision=prec)
-    S.solve_batch(G, precision="mixed")
-    S.solve_batch(G, precision="df")
-    out = {"requests": nreq, "rtol": 1e-8, "data": "g_c uniform in [-1,1]^3 (seed 7), g_0 = workload g"}
+    for _, prec in batch_forms:
+        S.solve_batch(G, precision=prec)
+    out = {"requests": nreq, "rtol": 1e-8, "data": "g_c uniform in [-1,1]^3 (seed 7), g_0 = workload g",
+           "forms": {"df": "double-float products (CUDA cores)", "mixed": "FP32 inner PCG, double-float residual",
+                     "tc": "double-float products on the tensor cores (integer slices)",
+                     "mixed_tc": "FP32 inner PCG, tensor-core double-float residual",
+                     "mixed_fp16": "scaled-FP16 tensor-core inner PCG, tensor-core double-float residual"}}
     ref = np.empty((nreq, S.n))
-    for name, prec in (("plain_fp64", "fp64"), ("df", "df"), ("mixed", "mixed")):
+    for name, prec in (("plain_fp64", "fp64"), ("df", "df"), ("mixed", "mixed"), ("tc", "tc"),
+                       ("mixed_tc", "mixed-tc")):
         lat, it = [], []
         for c in range(nreq):
             ms, r = _events(stream, lambda: S.solve(G[c], rtol=1e-8, precision=prec))
@@ -442,7 +450,7 @@ def solve_modes(S, geom, stream, nreq=16, seed=7):
         lat.sort()
         out[name] = {"solves_per_s": 1e3 * nreq / sum(lat), "p50_ms": lat[nreq // 2], "p99_ms": lat[-1],
                      "iters": [int(min(it)), int(max(it))], "mode": "one request per call"}
-    for name, prec in (("df_batch", "df"), ("mixed_batch", "mixed")):
+    for name, prec in batch_forms:
         ms, r = _events(stream, lambda: S.solve_batch(G, rtol=1e-8, precision=prec))
         diff = max(float(np.linalg.norm(r["density"][c] - ref[c]) / np.linalg.norm(ref[c])) for c in range(nreq))
         # true residuals with the double-float product
@@ -454,20 +462,30 @@ def solve_modes(S, geom, stream, nreq=16, seed=7):
                      "mode": f"{nreq} requests in one call"}
     base = out["plain_fp64"]["solves_per_s"]
     out["speedup_vs_plain_fp64"] = {k: out[k]["solves_per_s"] / base
-                                    for k in ("df", "mixed", "df_batch", "mixed_batch")}
+                                    for k in ("df", "mixed", "tc", "mixed_tc") + tuple(n for n, _ in batch_forms)}
     return out
 
 
+# bytes of W read per entry by each product: double-float planes, FP32 hi
+# plane, the six bf16 slices of the tensor-core double-float product, the
+# fp16 copy of the scaled-FP16 product
+MATVEC_BYTES = {"df": 8, "fp32": 4, "tc": 12, "fp16-tc": 2}
+
+
 def matvec_rooflines(S, N, stream, reps=5):
-    """Device time of the matrix-vector product kernel (msbem_apply reports the
-    kernel's own CUDA-event time) against its bound: HBM for one vector
-    (double-float: 8 bytes per entry of W, FP32: 4), the FP32 pipe for 16
-    double-float vectors (13 FP32 operations per entry and vector)."""
+    """Device time of the matrix-vector products (msbem_apply reports the
+    product kernels' own CUDA-event time) against their bound: HBM for the
+    products that read W once per call (double-float and FP32 for one vector,
+    the tensor-core products for any count: 12 or 2 bytes an entry), the FP32
+    pipe for 16 double-float vectors (13 FP32 operations per entry and
+    vector)."""
     hbm, src = measured_peaks()
     fp32_peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6
     rng = np.random.default_rng(3)
     out = {}
-    for name, prec, k in (("df_k1", "df", 1), ("fp32_k1", "fp32", 1), ("df_k16", "df", 16), ("fp32_k16", "fp32", 16)):
+    for name, prec, k in (("df_k1", "df", 1), ("fp32_k1", "fp32", 1), ("df_k16", "df", 16), ("fp32_k16", "fp32", 16),
+                          ("tc_k1", "tc", 1), ("tc_k16", "tc", 16), ("fp16tc_k1", "fp16-tc", 1),
+                          ("fp16tc_k16", "fp16-tc", 16)):
         X = rng.standard_normal((k, N))
         S.apply(X, precision=prec)
         ms = sorted(S.apply(X, precision=prec)[1] for _ in range(reps))[reps // 2]
@@ -477,10 +495,10 @@ def matvec_rooflines(S, N, stream, reps=5):
             out[name] = {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
                          "frac": ach / fp32_peak, "launch_ms": ms, "algorithmic": "13 x 16 x N^2 FP32 ops"}
         else:
-            b = (8 if prec == "df" else 4) * float(N) * N
+            b = MATVEC_BYTES[prec] * float(N) * N
             ach = b / (ms * 1e-3) / 1e9
             out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "launch_ms": ms, "algorithmic": f"{8 if prec == 'df' else 4} B x N^2 (W read once)",
+                         "launch_ms": ms, "algorithmic": f"{MATVEC_BYTES[prec]} B x N^2 (W read once)",
                          "peak_source": src}
     return out
 
@@ -517,16 +535,18 @@ def cube_bench(device, stream, reps: int = 3):
         G = rng.uniform(-1.0, 1.0, (16, 3))
         G[0] = geom.g
         S.solve(G[0], precision="fp64")              # makes the FP64 copy of W
+        S.solve(G[0], precision="mixed-tc")          # makes the slices of W
         forms = {}
-        for name, prec in (("plain_fp64", "fp64"), ("df", "df"), ("mixed", "mixed")):
+        for name, prec in (("plain_fp64", "fp64"), ("df", "df"), ("mixed", "mixed"), ("mixed_tc", "mixed-tc")):
             ms, it = [], 0
             for r in range(reps):
                 m, o = _events(stream, lambda: S.solve(G[r], rtol=1e-8, precision=prec))
                 ms.append(m)
                 it = o["iters"]
             forms[name] = {"solves_per_s": 1e3 / sorted(ms)[reps // 2], "iters": it}
-        m, o = _events(stream, lambda: S.solve_batch(G, rtol=1e-8, precision="mixed"))
-        forms["mixed_batch16"] = {"solves_per_s": 16e3 / m, "iters": int(o["iters"].max())}
+        for name, prec in (("mixed_batch16", "mixed"), ("mixed_tc_batch16", "mixed-tc"), ("tc_batch16", "tc")):
+            m, o = _events(stream, lambda: S.solve_batch(G, rtol=1e-8, precision=prec))
+            forms[name] = {"solves_per_s": 16e3 / m, "iters": int(o["iters"].max())}
         base = forms["plain_fp64"]["solves_per_s"]
         for v in forms.values():
             v["vs_plain_fp64"] = v["solves_per_s"] / base
@@ -535,7 +555,7 @@ def cube_bench(device, stream, reps: int = 3):
         N = float(S.n)
         roof = {}
         for name, prec, k in (("df_k1", "df", 1), ("fp32_k1", "fp32", 1), ("df_k16", "df", 16),
-                              ("fp32_k16", "fp32", 16)):
+                              ("fp32_k16", "fp32", 16), ("tc_k16", "tc", 16)):
             X = rng.standard_normal((k, S.n))
             S.apply(X, precision=prec)
             ms = sorted(S.apply(X, precision=prec)[1] for _ in range(reps))[reps // 2]
@@ -545,7 +565,7 @@ def cube_bench(device, stream, reps: int = 3):
                 roof[name] = {"bound": "alu", "achieved": a / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s",
                               "frac": a / pk, "launch_ms": ms}
             else:
-                b = (8 if prec == "df" else 4) * N * N / (ms * 1e-3) / 1e9
+                b = MATVEC_BYTES[prec] * N * N / (ms * 1e-3) / 1e9
                 roof[name] = {"bound": "hbm", "achieved": b, "peak": hbm, "unit": "GB/s", "frac": b / hbm,
                               "launch_ms": ms, "peak_source": src}
         out["roofline_matvec"] = roof
@@ -582,7 +602,7 @@ def serving_workload(R: int, seed: int = 0, new_fraction: float = 0.3):
     return geoms, reqs
 
 
-def serve_bench(R: int, device: int, stream, load: float = 1.5):
+def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str = "mixed"):
     """Serving: the plain FP64 comparator (one request at a time in arrival
     order, geometries cached once assembled) against the serving engine in
     mixed precision (continuous batching), on the same seeded requests.
@@ -634,7 +654,7 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5):
     arr = np.cumsum(rng.exponential(1.0 / rate, R))
 
     def run_engine(arrivals):
-        with M.Server(device=device, precision="mixed") as E:
+        with M.Server(device=device, precision=precision) as E:
             for key, gm in geoms.items():
                 E.add_geometry(key, gm)
             outs = [np.empty(E.ndof[k]) for k, _ in reqs]
@@ -672,12 +692,37 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5):
         "arrivals": f"Poisson, rate {rate:.1f}/s = {load} x plain FP64 capacity (seed 1)",
         "plain_fp64": pl,
         "plain_fp64_df_assembly": pld,
+        "engine_precision": precision,
         "engine_mixed": eng,
         "engine_mixed_saturated": {"capacity_solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"],
                                    "p99_ms": sat["p99_ms"], "all_ok": sat["all_ok"]},
         "capacity_vs_plain_fp64": sat["solves_per_s"] / cap_plain,
         "capacity_vs_plain_df_assembly": sat["solves_per_s"] * sum(service_df) / R,
     }
+
+
+def run_matvec(args):
+    """Microbenchmark for profiling: msbem_apply on K seeded vectors of the
+    workload's W (warm-up, then `steps` timed products); one JSON line with
+    the product kernels' median device time and their HBM rate."""
+    import torch
+    import paper_2310_09204_gb300 as M
+    from paper_2310_09204_gb300 import build as B
+    B.build()
+    geom = make_workload(args.workload)
+    with M.Solver(geom) as S:
+        S.assemble()
+        X = np.random.default_rng(5).standard_normal((args.matvec, S.n))
+        for _ in range(max(args.warmup, 1)):
+            S.apply(X, precision=args.matvec_precision)
+        ms = sorted(S.apply(X, precision=args.matvec_precision)[1] for _ in range(max(args.steps, 1)))
+        torch.cuda.synchronize()
+        med = ms[len(ms) // 2]
+        hbm, src = measured_peaks()
+        nb = MATVEC_BYTES.get(args.matvec_precision, 8) * float(S.n) ** 2
+        print(json.dumps({"matvec": args.matvec_precision, "k": args.matvec, "workload": geom.name, "N": S.n,
+                          "median_ms": med, "hbm_gbs": nb / (med * 1e-3) / 1e9, "hbm_peak_gbs": hbm,
+                          "peak_source": src}), flush=True)
 
 
 def main():

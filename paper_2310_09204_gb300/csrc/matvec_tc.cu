@@ -111,39 +111,39 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t group_strid
 }
 
 // ---- slicing ---------------------------------------------------------------
-// e_i: 2^e_i in (2 max_j |W_ij|, 4 max_j |W_ij|] (0 for a zero row)
-__global__ void tc_row_exp_kernel(const float* __restrict__ Wh, const float* __restrict__ Wl, int64_t ldw,
-                                  int64_t N, int* __restrict__ ex) {
-  __shared__ double sm[256];
+// e_i with |W_ij| < 2^(e_i - 1) for every j (0 for a zero row), from the hi
+// plane: max |hi| in [2^(k-1), 2^k) gives e_i = k + 1, and |hi + lo| <=
+// |hi| (1 + 2^-24) stays below 2^k
+__global__ void tc_row_exp_kernel(const float* __restrict__ Wh, int64_t ldw, int64_t N, int* __restrict__ ex) {
+  __shared__ float sm[256];
   const int64_t i = blockIdx.x;
-  double m = 0.0;
-  for (int64_t j = threadIdx.x; j < N; j += 256) m = fmax(m, fabs(df_to_double(Wh[i * ldw + j], Wl[i * ldw + j])));
+  float m = 0.f;
+  for (int64_t j = threadIdx.x; j < N; j += 256) m = fmaxf(m, fabsf(Wh[i * ldw + j]));
   sm[threadIdx.x] = m;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+    if (threadIdx.x < w) sm[threadIdx.x] = fmaxf(sm[threadIdx.x], sm[threadIdx.x + w]);
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    int e = 0;
-    if (sm[0] > 0.0) frexp(sm[0], &e);   // max in [2^(e-1), 2^e)
-    ex[i] = sm[0] > 0.0 ? e + 1 : 0;
+    int k = 0;
+    if (sm[0] > 0.f) frexpf(sm[0], &k);   // max in [2^(k-1), 2^k)
+    ex[i] = sm[0] > 0.f ? k + 1 : 0;
   }
 }
 
-// n digits of x in (-1/2, 1/2) in base 2^bits, rounded to nearest:
-// x = sum_s d_s 2^-(bits s) + r, |d_s| <= 2^(bits-1)
-template <typename T>
-__device__ __forceinline__ void tc_digits(double x, int n, int bits, T* d, int64_t stride) {
-  const double base = ldexp(1.0, bits);
-  for (int s = 0; s < n; ++s) {
-    x *= base;
-    const double a = rint(x);
-    x -= a;
-    if constexpr (std::is_same<T, __half>::value)
-      d[s * stride] = __float2half_rn((float)a);
-    else
-      d[s * stride] = __float2bfloat16((float)a);
+// n balanced digits of x in (-1/2, 1/2) in base 2^bits (n * bits <= 56):
+// X = x 2^(n bits) rounded to the nearest integer (exact in 64 bits), then
+// X = sum_s d_s 2^(bits (n - s)), d_s in [-2^(bits-1), 2^(bits-1)) taken
+// from the least significant end (|d_1| <= 2^(bits-1) as |x| < 1/2); so
+// x = sum_s d_s 2^-(bits s) + r, |r| <= 2^-(n bits + 1)
+__device__ __forceinline__ void tc_digits(double x, int n, int bits, __nv_bfloat16* d, int64_t stride) {
+  long long X = __double2ll_rn(ldexp(x, n * bits));
+  const long long half = 1ll << (bits - 1), mask = (1ll << bits) - 1;
+  for (int s = n - 1; s >= 0; --s) {
+    const long long dig = s == 0 ? X : ((X + half) & mask) - half;
+    d[s * stride] = __float2bfloat16((float)dig);
+    X = (X - dig) >> bits;
   }
 }
 
@@ -548,7 +548,7 @@ cudaError_t ensure_w_slices(DevGeom& g, int prec, cudaStream_t s) {
   const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64);
   if (!g.d_wexp) {
     if ((e = pool_alloc((void**)&g.d_wexp, sizeof(int) * N, g.pool, s)) != cudaSuccess) return e;
-    tc_row_exp_kernel<<<(unsigned)N, 256, 0, s>>>(g.d_Wh, g.wlo(), g.ldw, N, g.d_wexp);
+    tc_row_exp_kernel<<<(unsigned)N, 256, 0, s>>>(g.d_Wh, g.ldw, N, g.d_wexp);
     ++g.launches;
   }
   if (prec == 0) {
@@ -626,7 +626,7 @@ static cudaError_t launch_cfg(DevGeom& g, const CUtensorMap& tmW, int kb, const 
   cudaMemsetAsync(ps, 0, pbytes, s);
   cudaMemsetAsync(mx, 0, 256, s);
   const unsigned pblocks = (unsigned)std::min<int64_t>((N * kb + 255) / 256, 152 * 16);
-  tc_col_max_kernel<<<pblocks, 256, 0, s>>>(P, N, kb, mx);
+  tc_col_max_kernel<<<(unsigned)std::min<int64_t>((N * kb + 255) / 256, 152), 256, 0, s>>>(P, N, kb, mx);
   if constexpr (C::F16)
     tc_slice_p_kernel<__half><<<pblocks, 256, 0, s>>>(P, N, kb, C::NP, C::FSHIFT, mx, fx, (__half*)ps);
   else
