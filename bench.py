@@ -35,10 +35,10 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # (36 evaluations x 76 + 6 x 36 per-point updates), counted from far_df.cu
 FP32_OPS_PER_FAR_PAIR = 36 * 76 + 6 * 36
 # DRAM bytes (read + write) of one far_df_kernel launch, from an ncu capture of
-# the h=1/32 book (6,144 triangles: 1.37 MB read + 257.2 MB written), scaled to
-# the h=1/64 book by the number of triangle pairs (x16).  Valid for the kernel
-# as captured; reset to None when the kernel changes.
-FAR_DF_TRAFFIC_BOOK64 = None   # recapture after the kernel change (was 16 x (1.37 + 257.2) MB)
+# the h=1/32 book (6,144 triangles: 1.21 MB read + 257.52 MB written), scaled
+# to the h=1/64 book by the number of triangle pairs (x16).  Valid for the
+# kernel as captured; reset to None when the kernel changes.
+FAR_DF_TRAFFIC_BOOK64 = 16 * (1.211904e6 + 257.520640e6)
 # double-float multiply-add on the FP32 pipe (df.cuh df_fma_acc)
 FP32_OPS_PER_DF_FMA = 13
 
