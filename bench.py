@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving simulation")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-precision", default="mixed", choices=["mixed", "mixed-tc", "mixed-fp16", "df", "tc"])
+    ap.add_argument("--serve-config", default="mix", choices=["mix", "c5"],
+                    help="mix: 300-request stream of small geometries (default); c5: the serving configuration "
+                         "(2000 requests, squares / cubes / panels up to 40k dofs, 160 GB budget; minutes)")
     ap.add_argument("--no-cube", action="store_true", help="skip the cube-with-mid-planes section")
     ap.add_argument("--workload", default="book64", choices=["book64", "book48", "book32", "flat"],
                     help="book64 is the measured workload; book48, book32 and flat are for profiling")
@@ -317,7 +320,11 @@ def run_ours(args, world, rank, local, pg):
 
     serving = None
     if rank == 0 and not args.no_serve:
-        serving = serve_bench(args.serve_requests, local, stream, precision=args.serve_precision)
+        if args.serve_config == "c5":
+            serving = serve_bench(2000 if args.serve_requests == 300 else args.serve_requests, local, stream,
+                                  precision=args.serve_precision, config="c5", budget=160e9)
+        else:
+            serving = serve_bench(args.serve_requests, local, stream, precision=args.serve_precision)
     cube = None
     if rank == 0 and not args.no_cube:
         cube = cube_bench(local, stream)
@@ -602,7 +609,55 @@ def serving_workload(R: int, seed: int = 0, new_fraction: float = 0.3):
     return geoms, reqs
 
 
-def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str = "mixed"):
+# the request-stream configuration of the serving row: squares (h = 1/24 ..
+# 1/200), cubes with mid-planes (h = 1/12 .. 1/66) and hinged-panel screens,
+# 500 - 40k dofs; patches of 100 - 400 dofs
+C5_SQUARES = ((24, 2), (32, 2), (48, 3), (64, 4), (96, 6), (128, 8), (160, 10), (192, 12), (200, 10))
+C5_CUBES = tuple((n, 6) for n in range(12, 67, 6))
+
+
+def _c5_geometry(spec):
+    """One geometry of the C5 stream from its (family, parameters) spec (a
+    top-level function: it runs in the generator pool)."""
+    from paper_2310_09204_gb300 import workloads as WL
+    fam, a, b = spec
+    if fam == "square":
+        return WL.unit_square(a, b, "square")
+    if fam == "cube":
+        return WL.cube_midplanes(a, b, seed=b)
+    return WL.panels(a)
+
+
+def serving_workload_c5(R: int = 2000, seed: int = 0, new_fraction: float = 0.3):
+    """The serving configuration's stream: R requests; with probability
+    new_fraction (always for the first) a new geometry, drawn evenly from the
+    square, cube and panel families, else one used before; g in [-1,1]^3.
+    Geometries are generated in a pool of processes (spawned)."""
+    import multiprocessing as mp
+    rng = np.random.default_rng(seed)
+    specs, reqs = [], []
+    for i in range(R):
+        if i == 0 or rng.random() < new_fraction:
+            f = int(rng.integers(3))
+            if f == 0:
+                n, nc = C5_SQUARES[int(rng.integers(len(C5_SQUARES)))]
+                specs.append(("square", n, nc))
+            elif f == 1:
+                n, nc = C5_CUBES[int(rng.integers(len(C5_CUBES)))]
+                specs.append(("cube", n, nc))
+            else:
+                specs.append(("panels", 5000 + len(specs), 0))
+            key = len(specs)
+        else:
+            key = int(rng.integers(1, len(specs) + 1))
+        reqs.append((key, rng.uniform(-1.0, 1.0, 3)))
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        built = pool.map(_c5_geometry, specs, chunksize=4)
+    return {k + 1: g for k, g in enumerate(built)}, reqs
+
+
+def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str = "mixed", config: str = "mix",
+                budget: float = 0.0):
     """Serving: the plain FP64 comparator (one request at a time in arrival
     order, geometries cached once assembled) against the serving engine in
     mixed precision (continuous batching), on the same seeded requests.
@@ -617,18 +672,29 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str =
     comparator's."""
     import torch
     import paper_2310_09204_gb300 as M
-    geoms, reqs = serving_workload(R)
+    geoms, reqs = serving_workload(R) if config == "mix" else serving_workload_c5(R)
+    R = len(reqs)
 
     def plain(far_kernel):
-        """The comparator, back to back: (service times, densities)."""
-        cache, ref, service = {}, [], []
-        for key, g in reqs:
+        """The comparator, back to back: (service times, densities).  Its
+        geometry cache evicts the least recently used geometries beyond the
+        HBM budget (W as float pairs, its FP64 copy, the preconditioner)."""
+        cache, ref, service, used = {}, [], [], {}
+        lim = budget if budget > 0 else float("inf")
+
+        def bytes_of(key):
+            n = float(cache[key].n)
+            return 16.0 * n * n + 8.0 * n * 2000
+        for i, (key, g) in enumerate(reqs):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if key not in cache:
-                S = M.Solver(geoms[key], device=device)
-                S.assemble(far_kernel=far_kernel).factor()
-                cache[key] = S
+                cache[key] = M.Solver(geoms[key], device=device)
+                while sum(bytes_of(k) for k in cache) > lim and len(cache) > 1:
+                    old = min((k for k in cache if k != key), key=lambda k: used.get(k, -1))
+                    cache.pop(old).close()
+                cache[key].assemble(far_kernel=far_kernel).factor()
+            used[key] = i
             out = cache[key].solve(g, rtol=1e-8, precision="fp64")
             torch.cuda.synchronize()
             service.append(time.perf_counter() - t0)
@@ -654,7 +720,7 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str =
     arr = np.cumsum(rng.exponential(1.0 / rate, R))
 
     def run_engine(arrivals):
-        with M.Server(device=device, precision=precision) as E:
+        with M.Server(device=device, precision=precision, hbm_budget=budget) as E:
             for key, gm in geoms.items():
                 E.add_geometry(key, gm)
             outs = [np.empty(E.ndof[k]) for k, _ in reqs]
@@ -672,12 +738,13 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str =
             t_end = E.now()
             res = [E.result(x) for x in ids]
             st = E.stats()
+            ndofs = [E.ndof[k] for k in geoms]
         lat = sorted(r["latency_ms"] for r in res)
         diff = max(float(np.linalg.norm(o - r) / max(np.linalg.norm(r), 1e-300)) for o, r in zip(outs, ref))
         return {"solves_per_s": R / (t_end - t0 - arrivals[0]), "p50_ms": lat[R // 2],
                 "p99_ms": lat[min(R - 1, int(0.99 * R))], "max_relres": max(r["relres"] for r in res),
                 "all_ok": all(r["status"] == 0 for r in res), "maxdiff_vs_plain_fp64": diff,
-                "admissions": st["admissions"], "evictions": st["evictions"]}
+                "admissions": st["admissions"], "evictions": st["evictions"], "ndofs": ndofs}
 
     eng = run_engine(arr)
     sat = run_engine(np.zeros(R))
@@ -686,9 +753,16 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str =
                   "geometry cache; latencies by the FIFO recurrence")
     pld = fifo(service_df, arr)
     pld["mode"] = "as plain_fp64 but with the double-float assembly of W"
+    ndofs = eng.pop("ndofs")
+    sat.pop("ndofs")
     return {
-        "requests": R, "distinct_geometries": len(geoms), "new_geometry_fraction": len(geoms) / R,
-        "families": "squares h=1/24..1/96, three-page books h=1/32,1/48, panel screens (500-13.5k dofs)",
+        "config": config, "requests": R, "distinct_geometries": len(geoms), "new_geometry_fraction": len(geoms) / R,
+        "families": ("squares h=1/24..1/96, three-page books h=1/32,1/48, panel screens (500-13.5k dofs)"
+                     if config == "mix" else
+                     "squares h=1/24..1/200, cubes with mid-planes h=1/12..1/66, hinged panel screens "
+                     "(500-40k dofs)"),
+        "dofs_range": [int(min(ndofs)), int(max(ndofs))],
+        "hbm_budget_bytes": budget if budget > 0 else "80% of free",
         "arrivals": f"Poisson, rate {rate:.1f}/s = {load} x plain FP64 capacity (seed 1)",
         "plain_fp64": pl,
         "plain_fp64_df_assembly": pld,
