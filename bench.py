@@ -681,6 +681,7 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str =
         HBM budget (W as float pairs, its FP64 copy, the preconditioner)."""
         cache, ref, service, used = {}, [], [], {}
         lim = budget if budget > 0 else float("inf")
+        home = M.Solver(None, device=device)   # one context (and memory pool) for all cached geometries
 
         def bytes_of(key):
             n = float(cache[key].n)
@@ -689,7 +690,7 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str =
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if key not in cache:
-                cache[key] = M.Solver(geoms[key], device=device)
+                cache[key] = M.Solver(geoms[key], device=device, share=home)
                 while sum(bytes_of(k) for k in cache) > lim and len(cache) > 1:
                     old = min((k for k in cache if k != key), key=lambda k: used.get(k, -1))
                     cache.pop(old).close()
@@ -701,6 +702,7 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str =
             ref.append(out["density"].copy())
         for S in cache.values():
             S.close()
+        home.close()
         return service, ref
 
     def fifo(service, arr):

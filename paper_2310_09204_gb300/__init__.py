@@ -204,16 +204,21 @@ def msbem_ndofs(geom) -> int:
 
 
 class Solver:
-    """One context + one uploaded geometry."""
+    """One context + one uploaded geometry.  share=another Solver: use its
+    context (and memory pool) instead of a new one; closing this Solver then
+    frees only its geometry."""
 
-    def __init__(self, geom=None, device: int = 0, stream: int | None = None, **arrays):
-        if stream is None:
-            try:
-                import torch
-                stream = torch.cuda.current_stream(device).cuda_stream
-            except Exception:  # pragma: no cover - torch without CUDA
-                stream = 0
-        self.ctx = msbem_create(device, stream)
+    def __init__(self, geom=None, device: int = 0, stream: int | None = None, share=None, **arrays):
+        if share is not None:
+            self.ctx, self._owns_ctx = share.ctx, False
+        else:
+            if stream is None:
+                try:
+                    import torch
+                    stream = torch.cuda.current_stream(device).cuda_stream
+                except Exception:  # pragma: no cover - torch without CUDA
+                    stream = 0
+            self.ctx, self._owns_ctx = msbem_create(device, stream), True
         self.geom = None
         if geom is not None:
             self.upload(geom.xyz, geom.tri, geom.coarse_xyz, geom.coarse_tri, geom.parent, geom.patch)
@@ -228,7 +233,10 @@ class Solver:
 
     def close(self):
         if self.ctx is not None:
-            lib().msbem_destroy(self.ctx)
+            if self._owns_ctx:
+                lib().msbem_destroy(self.ctx)
+            else:
+                self.free_geometry()
             self.ctx = None
             self.geom = None
 

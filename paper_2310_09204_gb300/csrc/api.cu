@@ -65,6 +65,9 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// freed memory a context's pool keeps for reuse beyond what is in use
+constexpr uint64_t kPoolSpare = 8ull << 30;
+
 void free_dev(DevGeom& d, cudaStream_t s) {
   drop_pcg_graphs(d);
   void* ptrs[] = {d.d_hist, d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
@@ -534,6 +537,14 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   d.d_V = nullptr;
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "assemble");
+  if (d.pool) {
+    // the pool keeps at most kPoolSpare bytes of freed memory (V of the next
+    // assembly of a similar geometry) beyond what is in use, so that the V of
+    // a large geometry goes back to the device for other contexts
+    uint64_t used = 0;
+    cudaMemPoolGetAttribute(d.pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    cudaMemPoolTrimTo(d.pool, (size_t)(used + kPoolSpare));
+  }
   if (!panels) {
     cudaEventElapsedTime(&t_far, c->ev[0], c->ev[1]);
     cudaEventElapsedTime(&t_near, c->ev[1], c->ev[2]);
