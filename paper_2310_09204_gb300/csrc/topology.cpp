@@ -94,22 +94,38 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
     for (int64_t i = 1; i < nt; ++i)
       if (keys[i] == keys[i - 1]) { err = "duplicate triangle"; return MSBEM_NONCONFORMING; }
   }
-  // edges: (lo, hi, T) sorted
+  // edges: (lo, hi, T) sorted -- a counting sort on lo, then the few edges
+  // of each lo (a vertex's degree) by insertion on (hi, T)
   struct E { int32_t lo, hi, T; };
-  std::vector<E> edges;
-  edges.reserve(3 * nt);
-  for (int64_t T = 0; T < nt; ++T)
-    for (int a = 0; a < 3; ++a) {
-      int32_t i = o.tri[3 * T + a], k = o.tri[3 * T + (a + 1) % 3];
-      edges.push_back({std::min(i, k), std::max(i, k), (int32_t)T});
-    }
-  std::sort(edges.begin(), edges.end(), [](const E& x, const E& y) {
-    return x.lo != y.lo ? x.lo < y.lo : (x.hi != y.hi ? x.hi < y.hi : x.T < y.T);
-  });
+  std::vector<E> edges(3 * nt);
+  {
+    std::vector<int64_t> start(nv + 1, 0);
+    for (int64_t T = 0; T < nt; ++T)
+      for (int a = 0; a < 3; ++a)
+        start[std::min(o.tri[3 * T + a], o.tri[3 * T + (a + 1) % 3]) + 1]++;
+    for (int64_t v = 0; v < nv; ++v) start[v + 1] += start[v];
+    std::vector<int64_t> put(start.begin(), start.end() - 1);
+    for (int64_t T = 0; T < nt; ++T)
+      for (int a = 0; a < 3; ++a) {
+        int32_t i = o.tri[3 * T + a], k = o.tri[3 * T + (a + 1) % 3];
+        edges[put[std::min(i, k)]++] = {std::min(i, k), std::max(i, k), (int32_t)T};
+      }
+    for (int64_t v = 0; v < nv; ++v)
+      for (int64_t x = start[v] + 1; x < start[v + 1]; ++x) {
+        const E e = edges[x];
+        int64_t y = x;
+        while (y > start[v] && (edges[y - 1].hi > e.hi || (edges[y - 1].hi == e.hi && edges[y - 1].T > e.T))) {
+          edges[y] = edges[y - 1];
+          --y;
+        }
+        edges[y] = e;
+      }
+  }
   Dsu side(6 * nt);   // node (2T+s)*3 + a
   Dsu fan(3 * nt);    // node 3T + a
   auto node = [](int64_t T, int s, int a) { return (2 * T + s) * 3 + a; };
   std::vector<std::pair<double, int>> ang;
+  std::vector<int> up;
   for (size_t e0 = 0; e0 < edges.size();) {
     size_t e1 = e0;
     while (e1 < edges.size() && edges[e1].lo == edges[e0].lo && edges[e1].hi == edges[e0].hi) ++e1;
@@ -128,7 +144,7 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
       for (int k = 0; k < 3; ++k) u[k] /= nu;
       double ref1[3] = {0, 0, 0}, ref2[3];
       ang.clear();
-      std::vector<int> up(m);
+      up.assign(m, 0);
       for (int j = 0; j < m; ++j) {
         int32_t T = edges[e0 + j].T;
         const int32_t* t = &o.tri[3 * T];
