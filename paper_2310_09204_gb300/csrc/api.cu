@@ -554,6 +554,12 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   d.times[1] = t_near;
   d.times[2] = t_con;
   d.panel_rows = panels ? panel : 0;
+  // column splits of the CUDA-core products for this W (timed once per
+  // order N in the process); on any failure the N-only defaults stay
+  if (matvec_autotune(d, s) != cudaSuccess) {
+    cudaGetLastError();
+    d.mv_split[0] = d.mv_split[1] = 0;
+  }
   d.assembled = 1;
   d.factored = 0;
   return MSBEM_OK;

@@ -68,13 +68,13 @@ __global__ void ah_kernel(const double* __restrict__ WPt, int64_t N, int64_t NH,
 // ---------------------------------------------------------------------------
 // Blocked Gauss-Jordan inversion of a batch of SPD matrices, in place.
 // Pivot panels of GB = 32 rows/columns K; for every active matrix:
-//   P = A_KK^{-1}                       (bgj_pivot_kernel, FP64 in shared memory)
+//   P = A_KK^{-1}                       (bgj_pivot_kernel, double-float in shared memory)
 //   C'_I = -A_IK P,  R_J = A_KJ (old)   (bgj_panel_kernel, double-float)
 //   A_IJ += C'_I R_J, A_KJ = P R_J, A_IK = C'_I, A_KK = P
 //                                       (bgj_update_kernel, double-float tiles)
 // which is the scalar Gauss-Jordan recursion applied 32 pivots at a time; after
 // the last panel A holds A^{-1}.  Rank-32 updates run as double-float products
-// on the FP32 pipe (GB300 FP64 is ~1/70 of FP32); P is formed in FP64.
+// on the FP32 pipe (GB300 FP64 is ~1/70 of FP32), and so is P.
 // ---------------------------------------------------------------------------
 #define GB 32
 
@@ -101,50 +101,71 @@ __device__ __forceinline__ int find_prefix(const int64_t* pre, int active, int64
   return lo;
 }
 
-__global__ void __launch_bounds__(256) bgj_pivot_kernel(BgjArgs g, int64_t k0) {
-  __shared__ double S[GB][GB + 1];
-  __shared__ double rowk[GB], colk[GB];  // pivot row scaled by 1/p, pivot column
-  __shared__ double s_ip;
+__global__ void __launch_bounds__(1024) bgj_pivot_kernel(BgjArgs g, int64_t k0) {
+  // the scalar recursion on the 32 x 32 pivot block in double-float on the
+  // FP32 pipe (GB300's FP64 pipe would make these 32 dependent steps the
+  // critical path of every panel step); one thread per entry, so that the
+  // latency of each step's chain is hidden by 32 warps
+  __shared__ float2 S[GB][GB + 1];
+  __shared__ float2 rowk[GB], colk[GB];  // pivot row scaled by 1/p, pivot column
+  __shared__ float2 s_ip;
   const int a = blockIdx.x;
   const int b = g.order[a];
   const int64_t n = g.bsize[b];
   const int kb = (int)(n - k0 < GB ? n - k0 : GB);
   const double* A = g.A + g.boff[b];
   for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
-    int i = e / GB, j = e % GB;
-    S[i][j] = (i < kb && j < kb) ? A[(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
+    const int i = e / GB, j = e % GB;
+    const double v = (i < kb && j < kb) ? A[(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
+    float h, l;
+    split_df(v, h, l);
+    S[i][j] = make_float2(h, l);
   }
   __syncthreads();
   for (int k = 0; k < GB; ++k) {
     // one warp forms 1/p, the scaled pivot row and the pivot column
     if (threadIdx.x < 32) {
-      const double p = S[k][k];
-      const double ip = 1.0 / p;
+      const float2 pk = S[k][k];
+      // 1/p in double-float without the FP64 pipe: the correctly rounded FP32
+      // reciprocal r, then one Newton step on the residual 1 - p r formed
+      // with an exact FMA product (relative error ~2^-46)
+      const float r = __frcp_rn(pk.x);
+      const float t = fmaf(-pk.y, r, fmaf(-pk.x, r, 1.0f));
+      float iph, ipl;
+      two_sum(r, r * t, iph, ipl);
       if (threadIdx.x == 0) {
-        s_ip = ip;
-        if (!(p > 0.0 && isfinite(p))) atomicExch(g.flag, 1);
+        s_ip = make_float2(iph, ipl);
+        if (!(pk.x > 0.f && isfinite(pk.x))) atomicExch(g.flag, 1);
       }
-      rowk[threadIdx.x] = S[k][threadIdx.x] * ip;
+      const float2 skj = S[k][threadIdx.x];
+      float rh, rl;
+      df_mul(skj.x, skj.y, iph, ipl, rh, rl);
+      rowk[threadIdx.x] = make_float2(rh, rl);
       colk[threadIdx.x] = S[threadIdx.x][k];
     }
     __syncthreads();
-    const double ip = s_ip;
+    const float2 ip = s_ip;
     for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
       const int i = e / GB, j = e % GB;
-      double v;
-      if (i == k) v = (j == k) ? ip : rowk[j];
-      else if (j == k) v = -colk[i] * ip;
-      else v = fma(-colk[i], rowk[j], S[i][j]);
+      float2 v;
+      if (i == k) {
+        v = (j == k) ? ip : rowk[j];
+      } else if (j == k) {
+        float rh, rl;
+        df_mul(colk[i].x, colk[i].y, ip.x, ip.y, rh, rl);
+        v = make_float2(-rh, -rl);
+      } else {
+        float h = S[i][j].x, l = S[i][j].y;
+        df_fma_acc(-colk[i].x, -colk[i].y, rowk[j].x, rowk[j].y, h, l);
+        const float sh = h + l;
+        v = make_float2(sh, l - (sh - h));
+      }
       S[i][j] = v;
     }
     __syncthreads();
   }
   float2* P = g.Pf + (int64_t)a * GB * GB;
-  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
-    float h, l;
-    split_df(S[e / GB][e % GB], h, l);
-    P[e] = make_float2(h, l);
-  }
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) P[e] = S[e / GB][e % GB];
 }
 
 __global__ void __launch_bounds__(256) bgj_panel_kernel(BgjArgs g, int active, int64_t k0) {
@@ -239,14 +260,25 @@ __global__ void __launch_bounds__(256) bgj_update_kernel(BgjArgs g, int active, 
     sR[i][tx] = w;
   }
   __syncthreads();
+  // rows ty, ty + 8, ty + 16, ty + 24 of the tile at once: one read of the
+  // right factor per m, four independent accumulators
   const int64_t col = c0 + tx;
-  for (int i = ty; i < GB; i += 8) {
-    int64_t row = r0 + i;
+  float acch[4] = {0.f, 0.f, 0.f, 0.f}, accl[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int m = 0; m < kb; ++m) {
+    const float2 r = sR[m][tx];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 l = sL[ty + 8 * q][m];
+      df_fma_acc(l.x, l.y, r.x, r.y, acch[q], accl[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = ty + 8 * q;
+    const int64_t row = r0 + i;
     if (row >= n || col >= n) continue;
     if (I == kt && i >= kb) continue;
-    float acch = 0.f, accl = 0.f;
-    for (int m = 0; m < kb; ++m) df_fma_acc(sL[i][m].x, sL[i][m].y, sR[m][tx].x, sR[m][tx].y, acch, accl);
-    double upd = df_to_double(acch, accl);
+    const double upd = df_to_double(acch[q], accl[q]);
     A[row * n + col] = (I == kt) ? upd : A[row * n + col] + upd;
   }
 }
@@ -314,7 +346,7 @@ static cudaError_t gj_invert(double* d_A, const std::vector<int64_t>& boff,
   int active = nb;
   for (int64_t k0 = 0; k0 < nmax; k0 += GB) {
     while (active > 0 && bsize[inv_blocks[active - 1]] <= k0) --active;
-    bgj_pivot_kernel<<<active, 256, 0, s>>>(args, k0);
+    bgj_pivot_kernel<<<active, GB * GB, 0, s>>>(args, k0);
     bgj_panel_kernel<<<(unsigned)pt1[active], 256, 0, s>>>(args, active, k0);
     bgj_update_kernel<<<(unsigned)pt2[active], 256, 0, s>>>(args, active, k0);
     *launches += 3;
@@ -363,7 +395,7 @@ cudaError_t bgj_invert_single(double* A, int64_t n, unsigned char* scratch, size
   if (e == cudaSuccess) e = cudaMemcpyAsync(tail, h_tail, sizeof(h_tail), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   for (int64_t k0 = 0; k0 < n; k0 += GB) {
-    bgj_pivot_kernel<<<1, 256, 0, s>>>(args, k0);
+    bgj_pivot_kernel<<<1, GB * GB, 0, s>>>(args, k0);
     bgj_panel_kernel<<<(unsigned)nti, 256, 0, s>>>(args, 1, k0);
     bgj_update_kernel<<<(unsigned)(nti * nti), 256, 0, s>>>(args, 1, k0);
   }

@@ -32,6 +32,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <mutex>
 #include <vector>
 
@@ -427,6 +428,110 @@ int matvec_split(int64_t N, int mode) {
 
 size_t matvec_scratch_bytes(int64_t N, int kb, int split) {
   return split > 1 ? sizeof(float2) * (size_t)split * N * kb : 0;
+}
+
+int matvec_split_of(const DevGeom& g, int mode) {
+  const int m = mode == 1 ? 1 : 0;
+  return g.mv_split[m] > 0 ? g.mv_split[m] : matvec_split(g.ndof, mode);
+}
+
+// Candidate column splits (each must own at least one chunk), and the
+// process-wide record of the picks
+static const int kSplitCandidates[] = {1, 2, 3, 4, 6, 8};
+static std::mutex g_tune_mu;
+static std::vector<std::array<int64_t, 4>> g_tuned;   // (device, N, mode, split)
+
+cudaError_t matvec_autotune(DevGeom& g, cudaStream_t s) {
+  const int64_t N = g.ndof;
+  g.mv_split[0] = g.mv_split[1] = 0;
+  if (N <= 0) return cudaSuccess;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int64_t nchunks = (N + MV_KC - 1) / MV_KC;
+  bool todo[2] = {true, true};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& t : g_tuned)
+      if (t[0] == dev && t[1] == N) {
+        g.mv_split[t[2]] = (int)t[3];
+        todo[t[2]] = false;
+      }
+  }
+  for (int m = 0; m < 2; ++m)
+    if (todo[m] && nchunks < 16) {   // small matrices: one CTA per row block
+      g.mv_split[m] = 1;
+      todo[m] = false;
+    }
+  if (!todo[0] && !todo[1]) return cudaSuccess;
+  // scratch: 16 zero vectors, their planes, products, partial sums, the
+  // widest split's partials, flags
+  const int KBT = 16;
+  const size_t nvec = (size_t)N * KBT;
+  const size_t nparts = (size_t)KBT * matvec_blocks(N, 0) + (size_t)KBT * matvec_blocks(N, 1);
+  const size_t bytes = sizeof(double) * (2 * nvec + nparts) + sizeof(float) * 2 * KBT * g.ldw +
+                       matvec_scratch_bytes(N, KBT, 8) + 2 * sizeof(int) + 2048;
+  char* base = nullptr;
+  cudaError_t e = pool_alloc((void**)&base, bytes, g.pool, s);
+  if (e != cudaSuccess) return e;
+  auto take = [&](size_t b) { char* p = base; base += (b + 255) / 256 * 256; return p; };
+  char* const mem = base;
+  double* P = (double*)take(sizeof(double) * nvec);
+  double* Q = (double*)take(sizeof(double) * nvec);
+  double* part = (double*)take(sizeof(double) * nparts);
+  float* Pf = (float*)take(sizeof(float) * 2 * KBT * g.ldw);
+  void* scr = take(matvec_scratch_bytes(N, KBT, 8));
+  int* flags = (int*)take(2 * sizeof(int));
+  cudaMemsetAsync(mem, 0, bytes, s);
+  cudaEvent_t ev[2];
+  cudaEventCreate(&ev[0]);
+  cudaEventCreate(&ev[1]);
+  for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
+    if (!todo[m]) continue;
+    float best = 3.4e38f;
+    int pick = matvec_split(N, m);
+    for (int S : kSplitCandidates) {
+      if (S > 1 && ((S - 1) * ((nchunks + S - 1) / S) >= nchunks || nchunks / S < 2)) continue;
+      float total = 0.f;
+      for (int kb : {1, KBT}) {
+        CUtensorMap tmP;
+        if ((e = encode_planes(&tmP, Pf, g.ldw, kb, kb * g.ldw, m == 0 ? 2 : 1, matvec_pad(kb))) != cudaSuccess)
+          break;
+        const CUtensorMap& tmW = m == 0 ? g.tm_W : g.tm_Whi;
+        float t = 3.4e38f;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+          cudaEventRecord(ev[0], s);
+          e = launch_matvec(m, tmW, tmP, N, kb, P, Q, part, flags, flags + 1, s, S, scr);
+          cudaEventRecord(ev[1], s);
+          if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+          float ms = 0.f;
+          if (e == cudaSuccess && rep > 0) {   // the first launch warms up
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            t = std::min(t, ms);
+          }
+        }
+        total += t;
+      }
+      if (e != cudaSuccess) break;
+      if (total < best) {
+        best = total;
+        pick = S;
+      }
+    }
+    g.launches += 36;
+    if (e == cudaSuccess) {
+      g.mv_split[m] = pick;
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tuned.push_back({dev, N, m, pick});
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  int err = 0;
+  cudaMemcpyAsync(&err, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(mem, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && err) e = cudaErrorTimeout;
+  return e != cudaSuccess ? e : e2;
 }
 
 template <int MODE, int KB>

@@ -126,6 +126,8 @@ struct DevGeom {
   int* d_wexp = nullptr;
   CUtensorMap tm_wsl, tm_wf16;
   int64_t panel_rows = 0;        // rows of V per panel in the last assembly (0: V in one piece)
+  int mv_split[2] = {0, 0};      // column splits of the CUDA-core products (modes 0, 1) picked
+                                 // by the autotuner at assembly (0: the N-only default)
   int ncells = 0;                // closed cells: W holds W + rho Q Q^T (Q: [N][ncells], orthonormal)
   double* d_cellZ = nullptr;     // Q
   double rho = 0.0;
@@ -206,6 +208,12 @@ cudaError_t launch_matvec(int mode, const CUtensorMap& tmW, const CUtensorMap& t
                           cudaStream_t s, int split = 1, void* scratch = nullptr);
 int matvec_split(int64_t N, int mode);
 size_t matvec_scratch_bytes(int64_t N, int kb, int split);
+// the split this geometry's products use: the autotuned one, else the default
+int matvec_split_of(const DevGeom& g, int mode);
+// Autotuner: times the candidate column splits of both CUDA-core products on
+// this geometry's W (16 vectors and 1 vector) and keeps the fastest in
+// g.mv_split; results are cached per (device, N, mode) for the process.
+cudaError_t matvec_autotune(DevGeom& g, cudaStream_t s);
 
 // Q = W P on the tensor cores from integer slices of W and P (matvec_tc.cu);
 // prec 0 double-float accuracy, 1 scaled FP16 (W to 11 bits under its row

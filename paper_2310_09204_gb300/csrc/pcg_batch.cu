@@ -500,7 +500,7 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, BRED);
   const size_t hsz = (size_t)kb * (maxit + 1) + 2 * (size_t)kb * maxit;
-  const int split = tc ? 1 : matvec_split(N, mv_mode);
+  const int split = tc ? 1 : matvec_split_of(g, mv_mode);
   const size_t scr_bytes = tc ? tc_work_bytes(g) : matvec_scratch_bytes(N, kb, split);
   const size_t bytes = sizeof(double) * (4 * nvec + 2 * NH * kb + nparts + hsz) +
                        sizeof(float) * 2 * kb * g.ldw + sizeof(float2) * nvec + sizeof(ColState) * kb +
@@ -676,7 +676,7 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
   const unsigned gemv_blocks = matvec_blocks(N, 0);
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, BRED);
-  const int split = tensor ? 1 : matvec_split(N, 0);
+  const int split = tensor ? 1 : matvec_split_of(g, 0);
   const size_t scr_bytes = tensor ? tc_work_bytes(g) : matvec_scratch_bytes(N, kb, split);
   const size_t bytes = sizeof(double) * (5 * nvec + nparts + 3 * kb + 2 * kb) + sizeof(float) * 2 * kb * g.ldw +
                        sizeof(int) * kb + sizeof(BatchState) + scr_bytes + 256;
@@ -807,7 +807,7 @@ cudaError_t apply_w(DevGeom& g, const double* X_in, bool in_dev, int kb, int mod
   const unsigned gemv_blocks = matvec_blocks(N, 0);
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, (unsigned)((N + 15) / 16));
-  const int split = mode >= 2 ? 1 : matvec_split(N, mode);
+  const int split = mode >= 2 ? 1 : matvec_split_of(g, mode);
   const size_t scr_bytes = mode >= 3 ? tc_work_bytes(g) : matvec_scratch_bytes(N, kb, split);
   const size_t bytes = sizeof(double) * (3 * nvec + nparts) + sizeof(float) * 2 * kb * g.ldw +
                        sizeof(BatchState) + scr_bytes + 256;

@@ -272,7 +272,7 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
   const size_t nvec = (size_t)N * kb;
   const size_t nparts = (size_t)kb * std::max<unsigned>(matvec_blocks(N, 0), BRED);
   const size_t hsz = (size_t)kb * (maxit + 1) + 2 * (size_t)kb * maxit;
-  B->split = std::max(matvec_split(N, 0), matvec_split(N, 1));
+  B->split = std::max(matvec_split_of(g, 0), matvec_split_of(g, 1));
   const int prec = S->opts.precision;
   size_t scr = matvec_scratch_bytes(N, kb, B->split);
   if (tc_residual(prec)) {
@@ -514,7 +514,7 @@ void schedule(msbem_server* S, GeomEntry& e) {
     } else {
       bsplit_kernel<<<grid, 256, 0, s>>>(B.Xo, B.Xf, g.ldw, N, kb);
       launch_matvec(0, g.tm_W, B.tmX, N, kb, B.Xo, B.b.Q, B.b.part, &B.fl->all_done, &B.fl->err, s,
-                    matvec_split(N, 0), B.scratch);
+                    matvec_split_of(g, 0), B.scratch);
     }
     s_resid_cols<<<grid, 256, 0, s>>>(B.L, B.b.Q, B.Ro, N, kb, B.mask);
     bdot_kernel<<<rgrid, 256, 0, s>>>(B.Ro, B.Ro, N, kb, B.b.part, B.fl);
@@ -598,7 +598,7 @@ void schedule(msbem_server* S, GeomEntry& e) {
   // 4. iterate the running slots
   if (e.active > 0) {
     const int mv_mode = inner_mode(prec);
-    const int split = mv_mode >= 3 ? 1 : matvec_split(N, mv_mode);
+    const int split = mv_mode >= 3 ? 1 : matvec_split_of(g, mv_mode);
     for (int it = 0; it < S->opts.chunk; ++it)
       enqueue_batch_iteration(g, B.b, kb, 1, mv_mode, B.tmP, split, B.scratch, S->opts.maxit, s);
     cudaMemcpyAsync(B.h_cs, B.b.cs, sizeof(ColState) * kb, cudaMemcpyDeviceToHost, s);

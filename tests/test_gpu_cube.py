@@ -169,3 +169,32 @@ def test_cube_config_full_size():
         assert abs(pl["iters"] - df["iters"]) <= 1
         mx = S.solve(geom.g, rtol=1e-8, precision="mixed")
         assert np.linalg.norm(mx["density"] - df["density"]) <= 1e-7 * np.linalg.norm(df["density"])
+        # the tensor-core products at this size (84 GB of slices): sampled rows
+        # against the exactly rounded product of the device's own rows, and the
+        # tensor-core solve forms to the true residual
+        import math
+        rng = np.random.default_rng(4)
+        X = rng.standard_normal((16, S.n))
+        Ytc, _ = S.apply(X, precision="tc")
+        for r in rows:
+            wg = S.matrix(r, 1)[0]
+            for c in range(16):
+                t = wg * X[c]
+                ex = math.fsum(np.concatenate([t] + _two_prod_err(wg, X[c], t)))
+                assert abs(Ytc[c, r] - ex) <= 2.0 ** -42 * np.abs(wg).max() * np.abs(X[c]).sum()
+        for prec in ("tc", "mixed-tc"):
+            o = S.solve(geom.g, rtol=1e-8, precision=prec)
+            Y, _ = S.apply(o["density"][None, :])
+            assert np.linalg.norm(L - Y[0]) <= 1.05e-8 * np.linalg.norm(L), prec
+
+
+def _two_prod_err(a, b, p):
+    """Terms whose exact sum is the rounding error a*b - p of the products
+    p = a*b (Veltkamp splitting; each term exact in FP64 barring underflow)."""
+    def split(x):
+        c = x * 134217729.0
+        hi = c - (c - x)
+        return hi, x - hi
+    ah, al = split(a)
+    bh, bl = split(b)
+    return [ah * bh - p, ah * bl, al * bh, al * bl]

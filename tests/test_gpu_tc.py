@@ -148,6 +148,12 @@ def test_tc_product_full_size_book():
         scale = np.abs(W).max(axis=1)[None, :] * np.abs(X).sum(axis=1)[:, None]
         assert np.all(np.abs(Ytc - Ydf) <= 2 * BOUND * scale)
         print(f"book N={n}: tc {ms_tc:.3f} ms, df {ms_df:.3f} ms (16 vectors)")
+        # the column split the autotuner picked at assembly serves every batch
+        # size alike: a vector's product is the same alone and among 16
+        for prec in ("df", "fp32", "tc"):
+            Y16, _ = S.apply(X, precision=prec)
+            Y1, _ = S.apply(X[5:6], precision=prec)
+            assert np.array_equal(Y1[0], Y16[5]), prec
 
 
 @pytest.mark.parametrize("geom", [WL.book(8, 2, jitter=True, seed=3), WL.panels(7, n=6)], ids=lambda g: g.name)
