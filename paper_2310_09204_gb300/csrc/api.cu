@@ -5,6 +5,7 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -190,13 +191,16 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   std::string err;
   int st = build_topology(xyz, nv, tri, nt, g->fine, err);
   if (st) return fail(c, st, "fine mesh: " + err);
+  // the near-pair list (read-only use of the fine topology) on a second host
+  // thread while the cells, the coarse topology and the split are built
+  std::vector<NearPair> near;
+  std::thread near_th([&] { build_near_pairs(g->fine, near); });
   build_cells(g->fine);
   st = build_topology(cxyz, ncv, ctri, nct, g->coarse, err);
-  if (st) return fail(c, st, "coarse mesh: " + err);
-  st = build_split(g->fine, g->coarse, parent, patch, g->split, err);
+  if (st) err = "coarse mesh: " + err;
+  else st = build_split(g->fine, g->coarse, parent, patch, g->split, err);
+  near_th.join();
   if (st) return fail(c, st, err);
-  std::vector<NearPair> near;
-  build_near_pairs(g->fine, near);
   const Topo& f = g->fine;
   const Split& sp = g->split;
   DevGeom& d = g->dev;
