@@ -171,6 +171,9 @@ struct Batch {
   int* h_mask = nullptr;
   BatchState* h_bs = nullptr;
   bool in_flight = false;
+  // the `chunk` PCG iterations of a scheduling point, captured once as a CUDA
+  // graph (the batch's buffers, split and mode never change) and replayed
+  cudaGraphExec_t iter_exec = nullptr;
   Slot slot[BK];
 };
 
@@ -253,6 +256,8 @@ size_t transient_bytes(const GeomEntry& e) { return sizeof(float2) * (size_t)e.n
 void free_batch(Batch* B) {
   if (!B) return;
   if (B->s) cudaStreamSynchronize(B->s);
+  if (B->iter_exec) cudaGraphExecDestroy(B->iter_exec);
+  B->iter_exec = nullptr;
   if (B->base) cudaFreeAsync(B->base, B->s);
   if (B->s) cudaStreamSynchronize(B->s);
   if (B->h_cs) cudaFreeHost(B->h_cs);
@@ -595,12 +600,29 @@ void schedule(msbem_server* S, GeomEntry& e) {
     s_start_cols<<<1, BK, 0, s>>>(B.b.cs, kb, B.mask);
     g.launches += 9;
   }
-  // 4. iterate the running slots
+  // 4. iterate the running slots: the chunk of iterations as one graph launch
   if (e.active > 0) {
     const int mv_mode = inner_mode(prec);
     const int split = mv_mode >= 3 ? 1 : matvec_split_of(g, mv_mode);
-    for (int it = 0; it < S->opts.chunk; ++it)
-      enqueue_batch_iteration(g, B.b, kb, 1, mv_mode, B.tmP, split, B.scratch, S->opts.maxit, s);
+    auto enqueue_chunk = [&] {
+      for (int it = 0; it < S->opts.chunk; ++it)
+        enqueue_batch_iteration(g, B.b, kb, 1, mv_mode, B.tmP, split, B.scratch, S->opts.maxit, s);
+    };
+    if (!B.iter_exec) {
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        enqueue_chunk();
+        if (cudaStreamEndCapture(s, &graph) == cudaSuccess && graph) {
+          if (cudaGraphInstantiate(&B.iter_exec, graph, 0) != cudaSuccess) B.iter_exec = nullptr;
+          cudaGraphDestroy(graph);
+        }
+      }
+      cudaGetLastError();
+    }
+    if (B.iter_exec)
+      cudaGraphLaunch(B.iter_exec, s);
+    else
+      enqueue_chunk();   // without a graph, the same launches one by one
     cudaMemcpyAsync(B.h_cs, B.b.cs, sizeof(ColState) * kb, cudaMemcpyDeviceToHost, s);
     cudaEventRecord(B.ev, s);
     B.in_flight = true;
