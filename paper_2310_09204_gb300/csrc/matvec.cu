@@ -458,7 +458,10 @@ cudaError_t matvec_autotune(DevGeom& g, cudaStream_t s) {
       }
   }
   for (int m = 0; m < 2; ++m)
-    if (todo[m] && nchunks < 16) {   // small matrices: one CTA per row block
+    if (todo[m] && (nchunks < 16 || matvec_blocks(N, m) >= 4 * 2 * 152)) {
+      // small matrices, and large ones whose row blocks alone fill four
+      // waves: one CTA per row block, no timing (it would cost a second of
+      // products at the cube's size)
       g.mv_split[m] = 1;
       todo[m] = false;
     }
