@@ -210,6 +210,10 @@ int msbem_solve(msbem_geom* g, const double gvec[3], const msbem_solve_opts* opt
  *   gvecs[3*k]         the data g_c
  *   densities[k*N]     output, row c = Phi_c (host or device pointer)
  *   iters[k], relres[k], kappa_est[k]  per-column results (each may be NULL)
+ * opts->precision as in msbem_solve: 0 and 3 run the double-float recursion
+ * (CUDA-core or tensor-core products), 2, 4 and 5 the mixed refinement, 1 the
+ * plain FP64 comparator one column at a time.  A column's result does not
+ * depend on the other columns of its call (bit for bit).
  * Returns the worst status over the columns (NOT_CONVERGED / BREAKDOWN as in
  * msbem_solve; densities always written). */
 int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_solve_opts* opts,
