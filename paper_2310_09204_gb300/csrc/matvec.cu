@@ -123,54 +123,6 @@ struct MvCfg {
                                   sizeof(double) * 8 * V;
 };
 
-// Warp reduction of LEN sums per lane at once ("transposed" butterfly): at the
-// step of lane mask m, the lanes with that bit set keep the upper half of their
-// values and the others the lower half, each adding its partner's half, so
-// LEN values cost LEN - 1 shuffles instead of 5 LEN.  Every value is summed
-// over the same lane pairing as a plain xor butterfly, so the result of a sum
-// does not depend on how many others are reduced with it.  On return (LEN = V
-// at the start) lane L holds the sums of indices L * V/32 + j when V >= 32,
-// else index L >> log2(32/V).
-template <int LEN, int MASK, bool DF>
-__device__ __forceinline__ void warp_xreduce(float* h, float* l, int lane) {
-  if constexpr (MASK > 0) {
-    if constexpr (LEN >= 2) {
-      constexpr int HALF = LEN / 2;
-      const bool up = (lane & MASK) != 0;
-#pragma unroll
-      for (int i = 0; i < HALF; ++i) {
-        const float sh = up ? h[i] : h[HALF + i];
-        const float kh = up ? h[HALF + i] : h[i];
-        const float rh = __shfl_xor_sync(0xffffffffu, sh, MASK);
-        if constexpr (DF) {
-          const float sl = up ? l[i] : l[HALF + i];
-          const float kl = up ? l[HALF + i] : l[i];
-          const float rl = __shfl_xor_sync(0xffffffffu, sl, MASK);
-          float s, e;
-          two_sum(kh, rh, s, e);
-          h[i] = s;
-          l[i] = (kl + rl) + e;
-        } else {
-          h[i] = kh + rh;
-        }
-      }
-      warp_xreduce<HALF, MASK / 2, DF>(h, l, lane);
-    } else {
-      const float rh = __shfl_xor_sync(0xffffffffu, h[0], MASK);
-      if constexpr (DF) {
-        const float rl = __shfl_xor_sync(0xffffffffu, l[0], MASK);
-        float s, e;
-        two_sum(h[0], rh, s, e);
-        h[0] = s;
-        l[0] = (l[0] + rl) + e;
-      } else {
-        h[0] += rh;
-      }
-      warp_xreduce<1, MASK / 2, DF>(h, l, lane);
-    }
-  }
-}
-
 template <int MODE, int KB>
 __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ CUtensorMap tmW,
                                                         const __grid_constant__ CUtensorMap tmP,

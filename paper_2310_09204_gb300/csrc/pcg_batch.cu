@@ -224,32 +224,20 @@ __global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restri
       }
     }
   }
+  // the 2 rows x 16 vectors of sums at once (transposed butterfly: 31
+  // shuffles, each sum over the same lane pairs as a plain butterfly); lane L
+  // ends with the sum of row L / 16, vector L % 16
+  float* hh = &h[0][0];
+  float* ll = &l[0][0];
+  if (F32) {
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
+    for (int v = 0; v < 2 * BK; ++v) hh[v] += ll[v];
+  }
+  warp_xreduce<2 * BK, 16, !F32>(hh, ll, lane);
+  {
+    const int r = lane / BK, c = lane % BK;
     const bool ok = r == 0 ? ok0 : ok1;
-    const int64_t i = i0 + r;
-#pragma unroll
-    for (int c = 0; c < BK; ++c) {
-      if (c >= kb) break;
-      if (F32) {
-        float acc = h[r][c] + l[r][c];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (ok && lane == 0) Z[(int64_t)d[i] * kb + c] = (double)acc;
-        continue;
-      }
-      float acch = h[r][c], accl = l[r][c];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, acch, off);
-        const float ol = __shfl_xor_sync(0xffffffffu, accl, off);
-        float sh, se;
-        two_sum(acch, oh, sh, se);
-        acch = sh;
-        accl = accl + ol + se;
-      }
-      if (ok && lane == 0) Z[(int64_t)d[i] * kb + c] = df_to_double(acch, accl);
-    }
+    if (ok && c < kb) Z[(int64_t)d[i0 + r] * kb + c] = F32 ? (double)hh[0] : df_to_double(hh[0], ll[0]);
   }
 }
 
