@@ -69,6 +69,8 @@ def parse():
                     help="mix: 300-request stream of small geometries (default); c5: the serving configuration "
                          "(2000 requests, squares / cubes / panels up to 40k dofs, 160 GB budget; minutes)")
     ap.add_argument("--no-cube", action="store_true", help="skip the cube-with-mid-planes section")
+    ap.add_argument("--no-panels", action="store_true",
+                    help="skip the sixteen hinged-panel instances (grouped factorisation, batched solves)")
     ap.add_argument("--workload", default="book64", choices=["book64", "book48", "book32", "flat"],
                     help="book64 is the measured workload; book48, book32 and flat are for profiling")
     ap.add_argument("--matvec", type=int, default=0,
@@ -328,6 +330,9 @@ def run_ours(args, world, rank, local, pg):
     cube = None
     if rank == 0 and not args.no_cube:
         cube = cube_bench(local, stream)
+    panels = None
+    if rank == 0 and not args.no_panels:
+        panels = panels_bench(local, stream)
 
     # end to end through the C ABI with host buffers: upload (host topology +
     # H2D from pinned memory) + assemble + factor + solve + D2H of the density
@@ -399,6 +404,7 @@ def run_ours(args, world, rank, local, pg):
             "solve_modes": modes,
             "serving": serving,
             "cube": cube,
+            "panels16": panels,
             "clocks": ck,
             "gpu_launches": int(launches),
             "e2e": e2e,
@@ -576,6 +582,84 @@ def cube_bench(device, stream, reps: int = 3):
                 roof[name] = {"bound": "hbm", "achieved": b, "peak": hbm, "unit": "GB/s", "frac": b / hbm,
                               "launch_ms": ms, "peak_source": src}
         out["roofline_matvec"] = roof
+    return out
+
+
+def panels_bench(device, stream, nreq: int = 4):
+    """The sixteen hinged-panel multiscreens (2-6 unit squares at seeded
+    dihedral angles, h in {1/24, 1/32, 1/48}) resident in one context: the
+    preconditioners factored one geometry per call and then all sixteen in one
+    grouped inversion (msbem_factor_group), and nreq seeded requests per
+    instance solved by the plain FP64 comparator (request by request) and by
+    the batched mixed-precision forms (nreq per call).  Errors are per
+    instance: the relative l2 difference from the plain FP64 density and the
+    true relative residual with the double-float product."""
+    import torch
+    import paper_2310_09204_gb300 as M
+    from paper_2310_09204_gb300 import workloads as WL
+    geoms = WL.panels_config()
+    first = M.Solver(geoms[0], device=device)
+    group = [first] + [M.Solver(g, share=first) for g in geoms[1:]]
+    out = {"workload": "16 hinged-panel multiscreens (seeds 0-15), 2-6 unit squares, h in {1/24,1/32,1/48}, "
+                       f"{nreq} requests each (g_0 = workload g, then uniform in [-1,1]^3)",
+           "dofs": [int(S.n) for S in group]}
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for S in group:
+            S.assemble()
+        torch.cuda.synchronize()
+        out["assemble_s"] = time.perf_counter() - t0
+        for S in group:                              # warm-up (pool)
+            S.factor()
+        t0 = time.perf_counter()
+        for S in group:
+            S.factor()
+        torch.cuda.synchronize()
+        out["factor_one_by_one_s"] = time.perf_counter() - t0
+        M.msbem_factor_group(group)                  # warm-up
+        t0 = time.perf_counter()
+        M.msbem_factor_group(group)
+        torch.cuda.synchronize()
+        out["factor_grouped_s"] = time.perf_counter() - t0
+        forms = {"plain_fp64": [], "mixed_tc_batch": [], "mixed_fp16_batch": []}
+        per_inst = []
+        for i, (S, geom) in enumerate(zip(group, geoms)):
+            rng = np.random.default_rng(geom.meta["seed"])
+            G = rng.uniform(-1.0, 1.0, (nreq, 3))
+            G[0] = geom.g
+            for prec in ("fp64", "mixed-tc"):
+                S.solve(G[0], precision=prec)        # FP64 copy and slices of W, graphs
+            S.solve_batch(G, precision="mixed-fp16")
+            ref = np.empty((nreq, S.n))
+            for c in range(nreq):
+                ms, r = _events(stream, lambda: S.solve(G[c], rtol=1e-8, precision="fp64"))
+                forms["plain_fp64"].append(ms)
+                ref[c] = r["density"]
+            L = np.stack([S.rhs(G[c]) for c in range(nreq)])
+            row = {"n": int(S.n)}
+            for name, prec in (("mixed_tc_batch", "mixed-tc"), ("mixed_fp16_batch", "mixed-fp16")):
+                ms, r = _events(stream, lambda: S.solve_batch(G, rtol=1e-8, precision=prec))
+                forms[name].append(ms)
+                Y, _ = S.apply(r["density"])
+                row[name] = {"maxdiff_vs_fp64": max(float(np.linalg.norm(r["density"][c] - ref[c]) /
+                                                          np.linalg.norm(ref[c])) for c in range(nreq)),
+                             "max_true_relres": max(float(np.linalg.norm(L[c] - Y[c]) / np.linalg.norm(L[c]))
+                                                    for c in range(nreq)),
+                             "iters": int(r["iters"].max())}
+            per_inst.append(row)
+        total = len(geoms) * nreq
+        res = {k: {"solves_per_s": 1e3 * total / sum(v), "total_ms": sum(v)} for k, v in forms.items()}
+        for v in res.values():
+            v["vs_plain_fp64"] = v["solves_per_s"] / res["plain_fp64"]["solves_per_s"]
+        out["solves"] = res
+        out["per_instance"] = per_inst
+        out["worst"] = {k: {"maxdiff_vs_fp64": max(r[k]["maxdiff_vs_fp64"] for r in per_inst),
+                            "max_true_relres": max(r[k]["max_true_relres"] for r in per_inst)}
+                        for k in ("mixed_tc_batch", "mixed_fp16_batch")}
+    finally:
+        for S in reversed(group):
+            S.close()
     return out
 
 

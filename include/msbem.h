@@ -159,6 +159,28 @@ typedef struct msbem_precond_opts {
  * CUDA_ERROR. */
 int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts);
 
+/* msbem_factor for n geometries of ONE context at once: the face, wire-basket
+ * and coarse blocks of all of them (Sec. 5, eq. jumpSplit) are inverted by one
+ * grouped sequence of launches (per 32-column step of the blocked Gauss-Jordan
+ * recursion, one pivot, one panel and one update launch over every block of
+ * every geometry), so that many small instances fill the GPU together.  The
+ * inverses are the same, bit for bit, as those msbem_factor gives each
+ * geometry alone.
+ *   geoms   n distinct geometries (caller-owned array), all assembled, all
+ *           uploaded to the same context;
+ *   opts    applied to every geometry, may be NULL;
+ *   status  NULL or n ints (caller-owned): per geometry MSBEM_OK or
+ *           MSBEM_BREAKDOWN.
+ * Geometries whose status is MSBEM_OK are factored even when others broke
+ * down.  The set-up time (msbem_last_timings, factor_ms) of each geometry is
+ * that of the whole group, and the group's inversion launches count in the
+ * first geometry's msbem_counters.
+ * Errors: INVALID_ARG (n < 1, a NULL or repeated geometry, geometries of
+ * different contexts), NOT_READY (one is not assembled; nothing is factored),
+ * BREAKDOWN (a block of some geometry is not positive definite), OOM,
+ * CUDA_ERROR. */
+int msbem_factor_group(msbem_geom* const* geoms, int n, const msbem_precond_opts* opts, int* status);
+
 typedef struct msbem_solve_opts {
   double rtol;        /* stop when ||L - W Phi_k|| <= rtol ||L|| (default 1e-8)*/
   int maxit;          /* iteration cap (default 1000)                          */

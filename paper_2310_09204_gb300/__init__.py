@@ -81,6 +81,7 @@ def lib():
         "msbem_copy_matrix": ([P, i64, i64, P], i32),
         "msbem_rhs": ([P, P, P], i32),
         "msbem_factor": ([P, ctypes.POINTER(PrecondOpts)], i32),
+        "msbem_factor_group": ([P, i32, ctypes.POINTER(PrecondOpts), P], i32),
         "msbem_solve": ([P, P, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(i32), P, i32,
                          ctypes.POINTER(d)], i32),
         "msbem_last_timings": ([P, P], i32),
@@ -195,6 +196,21 @@ def msbem_spd_inverse_noalloc(A, Ainv, stream: int = 0) -> int:
     device allocation; returns the C status (0 on success)."""
     n = int(A.shape[0])
     return lib().msbem_spd_inverse_noalloc(_ptr(A), n, _ptr(Ainv), stream)
+
+
+def msbem_factor_group(solvers, wire_basket: int = 0, use_coarse: int = 1):
+    """Factor the preconditioners of several Solvers that share one context
+    (Solver(share=...)) with one grouped inversion; returns the per-geometry
+    C statuses (0, or MSBEM_BREAKDOWN) and raises when any is not 0."""
+    solvers = list(solvers)
+    if not solvers:
+        raise ValueError("msbem_factor_group: no solvers")
+    geoms = (ctypes.c_void_p * len(solvers))(*[S.geom.value for S in solvers])
+    status = np.zeros(len(solvers), np.int32)
+    o = PrecondOpts(wire_basket, use_coarse)
+    _check(solvers[0].ctx, lib().msbem_factor_group(ctypes.cast(geoms, ctypes.c_void_p), len(solvers),
+                                                    ctypes.byref(o), _ptr(status)))
+    return status
 
 
 def msbem_ndofs(geom) -> int:

@@ -635,6 +635,63 @@ int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts) {
   return MSBEM_OK;
 }
 
+int msbem_factor_group(msbem_geom* const* geoms, int n, const msbem_precond_opts* opts, int* status) {
+  if (!geoms || n < 1) return MSBEM_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!geoms[i]) return MSBEM_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (geoms[j] == geoms[i]) return fail(geoms[0]->ctx, MSBEM_INVALID_ARG, "msbem_factor_group: repeated geometry");
+  }
+  msbem_ctx* c = geoms[0]->ctx;
+  for (int i = 0; i < n; ++i)
+    if (geoms[i]->ctx != c) return fail(c, MSBEM_INVALID_ARG, "msbem_factor_group: geometries of different contexts");
+  const int wb_diag = opts ? opts->wire_basket : 0;
+  if (wb_diag < 0 || wb_diag > 1) return fail(c, MSBEM_INVALID_ARG, "wire_basket must be 0 or 1");
+  for (int i = 0; i < n; ++i)
+    if (!geoms[i]->dev.assembled) return fail(c, MSBEM_NOT_READY, "msbem_factor_group: call msbem_assemble first");
+  cudaSetDevice(c->device);
+  cudaEventRecord(c->ev[4], c->stream);
+  InvPlan plan;
+  for (int i = 0; i < n; ++i) {
+    msbem_geom* g = geoms[i];
+    DevGeom& d = g->dev;
+    d.factored = 0;
+    d.use_coarse = opts ? (opts->use_coarse != 0) : 1;
+    d.wb_diag = (g->split.n_wb > 0) ? 0 : -1;
+    drop_pcg_graphs(d);
+    cudaError_t e = factor_gather(d, g->bptr, (g->split.n_wb > 0) ? wb_diag : 0, c->stream, plan, i);
+    if (e != cudaSuccess) return cuda_fail(c, e, "msbem_factor_group");
+  }
+  std::vector<int> bad;
+  cudaError_t e = factor_invert(plan, c->pool, c->stream, bad, &geoms[0]->dev.launches);
+  if (e != cudaSuccess) return cuda_fail(c, e, "msbem_factor_group");
+  std::vector<int> broke(n, 0);
+  for (size_t m = 0; m < bad.size(); ++m)
+    if (bad[m]) broke[plan.owner[m]] = 1;
+  for (int i = 0; i < n; ++i) {
+    msbem_geom* g = geoms[i];
+    DevGeom& d = g->dev;
+    if ((e = factor_finish(d, g->bptr, c->stream)) != cudaSuccess) return cuda_fail(c, e, "msbem_factor_group");
+    const int nblk = (int)g->bptr.size() - 1;
+    int64_t off = 0;
+    for (int b = 0; b < nblk; ++b) off += (g->bptr[b + 1] - g->bptr[b]) * (g->bptr[b + 1] - g->bptr[b]);
+    d.d_AHinv = d.d_binv + off;
+  }
+  cudaEventRecord(c->ev[5], c->stream);
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "msbem_factor_group");
+  float t;
+  cudaEventElapsedTime(&t, c->ev[4], c->ev[5]);
+  int any = 0;
+  for (int i = 0; i < n; ++i) {
+    geoms[i]->dev.times[3] = t;
+    geoms[i]->dev.factored = broke[i] ? 0 : 1;
+    if (status) status[i] = broke[i] ? MSBEM_BREAKDOWN : MSBEM_OK;
+    any |= broke[i];
+  }
+  if (any) return fail(c, MSBEM_BREAKDOWN, "msbem_factor_group: a block is not positive definite");
+  return MSBEM_OK;
+}
+
 int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts, double* density,
                 int* iters, double* hist, int hist_cap, double* kappa) {
   if (!g || !gv || !density) return MSBEM_INVALID_ARG;

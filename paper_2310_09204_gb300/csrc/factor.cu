@@ -10,6 +10,7 @@
 // without pivoting, which is stable for symmetric positive definite blocks; a
 // non-positive or non-finite pivot is reported as a breakdown.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "df.cuh"
@@ -79,8 +80,7 @@ __global__ void ah_kernel(const double* __restrict__ WPt, int64_t N, int64_t NH,
 #define GB 32
 
 struct BgjArgs {
-  double* A;
-  const int64_t* boff;    // per matrix id
+  double* const* Ap;      // per matrix id: the matrix (row-major, bsize x bsize)
   const int64_t* bsize;   // per matrix id
   const int32_t* order;   // matrix ids sorted by size (descending)
   const int64_t* pt1;     // prefix over sorted matrices of tiles per side
@@ -89,7 +89,7 @@ struct BgjArgs {
   float2* Pf;             // [sorted][GB*GB]
   float2* Cf;             // [soff] n x GB
   float2* Rf;             // [soff] GB x n
-  int* flag;
+  int* flag;              // per matrix id: 1 when a pivot was not positive
 };
 
 __device__ __forceinline__ int find_prefix(const int64_t* pre, int active, int64_t t) {
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(1024) bgj_pivot_kernel(BgjArgs g, int64_t k0) 
   const int b = g.order[a];
   const int64_t n = g.bsize[b];
   const int kb = (int)(n - k0 < GB ? n - k0 : GB);
-  const double* A = g.A + g.boff[b];
+  const double* A = g.Ap[b];
   for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
     const int i = e / GB, j = e % GB;
     const double v = (i < kb && j < kb) ? A[(k0 + i) * n + k0 + j] : (i == j ? 1.0 : 0.0);
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(1024) bgj_pivot_kernel(BgjArgs g, int64_t k0) 
       two_sum(r, r * t, iph, ipl);
       if (threadIdx.x == 0) {
         s_ip = make_float2(iph, ipl);
-        if (!(pk.x > 0.f && isfinite(pk.x))) atomicExch(g.flag, 1);
+        if (!(pk.x > 0.f && isfinite(pk.x))) g.flag[b] = 1;
       }
       const float2 skj = S[k][threadIdx.x];
       float rh, rl;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) bgj_panel_kernel(BgjArgs g, int active, i
   const int64_t n = g.bsize[b];
   const int I = (int)(t - g.pt1[a]);
   const int kb = (int)(n - k0 < GB ? n - k0 : GB);
-  const double* A = g.A + g.boff[b];
+  const double* A = g.Ap[b];
   float2* C = g.Cf + g.soff[a];
   float2* R = g.Rf + g.soff[a];
   const int64_t r0 = (int64_t)I * GB;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) bgj_update_kernel(BgjArgs g, int active, 
   const int I = (int)(loc / nti), J = (int)(loc % nti);
   const int kt = (int)(k0 / GB);
   const int kb = (int)(n - k0 < GB ? n - k0 : GB);
-  double* A = g.A + g.boff[b];
+  double* A = g.Ap[b];
   const float2* C = g.Cf + g.soff[a];
   const float2* R = g.Rf + g.soff[a];
   const float2* P = g.Pf + (int64_t)a * GB * GB;
@@ -302,61 +302,66 @@ cudaError_t upload(T** d, const std::vector<T>& h, cudaMemPool_t pool, cudaStrea
 }
 }  // namespace
 
-// Inverts the blocks listed in `inv_blocks` (ids into the packed layout given by
-// boff/bsize) in place.  bsize/boff are host vectors.
-static cudaError_t gj_invert(double* d_A, const std::vector<int64_t>& boff,
-                             const std::vector<int64_t>& bsize, std::vector<int32_t> inv_blocks,
-                             cudaMemPool_t pool, cudaStream_t s, int* not_spd, int64_t* launches) {
-  *not_spd = 0;
-  if (inv_blocks.empty()) return cudaSuccess;
-  std::sort(inv_blocks.begin(), inv_blocks.end(),
-            [&](int a, int b) { return bsize[a] > bsize[b]; });
-  const int nb = (int)inv_blocks.size();
+// Inverts in place the matrices plan.inv lists (ids into plan.ptr / plan.size),
+// all of them in one grouped sequence of launches: per 32-column step, one
+// pivot, one panel and one update launch over the tiles of every matrix still
+// active (matrices sorted by order, largest first).  bad[m] = 1 for each id m
+// whose recursion met a pivot that was not positive.
+cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t s, std::vector<int>& bad,
+                          int64_t* launches) {
+  const int nm = (int)plan.size.size();
+  bad.assign(nm, 0);
+  std::vector<int32_t> order;
+  for (int32_t m : plan.inv)
+    if (plan.size[m] > 0) order.push_back(m);
+  if (order.empty()) return cudaSuccess;
+  const std::vector<int64_t>& bsize = plan.size;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bsize[a] > bsize[b]; });
+  const int nb = (int)order.size();
   std::vector<int64_t> pt1(nb + 1, 0), pt2(nb + 1, 0), soff(nb + 1, 0);
   for (int a = 0; a < nb; ++a) {
-    int64_t n = bsize[inv_blocks[a]];
+    int64_t n = bsize[order[a]];
     int64_t nti = (n + GB - 1) / GB;
     pt1[a + 1] = pt1[a] + nti;
     pt2[a + 1] = pt2[a] + nti * nti;
     soff[a + 1] = soff[a] + n * GB;
   }
   BgjArgs args{};
-  args.A = d_A;
-  int64_t *d_boff = nullptr, *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt2 = nullptr, *d_soff = nullptr;
+  double** d_ptr = nullptr;
+  int64_t *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt2 = nullptr, *d_soff = nullptr;
   int32_t* d_order = nullptr;
   cudaError_t e;
-  if ((e = upload(&d_boff, boff, pool, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_ptr, plan.ptr, pool, s)) != cudaSuccess) return e;
   if ((e = upload(&d_bsize, bsize, pool, s)) != cudaSuccess) return e;
   if ((e = upload(&d_pt1, pt1, pool, s)) != cudaSuccess) return e;
   if ((e = upload(&d_pt2, pt2, pool, s)) != cudaSuccess) return e;
   if ((e = upload(&d_soff, soff, pool, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_order, inv_blocks, pool, s)) != cudaSuccess) return e;
+  if ((e = upload(&d_order, order, pool, s)) != cudaSuccess) return e;
   if ((e = pool_alloc((void**)&args.Pf, sizeof(float2) * nb * GB * GB, pool, s)) != cudaSuccess) return e;
   if ((e = pool_alloc((void**)&args.Cf, sizeof(float2) * soff[nb], pool, s)) != cudaSuccess) return e;
   if ((e = pool_alloc((void**)&args.Rf, sizeof(float2) * soff[nb], pool, s)) != cudaSuccess) return e;
-  if ((e = pool_alloc((void**)&args.flag, sizeof(int), pool, s)) != cudaSuccess) return e;
-  cudaMemsetAsync(args.flag, 0, sizeof(int), s);
-  args.boff = d_boff;
+  if ((e = pool_alloc((void**)&args.flag, sizeof(int) * nm, pool, s)) != cudaSuccess) return e;
+  cudaMemsetAsync(args.flag, 0, sizeof(int) * nm, s);
+  args.Ap = d_ptr;
   args.bsize = d_bsize;
   args.order = d_order;
   args.pt1 = d_pt1;
   args.pt2 = d_pt2;
   args.soff = d_soff;
-  const int64_t nmax = bsize[inv_blocks[0]];
+  const int64_t nmax = bsize[order[0]];
   int active = nb;
   for (int64_t k0 = 0; k0 < nmax; k0 += GB) {
-    while (active > 0 && bsize[inv_blocks[active - 1]] <= k0) --active;
+    while (active > 0 && bsize[order[active - 1]] <= k0) --active;
     bgj_pivot_kernel<<<active, GB * GB, 0, s>>>(args, k0);
     bgj_panel_kernel<<<(unsigned)pt1[active], 256, 0, s>>>(args, active, k0);
     bgj_update_kernel<<<(unsigned)pt2[active], 256, 0, s>>>(args, active, k0);
     *launches += 3;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int flag = 0;
-  cudaMemcpyAsync(&flag, args.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if ((e = cudaMemcpyAsync(bad.data(), args.flag, sizeof(int) * nm, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  *not_spd = flag;
-  void* tmp[] = {d_boff, d_bsize, d_pt1, d_pt2, d_soff, d_order, args.Pf, args.Cf, args.Rf, args.flag};
+  void* tmp[] = {d_ptr, d_bsize, d_pt1, d_pt2, d_soff, d_order, args.Pf, args.Cf, args.Rf, args.flag};
   for (void* p : tmp) cudaFreeAsync(p, s);
   return cudaSuccess;
 }
@@ -375,16 +380,18 @@ cudaError_t bgj_invert_single(double* A, int64_t n, unsigned char* scratch, size
   if (n < 1 || bytes < bgj_scratch_bytes(n)) return cudaErrorInvalidValue;
   const int64_t nti = (n + GB - 1) / GB;
   BgjArgs args{};
-  args.A = A;
   args.Pf = (float2*)scratch;
   args.Cf = args.Pf + GB * GB;
   args.Rf = args.Cf + n * GB;
   int64_t* idx = (int64_t*)(args.Rf + n * GB);
   int32_t* tail = (int32_t*)(idx + 9);
-  // boff[1] bsize[1] pt1[2] pt2[2] soff[2] (one spare slot) | order[1] flag[1]
-  const int64_t h_idx[9] = {0, n, 0, nti, 0, nti * nti, 0, n * GB, 0};
+  // ptr[1] bsize[1] pt1[2] pt2[2] soff[2] (one spare slot) | order[1] flag[1];
+  // the matrix pointer travels as its 8 bytes in the first slot
+  int64_t h_idx[9] = {0, n, 0, nti, 0, nti * nti, 0, n * GB, 0};
+  static_assert(sizeof(double*) == sizeof(int64_t), "pointer slot");
+  std::memcpy(&h_idx[0], &A, sizeof(double*));
   const int32_t h_tail[2] = {0, 0};
-  args.boff = idx;
+  args.Ap = (double* const*)idx;
   args.bsize = idx + 1;
   args.pt1 = idx + 2;
   args.pt2 = idx + 4;
@@ -408,13 +415,13 @@ cudaError_t bgj_invert_single(double* A, int64_t n, unsigned char* scratch, size
   return cudaSuccess;
 }
 
-// Gathers face / wire-basket blocks and the coarse matrix into g.d_binv and
-// inverts them.  bptr: block pointer (faces first, wire basket last if any).
-cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag, cudaStream_t s,
-                          int* not_spd) {
-  *not_spd = 0;
+// Gathers face / wire-basket blocks and the coarse matrix A_H = P^T W P into
+// g.d_binv and appends the matrices to invert to `plan` (owner: the tag the
+// plan records for them).  bptr: block pointer (faces first, wire basket last
+// if any).
+cudaError_t factor_gather(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag, cudaStream_t s,
+                          InvPlan& plan, int owner) {
   const int nblk = (int)bptr.size() - 1;
-  const bool has_wb = g.n_blocks > 0 && nblk > 0;  // caller guarantees layout
   std::vector<int64_t> bsize(nblk + 1), boff(nblk + 2, 0), prefix2(nblk + 1, 0);
   for (int b = 0; b < nblk; ++b) {
     bsize[b] = bptr[b + 1] - bptr[b];
@@ -424,7 +431,6 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
   const int64_t NH = g.use_coarse ? g.n_coarse : 0;
   bsize[nblk] = NH;
   boff[nblk + 1] = boff[nblk] + NH * NH;
-  (void)has_wb;
   cudaError_t e;
   if (g.d_binv) { cudaFreeAsync(g.d_binv, s); g.d_binv = nullptr; }
   if (g.d_boff) { cudaFreeAsync(g.d_boff, s); g.d_boff = nullptr; }
@@ -442,9 +448,14 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
         g.d_Wh, g.wlo(), g.ldw, g.d_bptr, g.d_bdofs, g.d_boff, d_prefix2, nblk, wb_block, wb_diag, g.d_binv);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   cudaFreeAsync(d_prefix2, s);
-  std::vector<int32_t> inv;
+  const int32_t base = (int32_t)plan.size.size();
+  for (int b = 0; b <= nblk; ++b) {
+    plan.ptr.push_back(g.d_binv + boff[b]);
+    plan.size.push_back(bsize[b]);
+    plan.owner.push_back(owner);
+  }
   for (int b = 0; b < nblk; ++b)
-    if (!(wb_diag && b == wb_block) && bsize[b] > 0) inv.push_back(b);
+    if (!(wb_diag && b == wb_block) && bsize[b] > 0) plan.inv.push_back(base + b);
   if (NH > 0 && g.ndof > 0) {
     // A_H = P^T W P in the last slot
     dim3 grid((unsigned)((g.ndof + 255) / 256), (unsigned)NH);
@@ -454,15 +465,19 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
                                     g.d_binv + boff[nblk]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     g.launches += 2;
-    inv.push_back(nblk);
+    plan.inv.push_back(base + nblk);
   }
-  std::vector<int64_t> bsz(bsize.begin(), bsize.end());
-  std::vector<int64_t> bof(boff.begin(), boff.end() - 1);
-  e = gj_invert(g.d_binv, bof, bsz, inv, g.pool, s, not_spd, &g.launches);
-  if (e != cudaSuccess) return e;
-  // float-pair copy of the face / wire-basket inverses for the preconditioner
+  return cudaSuccess;
+}
+
+// After the inversion: the float-pair copy of the face / wire-basket inverses
+// and the 16-row tiles (block id, first row) of the multi-vector application.
+cudaError_t factor_finish(DevGeom& g, const std::vector<int64_t>& bptr, cudaStream_t s) {
+  const int nblk = (int)bptr.size() - 1;
+  int64_t nf = 0;
+  for (int b = 0; b < nblk; ++b) nf += (bptr[b + 1] - bptr[b]) * (bptr[b + 1] - bptr[b]);
+  cudaError_t e;
   if (g.d_binvf) { cudaFreeAsync(g.d_binvf, s); g.d_binvf = nullptr; }
-  const int64_t nf = boff[nblk];
   if ((e = pool_alloc((void**)&g.d_binvf, sizeof(float2) * std::max<int64_t>(1, nf), g.pool, s)) !=
       cudaSuccess)
     return e;
@@ -471,11 +486,9 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
         g.d_binv, g.d_binvf, nf);
     ++g.launches;
   }
-  // 16-row tiles of the face / wire-basket blocks (block id, first row) for
-  // the multi-vector preconditioner application
   std::vector<int32_t> tiles;
   for (int b = 0; b < nblk; ++b)
-    for (int64_t r0 = 0; r0 < bsize[b]; r0 += 16) {
+    for (int64_t r0 = 0; r0 < bptr[b + 1] - bptr[b]; r0 += 16) {
       tiles.push_back(b);
       tiles.push_back((int32_t)r0);
     }
@@ -483,6 +496,18 @@ cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
   g.n_btiles = (int64_t)tiles.size() / 2;
   if ((e = upload(&g.d_btile, tiles, g.pool, s)) != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag, cudaStream_t s,
+                          int* not_spd) {
+  *not_spd = 0;
+  InvPlan plan;
+  cudaError_t e = factor_gather(g, bptr, wb_diag, s, plan, 0);
+  if (e != cudaSuccess) return e;
+  std::vector<int> bad;
+  if ((e = factor_invert(plan, g.pool, s, bad, &g.launches)) != cudaSuccess) return e;
+  for (int v : bad) *not_spd |= v;
+  return factor_finish(g, bptr, s);
 }
 
 }  // namespace msbem

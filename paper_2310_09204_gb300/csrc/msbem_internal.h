@@ -227,6 +227,21 @@ size_t tc_work_bytes(const DevGeom& g);
 cudaError_t launch_matvec_tc(DevGeom& g, int prec, int kb, const double* P, double* Q, double* part,
                              const int* stop, int* err, void* work, cudaStream_t s);
 
+// Preconditioner set-up (factor.cu).  factor_blocks = factor_gather +
+// factor_invert + factor_finish for one geometry; a group of geometries
+// gathers each into one InvPlan, inverts them all in one grouped sequence of
+// launches and finishes each.
+struct InvPlan {
+  std::vector<double*> ptr;    // per matrix id: the n x n matrix, row-major
+  std::vector<int64_t> size;   // per matrix id: n
+  std::vector<int> owner;      // per matrix id: the tag given to factor_gather
+  std::vector<int32_t> inv;    // the ids to invert in place
+};
+cudaError_t factor_gather(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag, cudaStream_t s,
+                          InvPlan& plan, int owner);
+cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t s, std::vector<int>& bad,
+                          int64_t* launches);
+cudaError_t factor_finish(DevGeom& g, const std::vector<int64_t>& bptr, cudaStream_t s);
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag,
                           cudaStream_t s, int* not_spd);
 

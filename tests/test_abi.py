@@ -70,3 +70,12 @@ def test_cells_match_oracle(L, geom):
     Zo = Topology(geom.xyz, geom.tri).cells()
     assert Zg.shape == Zo.shape
     assert np.array_equal(Zg, Zo)
+
+
+def test_factor_group_rejects_empty_groups(L):
+    # argument checks that return before any device call
+    import ctypes
+    assert L.msbem_factor_group(None, 1, None, None) == -1
+    geoms = (ctypes.c_void_p * 1)(None)
+    assert L.msbem_factor_group(ctypes.cast(geoms, ctypes.c_void_p), 0, None, None) == -1
+    assert L.msbem_factor_group(ctypes.cast(geoms, ctypes.c_void_p), 1, None, None) == -1
