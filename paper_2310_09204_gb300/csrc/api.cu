@@ -432,6 +432,10 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
     }
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "far constants");
+  // W is rewritten from here on: until it is complete the geometry counts as
+  // neither assembled nor factored (a failed assembly leaves it unusable)
+  d.assembled = 0;
+  d.factored = 0;
   // V (nt^2 float pairs) is scratch of the assembly only: taken from the pool
   // here and returned once W is formed, so a resident geometry holds W alone
   drop_pcg_graphs(d);
@@ -613,9 +617,12 @@ int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts) {
   cudaSetDevice(c->device);
   DevGeom& d = g->dev;
   int wb_diag = opts ? opts->wire_basket : 0;
-  d.use_coarse = opts ? (opts->use_coarse != 0) : 1;
   if (wb_diag < 0 || wb_diag > 1) return fail(c, MSBEM_INVALID_ARG, "wire_basket must be 0 or 1");
+  // nothing of the geometry changes before the options are checked: the old
+  // inverses and their coarse layout stay usable after a rejected call
+  d.use_coarse = opts ? (opts->use_coarse != 0) : 1;
   d.wb_diag = (g->split.n_wb > 0) ? 0 : -1;  // marks whether the last block is the wire basket
+  d.factored = 0;      // until the new inverses are complete
   drop_pcg_graphs(d);  // the captured iterations address the old inverses
   cudaEventRecord(c->ev[4], c->stream);
   int not_spd = 0;
@@ -860,8 +867,10 @@ int msbem_dl_potential(msbem_geom* g, const double* density, const double* targe
   double *dx = nullptr, *dout = nullptr;
   if (!xdev && (e = pool_alloc((void**)&dx, sizeof(double) * std::max<int64_t>(1, 3 * M), c->pool, s)) != cudaSuccess)
     return cuda_fail(c, e, "msbem_dl_potential");
-  if (!odev && (e = pool_alloc((void**)&dout, sizeof(double) * std::max<int64_t>(1, M), c->pool, s)) != cudaSuccess)
+  if (!odev && (e = pool_alloc((void**)&dout, sizeof(double) * std::max<int64_t>(1, M), c->pool, s)) != cudaSuccess) {
+    if (dx) cudaFreeAsync(dx, s);
     return cuda_fail(c, e, "msbem_dl_potential");
+  }
   if (!xdev) cudaMemcpyAsync(dx, targets, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, s);
   float ms = 0.f;
   e = dl_potential(g->dev, J, xdev ? targets : dx, M, refine, odev ? out : dout, &ms, s);

@@ -293,6 +293,38 @@ __global__ void to_float_pairs_kernel(const double* __restrict__ x, float2* __re
 }
 
 namespace {
+// Scratch of one call: buffers taken from the pool, all returned (stream
+// ordered) when the object goes out of scope, on every return path.
+class PoolScratch {
+ public:
+  PoolScratch(cudaMemPool_t pool, cudaStream_t s) : pool_(pool), s_(s) {}
+  PoolScratch(const PoolScratch&) = delete;
+  PoolScratch& operator=(const PoolScratch&) = delete;
+  ~PoolScratch() {
+    for (void* q : held_) cudaFreeAsync(q, s_);
+  }
+  template <class T>
+  cudaError_t take(T** d, size_t n) {
+    void* q = nullptr;
+    cudaError_t e = pool_alloc(&q, sizeof(T) * std::max<size_t>(1, n), pool_, s_);
+    if (e != cudaSuccess) return e;
+    held_.push_back(q);
+    *d = (T*)q;
+    return cudaSuccess;
+  }
+  template <class T>
+  cudaError_t put(T** d, const std::vector<T>& h) {
+    cudaError_t e = take(d, h.size());
+    if (e != cudaSuccess || h.empty()) return e;
+    return cudaMemcpyAsync(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s_);
+  }
+
+ private:
+  cudaMemPool_t pool_;
+  cudaStream_t s_;
+  std::vector<void*> held_;
+};
+
 template <class T>
 cudaError_t upload(T** d, const std::vector<T>& h, cudaMemPool_t pool, cudaStream_t s) {
   cudaError_t e = pool_alloc((void**)d, sizeof(T) * std::max<size_t>(1, h.size()), pool, s);
@@ -330,17 +362,18 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
   double** d_ptr = nullptr;
   int64_t *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt2 = nullptr, *d_soff = nullptr;
   int32_t* d_order = nullptr;
+  PoolScratch scratch(pool, s);
   cudaError_t e;
-  if ((e = upload(&d_ptr, plan.ptr, pool, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_bsize, bsize, pool, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_pt1, pt1, pool, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_pt2, pt2, pool, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_soff, soff, pool, s)) != cudaSuccess) return e;
-  if ((e = upload(&d_order, order, pool, s)) != cudaSuccess) return e;
-  if ((e = pool_alloc((void**)&args.Pf, sizeof(float2) * nb * GB * GB, pool, s)) != cudaSuccess) return e;
-  if ((e = pool_alloc((void**)&args.Cf, sizeof(float2) * soff[nb], pool, s)) != cudaSuccess) return e;
-  if ((e = pool_alloc((void**)&args.Rf, sizeof(float2) * soff[nb], pool, s)) != cudaSuccess) return e;
-  if ((e = pool_alloc((void**)&args.flag, sizeof(int) * nm, pool, s)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_ptr, plan.ptr)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_bsize, bsize)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_pt1, pt1)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_pt2, pt2)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_soff, soff)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_order, order)) != cudaSuccess) return e;
+  if ((e = scratch.take(&args.Pf, (size_t)nb * GB * GB)) != cudaSuccess) return e;
+  if ((e = scratch.take(&args.Cf, (size_t)soff[nb])) != cudaSuccess) return e;
+  if ((e = scratch.take(&args.Rf, (size_t)soff[nb])) != cudaSuccess) return e;
+  if ((e = scratch.take(&args.flag, (size_t)nm)) != cudaSuccess) return e;
   cudaMemsetAsync(args.flag, 0, sizeof(int) * nm, s);
   args.Ap = d_ptr;
   args.bsize = d_bsize;
@@ -360,10 +393,7 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(bad.data(), args.flag, sizeof(int) * nm, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  void* tmp[] = {d_ptr, d_bsize, d_pt1, d_pt2, d_soff, d_order, args.Pf, args.Cf, args.Rf, args.flag};
-  for (void* p : tmp) cudaFreeAsync(p, s);
-  return cudaSuccess;
+  return cudaStreamSynchronize(s);
 }
 
 // Blocked Gauss-Jordan inversion of one SPD matrix A (n x n, row-major,

@@ -448,13 +448,17 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
     if ((e = pool_alloc((void**)&hist, sizeof(double) * (3 * (size_t)hcap + 1), g.pool, s)) != cudaSuccess)
       return e;
   }
+  auto drop = [&](cudaError_t err) {  // error exit: a temporary history goes back to the pool
+    if (hist != g.d_hist) cudaFreeAsync(hist, s);
+    return err;
+  };
   PcgState h_st = {0, 0, maxit, fixed, 0};
   cudaMemcpyAsync(st, &h_st, sizeof(PcgState), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(x, 0, sizeof(double) * N, s);
-  if ((e = launch_rhs(g, gvec, r, s)) != cudaSuccess) return e;
+  if ((e = launch_rhs(g, gvec, r, s)) != cudaSuccess) return drop(e);
   dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, r, N, part, st);
   reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 6, st);
-  if (plain && (e = ensure_w64(g, s)) != cudaSuccess) return e;
+  if (plain && (e = ensure_w64(g, s)) != cudaSuccess) return drop(e);
   apply_M(g, r, z, t, u, precondition, plain, st, s);
   update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, g.d_pfp, g.ldw, z, scal, N, 1, st);
   dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
@@ -463,8 +467,8 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
   g.launches += 6;
   double nL2 = 0.0;
   if ((e = cudaMemcpyAsync(&nL2, scal + 6, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return e;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    return drop(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return drop(e);
   if (nL2 == 0.0) {
     out.hist.push_back(0.0);
     out.status = MSBEM_OK;
@@ -478,14 +482,14 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
     // capture one chunk of iterations on the private stream
     cudaGraph_t graph = nullptr;
     if ((e = cudaStreamBeginCapture(g.cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-      return e;
+      return drop(e);
     const int64_t before = g.launches;
     for (int c = 0; c < PCG_CHUNK; ++c) enqueue_iteration(g, precondition, plain, hist, hcap, g.cap_stream);
     g.launches = before;
-    if ((e = cudaStreamEndCapture(g.cap_stream, &graph)) != cudaSuccess) return e;
+    if ((e = cudaStreamEndCapture(g.cap_stream, &graph)) != cudaSuccess) return drop(e);
     e = cudaGraphInstantiate(&g.pcg_exec[gi], graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return drop(e);
   }
   int enq = 0;
   while (enq < maxit) {
@@ -494,17 +498,17 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
       enqueue_iteration(g, precondition, plain, hist, hcap, nullptr);  // count only
       const int64_t per_iter = g.launches - before;
       g.launches = before + per_iter * PCG_CHUNK;
-      if ((e = cudaGraphLaunch(g.pcg_exec[gi], s)) != cudaSuccess) return e;
+      if ((e = cudaGraphLaunch(g.pcg_exec[gi], s)) != cudaSuccess) return drop(e);
       enq += PCG_CHUNK;
     } else {
       const int chunk = std::min(PCG_CHUNK, maxit - enq);
       for (int c = 0; c < chunk; ++c) enqueue_iteration(g, precondition, plain, hist, hcap, s);
       enq += chunk;
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return drop(e);
     if ((e = cudaMemcpyAsync(&h_st, st, sizeof(PcgState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-      return e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+      return drop(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return drop(e);
     if (h_st.done) break;
   }
   const int it = h_st.iter;

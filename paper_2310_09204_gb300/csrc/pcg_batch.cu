@@ -535,10 +535,14 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz), b.bs);
   g.launches += 6;
   // columns with zero data are finished before the first iteration
+  auto drop = [&](cudaError_t err) {  // error exit: the buffer goes back to the pool
+    cudaFreeAsync(base, s);
+    return err;
+  };
   if ((e = cudaMemcpyAsync(h_cs.data(), b.cs, sizeof(ColState) * kb, cudaMemcpyDeviceToHost, s)) !=
       cudaSuccess)
-    return e;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    return drop(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return drop(e);
   int zero_cols = 0;
   for (int c = 0; c < kb; ++c)
     if (h_cs[c].nL2 == 0.0) {
@@ -556,10 +560,10 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
     for (int it = 0; it < chunk; ++it)
       enqueue_batch_iteration(g, b, kb, precondition, mv_mode, tmP, split, scratch, maxit, s);
     enq += chunk;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return drop(e);
     if ((e = cudaMemcpyAsync(&h_bs, b.bs, sizeof(BatchState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-      return e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+      return drop(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return drop(e);
   }
   std::vector<double> h(hsz);
   cudaMemcpyAsync(h.data(), b.hist, sizeof(double) * hsz, cudaMemcpyDeviceToHost, s);

@@ -656,17 +656,24 @@ int msbem_server_create(msbem_ctx* ctx, const msbem_server_opts* opts, msbem_ser
   S->device = msbem_ctx_device(ctx);
   cudaSetDevice(S->device);
   const int nw = o.admission_threads > 0 ? std::min(o.admission_threads, 8) : 4;
+  auto undo = [&](int st) {  // a failed set-up releases the workers made so far
+    for (auto& w : S->workers) {
+      msbem_destroy(w->ctx);
+      cudaStreamDestroy(w->stream);
+    }
+    S->workers.clear();
+    return st;
+  };
   for (int i = 0; i < nw; ++i) {
     auto W = std::make_unique<msbem_server::Worker>();
-    if (cudaStreamCreateWithFlags(&W->stream, cudaStreamNonBlocking) != cudaSuccess) return MSBEM_CUDA_ERROR;
+    if (cudaStreamCreateWithFlags(&W->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return undo(MSBEM_CUDA_ERROR);
+    }
     const int st = msbem_create(&W->ctx, S->device, W->stream);
     if (st) {
       cudaStreamDestroy(W->stream);
-      for (auto& w : S->workers) {
-        msbem_destroy(w->ctx);
-        cudaStreamDestroy(w->stream);
-      }
-      return st;
+      return undo(st);
     }
     S->workers.push_back(std::move(W));
   }

@@ -103,3 +103,16 @@ def test_sixteen_instances_grouped_mixed_tc():
         print("grouped factorisation, mixed-tc: worst true relative residual", worst)
     finally:
         _close(group)
+
+
+def test_rejected_factor_keeps_inverses():
+    # options are checked before anything of the geometry changes
+    geom = SMALL[1]
+    with M.Solver(geom) as S:
+        S.assemble().factor()
+        ref = S.solve(geom.g, rtol=0.0, maxit=6, fixed=True)["density"]
+        with pytest.raises(M.MsbemError) as e:
+            S.factor(wire_basket=2, use_coarse=0)
+        assert e.value.status == -1
+        out = S.solve(geom.g, rtol=0.0, maxit=6, fixed=True)["density"]
+        assert np.array_equal(out, ref)
