@@ -79,6 +79,15 @@ def parse():
     return ap.parse_args()
 
 
+BOOK64_TEXT = ("three-page book h=1/64, N=12033 dofs, 24576 triangles, 48 jittered patches (seed 0), "
+               "coarse H=1/4 (33 dofs), g=(1,0.5,0.25), rtol 1e-8")
+
+
+def workload_text(name: str, geom) -> str:
+    """The config.workload string both arms print for the same --workload."""
+    return BOOK64_TEXT if name == "book64" else f"{geom.name} (profiling case)"
+
+
 def make_workload(name):
     from paper_2310_09204_gb300 import workloads as WL
     if name == "book64":
@@ -225,9 +234,8 @@ def run_reference(args, world, rank, pg):
     if rank != 0:
         return
     from oracle import core
-    from paper_2310_09204_gb300 import workloads as WL
     core.build()
-    geom = WL.book_config()
+    geom = make_workload(args.workload)
     state = {}
     for _ in range(args.warmup):
         # untimed warm-up: the topology and one V row (cheap) plus the one-time W
@@ -245,9 +253,8 @@ def run_reference(args, world, rank, pg):
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "three-page book h=1/64, N=12033 dofs, 48 jittered patches, coarse H=1/4, "
-                                   "g=(1,0.5,0.25), rtol 1e-8", "global_batch": 1, "seq_len": 12033,
-                       "parallelism": "replicas"},
+            "config": {"workload": workload_text(args.workload, geom), "global_batch": 1,
+                       "seq_len": int(state["pb"].top.ndof), "parallelism": "rank 0 only (host cores)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
                              "sample": "V on 1/8 of its rows (scaled); topology, contraction, "
                                        "preconditioner and PCG in full", "phases": details[-1]},
@@ -386,9 +393,7 @@ def run_ours(args, world, rank, local, pg):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 (double-float far field)" if args.far_kernel == 0 else "f64",
             "data": "synthetic",
-            "config": {"workload": ("three-page book h=1/64, N=12033 dofs, 24576 triangles, 48 jittered "
-                                    "patches (seed 0), coarse H=1/4 (33 dofs), g=(1,0.5,0.25), rtol 1e-8")
-                       if args.workload == "book64" else f"{geom.name} (profiling case)",
+            "config": {"workload": workload_text(args.workload, geom),
                        "global_batch": world, "seq_len": N, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (W 1.16 GB, V 4.8 GB)"},
             "latency_ms": {"p50": p50, "p99": p99},
