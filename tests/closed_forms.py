@@ -81,3 +81,59 @@ def V_vertex_fan(A, B, C, t1=0.3, t2=0.7):
     v23 = (F(A, M1, C) - F(A, M1, M2) - F(A, M2, C)) / 2.0
     v13 = (F(A, B, C) - F(A, B, M1) - F(A, M1, M2) - F(A, M2, C)) / 2.0 - v12 - v23
     return np.array([A, B, M1]), np.array([A, M2, C]), v13 / (4.0 * math.pi)
+
+
+def triangle_potential(T, r) -> float:
+    """u(r) = int_T dS'/|r - r'| for a flat triangle T (3 x 3 vertices) and any
+    point r outside T or at one of its vertices: the edge-by-edge closed form of Wilton et al. (IEEE Trans.
+    Antennas Propag. 32, 1984), restated.  With n the unit normal, d the height
+    of r over the plane and rho its foot, each edge (a, b) with unit tangent t
+    and in-plane outward normal m contributes
+        P0 ln((R+ + l+) / (R- + l-)) - |d| [atan(P0 l+ / (R0^2 + |d| R+))
+                                          - atan(P0 l- / (R0^2 + |d| R-))],
+    P0 = (a - rho).m, l-/+ = (a/b - rho).t, R0^2 = P0^2 + d^2, R-/+ = |r - a/b|."""
+    T = np.asarray(T, float)
+    r = np.asarray(r, float)
+    n = np.cross(T[1] - T[0], T[2] - T[0])
+    n /= np.linalg.norm(n)
+    d = float(np.dot(r - T[0], n))
+    rho = r - d * n
+    c = T.mean(axis=0)
+    ad = abs(d)
+    u = 0.0
+    for i in range(3):
+        a, b = T[i], T[(i + 1) % 3]
+        t = (b - a) / np.linalg.norm(b - a)
+        m = np.cross(t, n)
+        if np.dot(c - a, m) > 0:          # outward from the triangle
+            m = -m
+        P0 = float(np.dot(a - rho, m))
+        lm, lp = float(np.dot(a - rho, t)), float(np.dot(b - rho, t))
+        R0s = P0 * P0 + d * d
+        Rm, Rp = float(np.linalg.norm(r - a)), float(np.linalg.norm(r - b))
+        if abs(P0) > 1e-14 * (Rm + Rp):   # r on the edge's line: no log term
+            u += P0 * math.log((Rp + lp) / (Rm + lm))
+        u -= ad * (math.atan2(P0 * lp, R0s + ad * Rp) - math.atan2(P0 * lm, R0s + ad * Rm))
+    return u
+
+
+def collapsed_gauss(T, f, n: int = 24) -> float:
+    """int_T f dS by the n x n Gauss-Legendre rule on the square collapsed onto
+    T (x = A + s (B - A) + t (1 - s) (C - A), Jacobian 2|T| (1 - s)); for
+    smooth f."""
+    T = np.asarray(T, float)
+    x, w = np.polynomial.legendre.leggauss(n)
+    x, w = 0.5 * (x + 1.0), 0.5 * w
+    area2 = float(np.linalg.norm(np.cross(T[1] - T[0], T[2] - T[0])))
+    tot = 0.0
+    for i in range(n):
+        for j in range(n):
+            p = T[0] + x[i] * (T[1] - T[0]) + x[j] * (1.0 - x[i]) * (T[2] - T[0])
+            tot += w[i] * w[j] * (1.0 - x[i]) * f(p)
+    return area2 * tot
+
+
+def V_separated(P, Q, n: int = 24) -> float:
+    """V_PQ = int_P int_Q 1/(4 pi |x - y|) for triangles that share no point:
+    the closed-form inner potential over P, integrated over Q."""
+    return collapsed_gauss(Q, lambda y: triangle_potential(P, y), n) / (4.0 * math.pi)

@@ -183,3 +183,56 @@ def test_far_rule_symmetric_and_consistent():
     assert abs(a - b) < 1e-15 * a
     # well separated: the 6-point product rule matches a high-order rule closely
     assert abs(a - core.rule_far(P, Q, 0, 12)) < 1e-6 * a
+
+
+# --- separated pairs against the closed-form potential of a flat triangle ---
+
+P_GEN = np.array([[0.2, 0.1, 0.3], [0.9, 0.2, 0.1], [0.4, 0.8, 0.6]])
+Q_GEN = np.array([[0.0, 0.0, 0.0], [0.7, 0.3, 0.2], [0.1, 0.6, -0.4]])
+
+
+def test_triangle_potential_two_derivations_agree():
+    # at a vertex, in the plane: the edge formula against the polar one
+    A, B, C = np.array([0., 0, 0]), np.array([1.0, 0.1, 0]), np.array([0.3, 0.9, 0])
+    T = np.array([A, B, C])
+    for v, (a, b, c) in ((A, (A, B, C)), (B, (B, C, A)), (C, (C, A, B))):
+        assert abs(cf.triangle_potential(T, v) - cf.potential_at_vertex(a, b, c)) < 1e-14
+    # off the plane, against a high-order rule of the smooth integrand
+    for r in ([0.4, 0.3, 0.5], [2.4, -0.3, -0.2], [-0.5, 1.2, 0.3], [0.5, 0.4, -2.0]):
+        r = np.array(r)
+        ref = cf.collapsed_gauss(T, lambda x: 1.0 / np.linalg.norm(r - x), 60)
+        assert abs(cf.triangle_potential(T, r) - ref) < 1e-13 * ref
+    # far away it is the monopole area / distance
+    r = np.array([300.0, 200.0, 400.0])
+    area = 0.5 * np.linalg.norm(np.cross(B - A, C - A))
+    mono = area / np.linalg.norm(r - T.mean(axis=0))
+    assert abs(cf.triangle_potential(T, r) - mono) < 1e-5 * mono
+
+
+def test_far_rule_against_exact_entries():
+    """V for separated pairs: the oracle's high-order far rule equals the exact
+    value, and its 6-point product rule (degree 4 on each triangle) errs like
+    (diameter / distance)^6."""
+    e6 = []
+    for dist in (1.5, 3.0, 6.0, 12.0):
+        Q = Q_GEN + np.array([dist, 0.3 * dist, -0.2 * dist])
+        exact = cf.V_separated(P_GEN, Q)
+        assert abs(core.rule_far(P_GEN, Q, 0, 12) - exact) < 1e-12 * exact
+        e6.append(abs(core.rule_far(P_GEN, Q) - exact) / exact)
+    assert e6[0] < 3e-5
+    for a, b in zip(e6, e6[1:]):
+        assert a / b > 32.0, e6
+
+
+def test_oracle_entry_of_a_mesh_pair_is_the_exact_integral():
+    # two triangles of the flat h = 1/16 screen, far apart: the oracle's pair
+    # entry (classification, vertex order, areas) against the exact integral
+    from paper_2310_09204_gb300 import workloads as WL
+    geom = WL.flat_config()
+    xyz, tri = geom.xyz, geom.tri
+    cen = xyz[tri].mean(axis=1)
+    T = 0
+    S = int(np.argmax(np.linalg.norm(cen - cen[T], axis=1)))
+    exact = cf.V_separated(xyz[tri[T]], xyz[tri[S]])
+    assert abs(core.pair(xyz, tri, T, S, far_order=12) - exact) < 1e-12 * exact
+    assert abs(core.pair(xyz, tri, T, S) - exact) < 1e-9 * exact
