@@ -131,7 +131,9 @@ typedef struct msbem_assemble_opts {
  * NULL (defaults).  W (N x N, row-major) stays on the device, held as pairs of
  * floats (hi, lo) whose sum carries a 48-bit significand (relative precision
  * 2^-47, FP64-level for the solve); msbem_copy_matrix returns it as FP64.
- * Errors: NOT_READY, OOM, CUDA_ERROR. */
+ * A new assembly discards the preconditioner (msbem_factor again); a failed
+ * one leaves the geometry neither assembled nor factored.
+ * Errors: INVALID_ARG (options), NOT_READY, OOM, CUDA_ERROR. */
 int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts);
 
 /* Copy rows [row0, row0+nrows) of W into out (host or device, nrows*N
@@ -155,8 +157,10 @@ typedef struct msbem_precond_opts {
 /* Set up M(H;h) (Sec. 2.1 Remark on PCG, eq. jumpSplit): the principal blocks
  * A_F = W[F,F] of every face space and A_W of the wire basket, and the coarse
  * matrix A_H = P^T W P, all inverted (FP64).  opts may be NULL.
- * Errors: NOT_READY (no W), BREAKDOWN (a block is not positive definite), OOM,
- * CUDA_ERROR. */
+ * Rejected options (INVALID_ARG) change nothing; any other failure leaves the
+ * geometry unfactored (solves with the preconditioner return NOT_READY).
+ * Errors: INVALID_ARG, NOT_READY (no W), BREAKDOWN (a block is not positive
+ * definite), OOM, CUDA_ERROR. */
 int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts);
 
 /* msbem_factor for n geometries of ONE context at once: the face, wire-basket
