@@ -113,7 +113,7 @@ int msbem_split_info(const msbem_geom* g, int64_t* n_faces, int64_t* n_wire_bask
 
 typedef struct msbem_assemble_opts {
   int ss_order;    /* Gauss-Legendre points per dimension of the singular     */
-                   /* (Sauter-Schwab-type) rules, 1..16; default 5            */
+                   /* (Sauter-Schwab-type) rules, 2..16; <= 0: default 5      */
   int far_kernel;  /* pair integrals: 0 = double-float arithmetic on the FP32 */
                    /* pipe (default), 1 = native FP64 (far and near field)    */
   int64_t panel_rows; /* 0 (default): V (nt x nt float pairs) in one piece    */
