@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -222,11 +223,20 @@ def msbem_ndofs(geom) -> int:
 class Solver:
     """One context + one uploaded geometry.  share=another Solver: use its
     context (and memory pool) instead of a new one; closing this Solver then
-    frees only its geometry."""
+    frees only its geometry.  The Solver that created the context stays alive
+    while any Solver shares it, and closing it first also invalidates the
+    geometries of the Solvers sharing its context (the context frees them)."""
 
     def __init__(self, geom=None, device: int = 0, stream: int | None = None, share=None, **arrays):
+        self.ctx, self.geom, self._owns_ctx = None, None, False
+        self._sharers = weakref.WeakSet()   # Solvers using this one's context
+        self._root = None                   # the Solver owning the shared context
         if share is not None:
-            self.ctx, self._owns_ctx = share.ctx, False
+            root = share._root if share._root is not None else share
+            if root.ctx is None:
+                raise ValueError("Solver(share=...): that Solver is closed")
+            self.ctx, self._root = root.ctx, root
+            root._sharers.add(self)
         else:
             if stream is None:
                 try:
@@ -250,11 +260,19 @@ class Solver:
     def close(self):
         if self.ctx is not None:
             if self._owns_ctx:
+                # msbem_destroy frees every geometry of the context, the
+                # sharers' included: they must not free theirs again
+                for other in list(self._sharers):
+                    other.ctx, other.geom = None, None
+                self._sharers.clear()
                 lib().msbem_destroy(self.ctx)
             else:
                 self.free_geometry()
+                if self._root is not None:
+                    self._root._sharers.discard(self)
             self.ctx = None
             self.geom = None
+            self._root = None
 
     def __del__(self):
         try:
