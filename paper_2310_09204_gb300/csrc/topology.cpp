@@ -18,21 +18,27 @@
 namespace msbem {
 namespace {
 
+// Union-find whose root is the smallest index of its set: unite links the
+// larger root under the smaller and path halving only moves links down, so
+// p[i] <= i always, and one pass in index order (flatten) then points every
+// node at its root.  Indices fit in 32 bits (at most 6 * 2^28 nodes).
 struct Dsu {
-  std::vector<int64_t> p;
+  std::vector<int32_t> p;
   explicit Dsu(int64_t n) : p(n) { std::iota(p.begin(), p.end(), 0); }
-  int64_t find(int64_t a) {
+  int32_t find(int64_t a) {
     while (p[a] != a) {
       p[a] = p[p[a]];
       a = p[a];
     }
-    return a;
+    return (int32_t)a;
   }
   void unite(int64_t a, int64_t b) {
-    a = find(a);
-    b = find(b);
-    if (a == b) return;
-    if (a < b) p[b] = a; else p[a] = b;
+    const int32_t ra = find(a), rb = find(b);
+    if (ra == rb) return;
+    if (ra < rb) p[rb] = ra; else p[ra] = rb;
+  }
+  void flatten() {
+    for (size_t i = 0; i < p.size(); ++i) p[i] = p[p[i]];
   }
 };
 
@@ -82,17 +88,28 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
     o.area[T] = 0.5 * nc;
     for (int k = 0; k < 3; ++k) o.normal[3 * T + k] = c[k] / nc;
   }
-  // duplicate triangles
+  // duplicate triangles: the sorted vertex triples, bucketed by their
+  // smallest vertex (counting sort); two equal triples share a bucket
   {
     std::vector<std::array<int32_t, 3>> keys(nt);
+    std::vector<int64_t> start(nv + 1, 0);
     for (int64_t T = 0; T < nt; ++T) {
       std::array<int32_t, 3> k = {o.tri[3 * T], o.tri[3 * T + 1], o.tri[3 * T + 2]};
-      std::sort(k.begin(), k.end());
+      if (k[0] > k[1]) std::swap(k[0], k[1]);
+      if (k[1] > k[2]) std::swap(k[1], k[2]);
+      if (k[0] > k[1]) std::swap(k[0], k[1]);
       keys[T] = k;
+      start[k[0] + 1]++;
     }
-    std::sort(keys.begin(), keys.end());
-    for (int64_t i = 1; i < nt; ++i)
-      if (keys[i] == keys[i - 1]) { err = "duplicate triangle"; return MSBEM_NONCONFORMING; }
+    for (int64_t v = 0; v < nv; ++v) start[v + 1] += start[v];
+    std::vector<std::array<int32_t, 3>> byv(nt);
+    std::vector<int64_t> put(start.begin(), start.end() - 1);
+    for (int64_t T = 0; T < nt; ++T) byv[put[keys[T][0]]++] = keys[T];
+    for (int64_t v = 0; v < nv; ++v) {
+      std::sort(byv.begin() + start[v], byv.begin() + start[v + 1]);
+      for (int64_t x = start[v] + 1; x < start[v + 1]; ++x)
+        if (byv[x] == byv[x - 1]) { err = "duplicate triangle"; return MSBEM_NONCONFORMING; }
+    }
   }
   // edges: (lo, hi, T) sorted -- a counting sort on lo, then the few edges
   // of each lo (a vertex's degree) by insertion on (hi, T)
@@ -136,6 +153,46 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
       for (int32_t v : {vi, vk}) {
         int a = local_index(&o.tri[3 * T], v);
         side.unite(node(T, 0, a), node(T, 1, a));
+      }
+    } else if (m == 2) {
+      // two triangles: the cyclic order is (0, 1) whatever their angle, so the
+      // wedges are (0 up, 1 down) and (1 up, 0 down).  The angle of the second
+      // about the edge, from the first, only decides whether they overlap
+      // (within 1e-10 of 0 or 2 pi); it can be that close only when its sine
+      // is tiny and its cosine positive, and only then is it computed
+      double u[3];
+      sub3(&o.xyz[3 * vk], &o.xyz[3 * vi], u);
+      const double nu = norm3(u);
+      for (int k = 0; k < 3; ++k) u[k] /= nu;
+      double d[2][3];
+      int up2[2];
+      for (int j = 0; j < 2; ++j) {
+        const int32_t T = edges[e0 + j].T;
+        const int32_t* t = &o.tri[3 * T];
+        const int32_t r = (t[0] != vi && t[0] != vk) ? t[0] : ((t[1] != vi && t[1] != vk) ? t[1] : t[2]);
+        sub3(&o.xyz[3 * r], &o.xyz[3 * vi], d[j]);
+        const double du = dot3(d[j], u);
+        for (int k = 0; k < 3; ++k) d[j][k] -= du * u[k];
+        const double nd = norm3(d[j]);
+        for (int k = 0; k < 3; ++k) d[j][k] /= nd;
+        double ud[3];
+        cross3(u, d[j], ud);
+        up2[j] = dot3(&o.normal[3 * T], ud) > 0 ? 0 : 1;   // side facing increasing angle
+      }
+      double ref2[3];
+      cross3(u, d[0], ref2);
+      const double cs = dot3(d[1], d[0]), sn = dot3(d[1], ref2);
+      if (cs > 0.0 && std::fabs(sn) < 1e-9) {
+        double th = std::atan2(sn, cs);
+        if (th < 0) th += 2.0 * M_PI;
+        if (th < 1e-10 || 2.0 * M_PI - th < 1e-10) { err = "overlapping triangles at an edge"; return MSBEM_NONCONFORMING; }
+      }
+      const int32_t T0 = edges[e0].T, T1 = edges[e0 + 1].T;
+      for (int32_t v : {vi, vk}) {
+        const int a0 = local_index(&o.tri[3 * T0], v), a1 = local_index(&o.tri[3 * T1], v);
+        side.unite(node(T0, up2[0], a0), node(T1, 1 - up2[1], a1));
+        side.unite(node(T1, up2[1], a1), node(T0, 1 - up2[0], a0));
+        fan.unite(3 * (int64_t)T0 + a0, 3 * (int64_t)T1 + a1);
       }
     } else {
       double u[3];
@@ -191,6 +248,8 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
     }
     e0 = e1;
   }
+  side.flatten();   // from here on p[x] is the root of x
+  fan.flatten();
   // corners per vertex (counting sort)
   std::vector<int64_t> cptr(nv + 1, 0);
   for (int64_t i = 0; i < 3 * nt; ++i) cptr[o.tri[i] + 1]++;
@@ -202,9 +261,9 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
   std::vector<std::pair<int64_t, int64_t>> roots;  // (min key, root)
   for (int64_t v = 0; v < nv; ++v) {
     if (cptr[v] == cptr[v + 1]) continue;
-    int64_t r0 = fan.find(corner[cptr[v]]);
+    const int32_t r0 = fan.p[corner[cptr[v]]];
     for (int64_t c = cptr[v]; c < cptr[v + 1]; ++c)
-      if (fan.find(corner[c]) != r0) {
+      if (fan.p[corner[c]] != r0) {
         err = "point contact at vertex " + std::to_string(v);
         return MSBEM_POINT_CONTACT;
       }
@@ -213,7 +272,7 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
       int64_t T = corner[c] / 3;
       int a = (int)(corner[c] % 3);
       for (int s = 0; s < 2; ++s) {
-        int64_t r = side.find(node(T, s, a));
+        const int64_t r = side.p[node(T, s, a)];
         int64_t key = 2 * T + s;
         bool found = false;
         for (auto& pr : roots)
@@ -227,7 +286,7 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
       int64_t T = corner[c] / 3;
       int a = (int)(corner[c] % 3);
       for (int s = 0; s < 2; ++s) {
-        int64_t r = side.find(node(T, s, a));
+        const int64_t r = side.p[node(T, s, a)];
         for (size_t j = 0; j < roots.size(); ++j)
           if (roots[j].second == r) { o.sector[(2 * T + s) * 3 + a] = (int32_t)j; break; }
       }
@@ -452,17 +511,26 @@ int build_split(const Topo& f, const Topo& c, const int32_t* parent, const int32
     if (patch[T] < 0) { err = "negative patch id"; return MSBEM_INVALID_ARG; }
   }
   // nesting check: fine vertices inside the parent's plane and triangle
-  auto bary = [&](int64_t Tc, const double* x, double lam[3]) {
+  // (the coarse triangles' edge vectors and Gram entries computed once each)
+  struct CoarseFrame { double e1[3], e2[3], d11, d12, d22, den, hs; };
+  std::vector<CoarseFrame> frame(c.nt);
+  for (int64_t Tc = 0; Tc < c.nt; ++Tc) {
     const int32_t* ct = &c.tri[3 * Tc];
-    const double *A = &c.xyz[3 * ct[0]], *B = &c.xyz[3 * ct[1]], *C = &c.xyz[3 * ct[2]];
-    double e1[3], e2[3], d[3];
-    sub3(B, A, e1);
-    sub3(C, A, e2);
-    sub3(x, A, d);
-    double d11 = dot3(e1, e1), d12 = dot3(e1, e2), d22 = dot3(e2, e2);
-    double p1 = dot3(d, e1), p2 = dot3(d, e2);
-    double den = d11 * d22 - d12 * d12;
-    double l1 = (d22 * p1 - d12 * p2) / den, l2 = (d11 * p2 - d12 * p1) / den;
+    CoarseFrame& F = frame[Tc];
+    sub3(&c.xyz[3 * ct[1]], &c.xyz[3 * ct[0]], F.e1);
+    sub3(&c.xyz[3 * ct[2]], &c.xyz[3 * ct[0]], F.e2);
+    F.d11 = dot3(F.e1, F.e1);
+    F.d12 = dot3(F.e1, F.e2);
+    F.d22 = dot3(F.e2, F.e2);
+    F.den = F.d11 * F.d22 - F.d12 * F.d12;
+    F.hs = std::sqrt(c.area[Tc]);
+  }
+  auto bary = [&](int64_t Tc, const double* x, double lam[3]) {
+    const CoarseFrame& F = frame[Tc];
+    double d[3];
+    sub3(x, &c.xyz[3 * c.tri[3 * Tc]], d);
+    double p1 = dot3(d, F.e1), p2 = dot3(d, F.e2);
+    double l1 = (F.d22 * p1 - F.d12 * p2) / F.den, l2 = (F.d11 * p2 - F.d12 * p1) / F.den;
     lam[0] = 1.0 - l1 - l2;
     lam[1] = l1;
     lam[2] = l2;
@@ -473,7 +541,7 @@ int build_split(const Topo& f, const Topo& c, const int32_t* parent, const int32
     for (int a = 0; a < 3; ++a) {
       double lam[3];
       double off = bary(parent[T], &f.xyz[3 * f.tri[3 * T + a]], lam);
-      double hs = std::sqrt(c.area[parent[T]]);
+      double hs = frame[parent[T]].hs;
       if (off > 1e-9 * hs || lam[0] < -1e-9 || lam[1] < -1e-9 || lam[2] < -1e-9) {
         err = "fine mesh not nested in the coarse mesh";
         return MSBEM_NONCONFORMING;
@@ -523,7 +591,6 @@ int build_split(const Topo& f, const Topo& c, const int32_t* parent, const int32
   o.p_ptr.assign(f.ndof + 1, 0);
   if (c.ndof == 0) return MSBEM_OK;
   // representative oriented triangle of every fine sector
-  std::vector<int64_t> rep(6 * nt, -1);  // indexed by first_dof-like sector slot per vertex
   std::vector<int64_t> sec_first(nv + 1, 0);
   for (int64_t v = 0; v < nv; ++v) sec_first[v + 1] = sec_first[v] + f.q[v];
   std::vector<int64_t> sec_rep(sec_first[nv], -1);  // (2T+s)*3+a
@@ -534,9 +601,13 @@ int build_split(const Topo& f, const Topo& c, const int32_t* parent, const int32
         int64_t slot = sec_first[v] + f.sector[(2 * T + s) * 3 + a];
         if (sec_rep[slot] < 0) sec_rep[slot] = (2 * T + s) * 3 + a;
       }
-  std::vector<std::vector<std::pair<int32_t, double>>> rows(f.ndof);
+  // rows of P in dof order: the dofs of a vertex are consecutive and the
+  // vertices are visited in increasing order, so each row is appended to the
+  // CSR arrays as soon as it is formed (entries sorted by coarse dof)
   std::vector<double> U;
   std::vector<int32_t> mus;
+  std::vector<std::pair<int32_t, double>> row;
+  int64_t done_dof = 0;   // rows of P written so far
   for (int64_t v = 0; v < nv; ++v) {
     const int qv = f.q[v];
     if (qv < 2) continue;
@@ -569,24 +640,29 @@ int build_split(const Topo& f, const Topo& c, const int32_t* parent, const int32
         }
       }
     }
+    std::vector<double> mean(mus.size(), 0.0);
     for (size_t m = 0; m < mus.size(); ++m) {
-      double mean = 0.0;
-      for (int j = 0; j < qv; ++j) mean += U[m * qv + j];
-      mean /= qv;
-      for (int j = 0; j + 1 < qv; ++j) {
-        double val = U[m * qv + j] - mean;
-        if (std::fabs(val) > 1e-15) rows[f.first_dof[v] + j].push_back({mus[m], val});
+      for (int j = 0; j < qv; ++j) mean[m] += U[m * qv + j];
+      mean[m] /= qv;
+    }
+    for (int j = 0; j + 1 < qv; ++j) {
+      const int64_t d = f.first_dof[v] + j;
+      for (; done_dof < d; ++done_dof) o.p_ptr[done_dof + 1] = o.p_ptr[done_dof];
+      row.clear();
+      for (size_t m = 0; m < mus.size(); ++m) {
+        double val = U[m * qv + j] - mean[m];
+        if (std::fabs(val) > 1e-15) row.push_back({mus[m], val});
       }
+      std::sort(row.begin(), row.end());
+      for (auto& pr : row) {
+        o.p_col.push_back(pr.first);
+        o.p_val.push_back(pr.second);
+      }
+      o.p_ptr[d + 1] = o.p_ptr[d] + (int64_t)row.size();
+      done_dof = d + 1;
     }
   }
-  for (int64_t d = 0; d < f.ndof; ++d) {
-    std::sort(rows[d].begin(), rows[d].end());
-    o.p_ptr[d + 1] = o.p_ptr[d] + (int64_t)rows[d].size();
-    for (auto& pr : rows[d]) {
-      o.p_col.push_back(pr.first);
-      o.p_val.push_back(pr.second);
-    }
-  }
+  for (; done_dof < f.ndof; ++done_dof) o.p_ptr[done_dof + 1] = o.p_ptr[done_dof];
   return MSBEM_OK;
 }
 
