@@ -158,34 +158,54 @@ int build_topology(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt
       // two triangles: the cyclic order is (0, 1) whatever their angle, so the
       // wedges are (0 up, 1 down) and (1 up, 0 down).  The angle of the second
       // about the edge, from the first, only decides whether they overlap
-      // (within 1e-10 of 0 or 2 pi); it can be that close only when its sine
-      // is tiny and its cosine positive, and only then is it computed
-      double u[3];
-      sub3(&o.xyz[3 * vk], &o.xyz[3 * vi], u);
-      const double nu = norm3(u);
-      for (int k = 0; k < 3; ++k) u[k] /= nu;
-      double d[2][3];
+      // (within 1e-10 of 0 or 2 pi).  It can be that close only when its
+      // sine is tiny and its cosine positive; a test on the unnormalised
+      // directions (a bound 1e3 looser) picks those rare edges, and only for
+      // them are the unit directions and the angle formed, as for m > 2.
+      const double* xi = &o.xyz[3 * vi];
+      double e[3];
+      sub3(&o.xyz[3 * vk], xi, e);
+      const double ee = dot3(e, e);
+      double w[2][3];   // third vertex minus its projection on the edge line
       int up2[2];
       for (int j = 0; j < 2; ++j) {
         const int32_t T = edges[e0 + j].T;
         const int32_t* t = &o.tri[3 * T];
         const int32_t r = (t[0] != vi && t[0] != vk) ? t[0] : ((t[1] != vi && t[1] != vk) ? t[1] : t[2]);
-        sub3(&o.xyz[3 * r], &o.xyz[3 * vi], d[j]);
-        const double du = dot3(d[j], u);
-        for (int k = 0; k < 3; ++k) d[j][k] -= du * u[k];
-        const double nd = norm3(d[j]);
-        for (int k = 0; k < 3; ++k) d[j][k] /= nd;
-        double ud[3];
-        cross3(u, d[j], ud);
-        up2[j] = dot3(&o.normal[3 * T], ud) > 0 ? 0 : 1;   // side facing increasing angle
+        double d[3];
+        sub3(&o.xyz[3 * r], xi, d);
+        const double de = dot3(d, e) / ee;
+        for (int k = 0; k < 3; ++k) w[j][k] = d[k] - de * e[k];
+        double ew[3];
+        cross3(e, w[j], ew);
+        // the side facing increasing angle (u x d is a positive multiple of e x w)
+        up2[j] = dot3(&o.normal[3 * T], ew) > 0 ? 0 : 1;
       }
-      double ref2[3];
-      cross3(u, d[0], ref2);
-      const double cs = dot3(d[1], d[0]), sn = dot3(d[1], ref2);
-      if (cs > 0.0 && std::fabs(sn) < 1e-9) {
-        double th = std::atan2(sn, cs);
-        if (th < 0) th += 2.0 * M_PI;
-        if (th < 1e-10 || 2.0 * M_PI - th < 1e-10) { err = "overlapping triangles at an edge"; return MSBEM_NONCONFORMING; }
+      double ew0[3];
+      cross3(e, w[0], ew0);
+      const double c0 = dot3(w[1], w[0]), s0 = dot3(w[1], ew0);
+      if (c0 > 0.0 && s0 * s0 < 1e-12 * ee * dot3(w[0], w[0]) * dot3(w[1], w[1])) {
+        double u[3];
+        const double nu = norm3(e);
+        for (int k = 0; k < 3; ++k) u[k] = e[k] / nu;
+        double d[2][3];
+        for (int j = 0; j < 2; ++j) {
+          const int32_t* t = &o.tri[3 * edges[e0 + j].T];
+          const int32_t r = (t[0] != vi && t[0] != vk) ? t[0] : ((t[1] != vi && t[1] != vk) ? t[1] : t[2]);
+          sub3(&o.xyz[3 * r], xi, d[j]);
+          const double du = dot3(d[j], u);
+          for (int k = 0; k < 3; ++k) d[j][k] -= du * u[k];
+          const double nd = norm3(d[j]);
+          for (int k = 0; k < 3; ++k) d[j][k] /= nd;
+        }
+        double ref2[3];
+        cross3(u, d[0], ref2);
+        const double cs = dot3(d[1], d[0]), sn = dot3(d[1], ref2);
+        if (cs > 0.0 && std::fabs(sn) < 1e-9) {
+          double th = std::atan2(sn, cs);
+          if (th < 0) th += 2.0 * M_PI;
+          if (th < 1e-10 || 2.0 * M_PI - th < 1e-10) { err = "overlapping triangles at an edge"; return MSBEM_NONCONFORMING; }
+        }
       }
       const int32_t T0 = edges[e0].T, T1 = edges[e0 + 1].T;
       for (int32_t v : {vi, vk}) {
