@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library builds and loads, exports every
 symbol include/msbem.h declares, and its host topology (the same code that
 msbem_upload runs) reproduces the oracle's dof numbering bit for bit."""
+import math
 import re
 import os
 
@@ -79,3 +80,21 @@ def test_factor_group_rejects_empty_groups(L):
     geoms = (ctypes.c_void_p * 1)(None)
     assert L.msbem_factor_group(ctypes.cast(geoms, ctypes.c_void_p), 0, None, None) == -1
     assert L.msbem_factor_group(ctypes.cast(geoms, ctypes.c_void_p), 1, None, None) == -1
+
+
+@pytest.mark.parametrize("ang,ok", [(0.0, False), (5e-11, False), (2e-10, True), (1e-8, True), (1e-3, True),
+                                    (math.pi, True), (2 * math.pi - 5e-11, False), (2 * math.pi - 2e-10, True)])
+@pytest.mark.parametrize("scale", [1.0, 3.0])
+def test_two_triangle_fold_threshold(L, ang, ok, scale):
+    # two triangles on one edge, the second turned by `ang` about it: they
+    # overlap (NONCONFORMING) when the angle is within 1e-10 of 0 or 2 pi
+    xyz = np.array([[0.1, 0.2, 0.3], [0.1, 1.7, 0.3], [1.3, 0.9, 0.3],
+                    [0.1 + scale * math.cos(ang), 0.9, 0.3 + scale * math.sin(ang)]])
+    tri = np.array([[0, 1, 2], [0, 1, 3]])
+    if ok:
+        n, v, s = M.msbem_mesh_dofs(xyz, tri)
+        assert n == 0          # an open screen of two triangles has no interior vertex
+    else:
+        with pytest.raises(M.MsbemError) as e:
+            M.msbem_mesh_dofs(xyz, tri)
+        assert e.value.status == -2
