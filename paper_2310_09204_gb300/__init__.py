@@ -206,6 +206,8 @@ def msbem_factor_group(solvers, wire_basket: int = 0, use_coarse: int = 1):
     solvers = list(solvers)
     if not solvers:
         raise ValueError("msbem_factor_group: no solvers")
+    if any(S.ctx is None or S.geom is None for S in solvers):
+        raise ValueError("msbem_factor_group: a Solver is closed or has no geometry")
     geoms = (ctypes.c_void_p * len(solvers))(*[S.geom.value for S in solvers])
     status = np.zeros(len(solvers), np.int32)
     o = PrecondOpts(wire_basket, use_coarse)

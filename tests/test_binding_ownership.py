@@ -115,3 +115,14 @@ def test_share_of_a_sharer_uses_the_owner(fake):
     with pytest.raises(ValueError):
         M.Solver(None, share=group[1])
     assert fake.errors == []
+
+
+def test_factor_group_rejects_closed_solvers(fake):
+    group = _group(2)
+    group[1].close()
+    with pytest.raises(ValueError):
+        M.msbem_factor_group(group)
+    with pytest.raises(ValueError):
+        M.msbem_factor_group([])
+    group[0].close()
+    assert fake.errors == []
