@@ -315,15 +315,18 @@ int msbem_last_timings(const msbem_geom* g, double t[5]);
  * The method is the same blocked Gauss-Jordan recursion msbem_factor uses
  * (32-wide panels, rank-32 updates in double-float).  Its scratch -- about
  * 1 MiB: the pivot block, two n x 32 panels, index words and the breakdown
- * flag -- is one file-scope device array that every GPU loading the library
- * holds until exit.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  Every call shares the array and clears what must
- * start at zero, so calls that overlap on the GPU (on different streams or
- * from different threads) race and must not be issued.  The call copies a few
- * index words from the host and waits for the stream to read the breakdown
- * flag.  Returns BREAKDOWN if a pivot is not positive, CUDA_ERROR on a CUDA
- * failure. */
+ * flag -- is one file-scope device array.  It exists on a GPU once the
+ * library's device code is loaded there and stays until the process exits.
+ * Each call looks up that array's device address (cudaGetSymbolAddress) on the
+ * current device, so A, Ainv and the stream must belong to the current device.
+ * Every call shares the array and clears what must start at zero, so calls
+ * that overlap on the GPU (on different streams or from different threads)
+ * race and must not be issued.  The call copies a few index words from
+ * pageable host memory and waits for the stream to read the breakdown flag,
+ * so it cannot be called while the stream (or, for the legacy stream, any
+ * stream) is being captured: it then returns INVALID_ARG (or CUDA_ERROR)
+ * without doing any work.  Returns BREAKDOWN if a pivot is not positive (Ainv
+ * then holds no inverse), CUDA_ERROR on a CUDA failure. */
 int msbem_spd_inverse_noalloc(const double* A, int64_t n, double* Ainv, void* cuda_stream);
 
 /* Counters of this geometry: *launches = number of CUDA kernels the library

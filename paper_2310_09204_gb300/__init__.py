@@ -193,10 +193,35 @@ NOALLOC_MAX_N = 2048
 
 
 def msbem_spd_inverse_noalloc(A, Ainv, stream: int = 0) -> int:
-    """Inverse of an SPD matrix (device tensors, n x n FP64) without any
-    device allocation; returns the C status (0 on success)."""
+    """Inverse of an SPD matrix without any device allocation; returns the C
+    status (0 on success, MSBEM_BREAKDOWN for a non-positive pivot).
+
+    A and Ainv are CUDA tensors of shape (n, n), float64, contiguous, on one
+    device (Ainv may be A itself: in place); stream is a raw cudaStream_t of
+    that device (0: the legacy default stream).  Anything else raises
+    ValueError before the library is called, since the C side only sees raw
+    pointers and would read or write past a smaller or differently laid out
+    tensor.  The call runs with A's device current, so the library uses that
+    device's scratch array."""
+    import torch
+    for name, t in (("A", A), ("Ainv", Ainv)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"msbem_spd_inverse_noalloc: {name} must be a CUDA tensor")
+        if t.dtype != torch.float64:
+            raise ValueError(f"msbem_spd_inverse_noalloc: {name} must be float64, got {t.dtype}")
+        if t.dim() != 2 or t.shape[0] != t.shape[1]:
+            raise ValueError(f"msbem_spd_inverse_noalloc: {name} must be square, got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"msbem_spd_inverse_noalloc: {name} must be contiguous")
+    if A.shape != Ainv.shape:
+        raise ValueError(f"msbem_spd_inverse_noalloc: shapes differ: {tuple(A.shape)} and {tuple(Ainv.shape)}")
+    if A.device != Ainv.device:
+        raise ValueError(f"msbem_spd_inverse_noalloc: tensors on {A.device} and {Ainv.device}")
     n = int(A.shape[0])
-    return lib().msbem_spd_inverse_noalloc(_ptr(A), n, _ptr(Ainv), stream)
+    if not 1 <= n <= NOALLOC_MAX_N:
+        raise ValueError(f"msbem_spd_inverse_noalloc: order {n} outside 1..{NOALLOC_MAX_N}")
+    with torch.cuda.device(A.device):
+        return lib().msbem_spd_inverse_noalloc(_ptr(A), n, _ptr(Ainv), stream)
 
 
 def msbem_factor_group(solvers, wire_basket: int = 0, use_coarse: int = 1):

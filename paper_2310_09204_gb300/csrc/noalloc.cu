@@ -9,10 +9,9 @@
 // the device and may fail under memory pressure.  This entry point therefore
 // takes its scratch -- the pivot block and the two panels of the blocked
 // Gauss-Jordan recursion, a few index words and the breakdown flag -- from one
-// file-scope device array of fixed size.  Every GPU that loads the library holds
-// that array until the process exits.
-#include <mutex>
-
+// file-scope device array of fixed size.  The array exists on a GPU once the
+// library's device code is loaded there (at the first use of the library on that
+// GPU, under lazy module loading) and stays until the process exits.
 #include "msbem_internal.h"
 
 // Bytes the largest admissible matrix needs (see bgj_scratch_bytes in factor.cu):
@@ -26,22 +25,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
-std::mutex g_mu;
-constexpr int kMaxDevices = 64;
-unsigned char* g_addr[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on `device` (the current device), looked
-// up once per device.
-cudaError_t scratch_address(int device, unsigned char** out) {
-  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[device] = (unsigned char*)p;
-  }
-  *out = g_addr[device];
+// Device address of g_noalloc_scratch on the current device.  It is looked up
+// on every call (a cheap query): a cached address would go stale when the
+// caller resets the device and the module is loaded again.
+cudaError_t scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = (unsigned char*)p;
   return cudaSuccess;
 }
 
@@ -49,11 +40,14 @@ cudaError_t scratch_address(int device, unsigned char** out) {
 
 extern "C" int msbem_spd_inverse_noalloc(const double* A, int64_t n, double* Ainv, void* cuda_stream) {
   if (!A || !Ainv || n < 1 || n > MSBEM_NOALLOC_MAX_N) return MSBEM_INVALID_ARG;
-  int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess) return MSBEM_CUDA_ERROR;
-  unsigned char* scratch = nullptr;
-  if (scratch_address(device, &scratch) != cudaSuccess) return MSBEM_CUDA_ERROR;
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the call copies index words from pageable host memory and waits on the
+  // stream for the breakdown flag, neither of which a stream capture allows
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return MSBEM_CUDA_ERROR;
+  if (cap != cudaStreamCaptureStatusNone) return MSBEM_INVALID_ARG;
+  unsigned char* scratch = nullptr;
+  if (scratch_address(&scratch) != cudaSuccess) return MSBEM_CUDA_ERROR;
   if (A != Ainv &&
       cudaMemcpyAsync(Ainv, A, sizeof(double) * (size_t)n * (size_t)n, cudaMemcpyDeviceToDevice, s) !=
           cudaSuccess)

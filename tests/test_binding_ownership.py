@@ -126,3 +126,20 @@ def test_factor_group_rejects_closed_solvers(fake):
         M.msbem_factor_group([])
     group[0].close()
     assert fake.errors == []
+
+
+def test_noalloc_binding_rejects_host_and_mistyped_tensors(monkeypatch):
+    """msbem_spd_inverse_noalloc's binding refuses what raw pointers cannot
+    describe (host memory, wrong dtype or shape) before reaching the library:
+    a library call would fail this test."""
+    import torch
+
+    class NoCall:
+        def __getattr__(self, name):
+            raise AssertionError(f"library called: {name}")
+
+    monkeypatch.setattr(M, "_lib", NoCall())
+    eye = torch.eye(4, dtype=torch.float64)
+    for A, Ainv in ((eye, eye), (eye.float(), eye), (torch.zeros(4, 3, dtype=torch.float64),) * 2):
+        with pytest.raises(ValueError):
+            M.msbem_spd_inverse_noalloc(A, Ainv)
