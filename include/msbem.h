@@ -336,6 +336,29 @@ int msbem_spd_inverse_noalloc(const double* A, int64_t n, double* Ainv, void* cu
 int msbem_counters(const msbem_geom* g, int64_t* launches, int64_t* far_pairs);
 
 /* ------------------------------------------------------------------------
+ * Test hooks of the error paths (no counterpart in the paper).  They let the
+ * tests drive the library's failure handling without a GPU fault: an
+ * allocation that fails on the host side, and a bounded device-side wait that
+ * runs out.  Process-wide; not for production use.
+ * ------------------------------------------------------------------------ */
+
+/* The (after + 1)-th device allocation the library makes from its memory
+ * pools from now on fails as if the device were out of memory, once (the
+ * hook then turns itself off); after = -1 turns a pending failure off.  The
+ * failing call returns OOM and leaves its object as a failed call would
+ * (e.g. a geometry neither assembled nor factored).  INVALID_ARG for after < -1. */
+int msbem_test_fail_alloc(int64_t after);
+
+/* ns > 0: on the current device, every CTA of the matrix-vector product
+ * kernels (CUDA-core and tensor-core) first waits up to ns nanoseconds on a
+ * device flag that nothing sets, then takes the path of a copy that never
+ * completed: it lets its copies in flight land (bounded waits), frees what it
+ * holds, sets the error flag and returns.  The calls whose products ran then
+ * return DEVICE_TIMEOUT and the context stays usable.  ns = 0 turns it off.
+ * Synchronizes the device.  INVALID_ARG for ns < 0. */
+int msbem_test_expire_waits(int64_t ns);
+
+/* ------------------------------------------------------------------------
  * Serving engine (no counterpart in the paper: it serves many solves of the
  * paper's problem).  Geometries (mesh + partition) are registered under a
  * key; solve requests (key, g) are queued, and msbem_server_progress admits

@@ -105,6 +105,8 @@ def lib():
                                  ctypes.POINTER(i32)], i32),
         "msbem_server_stats_get": ([P, ctypes.POINTER(ServerStats)], i32),
         "msbem_mesh_dofs": ([P, i64, P, i64, ctypes.POINTER(i64), P, P, i64, ctypes.c_char_p, i32], i32),
+        "msbem_test_fail_alloc": ([i64], i32),
+        "msbem_test_expire_waits": ([i64], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -222,6 +224,18 @@ def msbem_spd_inverse_noalloc(A, Ainv, stream: int = 0) -> int:
         raise ValueError(f"msbem_spd_inverse_noalloc: order {n} outside 1..{NOALLOC_MAX_N}")
     with torch.cuda.device(A.device):
         return lib().msbem_spd_inverse_noalloc(_ptr(A), n, _ptr(Ainv), stream)
+
+
+def msbem_test_fail_alloc(after: int) -> int:
+    """Test hook: the (after + 1)-th device allocation of the library from now
+    fails as if out of memory, once (-1: off).  Returns the C status."""
+    return lib().msbem_test_fail_alloc(int(after))
+
+
+def msbem_test_expire_waits(ns: int) -> int:
+    """Test hook: the product kernels' bounded waits run out after ns
+    nanoseconds on a flag nothing sets (0: off; current device)."""
+    return lib().msbem_test_expire_waits(int(ns))
 
 
 def msbem_factor_group(solvers, wire_basket: int = 0, use_coarse: int = 1):

@@ -1,6 +1,7 @@
 // C ABI of the msbem library (include/msbem.h): context and geometry handles,
 // host topology at upload, orchestration of the device kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -889,4 +890,36 @@ int msbem_last_timings(const msbem_geom* g, double t[5]) {
   return MSBEM_OK;
 }
 
+
+// ---- test hooks of the error paths ------------------------------------------
+// (after + 1)-th pool allocation from now fails, once; -1: off
+static std::atomic<long long> g_alloc_countdown{-1};
+
+int msbem_test_fail_alloc(int64_t after) {
+  if (after < -1) return MSBEM_INVALID_ARG;
+  g_alloc_countdown.store(after);
+  return MSBEM_OK;
+}
+
+int msbem_test_expire_waits(int64_t ns) {
+  if (ns < 0) return MSBEM_INVALID_ARG;
+  cudaError_t e = set_matvec_expire_ns((long long)ns);
+  if (e == cudaSuccess) e = set_matvec_tc_expire_ns((long long)ns);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? MSBEM_OK : MSBEM_CUDA_ERROR;
+}
+
 }  // extern "C"
+
+namespace msbem {
+
+bool test_alloc_fails() {
+  long long v = g_alloc_countdown.load(std::memory_order_relaxed);
+  while (v >= 0) {
+    // v == 0: this allocation fails and the hook turns itself off
+    if (g_alloc_countdown.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
+
+}  // namespace msbem

@@ -83,6 +83,22 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Test hook of the error path (msbem_test_expire_waits): when non-zero, every
+// product CTA first waits up to this many nanoseconds for g_mv_never, a flag
+// that nothing sets, and on expiry takes the path of a copy that never
+// completed.  Zero in normal use: one global load per CTA.
+__device__ long long g_mv_expire_ns = 0;
+__device__ int g_mv_never = 0;
+
+__device__ __noinline__ bool mv_wait_never(long long limit_ns) {
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < (1 << 24); ++it) {
+    if (*(volatile int*)&g_mv_never) return true;
+    if (global_ns() - t0 > (uint64_t)limit_ns) return false;
+  }
+  return false;
+}
+
 // wait for the given phase parity; false after ~2 s or 2^24 polls
 __device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -168,7 +184,13 @@ __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ 
   for (int i = 0; i < (MODE == 0 ? V : 1); ++i) l[i] = 0.f;
 
   int failed_at = -1;
-  for (int t = 0; t < nchunks; ++t) {
+  const long long expire = g_mv_expire_ns;
+  if (expire > 0) {
+    bool got = true;
+    if (tid == 0) got = mv_wait_never(expire);
+    if (__syncthreads_or(!got)) failed_at = 0;
+  }
+  for (int t = 0; failed_at < 0 && t < nchunks; ++t) {
     const int s = t % ST;
     const bool got = mbar_wait_bounded(&bar[s], (uint32_t)((t / ST) & 1));
     // every thread has finished chunk t-1 once past this barrier
@@ -215,9 +237,12 @@ __global__ void __launch_bounds__(256, 2) matvec_kernel(const __grid_constant__ 
     }
   }
   if (failed_at >= 0) {
-    // drain the copies still in flight (chunks failed_at .. failed_at+ST-2)
+    // drain the copies still in flight: chunks 0 .. ST-1 when nothing was
+    // consumed yet, else failed_at .. failed_at+ST-2 (chunk failed_at-1+ST is
+    // issued only after chunk failed_at has landed)
     if (tid == 0) {
-      for (int u = failed_at; u < nchunks && u <= failed_at + ST - 2; ++u)
+      const int last = failed_at == 0 ? ST - 1 : failed_at + ST - 2;
+      for (int u = failed_at; u < nchunks && u <= last; ++u)
         mbar_wait_bounded(&bar[u % ST], (uint32_t)((u / ST) & 1));
       atomicExch(err, 1);
     }
@@ -515,6 +540,10 @@ static cudaError_t launch_mode(const CUtensorMap& tmW, const CUtensorMap& tmP, i
     case 8: return launch_cfg<MODE, 8>(tmW, tmP, N, kb, split, P, Q, part, scr, stop, err, s);
     default: return launch_cfg<MODE, 16>(tmW, tmP, N, kb, split, P, Q, part, scr, stop, err, s);
   }
+}
+
+cudaError_t set_matvec_expire_ns(long long ns) {
+  return cudaMemcpyToSymbol(g_mv_expire_ns, &ns, sizeof(ns));
 }
 
 cudaError_t launch_matvec(int mode, const CUtensorMap& tmW, const CUtensorMap& tmP, int64_t N, int kb,

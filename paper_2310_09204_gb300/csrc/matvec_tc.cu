@@ -103,6 +103,22 @@ __device__ __noinline__ bool tc_wait(uint64_t* bar, uint32_t parity, const volat
   }
   return false;
 }
+// Test hook of the error path (msbem_test_expire_waits): when non-zero, the
+// producer of every CTA first waits up to this many nanoseconds for
+// g_tc_never, a flag that nothing sets, and on expiry gives up before its first
+// copy, as if a copy had never completed.  Zero in normal use.
+__device__ long long g_tc_expire_ns = 0;
+__device__ int g_tc_never = 0;
+
+__device__ __noinline__ bool tc_wait_never(long long limit_ns) {
+  const uint64_t t0 = tc_ns();
+  for (int it = 0; it < (1 << 24); ++it) {
+    if (*(volatile int*)&g_tc_never) return true;
+    if (tc_ns() - t0 > (uint64_t)limit_ns) return false;
+  }
+  return false;
+}
+
 // shared-memory matrix descriptor: K-major, 128-byte rows under the 128-byte
 // swizzle (layout 2), 8-row groups group_stride bytes apart
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t group_stride) {
@@ -299,7 +315,9 @@ __global__ void __launch_bounds__(192, 1) tc_matvec_kernel(const __grid_constant
   if (warp == 5) {
     // ---- producer: the copies of chunk t once the MMAs of chunk t - ST are done
     if (lane == 0) {
-      for (int t = 0; t < nchunks; ++t) {
+      const long long expire = g_tc_expire_ns;
+      if (expire > 0 && !tc_wait_never(expire)) *s_fail = 1;
+      for (int t = 0; *s_fail == 0 && t < nchunks; ++t) {
         const int st = t % ST;
         if (t >= ST && !tc_wait(&empty[st], (uint32_t)((t / ST - 1) & 1), s_fail)) {
           *s_fail = 1;
@@ -473,6 +491,10 @@ __global__ void __launch_bounds__(256) tc_combine_kernel(const double* __restric
 }
 
 // ---- host side ------------------------------------------------------------------
+cudaError_t set_matvec_tc_expire_ns(long long ns) {
+  return cudaMemcpyToSymbol(g_tc_expire_ns, &ns, sizeof(ns));
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

@@ -86,7 +86,11 @@ void six_point_rule(double bary[6][3], double w[6]);
 // ---------------------------------------------------------------------------
 // Stream-ordered allocation from the context's pool (which keeps freed memory
 // for reuse, so repeated uploads of similar geometries do not remap HBM).
+// Test hook (msbem_test_fail_alloc, api.cu): true when the injected failure
+// is due, which makes this allocation fail as if the device were out of memory.
+bool test_alloc_fails();
 inline cudaError_t pool_alloc(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t s) {
+  if (test_alloc_fails()) return cudaErrorMemoryAllocation;
   return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
 }
 
@@ -201,6 +205,9 @@ unsigned matvec_blocks(int64_t N, int mode);
 int matvec_pad(int kb);      // box rows of tmP for kb vectors (1, 2, 4, 8 or 16)
 int matvec_rows(int mode);   // box rows of tmW (16 double-float, 32 FP32)
 cudaError_t matvec_init();   // per device, before the first launch_matvec
+// test hooks of the bounded waits (current device): 0 off
+cudaError_t set_matvec_expire_ns(long long ns);
+cudaError_t set_matvec_tc_expire_ns(long long ns);
 // split > 1 divides the columns among split CTAs per row block (scratch of
 // matvec_scratch_bytes; a second kernel adds the partials in split order).
 cudaError_t launch_matvec(int mode, const CUtensorMap& tmW, const CUtensorMap& tmP, int64_t N, int kb,

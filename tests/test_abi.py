@@ -98,3 +98,11 @@ def test_two_triangle_fold_threshold(L, ang, ok, scale):
         with pytest.raises(M.MsbemError) as e:
             M.msbem_mesh_dofs(xyz, tri)
         assert e.value.status == -2
+
+
+def test_test_hooks_check_their_arguments():
+    """The error-path test hooks reject bad arguments before any CUDA call."""
+    M.lib()
+    assert M.msbem_test_fail_alloc(-2) == -1
+    assert M.msbem_test_fail_alloc(-1) == 0          # off: nothing pending
+    assert M.msbem_test_expire_waits(-1) == -1
