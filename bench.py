@@ -717,22 +717,25 @@ def _c5_geometry(spec):
     return WL.panels(a)
 
 
-def serving_workload_c5(R: int = 2000, seed: int = 0, new_fraction: float = 0.3):
+def serving_workload_c5(R: int = 2000, seed: int = 0, new_fraction: float = 0.3, small: bool = False):
     """The serving configuration's stream: R requests; with probability
     new_fraction (always for the first) a new geometry, drawn evenly from the
     square, cube and panel families, else one used before; g in [-1,1]^3.
-    Geometries are generated in a pool of processes (spawned)."""
+    small: the three smallest squares and two smallest cubes only (a warm-up
+    stream).  Geometries are generated in a pool of processes (spawned)."""
     import multiprocessing as mp
     rng = np.random.default_rng(seed)
+    squares = C5_SQUARES[:3] if small else C5_SQUARES
+    cubes = C5_CUBES[:2] if small else C5_CUBES
     specs, reqs = [], []
     for i in range(R):
         if i == 0 or rng.random() < new_fraction:
-            f = int(rng.integers(3))
+            f = int(rng.integers(2 if small else 3))
             if f == 0:
-                n, nc = C5_SQUARES[int(rng.integers(len(C5_SQUARES)))]
+                n, nc = squares[int(rng.integers(len(squares)))]
                 specs.append(("square", n, nc))
             elif f == 1:
-                n, nc = C5_CUBES[int(rng.integers(len(C5_CUBES)))]
+                n, nc = cubes[int(rng.integers(len(cubes)))]
                 specs.append(("cube", n, nc))
             else:
                 specs.append(("panels", 5000 + len(specs), 0))

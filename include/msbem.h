@@ -213,6 +213,13 @@ typedef struct msbem_solve_opts {
                       /*    by a power of two per row (each entry to 2^-11 of  */
                       /*    itself; N*N*2 more bytes)                          */
   double inner_rtol;  /* precision 2, 4, 5: inner tolerance (<= 0: 1e-4)       */
+  double density_tol; /* precision 2, 4, 5: when > 0, a result also needs its  */
+                      /*   estimated relative error (l2) <= density_tol: with  */
+                      /*   the refinement's corrections D_k and their          */
+                      /*   contraction eta = ||D_k|| / ||D_k-1||, the error of */
+                      /*   X_k+1 is estimated as eta/(1-eta) ||D_k|| / ||X_k+1||*/
+                      /*   (so at least two refinement steps); 0: residual     */
+                      /*   test alone (default); must be < 1                   */
 } msbem_solve_opts;
 
 /* Solve W Phi = L for constant Neumann data g by PCG from Phi_0 = 0
@@ -381,12 +388,23 @@ typedef struct msbem_server_opts {
   int chunk;                /* PCG iterations between scheduling points (0: 4)         */
   int admission_threads;    /* host threads admitting new geometries, each with its   */
                             /* own context and stream (0: 4; at most 8)                */
+  double density_tol;       /* mixed precisions: as msbem_solve_opts.density_tol (0:   */
+                            /* residual test alone)                                     */
 } msbem_server_opts;
 
 typedef struct msbem_server_stats {
   int64_t submitted, completed, admissions, evictions;
   double resident_bytes;
   int resident_geometries;
+  /* work of the admissions finished so far (CUDA events inside each call, on
+   * the stream the kernels ran on): far-field kernel time and its unit count
+   * (unordered triangle pairs sharing no vertex), whole assemblies and
+   * preconditioner set-ups; kernels launched for all geometries, resident or
+   * evicted */
+  double far_ms;
+  int64_t far_pairs;
+  double assemble_ms, factor_ms;
+  int64_t launches;
 } msbem_server_stats;
 
 /* Create an engine on ctx (opts may be NULL).  Errors: INVALID_ARG, CUDA_ERROR. */

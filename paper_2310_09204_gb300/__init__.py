@@ -41,19 +41,21 @@ class PrecondOpts(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int),
-                ("precondition", ctypes.c_int), ("precision", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
+                ("precondition", ctypes.c_int), ("precision", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("density_tol", ctypes.c_double)]
 
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("precision", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("inner_rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("chunk", ctypes.c_int),
-                ("admission_threads", ctypes.c_int)]
+                ("admission_threads", ctypes.c_int), ("density_tol", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("admissions", ctypes.c_int64),
                 ("evictions", ctypes.c_int64), ("resident_bytes", ctypes.c_double),
-                ("resident_geometries", ctypes.c_int)]
+                ("resident_geometries", ctypes.c_int), ("far_ms", ctypes.c_double), ("far_pairs", ctypes.c_int64),
+                ("assemble_ms", ctypes.c_double), ("factor_ms", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
 #: arithmetic of the solve's matrix-vector products (msbem_solve_opts.precision)
@@ -420,8 +422,10 @@ class Solver:
 
     def solve_batch(self, G, rtol: float = 1e-8, maxit: int = 1000, fixed: bool = False,
                     precondition: bool = True, out=None, raise_on_status=True, precision="df",
-                    inner_rtol: float = 0.0):
-        """k solves sharing the matrix-vector products; G is k x 3."""
+                    inner_rtol: float = 0.0, density_tol: float = 0.0):
+        """k solves sharing the matrix-vector products; G is k x 3.
+        density_tol (mixed precisions): also stop only when the refinement's
+        estimated relative error is below it (0: residual test alone)."""
         G = np.ascontiguousarray(G, np.float64).reshape(-1, 3)
         k = G.shape[0]
         if out is None:
@@ -429,7 +433,7 @@ class Solver:
         iters = np.zeros(k, np.int32)
         rel = np.zeros(k, np.float64)
         kap = np.zeros(k, np.float64)
-        o = SolveOpts(rtol, maxit, int(fixed), int(precondition), PRECISION[precision], inner_rtol)
+        o = SolveOpts(rtol, maxit, int(fixed), int(precondition), PRECISION[precision], inner_rtol, density_tol)
         st = lib().msbem_solve_batch(self.geom, _ptr(G), k, ctypes.byref(o), _ptr(out), _ptr(iters),
                                      _ptr(rel), _ptr(kap))
         if raise_on_status:
@@ -438,7 +442,7 @@ class Solver:
 
     def solve(self, g, rtol: float = 1e-8, maxit: int = 1000, fixed: bool = False,
               precondition: bool = True, out=None, hist_cap: int = 4096, raise_on_status=True,
-              precision="df", inner_rtol: float = 0.0):
+              precision="df", inner_rtol: float = 0.0, density_tol: float = 0.0):
         """One solve.  precision: "df" (double-float products, default), "fp64"
         (the plain FP64 comparator) or "mixed" (FP32 inner PCG inside
         double-float iterative refinement; hist then holds the true relative
@@ -449,7 +453,7 @@ class Solver:
         it = ctypes.c_int()
         kap = ctypes.c_double()
         hist = np.full(hist_cap, np.nan)
-        o = SolveOpts(rtol, maxit, int(fixed), int(precondition), PRECISION[precision], inner_rtol)
+        o = SolveOpts(rtol, maxit, int(fixed), int(precondition), PRECISION[precision], inner_rtol, density_tol)
         st = lib().msbem_solve(self.geom, _ptr(gv), ctypes.byref(o), _ptr(out), ctypes.byref(it),
                                _ptr(hist), hist_cap, ctypes.byref(kap))
         if raise_on_status:
@@ -467,9 +471,10 @@ class Server:
 
     def __init__(self, device: int = 0, stream=None, precision="mixed", rtol: float = 1e-8,
                  inner_rtol: float = 0.0, hbm_budget: float = 0.0, maxit: int = 1000, chunk: int = 4,
-                 admission_threads: int = 0):
+                 admission_threads: int = 0, density_tol: float = 0.0):
         self.ctx = msbem_create(device, stream)
-        o = ServerOpts(float(hbm_budget), PRECISION[precision], rtol, inner_rtol, maxit, chunk, admission_threads)
+        o = ServerOpts(float(hbm_budget), PRECISION[precision], rtol, inner_rtol, maxit, chunk, admission_threads,
+                       density_tol)
         h = ctypes.c_void_p()
         st = lib().msbem_server_create(self.ctx, ctypes.byref(o), ctypes.byref(h))
         if st:
@@ -478,7 +483,10 @@ class Server:
         self.h = h.value
         self.ndof = {}
 
-    def add_geometry(self, key: int, geom) -> None:
+    def add_geometry(self, key: int, geom, ndof: int | None = None) -> None:
+        """Register a geometry (host copies; nothing goes to the device until a
+        request for it is admitted).  ndof: its dof count when the caller knows
+        it already (else computed here from the mesh)."""
         xyz = np.ascontiguousarray(geom.xyz, np.float64)
         tri = np.ascontiguousarray(geom.tri, np.int32)
         cxyz = np.ascontiguousarray(geom.coarse_xyz, np.float64)
@@ -488,7 +496,7 @@ class Server:
         _check(self.ctx, lib().msbem_server_add_geometry(self.h, key, _ptr(xyz), len(xyz), _ptr(tri), len(tri),
                                                          _ptr(cxyz), len(cxyz), _ptr(ctri), len(ctri),
                                                          _ptr(par), _ptr(pat)))
-        self.ndof[key] = msbem_mesh_dofs(xyz, tri)[0]
+        self.ndof[key] = int(ndof) if ndof is not None else msbem_mesh_dofs(xyz, tri)[0]
 
     def footprint(self, key: int) -> float:
         """Bytes the admission of geometry `key` asks of the HBM budget."""

@@ -711,6 +711,8 @@ int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts,
   int prec = opts ? opts->precondition : 1;
   const int precision = opts ? opts->precision : 0;
   const double inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-4;
+  const double dtol = opts ? opts->density_tol : 0.0;
+  if (!(dtol >= 0.0 && dtol < 1.0)) return fail(c, MSBEM_INVALID_ARG, "density_tol must be in [0, 1)");
   if (!(rtol >= 0.0) || maxit < 1) return fail(c, MSBEM_INVALID_ARG, "rtol >= 0 and maxit >= 1 required");
   if (precision < 0 || precision > 5) return fail(c, MSBEM_INVALID_ARG, "precision must be 0 .. 5");
   if ((precision == 2 || precision >= 4) && (fixed || !(inner < 1.0)))
@@ -726,7 +728,7 @@ int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts,
   if (precision == 2 || precision >= 4) {
     std::vector<PcgOut> outs;
     e = run_ir_batch(d, gv, 1, rtol, maxit, inner, prec, d.d_vec, true, outs, nullptr, c->stream, precision >= 4,
-                     precision == 5);
+                     precision == 5, dtol);
     if (e == cudaSuccess) po = outs[0];
   } else if (precision == 3) {
     std::vector<PcgOut> outs;
@@ -773,6 +775,8 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
   int prec = opts ? opts->precondition : 1;
   const int precision = opts ? opts->precision : 0;
   const double inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-4;
+  const double dtol = opts ? opts->density_tol : 0.0;
+  if (!(dtol >= 0.0 && dtol < 1.0)) return fail(c, MSBEM_INVALID_ARG, "density_tol must be in [0, 1)");
   if (!(rtol >= 0.0) || maxit < 1) return fail(c, MSBEM_INVALID_ARG, "rtol >= 0 and maxit >= 1 required");
   if (precision < 0 || precision > 5) return fail(c, MSBEM_INVALID_ARG, "precision must be 0 .. 5");
   if ((precision == 2 || precision >= 4) && (fixed || !(inner < 1.0)))
@@ -797,7 +801,7 @@ int msbem_solve_batch(msbem_geom* g, const double* gvecs, int k, const msbem_sol
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     } else if (precision == 2 || precision >= 4) {
       e = run_ir_batch(d, gvecs + 3 * c0, kb, rtol, maxit, inner, prec, density + (size_t)c0 * N, dev_out,
-                       outs, nullptr, c->stream, precision >= 4, precision == 5);
+                       outs, nullptr, c->stream, precision >= 4, precision == 5, dtol);
     } else {
       e = run_pcg_batch(d, gvecs + 3 * c0, kb, rtol, maxit, fixed, prec, density + (size_t)c0 * N, dev_out,
                         outs, c->stream, precision == 3);

@@ -261,6 +261,7 @@ cudaError_t bgj_invert_single(double* A, int64_t n, unsigned char* scratch, size
 struct PcgOut {
   int iters = 0;
   int status = 0;
+  double err_est = 0.0;   // refinement with a density test: estimated relative error of the result
   std::vector<double> hist, alpha, beta;
 };
 // precision: 0 double-float matrix products (default), 1 the plain FP64
@@ -285,7 +286,8 @@ cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, 
 // (pcg_batch.cu); *refinements receives the number of refinement steps
 cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, double inner_rtol,
                          int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
-                         int* refinements, cudaStream_t s, int tensor = 0, int inner_fp16 = 0);
+                         int* refinements, cudaStream_t s, int tensor = 0, int inner_fp16 = 0,
+                         double density_tol = 0.0);
 
 // double-layer potential at M targets (device arrays) from the jump values
 // J[T][a] (host, 3 per triangle); refine: 4^refine sub-triangles (potential.cu)

@@ -654,7 +654,7 @@ cudaError_t run_pcg_batch(DevGeom& g, const double* gvecs, int kb, double rtol, 
 // of the first inner solve.
 cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, int maxit, double inner_rtol,
                          int precondition, double* X_out, bool out_on_device, std::vector<PcgOut>& outs,
-                         int* refinements, cudaStream_t s, int tensor, int inner_fp16) {
+                         int* refinements, cudaStream_t s, int tensor, int inner_fp16, double density_tol) {
   const int64_t N = g.ndof;
   outs.assign(kb, PcgOut());
   if (refinements) *refinements = 0;
@@ -670,7 +670,7 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
   const size_t nparts = (size_t)kb * std::max<unsigned>(gemv_blocks, BRED);
   const int split = tensor ? 1 : matvec_split_of(g, 0);
   const size_t scr_bytes = tensor ? tc_work_bytes(g) : matvec_scratch_bytes(N, kb, split);
-  const size_t bytes = sizeof(double) * (5 * nvec + nparts + 3 * kb + 2 * kb) + sizeof(float) * 2 * kb * g.ldw +
+  const size_t bytes = sizeof(double) * (5 * nvec + nparts + 3 * kb + 4 * kb) + sizeof(float) * 2 * kb * g.ldw +
                        sizeof(int) * kb + sizeof(BatchState) + scr_bytes + 256;
   char* base = nullptr;
   if ((e = pool_alloc((void**)&base, bytes, g.pool, s)) != cudaSuccess) return e;
@@ -682,7 +682,7 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
   double* Q = cv.take<double>(nvec);
   double* part = cv.take<double>(nparts);
   double* gv = cv.take<double>(3 * kb);
-  double* nrm = cv.take<double>(2 * kb);
+  double* nrm = cv.take<double>(4 * kb);     // ||L||^2, ||R||^2, ||D||^2, ||X||^2 per column
   float* Xf = cv.take<float>(2 * kb * g.ldw);
   int* skip = cv.take<int>(kb);
   BatchState* fl = cv.take<BatchState>(1);   // all_done = 0 throughout; err from the product
@@ -704,7 +704,7 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
   bdot_kernel<<<rgrid, 256, 0, s>>>(L, L, N, kb, part, fl);
   bsum_kernel<<<kb, 256, 0, s>>>(part, BRED, nrm);
   g.launches += 2;
-  std::vector<double> h_nrm(2 * kb);
+  std::vector<double> h_nrm(4 * kb, 0.0), dprev(kb, 0.0);
   std::vector<int> h_skip(kb, 0), inner_total(kb, 0), st(kb, MSBEM_OK);
   std::vector<char> conv(kb, 0);
   const int max_outer = 12;
@@ -713,14 +713,27 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
     bdot_kernel<<<rgrid, 256, 0, s>>>(R, R, N, kb, part, fl);
     bsum_kernel<<<kb, 256, 0, s>>>(part, BRED, nrm + kb);
     g.launches += 2;
-    cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * 2 * kb, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * 4 * kb, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return finish(e);
     bool all = true;
     for (int c = 0; c < kb; ++c) {
       const double nl = h_nrm[c];
       const double rel = nl > 0.0 ? std::sqrt(h_nrm[kb + c] / nl) : 0.0;
       if (!conv[c]) outs[c].hist.push_back(rel);
-      if (!conv[c] && (nl == 0.0 || rel <= rtol)) conv[c] = 1;
+      // density test (density_tol > 0): the error of X_{k+1} = X_k + D_k is
+      // estimated from the contraction eta of consecutive corrections,
+      // eta = ||D_k|| / ||D_{k-1}||, as eta / (1 - eta) ||D_k|| (the error of
+      // X_k is at most ||D_k|| / (1 - eta), and the next one eta times that)
+      bool dens = density_tol <= 0.0;
+      if (!conv[c] && !dens && outer >= 2) {
+        const double dn = std::sqrt(h_nrm[2 * kb + c]), xn = std::sqrt(h_nrm[3 * kb + c]);
+        const double eta = dprev[c] > 0.0 ? dn / dprev[c] : 1.0;
+        const double est = eta < 1.0 ? eta / (1.0 - eta) * dn : INFINITY;
+        outs[c].err_est = xn > 0.0 ? est / xn : 0.0;
+        dens = est <= density_tol * xn;
+      }
+      if (!conv[c] && outer >= 1) dprev[c] = std::sqrt(h_nrm[2 * kb + c]);
+      if (!conv[c] && (nl == 0.0 || (rel <= rtol && dens))) conv[c] = 1;
       if (!std::isfinite(rel)) { conv[c] = 1; st[c] = MSBEM_BREAKDOWN; }
       all = all && conv[c];
     }
@@ -751,6 +764,13 @@ cudaError_t run_ir_batch(DevGeom& g, const double* gvecs, int kb, double rtol, i
       if (in[c].status == MSBEM_DEVICE_TIMEOUT) st[c] = MSBEM_DEVICE_TIMEOUT;
     }
     baxpy_kernel<<<kStrideBlocks, 256, 0, s>>>(X, D, (int64_t)nvec);
+    if (density_tol > 0.0) {
+      bdot_kernel<<<rgrid, 256, 0, s>>>(D, D, N, kb, part, fl);
+      bsum_kernel<<<kb, 256, 0, s>>>(part, BRED, nrm + 2 * kb);
+      bdot_kernel<<<rgrid, 256, 0, s>>>(X, X, N, kb, part, fl);
+      bsum_kernel<<<kb, 256, 0, s>>>(part, BRED, nrm + 3 * kb);
+      g.launches += 4;
+    }
     if (tensor) {
       launch_matvec_tc(g, 0, kb, X, Q, part, &fl->all_done, &fl->err, scratch, s);
     } else {

@@ -151,6 +151,7 @@ struct Slot {
   int inner_total = 0;
   int refinements = 0;
   double nL = 0.0;         // ||L_c||^2
+  double dprev = 0.0;      // ||D|| of the previous refinement step (density test)
 };
 
 struct Batch {
@@ -223,6 +224,9 @@ struct msbem_server {
   std::mutex mu;
   std::condition_variable cv;
   bool stop = false;
+  // admission work (under mu) and kernels of released geometries
+  double far_ms = 0.0, assemble_ms = 0.0, factor_ms = 0.0;
+  int64_t far_pairs = 0, launches_released = 0;
 };
 
 namespace {
@@ -292,7 +296,7 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
     }
     scr = std::max(scr, tc_work_bytes(g));
   }
-  B->bytes = sizeof(double) * (8 * nvec + 2 * NH * kb + nparts + hsz + 3 * kb + 2 * kb + N) +
+  B->bytes = sizeof(double) * (8 * nvec + 2 * NH * kb + nparts + hsz + 3 * kb + 4 * kb + N) +
              sizeof(float) * 4 * kb * g.ldw + sizeof(float2) * nvec + sizeof(ColState) * kb +
              2 * sizeof(BatchState) + sizeof(int) * kb + scr + 1024;
   if (pool_alloc((void**)&B->base, B->bytes, g.pool, B->s) != cudaSuccess) {
@@ -319,7 +323,7 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
   B->L = cv.take<double>(nvec);
   B->Xo = cv.take<double>(nvec);
   B->Ro = cv.take<double>(nvec);
-  B->nrm = cv.take<double>(2 * kb);
+  B->nrm = cv.take<double>(4 * kb);     // ||.||^2 of R, L | D | X per column
   B->out = cv.take<double>(N);
   B->Xf = cv.take<float>(2 * kb * g.ldw);
   B->mask = cv.take<int>(kb);
@@ -328,10 +332,10 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
   cudaError_t ce = encode_planes(&B->tmP, b.Pf, g.ldw, kb, kb * g.ldw, inner_mode(prec) == 1 ? 1 : 2,
                                  matvec_pad(kb));
   if (ce == cudaSuccess) ce = encode_planes(&B->tmX, B->Xf, g.ldw, kb, kb * g.ldw, 2, matvec_pad(kb));
-  // pinned snapshots: ColState[kb], nrm[2kb], mask[kb], BatchState
+  // pinned snapshots: ColState[kb], nrm[4kb], mask[kb], BatchState
   void* pin = nullptr;
   if (ce == cudaSuccess)
-    ce = cudaMallocHost(&pin, sizeof(ColState) * kb + sizeof(double) * 2 * kb + sizeof(int) * kb +
+    ce = cudaMallocHost(&pin, sizeof(ColState) * kb + sizeof(double) * 4 * kb + sizeof(int) * kb +
                                   sizeof(BatchState) + 64);
   if (ce != cudaSuccess) {
     cudaGetLastError();
@@ -340,7 +344,7 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
   }
   B->h_cs = (ColState*)pin;
   B->h_nrm = (double*)(B->h_cs + kb);
-  B->h_mask = (int*)(B->h_nrm + 2 * kb);
+  B->h_mask = (int*)(B->h_nrm + 4 * kb);
   B->h_bs = (BatchState*)(B->h_mask + kb);
   for (int c = 0; c < kb; ++c) B->h_cs[c] = ColState{0, 0, 0, 0, 0, 0, 0, 6, 0, 0, 0};
   const double inner = is_mixed(prec) ? S->opts.inner_rtol : S->opts.rtol;
@@ -356,11 +360,18 @@ int alloc_batch(msbem_server* S, GeomEntry& e) {
   return MSBEM_OK;
 }
 
-// on the admission thread
-void release_geometry(GeomEntry& e) {
+// on the admission thread (or at destruction, after the threads have ended)
+void release_geometry(msbem_server* S, GeomEntry& e) {
   free_batch(e.batch.get());
   e.batch.reset();
-  if (e.geom) msbem_geom_free(e.geom);
+  if (e.geom) {
+    const int64_t n = msbem_geom_dev(e.geom).launches;
+    {
+      std::lock_guard<std::mutex> lock(S->mu);
+      S->launches_released += n;
+    }
+    msbem_geom_free(e.geom);
+  }
   e.geom = nullptr;
 }
 
@@ -373,6 +384,14 @@ int admit_now(msbem_server* S, msbem_ctx* actx, GeomEntry& e) {
   if ((st = msbem_assemble(g, nullptr)) || (st = msbem_factor(g, nullptr))) {
     msbem_geom_free(g);
     return st;
+  }
+  {
+    const DevGeom& d = msbem_geom_dev(g);
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->far_ms += d.times[0];
+    S->assemble_ms += (double)d.times[0] + d.times[1] + d.times[2];
+    S->factor_ms += d.times[3];
+    S->far_pairs += d.n_far_pairs;
   }
   e.geom = g;
   if ((st = alloc_batch(S, e))) {
@@ -403,7 +422,7 @@ void admission_thread(msbem_server* S, int w) {
     }
     GeomEntry& e = *t.second;
     if (t.first == 2) {
-      release_geometry(e);
+      release_geometry(S, e);
       e.state.store(G_OUT);
     } else {
       const int st = admit_now(S, W.ctx, e);
@@ -524,14 +543,34 @@ void schedule(msbem_server* S, GeomEntry& e) {
     s_resid_cols<<<grid, 256, 0, s>>>(B.L, B.b.Q, B.Ro, N, kb, B.mask);
     bdot_kernel<<<rgrid, 256, 0, s>>>(B.Ro, B.Ro, N, kb, B.b.part, B.fl);
     bsum_kernel<<<kb, 256, 0, s>>>(B.b.part, BRED, B.nrm);
-    cudaMemcpyAsync(B.h_nrm, B.nrm, sizeof(double) * kb, cudaMemcpyDeviceToHost, s);
+    const double dtol = S->opts.density_tol;
+    if (dtol > 0.0) {
+      // norms of the correction D (in b.X) and of the updated X
+      bdot_kernel<<<rgrid, 256, 0, s>>>(B.b.X, B.b.X, N, kb, B.b.part, B.fl);
+      bsum_kernel<<<kb, 256, 0, s>>>(B.b.part, BRED, B.nrm + 2 * kb);
+      bdot_kernel<<<rgrid, 256, 0, s>>>(B.Xo, B.Xo, N, kb, B.b.part, B.fl);
+      bsum_kernel<<<kb, 256, 0, s>>>(B.b.part, BRED, B.nrm + 3 * kb);
+      g.launches += 4;
+    }
+    cudaMemcpyAsync(B.h_nrm, B.nrm, sizeof(double) * 4 * kb, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     g.launches += 6;
     for (int c : refine) {
       Slot& sl = B.slot[c];
       ++sl.refinements;
       const double rel = sl.nL > 0.0 ? std::sqrt(B.h_nrm[c] / sl.nL) : 0.0;
-      if (rel <= S->opts.rtol)
+      // density test as in msbem_solve_opts.density_tol: error of X estimated
+      // from the contraction of consecutive corrections (from the second on)
+      bool dens = dtol <= 0.0;
+      if (!dens) {
+        const double dn = std::sqrt(B.h_nrm[2 * kb + c]), xn = std::sqrt(B.h_nrm[3 * kb + c]);
+        if (sl.refinements >= 2 && sl.dprev > 0.0) {
+          const double eta = dn / sl.dprev;
+          dens = eta < 1.0 && eta / (1.0 - eta) * dn <= dtol * xn;
+        }
+        sl.dprev = dn;
+      }
+      if (rel <= S->opts.rtol && dens)
         finish(S, e, c, MSBEM_OK, sl.inner_total, rel, B.Xo);
       else if (sl.inner_total >= S->opts.maxit || sl.refinements >= 12)
         finish(S, e, c, MSBEM_NOT_CONVERGED, sl.inner_total, rel, B.Xo);
@@ -647,6 +686,7 @@ int msbem_server_create(msbem_ctx* ctx, const msbem_server_opts* opts, msbem_ser
   if (o.chunk <= 0) o.chunk = 4;
   if (o.precision < 0 || o.precision > 5 || o.precision == 1) return MSBEM_INVALID_ARG;
   if (!(o.inner_rtol < 1.0)) return MSBEM_INVALID_ARG;
+  if (!(o.density_tol >= 0.0 && o.density_tol < 1.0)) return MSBEM_INVALID_ARG;
   if (o.hbm_budget_bytes <= 0.0) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return MSBEM_CUDA_ERROR;
@@ -693,7 +733,7 @@ int msbem_server_destroy(msbem_server* S) {
   for (auto& w : S->workers)
     if (w->th.joinable()) w->th.join();
   cudaSetDevice(S->device);
-  for (auto& kv : S->geoms) release_geometry(*kv.second);
+  for (auto& kv : S->geoms) release_geometry(S, *kv.second);
   for (auto& w : S->workers) {
     msbem_destroy(w->ctx);
     cudaStreamDestroy(w->stream);
@@ -858,7 +898,19 @@ int msbem_server_result(msbem_server* S, uint64_t id, int* status, int* iters, d
 
 int msbem_server_stats_get(const msbem_server* S, msbem_server_stats* out) {
   if (!S || !out) return MSBEM_INVALID_ARG;
+  msbem_server* M = const_cast<msbem_server*>(S);
+  std::lock_guard<std::mutex> lock(M->mu);
   *out = S->st;
+  out->far_ms = S->far_ms;
+  out->far_pairs = S->far_pairs;
+  out->assemble_ms = S->assemble_ms;
+  out->factor_ms = S->factor_ms;
+  int64_t launches = S->launches_released;
+  for (auto& kv : S->geoms) {
+    const GeomEntry& e = *kv.second;
+    if (e.state.load() == G_READY && e.geom) launches += msbem_geom_dev(e.geom).launches;
+  }
+  out->launches = launches;
   return MSBEM_OK;
 }
 

@@ -186,6 +186,58 @@ def test_cube_config_full_size():
             o = S.solve(geom.g, rtol=1e-8, precision=prec)
             Y, _ = S.apply(o["density"][None, :])
             assert np.linalg.norm(L - Y[0]) <= 1.05e-8 * np.linalg.norm(L), prec
+        # density bar of the mixed forms with the refinement's density test,
+        # against the double-float PCG (held to the oracle above) run to 1e-13
+        tight = S.solve(geom.g, rtol=1e-13, maxit=3000)["density"]
+        for prec in ("mixed", "mixed-tc"):
+            o = S.solve(geom.g, rtol=1e-8, precision=prec, density_tol=1e-9)
+            e = np.linalg.norm(o["density"] - tight) / np.linalg.norm(tight)
+            print(prec, "relative l2 error against the tight solve", e)
+            assert e <= 1e-8, (prec, e)
+        # W + rho Q Q^T on a wider sample: 300 rows stratified by the number of
+        # sheets at their vertex (faces, mid-planes, junction lines, the centre),
+        # each against the oracle's entries at its diagonal, its neighbours
+        # (dofs sharing a triangle) and eight random columns
+        _sampled_entries(S, top, geom, Qo, rho_o, scale)
+
+
+def _sampled_entries(S, top, geom, Qo, rho_o, scale):
+    rng = np.random.default_rng(5)
+    q_of = top.q[top.dof_vertex]
+    rows = []
+    for qv in np.unique(q_of):
+        pool = np.flatnonzero(q_of == qv)
+        rows.extend(rng.choice(pool, min(len(pool), 75), replace=False).tolist())
+    rows = np.array(sorted(set(rows)))[:300]
+    # neighbours: dofs at the vertices of the triangles around the row's vertex
+    tri = geom.tri
+    nv = len(top.xyz)
+    vt = [[] for _ in range(nv)]
+    for t in range(top.nt):
+        for v in tri[t]:
+            vt[v].append(t)
+    first = top.first_dof
+    R, C, near = [], [], []
+    for r in rows:
+        vs = set(tri[vt[top.dof_vertex[r]]].ravel().tolist())
+        nb = sorted({d for v in vs for d in range(first[v], first[v + 1])})
+        far = rng.integers(0, top.ndof, 8).tolist()
+        for c in nb:
+            R.append(r); C.append(c); near.append(True)
+        for c in far:
+            R.append(r); C.append(c); near.append(False)
+    R, C, near = np.array(R), np.array(C), np.array(near)
+    wo = solver.W_entries(top, R, C) + rho_o * np.einsum("ij,ij->i", Qo[R], Qo[C])
+    wg = np.empty_like(wo)
+    for r in rows:
+        m = R == r
+        wg[m] = S.matrix(int(r), 1)[0][C[m]]
+    err = np.abs(wg - wo)
+    print("sampled entries:", len(wo), "rows:", len(rows), "max |dW| / scale", err.max() / scale)
+    assert err.max() <= 1e-12 * scale
+    big = near & (np.abs(wo) >= 1e-2 * scale)
+    assert big.sum() >= len(rows)
+    assert (err[big] <= 1e-12 * np.abs(wo[big])).all(), (err[big] / np.abs(wo[big])).max()
 
 
 def _two_prod_err(a, b, p):
