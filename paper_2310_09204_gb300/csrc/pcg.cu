@@ -358,8 +358,10 @@ static void apply_M(DevGeom& g, const double* r, double* z, double* t, double* u
 
 // one PCG iteration (all kernels guard on the device-side done flag); with a
 // null stream only the launch counter is advanced
+// count_only: add this iteration's launches to g.launches without launching
+// (s may then be anything; a null s is the legacy default stream otherwise)
 static void enqueue_iteration(DevGeom& g, int precondition, bool plain, double* hist, int hcap,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool count_only = false) {
   const int64_t N = g.ndof;
   double* x = g.d_vec;
   double* r = x + N;
@@ -372,7 +374,7 @@ static void enqueue_iteration(DevGeom& g, int precondition, bool plain, double* 
   PcgState* st = (PcgState*)(scal + 8);
   double* part = scal + 16;
   const unsigned gemv_blocks = matvec_blocks(N, 0);
-  if (!s) {
+  if (count_only) {
     g.launches += 10 + 1 + ((precondition && !plain) ? 1 : 0) +
                   ((precondition && g.use_coarse && g.n_coarse > 0) ? 3 : 0);
     return;
@@ -495,7 +497,7 @@ cudaError_t run_pcg(DevGeom& g, const double gvec[3], double rtol, int maxit, in
   while (enq < maxit) {
     if (graphed) {
       const int64_t before = g.launches;
-      enqueue_iteration(g, precondition, plain, hist, hcap, nullptr);  // count only
+      enqueue_iteration(g, precondition, plain, hist, hcap, nullptr, true);  // count only
       const int64_t per_iter = g.launches - before;
       g.launches = before + per_iter * PCG_CHUNK;
       if ((e = cudaGraphLaunch(g.pcg_exec[gi], s)) != cudaSuccess) return drop(e);

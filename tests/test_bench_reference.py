@@ -30,12 +30,29 @@ def test_reference_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["seq_len"] == 225                     # the flat screen's dofs
     sys.path.insert(0, ROOT)
     import bench
     from paper_2310_09204_gb300 import workloads as WL
-    assert d["config"]["workload"] == bench.workload_text("flat", WL.flat_config())
-    assert d["cpu_baseline"]["phases"]["iters"] > 0
+    # the GPU arm prints the same config for the same workload and N
+    assert d["config"] == bench.book_config("flat", WL.flat_config(), 1)
+    assert d["cpu_baseline"]["phases_last"]["iters"] > 0
+    assert d["cpu_baseline"]["phases_last"]["ndof"] == 225       # the flat screen's dofs
+
+
+def test_reference_line_serving_stream():
+    """The serving workload: each step one full oracle solve of a small request
+    of the stream (here a 40-request stream, two steps)."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--serve-requests", "40",
+                        "--steps", "2", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = _lines(r.stdout)
+    assert len(lines) == 1
+    d = lines[0]
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.c5_config(40, 2, 1)
+    assert d["value"] > 0 and d["cpu_baseline"]["phases_last"]["iters"] > 0
+    assert d["cpu_baseline"]["phases_last"]["ndof"] <= 7000
 
 
 def _port():

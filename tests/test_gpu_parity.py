@@ -228,3 +228,18 @@ def test_book_config_full_size(far_kernel):
         assert _rel(fixed["density"], ref.x, pb.W) <= 1e-8
         info = S.split_info()
         assert info["n_coarse"] == 33 and info["n_faces"] == 48
+
+
+def test_solve_beyond_the_history_capacity():
+    """maxit above the geometry's persistent history (1,024 iterations): the
+    iterations run launch by launch on the caller's stream (here the legacy
+    default stream) with a temporary history, and give bit for bit the result
+    of the graph-launched chunks."""
+    geom = WL.flat_config()
+    with M.Solver(geom) as S:
+        S.assemble().factor()
+        a = S.solve(geom.g, rtol=1e-8)
+        b = S.solve(geom.g, rtol=1e-8, maxit=1500)
+        assert a["iters"] == b["iters"] > 0
+        assert np.array_equal(a["density"], b["density"])
+        assert np.array_equal(a["hist"], b["hist"])
