@@ -152,11 +152,20 @@ typedef struct msbem_precond_opts {
                      /* 1 = diagonal ("pointwise scalar product", Remark     */
                      /*     "Approximate solvers", Sec. 2.1)                  */
   int use_coarse;    /* 1 (default) = include the coarse space V~_H          */
+  int precision;     /* 0 (default) = face and wire-basket inverses in       */
+                     /*     double-float (FP64 accuracy);                     */
+                     /* 1 = those inverses in FP32 (Gauss-Jordan in FP32,    */
+                     /*     symmetrised): for the mixed-precision solves     */
+                     /*     (precision 2, 4, 5), whose inner PCG reads FP32   */
+                     /*     inverses anyway; the other solves still converge  */
+                     /*     but with a less exact preconditioner.  The coarse */
+                     /*     block A_H stays double-float.                     */
 } msbem_precond_opts;
 
 /* Set up M(H;h) (Sec. 2.1 Remark on PCG, eq. jumpSplit): the principal blocks
  * A_F = W[F,F] of every face space and A_W of the wire basket, and the coarse
- * matrix A_H = P^T W P, all inverted (FP64).  opts may be NULL.
+ * matrix A_H = P^T W P, all inverted (FP64 accuracy unless opts->precision
+ * is 1).  opts may be NULL.
  * Rejected options (INVALID_ARG) change nothing; any other failure leaves the
  * geometry unfactored (solves with the preconditioner return NOT_READY).
  * Errors: INVALID_ARG, NOT_READY (no W), BREAKDOWN (a block is not positive

@@ -36,7 +36,7 @@ class AssembleOpts(ctypes.Structure):
 
 
 class PrecondOpts(ctypes.Structure):
-    _fields_ = [("wire_basket", ctypes.c_int), ("use_coarse", ctypes.c_int)]
+    _fields_ = [("wire_basket", ctypes.c_int), ("use_coarse", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -240,7 +240,7 @@ def msbem_test_expire_waits(ns: int) -> int:
     return lib().msbem_test_expire_waits(int(ns))
 
 
-def msbem_factor_group(solvers, wire_basket: int = 0, use_coarse: int = 1):
+def msbem_factor_group(solvers, wire_basket: int = 0, use_coarse: int = 1, precision: str = "df"):
     """Factor the preconditioners of several Solvers that share one context
     (Solver(share=...)) with one grouped inversion; returns the per-geometry
     C statuses (0, or MSBEM_BREAKDOWN) and raises when any is not 0."""
@@ -251,7 +251,7 @@ def msbem_factor_group(solvers, wire_basket: int = 0, use_coarse: int = 1):
         raise ValueError("msbem_factor_group: a Solver is closed or has no geometry")
     geoms = (ctypes.c_void_p * len(solvers))(*[S.geom.value for S in solvers])
     status = np.zeros(len(solvers), np.int32)
-    o = PrecondOpts(wire_basket, use_coarse)
+    o = PrecondOpts(wire_basket, use_coarse, {"df": 0, "fp32": 1}[precision])
     _check(solvers[0].ctx, lib().msbem_factor_group(ctypes.cast(geoms, ctypes.c_void_p), len(solvers),
                                                     ctypes.byref(o), _ptr(status)))
     return status
@@ -378,8 +378,11 @@ class Solver:
         _check(self.ctx, lib().msbem_rhs(self.geom, _ptr(gv), _ptr(out)))
         return out
 
-    def factor(self, wire_basket: int = 0, use_coarse: int = 1):
-        o = PrecondOpts(wire_basket, use_coarse)
+    def factor(self, wire_basket: int = 0, use_coarse: int = 1, precision: str = "df"):
+        """Set up M(H;h).  precision "df" (default): double-float inverses;
+        "fp32": FP32 inverses of the face and wire-basket blocks (for the
+        mixed-precision solves)."""
+        o = PrecondOpts(wire_basket, use_coarse, {"df": 0, "fp32": 1}[precision])
         _check(self.ctx, lib().msbem_factor(self.geom, ctypes.byref(o)))
         return self
 

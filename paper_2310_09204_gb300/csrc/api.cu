@@ -619,6 +619,8 @@ int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts) {
   DevGeom& d = g->dev;
   int wb_diag = opts ? opts->wire_basket : 0;
   if (wb_diag < 0 || wb_diag > 1) return fail(c, MSBEM_INVALID_ARG, "wire_basket must be 0 or 1");
+  const int prec32 = opts ? opts->precision : 0;
+  if (prec32 < 0 || prec32 > 1) return fail(c, MSBEM_INVALID_ARG, "precision must be 0 or 1");
   // nothing of the geometry changes before the options are checked: the old
   // inverses and their coarse layout stay usable after a rejected call
   d.use_coarse = opts ? (opts->use_coarse != 0) : 1;
@@ -627,7 +629,7 @@ int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts) {
   drop_pcg_graphs(d);  // the captured iterations address the old inverses
   cudaEventRecord(c->ev[4], c->stream);
   int not_spd = 0;
-  cudaError_t e = factor_blocks(d, g->bptr, (g->split.n_wb > 0) ? wb_diag : 0, c->stream, &not_spd);
+  cudaError_t e = factor_blocks(d, g->bptr, (g->split.n_wb > 0) ? wb_diag : 0, c->stream, &not_spd, prec32);
   if (e != cudaSuccess) return cuda_fail(c, e, "msbem_factor");
   const int nblk = (int)g->bptr.size() - 1;
   int64_t off = 0;
@@ -655,6 +657,8 @@ int msbem_factor_group(msbem_geom* const* geoms, int n, const msbem_precond_opts
     if (geoms[i]->ctx != c) return fail(c, MSBEM_INVALID_ARG, "msbem_factor_group: geometries of different contexts");
   const int wb_diag = opts ? opts->wire_basket : 0;
   if (wb_diag < 0 || wb_diag > 1) return fail(c, MSBEM_INVALID_ARG, "wire_basket must be 0 or 1");
+  const int prec32 = opts ? opts->precision : 0;
+  if (prec32 < 0 || prec32 > 1) return fail(c, MSBEM_INVALID_ARG, "precision must be 0 or 1");
   for (int i = 0; i < n; ++i)
     if (!geoms[i]->dev.assembled) return fail(c, MSBEM_NOT_READY, "msbem_factor_group: call msbem_assemble first");
   cudaSetDevice(c->device);
@@ -667,7 +671,7 @@ int msbem_factor_group(msbem_geom* const* geoms, int n, const msbem_precond_opts
     d.use_coarse = opts ? (opts->use_coarse != 0) : 1;
     d.wb_diag = (g->split.n_wb > 0) ? 0 : -1;
     drop_pcg_graphs(d);
-    cudaError_t e = factor_gather(d, g->bptr, (g->split.n_wb > 0) ? wb_diag : 0, c->stream, plan, i);
+    cudaError_t e = factor_gather(d, g->bptr, (g->split.n_wb > 0) ? wb_diag : 0, c->stream, plan, i, prec32);
     if (e != cudaSuccess) return cuda_fail(c, e, "msbem_factor_group");
   }
   std::vector<int> bad;

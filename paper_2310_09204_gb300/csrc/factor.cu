@@ -283,6 +283,189 @@ __global__ void __launch_bounds__(256) bgj_update_kernel(BgjArgs g, int active, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same blocked Gauss-Jordan recursion in FP32, for the face and
+// wire-basket blocks of a preconditioner that only the mixed-precision solves
+// read (their inner PCG applies the FP32 inverses; the refinement's residual
+// uses W alone, so the preconditioner's precision sets the inner convergence
+// rate, not the accuracy of the result).  One FP32 FMA per update term instead
+// of a double-float product of 13 FP32 operations, and the matrices stay in
+// FP32 (half the bytes per pass).  The result is symmetrised.
+// ---------------------------------------------------------------------------
+struct Bgj32Args {
+  float* const* Ap;       // per matrix id: the matrix (row-major FP32, bsize x bsize)
+  const int64_t* bsize;   // per matrix id
+  const int32_t* order;   // matrix ids sorted by size (descending)
+  const int64_t* pt1;     // prefix over sorted matrices of tiles per side
+  const int64_t* pt2;     // prefix of tiles^2
+  const int64_t* soff;    // prefix of n * GB (scratch panels), sorted order
+  float* Pf;              // [sorted][GB*GB]
+  float* Cf;              // [soff] n x GB
+  float* Rf;              // [soff] GB x n
+  int* flag;              // per matrix id: 1 when a pivot was not positive
+};
+
+__global__ void __launch_bounds__(1024) bgj32_pivot_kernel(Bgj32Args g, int64_t k0) {
+  __shared__ float S[GB][GB + 1];
+  __shared__ float rowk[GB], colk[GB];
+  __shared__ float s_ip;
+  const int a = blockIdx.x;
+  const int b = g.order[a];
+  const int64_t n = g.bsize[b];
+  const int kb = (int)(n - k0 < GB ? n - k0 : GB);
+  const float* A = g.Ap[b];
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
+    const int i = e / GB, j = e % GB;
+    S[i][j] = (i < kb && j < kb) ? A[(k0 + i) * n + k0 + j] : (i == j ? 1.0f : 0.0f);
+  }
+  __syncthreads();
+  for (int k = 0; k < GB; ++k) {
+    if (threadIdx.x < 32) {
+      const float pk = S[k][k];
+      const float ip = 1.0f / pk;
+      if (threadIdx.x == 0) {
+        s_ip = ip;
+        if (!(pk > 0.f && isfinite(pk))) g.flag[b] = 1;
+      }
+      rowk[threadIdx.x] = S[k][threadIdx.x] * ip;
+      colk[threadIdx.x] = S[threadIdx.x][k];
+    }
+    __syncthreads();
+    const float ip = s_ip;
+    for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
+      const int i = e / GB, j = e % GB;
+      float v;
+      if (i == k) v = (j == k) ? ip : rowk[j];
+      else if (j == k) v = -colk[i] * ip;
+      else v = fmaf(-colk[i], rowk[j], S[i][j]);
+      S[i][j] = v;
+    }
+    __syncthreads();
+  }
+  float* P = g.Pf + (int64_t)a * GB * GB;
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) P[e] = S[e / GB][e % GB];
+}
+
+__global__ void __launch_bounds__(256) bgj32_panel_kernel(Bgj32Args g, int active, int64_t k0) {
+  __shared__ float sP[GB][GB + 1];
+  __shared__ float sA[GB][GB + 1];
+  const int64_t t = blockIdx.x;
+  const int a = find_prefix(g.pt1, active, t);
+  const int b = g.order[a];
+  const int64_t n = g.bsize[b];
+  const int I = (int)(t - g.pt1[a]);
+  const int kb = (int)(n - k0 < GB ? n - k0 : GB);
+  const float* A = g.Ap[b];
+  float* C = g.Cf + g.soff[a];
+  float* R = g.Rf + g.soff[a];
+  const int64_t r0 = (int64_t)I * GB;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int m = ty; m < kb; m += 8) {
+    const int64_t col = r0 + tx;
+    if (col < n) R[m * n + col] = A[(k0 + m) * n + col];
+  }
+  if (r0 == k0) return;
+  const float* P = g.Pf + (int64_t)a * GB * GB;
+  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) sP[e / GB][e % GB] = P[e];
+  for (int i = ty; i < GB; i += 8) {
+    const int64_t row = r0 + i;
+    sA[i][tx] = (row < n && tx < kb) ? A[row * n + k0 + tx] : 0.f;
+  }
+  __syncthreads();
+  for (int i = ty; i < GB; i += 8) {
+    const int64_t row = r0 + i;
+    if (row >= n || tx >= kb) continue;
+    float acc = 0.f;
+    for (int m = 0; m < kb; ++m) acc = fmaf(sA[i][m], sP[m][tx], acc);
+    C[row * GB + tx] = -acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) bgj32_update_kernel(Bgj32Args g, int active, int64_t k0) {
+  __shared__ float sL[GB][GB + 1];
+  __shared__ float sR[GB][GB + 1];
+  const int64_t t = blockIdx.x;
+  const int a = find_prefix(g.pt2, active, t);
+  const int b = g.order[a];
+  const int64_t n = g.bsize[b];
+  const int nti = (int)((n + GB - 1) / GB);
+  const int64_t loc = t - g.pt2[a];
+  const int I = (int)(loc / nti), J = (int)(loc % nti);
+  const int kt = (int)(k0 / GB);
+  const int kb = (int)(n - k0 < GB ? n - k0 : GB);
+  float* A = g.Ap[b];
+  const float* C = g.Cf + g.soff[a];
+  const float* R = g.Rf + g.soff[a];
+  const float* P = g.Pf + (int64_t)a * GB * GB;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)I * GB, c0 = (int64_t)J * GB;
+  if (I == kt && J == kt) {
+    for (int i = ty; i < kb; i += 8)
+      if (tx < kb) A[(k0 + i) * n + k0 + tx] = P[i * GB + tx];
+    return;
+  }
+  if (J == kt) {
+    for (int i = ty; i < GB; i += 8) {
+      const int64_t row = r0 + i;
+      if (row < n && tx < kb) A[row * n + k0 + tx] = C[row * GB + tx];
+    }
+    return;
+  }
+  for (int i = ty; i < GB; i += 8) {
+    float v = 0.f;
+    if (I == kt) {
+      if (i < kb && tx < kb) v = P[i * GB + tx];
+    } else {
+      const int64_t row = r0 + i;
+      if (row < n && tx < kb) v = C[row * GB + tx];
+    }
+    sL[i][tx] = v;
+    const int64_t col = c0 + tx;
+    sR[i][tx] = (i < kb && col < n) ? R[i * n + col] : 0.f;
+  }
+  __syncthreads();
+  const int64_t col = c0 + tx;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int m = 0; m < kb; ++m) {
+    const float r = sR[m][tx];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fmaf(sL[ty + 8 * q][m], r, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = ty + 8 * q;
+    const int64_t row = r0 + i;
+    if (row >= n || col >= n) continue;
+    if (I == kt && i >= kb) continue;
+    A[row * n + col] = (I == kt) ? acc[q] : A[row * n + col] + acc[q];
+  }
+}
+
+// FP32 copies of the listed matrices (from FP64) and back (symmetrised):
+// one CTA row per matrix, entries strided
+__global__ void f64_to_f32_kernel(double* const* src, float* const* dst, const int64_t* bsize,
+                                  const int32_t* ids) {
+  const int b = ids[blockIdx.y];
+  const int64_t nn = bsize[b] * bsize[b];
+  const double* s = src[b];
+  float* d = dst[b];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (float)s[e];
+}
+
+__global__ void f32_sym_to_f64_kernel(float* const* src, double* const* dst, const int64_t* bsize,
+                                      const int32_t* ids) {
+  const int b = ids[blockIdx.y];
+  const int64_t n = bsize[b];
+  const float* s = src[b];
+  double* d = dst[b];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    d[e] = 0.5 * ((double)s[i * n + j] + (double)s[j * n + i]);
+  }
+}
+
+
 __global__ void to_float_pairs_kernel(const double* __restrict__ x, float2* __restrict__ xf, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -334,6 +517,86 @@ cudaError_t upload(T** d, const std::vector<T>& h, cudaMemPool_t pool, cudaStrea
 }
 }  // namespace
 
+namespace {
+
+// Inverts the FP32 matrices of `ids` (their FP64 copies in plan.ptr, in place:
+// converted to FP32, inverted, symmetrised and written back).
+cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cudaMemPool_t pool, cudaStream_t s,
+                       std::vector<int>& bad, int64_t* launches) {
+  const int nm = (int)plan.size.size();
+  std::vector<int32_t> order(ids);
+  if (order.empty()) return cudaSuccess;
+  const std::vector<int64_t>& bsize = plan.size;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bsize[a] > bsize[b]; });
+  const int nb = (int)order.size();
+  std::vector<int64_t> pt1(nb + 1, 0), pt2(nb + 1, 0), soff(nb + 1, 0);
+  int64_t elems = 0;
+  for (int a = 0; a < nb; ++a) {
+    const int64_t n = bsize[order[a]];
+    const int64_t nti = (n + GB - 1) / GB;
+    pt1[a + 1] = pt1[a] + nti;
+    pt2[a + 1] = pt2[a] + nti * nti;
+    soff[a + 1] = soff[a] + n * GB;
+    elems += n * n;
+  }
+  PoolScratch scratch(pool, s);
+  cudaError_t e;
+  float* mats = nullptr;
+  if ((e = scratch.take(&mats, (size_t)elems)) != cudaSuccess) return e;
+  std::vector<float*> fptr(nm, nullptr);
+  int64_t off = 0;
+  for (int a = 0; a < nb; ++a) {
+    fptr[order[a]] = mats + off;
+    off += bsize[order[a]] * bsize[order[a]];
+  }
+  Bgj32Args args{};
+  double** d_dptr = nullptr;
+  float** d_fptr = nullptr;
+  int64_t *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt2 = nullptr, *d_soff = nullptr;
+  int32_t* d_order = nullptr;
+  if ((e = scratch.put(&d_dptr, plan.ptr)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_fptr, fptr)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_bsize, bsize)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_pt1, pt1)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_pt2, pt2)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_soff, soff)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_order, order)) != cudaSuccess) return e;
+  if ((e = scratch.take(&args.Pf, (size_t)nb * GB * GB)) != cudaSuccess) return e;
+  if ((e = scratch.take(&args.Cf, (size_t)soff[nb])) != cudaSuccess) return e;
+  if ((e = scratch.take(&args.Rf, (size_t)soff[nb])) != cudaSuccess) return e;
+  if ((e = scratch.take(&args.flag, (size_t)nm)) != cudaSuccess) return e;
+  cudaMemsetAsync(args.flag, 0, sizeof(int) * nm, s);
+  args.Ap = d_fptr;
+  args.bsize = d_bsize;
+  args.order = d_order;
+  args.pt1 = d_pt1;
+  args.pt2 = d_pt2;
+  args.soff = d_soff;
+  const dim3 cgrid(std::min<unsigned>(1024u, (unsigned)((bsize[order[0]] * bsize[order[0]] + 255) / 256)),
+                   (unsigned)nb);
+  f64_to_f32_kernel<<<cgrid, 256, 0, s>>>(d_dptr, d_fptr, d_bsize, d_order);
+  const int64_t nmax = bsize[order[0]];
+  int active = nb;
+  for (int64_t k0 = 0; k0 < nmax; k0 += GB) {
+    while (active > 0 && bsize[order[active - 1]] <= k0) --active;
+    bgj32_pivot_kernel<<<active, GB * GB, 0, s>>>(args, k0);
+    bgj32_panel_kernel<<<(unsigned)pt1[active], 256, 0, s>>>(args, active, k0);
+    bgj32_update_kernel<<<(unsigned)pt2[active], 256, 0, s>>>(args, active, k0);
+    *launches += 3;
+  }
+  f32_sym_to_f64_kernel<<<cgrid, 256, 0, s>>>(d_fptr, d_dptr, d_bsize, d_order);
+  *launches += 2;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  std::vector<int> h(nm, 0);
+  if ((e = cudaMemcpyAsync(h.data(), args.flag, sizeof(int) * nm, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  for (int m = 0; m < nm; ++m) bad[m] |= h[m];
+  return cudaSuccess;
+}
+
+}  // namespace
+
 // Inverts in place the matrices plan.inv lists (ids into plan.ptr / plan.size),
 // all of them in one grouped sequence of launches: per 32-column step, one
 // pivot, one panel and one update launch over the tiles of every matrix still
@@ -343,10 +606,10 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
                           int64_t* launches) {
   const int nm = (int)plan.size.size();
   bad.assign(nm, 0);
-  std::vector<int32_t> order;
+  std::vector<int32_t> order, order32;
   for (int32_t m : plan.inv)
-    if (plan.size[m] > 0) order.push_back(m);
-  if (order.empty()) return cudaSuccess;
+    if (plan.size[m] > 0) (m < (int)plan.f32.size() && plan.f32[m] ? order32 : order).push_back(m);
+  if (order.empty()) return invert_f32(plan, order32, pool, s, bad, launches);
   const std::vector<int64_t>& bsize = plan.size;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bsize[a] > bsize[b]; });
   const int nb = (int)order.size();
@@ -393,7 +656,8 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(bad.data(), args.flag, sizeof(int) * nm, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
-  return cudaStreamSynchronize(s);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  return invert_f32(plan, order32, pool, s, bad, launches);
 }
 
 // Blocked Gauss-Jordan inversion of one SPD matrix A (n x n, row-major,
@@ -450,7 +714,7 @@ cudaError_t bgj_invert_single(double* A, int64_t n, unsigned char* scratch, size
 // plan records for them).  bptr: block pointer (faces first, wire basket last
 // if any).
 cudaError_t factor_gather(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag, cudaStream_t s,
-                          InvPlan& plan, int owner) {
+                          InvPlan& plan, int owner, int prec32) {
   const int nblk = (int)bptr.size() - 1;
   std::vector<int64_t> bsize(nblk + 1), boff(nblk + 2, 0), prefix2(nblk + 1, 0);
   for (int b = 0; b < nblk; ++b) {
@@ -483,6 +747,7 @@ cudaError_t factor_gather(DevGeom& g, const std::vector<int64_t>& bptr, int wb_d
     plan.ptr.push_back(g.d_binv + boff[b]);
     plan.size.push_back(bsize[b]);
     plan.owner.push_back(owner);
+    plan.f32.push_back(prec32 && b < nblk ? 1 : 0);   // the coarse block stays double-float
   }
   for (int b = 0; b < nblk; ++b)
     if (!(wb_diag && b == wb_block) && bsize[b] > 0) plan.inv.push_back(base + b);
@@ -529,10 +794,10 @@ cudaError_t factor_finish(DevGeom& g, const std::vector<int64_t>& bptr, cudaStre
 }
 
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag, cudaStream_t s,
-                          int* not_spd) {
+                          int* not_spd, int prec32) {
   *not_spd = 0;
   InvPlan plan;
-  cudaError_t e = factor_gather(g, bptr, wb_diag, s, plan, 0);
+  cudaError_t e = factor_gather(g, bptr, wb_diag, s, plan, 0, prec32);
   if (e != cudaSuccess) return e;
   std::vector<int> bad;
   if ((e = factor_invert(plan, g.pool, s, bad, &g.launches)) != cudaSuccess) return e;

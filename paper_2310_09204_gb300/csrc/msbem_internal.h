@@ -243,14 +243,17 @@ struct InvPlan {
   std::vector<int64_t> size;   // per matrix id: n
   std::vector<int> owner;      // per matrix id: the tag given to factor_gather
   std::vector<int32_t> inv;    // the ids to invert in place
+  std::vector<char> f32;       // per matrix id: inverted in FP32 (else double-float)
 };
+// prec32: the face and wire-basket blocks are inverted in FP32 (the coarse
+// block stays double-float)
 cudaError_t factor_gather(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag, cudaStream_t s,
-                          InvPlan& plan, int owner);
+                          InvPlan& plan, int owner, int prec32 = 0);
 cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t s, std::vector<int>& bad,
                           int64_t* launches);
 cudaError_t factor_finish(DevGeom& g, const std::vector<int64_t>& bptr, cudaStream_t s);
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag,
-                          cudaStream_t s, int* not_spd);
+                          cudaStream_t s, int* not_spd, int prec32 = 0);
 
 // Single-matrix blocked Gauss-Jordan inversion with caller-provided scratch
 // (factor.cu); used by the allocation-free entry point.

@@ -381,7 +381,9 @@ int admit_now(msbem_server* S, msbem_ctx* actx, GeomEntry& e) {
                         e.cxyz.data(), (int64_t)e.cxyz.size() / 3, e.ctri.data(), (int64_t)e.ctri.size() / 3,
                         e.parent.data(), e.patch.data(), &g);
   if (st) return st;
-  if ((st = msbem_assemble(g, nullptr)) || (st = msbem_factor(g, nullptr))) {
+  // the mixed precisions' inner PCG reads FP32 block inverses: invert in FP32
+  const msbem_precond_opts po{0, 1, is_mixed(S->opts.precision) ? 1 : 0};
+  if ((st = msbem_assemble(g, nullptr)) || (st = msbem_factor(g, &po))) {
     msbem_geom_free(g);
     return st;
   }
