@@ -467,17 +467,21 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
   if (panels && far_kernel == 1)
     return fail(c, MSBEM_INVALID_ARG, "panel assembly uses the double-float pair kernel (far_kernel 0)");
   const int64_t vrows = panels ? panel : d.nt;
+  // V, and 256 bytes after it for the far-field kernel's error flag
+  const size_t vbytes = (sizeof(float2) * (size_t)std::max<int64_t>(1, vrows * d.nt) + 255) / 256 * 256;
   if (!d.d_V) {
-    e = pool_alloc((void**)&d.d_V, sizeof(float2) * std::max<int64_t>(1, vrows * d.nt), d.pool, s);
+    e = pool_alloc((void**)&d.d_V, vbytes + 256, d.pool, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(c, MSBEM_OOM, "assemble: no room for the pair matrix V");
     }
   }
+  int* far_err = (int*)((char*)d.d_V + vbytes);
+  if ((e = cudaMemsetAsync(far_err, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(c, e, "assemble");
   float t_far = 0.f, t_near = 0.f, t_con = 0.f;
   if (!panels) {
     cudaEventRecord(c->ev[0], s);
-    e = (far_kernel == 1) ? launch_far_fp64(d, s) : launch_far_df(d, s);
+    e = (far_kernel == 1) ? launch_far_fp64(d, s) : launch_far_df(d, far_err, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "far field");
     cudaEventRecord(c->ev[1], s);
     e = launch_near(d, n, glx, glw, far_kernel == 1, s);
@@ -508,7 +512,8 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
     for (int64_t p = 0; p < np && e == cudaSuccess; ++p) {
       const int64_t t0 = p * panel, t1 = std::min<int64_t>(d.nt, t0 + panel);
       cudaEventRecord(evs[4 * p], s);
-      e = launch_far_df_panel(d, (int)(t0 / 64), (int)((std::min<int64_t>(nt_pad, t0 + panel) - t0) / 64), s);
+      e = launch_far_df_panel(d, (int)(t0 / 64), (int)((std::min<int64_t>(nt_pad, t0 + panel) - t0) / 64),
+                              far_err, s);
       cudaEventRecord(evs[4 * p + 1], s);
       if (e == cudaSuccess) e = launch_near(d, n, glx, glw, 0, s, t0, t1);
       cudaEventRecord(evs[4 * p + 2], s);
@@ -542,10 +547,13 @@ int msbem_assemble(msbem_geom* g, const msbem_assemble_opts* opts) {
     if ((e = launch_augment(d, d.rho, s)) != cudaSuccess) return cuda_fail(c, e, "cells");
     ++d.launches;
   }
+  int h_far_err = 0;
+  e = cudaMemcpyAsync(&h_far_err, far_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(d.d_V, s);
   d.d_V = nullptr;
-  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "assemble");
+  if (h_far_err) return fail(c, MSBEM_DEVICE_TIMEOUT, "assemble: a far-field staging copy did not complete");
   if (d.pool) {
     // the pool keeps at most kPoolSpare bytes of freed memory (V of the next
     // assembly of a similar geometry) beyond what is in use, so that the V of

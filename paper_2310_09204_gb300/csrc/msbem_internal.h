@@ -177,13 +177,14 @@ struct DevGeom {
 
 // launch wrappers (assemble.cu, factor.cu, pcg.cu); all return cudaError_t
 cudaError_t launch_far_fp64(const DevGeom& g, cudaStream_t s);
-cudaError_t launch_far_df(const DevGeom& g, cudaStream_t s);
+// err: a device int set to 1 when a tile's staging copy never completed
+cudaError_t launch_far_df(const DevGeom& g, int* err, cudaStream_t s);
 // t0, t1: the rows of V held (panel mode); t1 < 0: all rows
 cudaError_t launch_near(const DevGeom& g, int ss_order, const double* gl_x, const double* gl_w,
                         int fp64, cudaStream_t s, int64_t t0 = 0, int64_t t1 = -1);
 cudaError_t launch_contract(const DevGeom& g, cudaStream_t s);
 // panel mode (V holds triangle rows tb0*64 .. (tb0+ntb)*64 - 1)
-cudaError_t launch_far_df_panel(const DevGeom& g, int tb0, int ntb, cudaStream_t s);
+cudaError_t launch_far_df_panel(const DevGeom& g, int tb0, int ntb, int* err, cudaStream_t s);
 cudaError_t launch_contract_panel(const DevGeom& g, int64_t t0, int64_t t1, int rt0, int nrt, cudaStream_t s);
 cudaError_t launch_rhs(const DevGeom& g, const double gvec[3], double* out, cudaStream_t s);
 cudaError_t copy_rows_to_double(const DevGeom& g, int64_t row0, int64_t nrows, double* out,
