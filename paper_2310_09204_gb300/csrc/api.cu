@@ -75,7 +75,8 @@ void free_dev(DevGeom& d, cudaStream_t s) {
   void* ptrs[] = {d.d_hist, d.d_qp, d.d_cen, d.d_qoff, d.d_area, d.d_tri, d.d_xyz, d.d_near, d.d_V,
                   d.d_jptr, d.d_jtri, d.d_jvec, d.d_jvecf, d.d_jrhs, d.d_Wh, d.d_bptr, d.d_bdofs, d.d_boff,
                   d.d_binv, d.d_pptr, d.d_pcol, d.d_pval, d.d_cptr, d.d_crow, d.d_cval, d.d_cvalf, d.d_pfp, d.d_rf, d.d_binvf,
-                  d.d_btile, d.d_W64, d.d_wsl, d.d_wf16, d.d_wexp, d.d_cellZ, d.d_WP, d.d_vec, d.d_scal};
+                  d.d_btile, d.d_W64, d.d_wsl, d.d_wf16, d.d_wexp, d.d_cellZ, d.d_WP, d.d_vec, d.d_scal,
+                  d.d_cendf, d.d_areadf};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
@@ -217,6 +218,13 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   std::vector<double> qp(d.nt_pad * 18, 0.0), cen(d.nt_pad * 3, 0.0), area(d.nt_pad, 0.0);
   std::vector<float> qoff(d.nt_pad * 36, 0.0f);
   std::vector<int32_t> tpad(d.nt_pad * 3, -1);
+  // centroids and areas also as float pairs (the separated pairs of the far
+  // field are formed in FP32 arithmetic alone)
+  std::vector<float2> cendf(d.nt_pad * 3, make_float2(0.f, 0.f)), areadf(d.nt_pad, make_float2(0.f, 0.f));
+  auto to_pair = [](double x) {
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+  };
   for (int64_t T = 0; T < nt; ++T) {
     const double* X[3] = {&f.xyz[3 * f.tri[3 * T]], &f.xyz[3 * f.tri[3 * T + 1]],
                           &f.xyz[3 * f.tri[3 * T + 2]]};
@@ -233,6 +241,8 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
       }
     area[T] = f.area[T];
     for (int a = 0; a < 3; ++a) tpad[3 * T + a] = f.tri[3 * T + a];
+    for (int k = 0; k < 3; ++k) cendf[3 * T + k] = to_pair(cen[3 * T + k]);
+    areadf[T] = to_pair(area[T]);
   }
   // curl vectors s_{T,nu} = coef (x_{a+1} - x_{a+2}) / (2|T|) and RHS weights
   const int64_t ne = f.jptr[f.ndof];
@@ -275,6 +285,8 @@ int msbem_upload(msbem_ctx* c, const double* xyz, int64_t nv, const int32_t* tri
   chk(dput(&d.d_cen, cen, c->pool, s));
   chk(dput(&d.d_qoff, qoff, c->pool, s));
   chk(dput(&d.d_area, area, c->pool, s));
+  chk(dput(&d.d_cendf, cendf, c->pool, s));
+  chk(dput(&d.d_areadf, areadf, c->pool, s));
   chk(dput(&d.d_tri, tpad, c->pool, s));
   chk(dput(&d.d_xyz, f.xyz, c->pool, s));
   d.n_near = (int64_t)near.size();

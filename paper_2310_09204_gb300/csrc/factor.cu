@@ -298,6 +298,7 @@ struct Bgj32Args {
   const int32_t* order;   // matrix ids sorted by size (descending)
   const int64_t* pt1;     // prefix over sorted matrices of tiles per side
   const int64_t* pt2;     // prefix of tiles^2
+  const int64_t* pt3;     // prefix of tiles x column-tile groups (update CTAs)
   const int64_t* soff;    // prefix of n * GB (scratch panels), sorted order
   float* Pf;              // [sorted][GB*GB]
   float* Cf;              // [soff] n x GB
@@ -381,16 +382,20 @@ __global__ void __launch_bounds__(256) bgj32_panel_kernel(Bgj32Args g, int activ
   }
 }
 
+// One CTA per (row tile I, group of BGJ32_JG column tiles): the left factor
+// (C'_I, or P for the pivot row) is loaded once and reused across the group.
+#define BGJ32_JG 8
 __global__ void __launch_bounds__(256) bgj32_update_kernel(Bgj32Args g, int active, int64_t k0) {
   __shared__ float sL[GB][GB + 1];
   __shared__ float sR[GB][GB + 1];
   const int64_t t = blockIdx.x;
-  const int a = find_prefix(g.pt2, active, t);
+  const int a = find_prefix(g.pt3, active, t);
   const int b = g.order[a];
   const int64_t n = g.bsize[b];
   const int nti = (int)((n + GB - 1) / GB);
-  const int64_t loc = t - g.pt2[a];
-  const int I = (int)(loc / nti), J = (int)(loc % nti);
+  const int njg = (nti + BGJ32_JG - 1) / BGJ32_JG;
+  const int64_t loc = t - g.pt3[a];
+  const int I = (int)(loc / njg), jg = (int)(loc % njg);
   const int kt = (int)(k0 / GB);
   const int kb = (int)(n - k0 < GB ? n - k0 : GB);
   float* A = g.Ap[b];
@@ -398,19 +403,7 @@ __global__ void __launch_bounds__(256) bgj32_update_kernel(Bgj32Args g, int acti
   const float* R = g.Rf + g.soff[a];
   const float* P = g.Pf + (int64_t)a * GB * GB;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t r0 = (int64_t)I * GB, c0 = (int64_t)J * GB;
-  if (I == kt && J == kt) {
-    for (int i = ty; i < kb; i += 8)
-      if (tx < kb) A[(k0 + i) * n + k0 + tx] = P[i * GB + tx];
-    return;
-  }
-  if (J == kt) {
-    for (int i = ty; i < GB; i += 8) {
-      const int64_t row = r0 + i;
-      if (row < n && tx < kb) A[row * n + k0 + tx] = C[row * GB + tx];
-    }
-    return;
-  }
+  const int64_t r0 = (int64_t)I * GB;
   for (int i = ty; i < GB; i += 8) {
     float v = 0.f;
     if (I == kt) {
@@ -420,24 +413,43 @@ __global__ void __launch_bounds__(256) bgj32_update_kernel(Bgj32Args g, int acti
       if (row < n && tx < kb) v = C[row * GB + tx];
     }
     sL[i][tx] = v;
+  }
+  const int J1 = min(nti, (jg + 1) * BGJ32_JG);
+  for (int J = jg * BGJ32_JG; J < J1; ++J) {
+    const int64_t c0 = (int64_t)J * GB;
+    if (J == kt) {
+      // the pivot column: P on the pivot block, C'_I elsewhere
+      for (int i = ty; i < GB; i += 8) {
+        const int64_t row = r0 + i;
+        if (I == kt) {
+          if (i < kb && tx < kb) A[(k0 + i) * n + k0 + tx] = P[i * GB + tx];
+        } else if (row < n && tx < kb) {
+          A[row * n + k0 + tx] = C[row * GB + tx];
+        }
+      }
+      continue;
+    }
+    __syncthreads();   // the previous tile's reads of sR are done (and sL is in place)
+    for (int i = ty; i < GB; i += 8) {
+      const int64_t col = c0 + tx;
+      sR[i][tx] = (i < kb && col < n) ? R[i * n + col] : 0.f;
+    }
+    __syncthreads();
     const int64_t col = c0 + tx;
-    sR[i][tx] = (i < kb && col < n) ? R[i * n + col] : 0.f;
-  }
-  __syncthreads();
-  const int64_t col = c0 + tx;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int m = 0; m < kb; ++m) {
-    const float r = sR[m][tx];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int m = 0; m < kb; ++m) {
+      const float r = sR[m][tx];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = fmaf(sL[ty + 8 * q][m], r, acc[q]);
-  }
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(sL[ty + 8 * q][m], r, acc[q]);
+    }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = ty + 8 * q;
-    const int64_t row = r0 + i;
-    if (row >= n || col >= n) continue;
-    if (I == kt && i >= kb) continue;
-    A[row * n + col] = (I == kt) ? acc[q] : A[row * n + col] + acc[q];
+    for (int q = 0; q < 4; ++q) {
+      const int i = ty + 8 * q;
+      const int64_t row = r0 + i;
+      if (row >= n || col >= n) continue;
+      if (I == kt && i >= kb) continue;
+      A[row * n + col] = (I == kt) ? acc[q] : A[row * n + col] + acc[q];
+    }
   }
 }
 
@@ -529,13 +541,14 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   const std::vector<int64_t>& bsize = plan.size;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bsize[a] > bsize[b]; });
   const int nb = (int)order.size();
-  std::vector<int64_t> pt1(nb + 1, 0), pt2(nb + 1, 0), soff(nb + 1, 0);
+  std::vector<int64_t> pt1(nb + 1, 0), pt2(nb + 1, 0), pt3(nb + 1, 0), soff(nb + 1, 0);
   int64_t elems = 0;
   for (int a = 0; a < nb; ++a) {
     const int64_t n = bsize[order[a]];
     const int64_t nti = (n + GB - 1) / GB;
     pt1[a + 1] = pt1[a] + nti;
     pt2[a + 1] = pt2[a] + nti * nti;
+    pt3[a + 1] = pt3[a] + nti * ((nti + BGJ32_JG - 1) / BGJ32_JG);
     soff[a + 1] = soff[a] + n * GB;
     elems += n * n;
   }
@@ -552,9 +565,10 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   Bgj32Args args{};
   double** d_dptr = nullptr;
   float** d_fptr = nullptr;
-  int64_t *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt2 = nullptr, *d_soff = nullptr;
+  int64_t *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt2 = nullptr, *d_pt3 = nullptr, *d_soff = nullptr;
   int32_t* d_order = nullptr;
   if ((e = scratch.put(&d_dptr, plan.ptr)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_pt3, pt3)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_fptr, fptr)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_bsize, bsize)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_pt1, pt1)) != cudaSuccess) return e;
@@ -571,6 +585,7 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   args.order = d_order;
   args.pt1 = d_pt1;
   args.pt2 = d_pt2;
+  args.pt3 = d_pt3;
   args.soff = d_soff;
   const dim3 cgrid(std::min<unsigned>(1024u, (unsigned)((bsize[order[0]] * bsize[order[0]] + 255) / 256)),
                    (unsigned)nb);
@@ -581,7 +596,7 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
     while (active > 0 && bsize[order[active - 1]] <= k0) --active;
     bgj32_pivot_kernel<<<active, GB * GB, 0, s>>>(args, k0);
     bgj32_panel_kernel<<<(unsigned)pt1[active], 256, 0, s>>>(args, active, k0);
-    bgj32_update_kernel<<<(unsigned)pt2[active], 256, 0, s>>>(args, active, k0);
+    bgj32_update_kernel<<<(unsigned)pt3[active], 256, 0, s>>>(args, active, k0);
     *launches += 3;
   }
   f32_sym_to_f64_kernel<<<cgrid, 256, 0, s>>>(d_fptr, d_dptr, d_bsize, d_order);

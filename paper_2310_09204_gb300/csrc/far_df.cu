@@ -119,6 +119,8 @@ template <bool PANEL>
 __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ cen,
                                                      const float* __restrict__ qoff,
                                                      const double* __restrict__ area,
+                                                     const float2* __restrict__ cendf,
+                                                     const float2* __restrict__ areadf,
                                                      const int32_t* __restrict__ tri, int nb,
                                                      int64_t nt, int64_t ldv,
                                                      float2* __restrict__ V, int tb0, int* __restrict__ err) {
@@ -126,6 +128,8 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
   __shared__ __align__(16) double s_cen[DF_TILE * 3];
   __shared__ __align__(16) double s_area[DF_TILE];
   __shared__ __align__(16) int32_t s_tri[DF_TILE * 3];
+  __shared__ __align__(16) float2 s_cdf[DF_TILE * 3];
+  __shared__ __align__(16) float2 s_adf[DF_TILE];
   __shared__ float s_rho[DF_TILE];
   __shared__ float2 s_out[DF_TILE][DF_TILE + 1];
   __shared__ __align__(8) uint64_t s_bar;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
   const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)bi * DF_TILE, col0 = (int64_t)bj * DF_TILE;
   constexpr uint32_t B_OFF = DF_TILE * 36 * 4, B_CEN = DF_TILE * 3 * 8, B_AREA = DF_TILE * 8,
-                     B_TRI = DF_TILE * 3 * 4;
+                     B_TRI = DF_TILE * 3 * 4, B_CDF = DF_TILE * 3 * 8, B_ADF = DF_TILE * 8;
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(fd_smem(&s_bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -159,11 +163,13 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
     // the column tile: offsets, centroids, areas and vertex ids (arrays padded
     // to whole tiles; every source offset is a multiple of 256 bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fd_smem(&s_bar)),
-                 "r"(B_OFF + B_CEN + B_AREA + B_TRI) : "memory");
+                 "r"(B_OFF + B_CEN + B_AREA + B_TRI + B_CDF + B_ADF) : "memory");
     fd_bulk(s_off, qoff + col0 * 36, B_OFF, &s_bar);
     fd_bulk(s_cen, cen + col0 * 3, B_CEN, &s_bar);
     fd_bulk(s_area, area + col0, B_AREA, &s_bar);
     fd_bulk(s_tri, tri + col0 * 3, B_TRI, &s_bar);
+    fd_bulk(s_cdf, cendf + col0 * 3, B_CDF, &s_bar);
+    fd_bulk(s_adf, areadf + col0, B_ADF, &s_bar);
   }
   // the row triangle of this thread, from global memory meanwhile
   const int r = tid & 63;
@@ -174,6 +180,8 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
   for (int k = 0; k < 36; ++k) a[k] = qoff[T * 36 + k];
   const double cx = cen[T * 3], cy = cen[T * 3 + 1], cz = cen[T * 3 + 2];
   const double aT = area[T];
+  const float2 cTx = cendf[T * 3], cTy = cendf[T * 3 + 1], cTz = cendf[T * 3 + 2];
+  const float2 aTdf = areadf[T];
   const int32_t t0 = tri[T * 3], t1 = tri[T * 3 + 1], t2 = tri[T * 3 + 2];
   float rhoT = 0.f;
 #pragma unroll
@@ -206,10 +214,12 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
                        (t1 == u2) | (t2 == u0) | (t2 == u1) | (t2 == u2) | (t0 < 0) | (u0 < 0);
     float2 v = make_float2(0.f, 0.f);
     if (!touch) {
+      // D = c_T - c_T' from the float-pair centroids (absolute error ~2^-48 of
+      // the coordinates; the close pairs below take it from the FP64 ones)
       float Dxh, Dxl, Dyh, Dyl, Dzh, Dzl;
-      split_df(cx - s_cen[3 * c], Dxh, Dxl);
-      split_df(cy - s_cen[3 * c + 1], Dyh, Dyl);
-      split_df(cz - s_cen[3 * c + 2], Dzh, Dzl);
+      df_add_raw(cTx.x, cTx.y, -s_cdf[3 * c].x, -s_cdf[3 * c].y, Dxh, Dxl);
+      df_add_raw(cTy.x, cTy.y, -s_cdf[3 * c + 1].x, -s_cdf[3 * c + 1].y, Dyh, Dyl);
+      df_add_raw(cTz.x, cTz.y, -s_cdf[3 * c + 2].x, -s_cdf[3 * c + 2].y, Dzh, Dzl);
       const float* b = &s_off[c * 36];
       float bq[36];
 #pragma unroll
@@ -259,8 +269,21 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
         df_fma_acc(c_wcls[0], c_wcls[1], sah, sal + sac, acch, accl);
         df_fma_acc(c_wcls[2], c_wcls[3], smh, sml + smc, acch, accl);
         df_fma_acc(c_wcls[4], c_wcls[5], sbh, sbl + sbc, acch, accl);
+        // V = S |T| |T'| / (4 pi) in double-float
+        constexpr double kq = 0.25 / M_PI;
+        constexpr float kqh = (float)kq;
+        constexpr float kql = (float)(kq - (double)kqh);
+        float sh, sl, vh, vl;
+        df_mul(aTdf.x, aTdf.y, s_adf[c].x, s_adf[c].y, sh, sl);
+        df_mul(sh, sl, kqh, kql, sh, sl);
+        df_mul(acch, accl, sh, sl, vh, vl);
+        v = make_float2(vh, vl);
       } else {
-        // close: exact differences, weights per evaluation
+        // close: D from the FP64 centroids (exact to 2^-53 |D|), exact
+        // differences, weights per evaluation
+        split_df(cx - s_cen[3 * c], Dxh, Dxl);
+        split_df(cy - s_cen[3 * c + 1], Dyh, Dyl);
+        split_df(cz - s_cen[3 * c + 2], Dzh, Dzl);
 #pragma unroll 1
         for (int p = 0; p < 6; ++p) {
           float uxh, uxl, uyh, uyl, uzh, uzl;   // u = a_p + D
@@ -298,10 +321,10 @@ __global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ 
           acch = s;
           accl += e + pe;
         }
+        float vh, vl;
+        split_df((widen(acch) + widen(accl)) * (aT * s_area[c]) * (0.25 / M_PI), vh, vl);
+        v = make_float2(vh, vl);
       }
-      float vh, vl;
-      split_df((widen(acch) + widen(accl)) * (aT * s_area[c]) * (0.25 / M_PI), vh, vl);
-      v = make_float2(vh, vl);
     }
     s_out[r][c] = v;
   }
@@ -344,8 +367,8 @@ cudaError_t launch_far_df(const DevGeom& g, int* err, cudaStream_t s) {
   int nb = (int)(g.nt_pad / DF_TILE);
   int64_t tiles = (int64_t)nb * (nb + 1) / 2;
   if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
-  far_df_kernel<false><<<(unsigned)tiles, 256, 0, s>>>(g.d_cen, g.d_qoff, g.d_area, g.d_tri, nb, g.nt, g.nt,
-                                                       g.d_V, 0, err);
+  far_df_kernel<false><<<(unsigned)tiles, 256, 0, s>>>(g.d_cen, g.d_qoff, g.d_area, g.d_cendf, g.d_areadf,
+                                                       g.d_tri, nb, g.nt, g.nt, g.d_V, 0, err);
   return cudaGetLastError();
 }
 
@@ -355,8 +378,8 @@ cudaError_t launch_far_df_panel(const DevGeom& g, int tb0, int ntb, int* err, cu
   int64_t tiles = (int64_t)ntb * nb;
   if (tiles <= 0) return cudaSuccess;
   if (tiles > 0x7fffffff) return cudaErrorInvalidValue;
-  far_df_kernel<true><<<(unsigned)tiles, 256, 0, s>>>(g.d_cen, g.d_qoff, g.d_area, g.d_tri, nb, g.nt, g.nt,
-                                                      g.d_V, tb0, err);
+  far_df_kernel<true><<<(unsigned)tiles, 256, 0, s>>>(g.d_cen, g.d_qoff, g.d_area, g.d_cendf, g.d_areadf,
+                                                      g.d_tri, nb, g.nt, g.nt, g.d_V, tb0, err);
   return cudaGetLastError();
 }
 

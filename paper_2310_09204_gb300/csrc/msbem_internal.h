@@ -102,6 +102,8 @@ struct DevGeom {
   double* d_cen = nullptr;       // [nt_pad][3] centroids
   float* d_qoff = nullptr;       // [nt_pad][6][3][2] point - centroid as (hi, lo) floats
   double* d_area = nullptr;      // [nt_pad]
+  float2* d_cendf = nullptr;     // [nt_pad][3] centroids as (hi, lo) floats
+  float2* d_areadf = nullptr;    // [nt_pad] areas as (hi, lo) floats
   int32_t* d_tri = nullptr;      // [nt_pad][3] (padding: -1)
   double* d_xyz = nullptr;       // [nv][3]
   NearPair* d_near = nullptr;    // [n_near]
