@@ -27,8 +27,12 @@ __global__ void gather_blocks_kernel(const float* __restrict__ Wh, const float* 
                                      int wb_diag, double* __restrict__ out) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= prefix2[nblk]) return;
-  int b = 0;
-  while (b + 1 < nblk && prefix2[b + 1] <= t) ++b;
+  // the block of entry t: largest b with prefix2[b] <= t (binary search)
+  int b = 0, hi = nblk - 1;
+  while (b < hi) {
+    const int mid = (b + hi + 1) >> 1;
+    if (prefix2[mid] <= t) b = mid; else hi = mid - 1;
+  }
   const int64_t n = bptr[b + 1] - bptr[b];
   const int64_t e = t - prefix2[b];
   const int64_t i = e / n, j = e % n;
