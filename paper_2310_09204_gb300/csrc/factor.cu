@@ -302,7 +302,7 @@ struct Bgj32Args {
   const int32_t* order;   // matrix ids sorted by size (descending)
   const int64_t* pt1;     // prefix over sorted matrices of tiles per side
   const int64_t* pt2;     // prefix of tiles^2
-  const int64_t* pt3;     // prefix of tiles x column-tile groups (update CTAs)
+  const int64_t* pt3;     // prefix of 64 x 64 update tiles
   const int64_t* soff;    // prefix of n * GB (scratch panels), sorted order
   float* Pf;              // [sorted][GB*GB]
   float* Cf;              // [soff] n x GB
@@ -386,73 +386,69 @@ __global__ void __launch_bounds__(256) bgj32_panel_kernel(Bgj32Args g, int activ
   }
 }
 
-// One CTA per (row tile I, group of BGJ32_JG column tiles): the left factor
-// (C'_I, or P for the pivot row) is loaded once and reused across the group.
-#define BGJ32_JG 8
+// Update of one 64 x 64 tile per CTA, 4 x 4 outputs per thread.  With K the
+// pivot rows / columns [k0, k0 + kb), L(r) = P[r - k0] for r in K, else C'_r,
+// and R[m][c] the old A[k0 + m][c]:
+//   A[r][c] = L(r)[c - k0]                         for c in K,
+//   A[r][c] = [r not in K] A[r][c] + L(r) . R[:, c]  otherwise,
+// which is the scalar Gauss-Jordan step on 32 pivots at once.
+#define UT 64
 __global__ void __launch_bounds__(256) bgj32_update_kernel(Bgj32Args g, int active, int64_t k0) {
-  __shared__ float sL[GB][GB + 1];
-  __shared__ float sR[GB][GB + 1];
+  __shared__ __align__(16) float sLT[GB][UT + 4];   // sLT[m][i] = L(r0 + i)[m] (padded: 4-way stores)
+  __shared__ __align__(16) float sR[GB][UT];    // sR[m][j]  = R[m][c0 + j]
   const int64_t t = blockIdx.x;
   const int a = find_prefix(g.pt3, active, t);
   const int b = g.order[a];
   const int64_t n = g.bsize[b];
-  const int nti = (int)((n + GB - 1) / GB);
-  const int njg = (nti + BGJ32_JG - 1) / BGJ32_JG;
+  const int nt = (int)((n + UT - 1) / UT);
   const int64_t loc = t - g.pt3[a];
-  const int I = (int)(loc / njg), jg = (int)(loc % njg);
-  const int kt = (int)(k0 / GB);
+  const int64_t r0 = (loc / nt) * UT, c0 = (loc % nt) * UT;
   const int kb = (int)(n - k0 < GB ? n - k0 : GB);
   float* A = g.Ap[b];
   const float* C = g.Cf + g.soff[a];
   const float* R = g.Rf + g.soff[a];
   const float* P = g.Pf + (int64_t)a * GB * GB;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t r0 = (int64_t)I * GB;
-  for (int i = ty; i < GB; i += 8) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < GB * UT; e += 256) {
+    const int i = e / GB, m = e % GB;           // consecutive threads: consecutive m (one row of L)
+    const int64_t r = r0 + i;
     float v = 0.f;
-    if (I == kt) {
-      if (i < kb && tx < kb) v = P[i * GB + tx];
-    } else {
-      const int64_t row = r0 + i;
-      if (row < n && tx < kb) v = C[row * GB + tx];
-    }
-    sL[i][tx] = v;
+    if (r < n && m < kb) v = (r >= k0 && r < k0 + kb) ? P[(r - k0) * GB + m] : C[r * GB + m];
+    sLT[m][i] = v;
+    const int mm = e / UT, jj = e % UT;         // consecutive threads: consecutive columns
+    const int64_t c = c0 + jj;
+    sR[mm][jj] = (mm < kb && c < n) ? R[mm * n + c] : 0.f;
   }
-  const int J1 = min(nti, (jg + 1) * BGJ32_JG);
-  for (int J = jg * BGJ32_JG; J < J1; ++J) {
-    const int64_t c0 = (int64_t)J * GB;
-    if (J == kt) {
-      // the pivot column: P on the pivot block, C'_I elsewhere
-      for (int i = ty; i < GB; i += 8) {
-        const int64_t row = r0 + i;
-        if (I == kt) {
-          if (i < kb && tx < kb) A[(k0 + i) * n + k0 + tx] = P[i * GB + tx];
-        } else if (row < n && tx < kb) {
-          A[row * n + k0 + tx] = C[row * GB + tx];
-        }
-      }
-      continue;
-    }
-    __syncthreads();   // the previous tile's reads of sR are done (and sL is in place)
-    for (int i = ty; i < GB; i += 8) {
-      const int64_t col = c0 + tx;
-      sR[i][tx] = (i < kb && col < n) ? R[i * n + col] : 0.f;
-    }
-    __syncthreads();
-    const int64_t col = c0 + tx;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int m = 0; m < kb; ++m) {
-      const float r = sR[m][tx];
+  __syncthreads();
+  const int ty = tid >> 4, tx = tid & 15;       // rows 4ty .. 4ty+3, columns 4tx .. 4tx+3
+  float acc[4][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(sL[ty + 8 * q][m], r, acc[q]);
-    }
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = ty + 8 * q;
-      const int64_t row = r0 + i;
-      if (row >= n || col >= n) continue;
-      if (I == kt && i >= kb) continue;
-      A[row * n + col] = (I == kt) ? acc[q] : A[row * n + col] + acc[q];
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  for (int m = 0; m < kb; ++m) {
+    const float4 l = *(const float4*)&sLT[m][4 * ty];
+    const float4 rr = *(const float4*)&sR[m][4 * tx];
+    const float lv[4] = {l.x, l.y, l.z, l.w}, rv[4] = {rr.x, rr.y, rr.z, rr.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(lv[u], rv[v], acc[u][v]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t r = r0 + 4 * ty + u;
+    if (r >= n) continue;
+    const bool rK = r >= k0 && r < k0 + kb;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t c = c0 + 4 * tx + v;
+      if (c >= n) continue;
+      float* dst = A + r * n + c;
+      if (c >= k0 && c < k0 + kb)
+        *dst = sLT[c - k0][4 * ty + u];
+      else
+        *dst = (rK ? 0.f : *dst) + acc[u][v];
     }
   }
 }
@@ -552,7 +548,8 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
     const int64_t nti = (n + GB - 1) / GB;
     pt1[a + 1] = pt1[a] + nti;
     pt2[a + 1] = pt2[a] + nti * nti;
-    pt3[a + 1] = pt3[a] + nti * ((nti + BGJ32_JG - 1) / BGJ32_JG);
+    const int64_t nt64 = (n + UT - 1) / UT;
+    pt3[a + 1] = pt3[a] + nt64 * nt64;
     soff[a + 1] = soff[a] + n * GB;
     elems += n * n;
   }
