@@ -263,45 +263,28 @@ __global__ void __launch_bounds__(256) near_df_kernel(const __grid_constant__ GL
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= npairs) return;
   const NearPair pr = pairs[w];
-  // the pair's FP64 set-up (areas, edge vectors and their float-pair splits)
-  // once per pair on lane 0, then broadcast: the other lanes issue no FP64
-  float2 v0[3], v1[3], v2[3], v3[3];
-  double aT = 0.0, aS = 0.0;
-  if (lane == 0) {
-    double P[9], Q[9];
+  double P[9], Q[9];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        P[3 * i + k] = xyz[3 * (int64_t)pr.v[i] + k];
-        Q[3 * i + k] = xyz[3 * (int64_t)pr.v[3 + i] + k];
-      }
-    aT = tri_area_d(P);
-    aS = tri_area_d(Q);
-    double ev[4][3];
-    // edge vectors (FP64 differences), split to float pairs
     for (int k = 0; k < 3; ++k) {
-      ev[0][k] = P[3 + k] - P[k];      // identical: e1 | edge: e | vertex: p1
-      ev[1][k] = P[6 + k] - P[3 + k];  // identical: e2 | edge: c | vertex: p2
-      ev[2][k] = Q[6 + k] - Q[3 + k];  //                edge: d | vertex: q2
-      ev[3][k] = Q[3 + k] - Q[k];      //                          vertex: q1
+      P[3 * i + k] = xyz[3 * (int64_t)pr.v[i] + k];
+      Q[3 * i + k] = xyz[3 * (int64_t)pr.v[3 + i] + k];
     }
-    split3(ev[0], v0);
-    split3(ev[1], v1);
-    split3(ev[2], v2);
-    split3(ev[3], v3);
-  }
-#pragma unroll
+  const double aT = tri_area_d(P), aS = tri_area_d(Q);
+  double ev[4][3];
+  // edge vectors (FP64 differences), split to float pairs
   for (int k = 0; k < 3; ++k) {
-    v0[k].x = __shfl_sync(0xffffffffu, v0[k].x, 0);
-    v0[k].y = __shfl_sync(0xffffffffu, v0[k].y, 0);
-    v1[k].x = __shfl_sync(0xffffffffu, v1[k].x, 0);
-    v1[k].y = __shfl_sync(0xffffffffu, v1[k].y, 0);
-    v2[k].x = __shfl_sync(0xffffffffu, v2[k].x, 0);
-    v2[k].y = __shfl_sync(0xffffffffu, v2[k].y, 0);
-    v3[k].x = __shfl_sync(0xffffffffu, v3[k].x, 0);
-    v3[k].y = __shfl_sync(0xffffffffu, v3[k].y, 0);
+    ev[0][k] = P[3 + k] - P[k];      // identical: e1 | edge: e | vertex: p1
+    ev[1][k] = P[6 + k] - P[3 + k];  // identical: e2 | edge: c | vertex: p2
+    ev[2][k] = Q[6 + k] - Q[3 + k];  //                edge: d | vertex: q2
+    ev[3][k] = Q[3 + k] - Q[k];      //                          vertex: q1
   }
+  float2 v0[3], v1[3], v2[3], v3[3];
+  split3(ev[0], v0);
+  split3(ev[1], v1);
+  split3(ev[2], v2);
+  split3(ev[3], v3);
   float acch = 0.f, accl = 0.f;
   double pref;
   const float2 one = make_float2(1.f, 0.f);
