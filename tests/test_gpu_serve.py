@@ -144,3 +144,31 @@ def test_concurrent_contexts_assemble_independently():
             t.join()
         for a, b in zip(out, seq):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed-tc"])
+def test_density_bar_in_the_engine(precision):
+    """With density_tol the engine's mixed-precision results (FP32 set-up of
+    the preconditioner, FP32 inner PCG, double-float refinement) meet the 1e-8
+    density bar against the oracle's direct solution, and each is still bit
+    for bit the result it gets alone."""
+    reqs = _requests(24, 41)
+    with M.Server(precision=precision, density_tol=1e-9) as S:
+        for k, g in GEOMS.items():
+            S.add_geometry(k, g)
+        outs = [np.full(S.ndof[k], np.nan) for k, _ in reqs]
+        ids = [S.submit(k, g, o) for (k, g), o in zip(reqs, outs)]
+        S.progress(block=True)
+        res = [S.result(i) for i in ids]
+    pbs = {k: solver.Problem(g) for k, g in GEOMS.items()}
+    for (k, g), x, r in zip(reqs, outs, res):
+        assert r["status"] == 0 and r["refinements"] >= 2
+        xs = pbs[k].direct(g)
+        assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+    with M.Server(precision=precision, density_tol=1e-9) as S:
+        k, g = reqs[5]
+        S.add_geometry(k, GEOMS[k])
+        alone = np.full(S.ndof[k], np.nan)
+        S.submit(k, g, alone)
+        S.progress(block=True)
+    assert np.array_equal(alone, outs[5])
