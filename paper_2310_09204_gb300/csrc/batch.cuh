@@ -58,8 +58,13 @@ __global__ void brhs_kernel(const int64_t* __restrict__ jptr, const double* __re
 __global__ void bsplit_kernel(const double* __restrict__ X, float* __restrict__ Xf, int64_t ldp, int64_t N,
                               int kb);
 
-// Z = M R for all columns (f32: FP32 block inverses and residual)
-void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precondition, int f32, cudaStream_t s);
+// Z = M R for all columns (f32: FP32 block inverses and residual).
+// in_iteration: within a PCG iteration -- the residual's float-pair split Rf
+// is already written (by the residual update), and the launch that ends the
+// application also leaves the partial sums of R . Z in b.part (bdot_kernel's
+// layout); otherwise Rf is made here and no sums are formed.
+void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precondition, int f32, cudaStream_t s,
+                   bool in_iteration);
 
 // One PCG iteration on every running column of the batch (the recursion of
 // Sec. 2.1 per column; columns that are not running are left untouched):

@@ -84,10 +84,13 @@ __global__ void alpha_kernel(double* scal, PcgState* st, double* alpha_hist) {
 }
 
 // x += alpha p; r -= alpha q; partial r.r
+// rf (may be null): r's float-pair split, written beside it for the block
+// solves of the preconditioner that follow
 __global__ void update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
                                  const double* __restrict__ p, const double* __restrict__ q,
                                  const double* __restrict__ scal, int64_t N,
-                                 double* __restrict__ part, const PcgState* __restrict__ st) {
+                                 double* __restrict__ part, float2* __restrict__ rf,
+                                 const PcgState* __restrict__ st) {
   if (st->done) return;
   __shared__ double s[256];
   const double alpha = scal[2];
@@ -96,6 +99,11 @@ __global__ void update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
     x[i] = fma(alpha, p[i], x[i]);
     double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
+    if (rf) {
+      float h, l;
+      split_df(ri, h, l);
+      rf[i] = make_float2(h, l);
+    }
     acc = fma(ri, ri, acc);
   }
   s[threadIdx.x] = acc;
@@ -122,17 +130,12 @@ __global__ void check_kernel(const double* scal, PcgState* st, double* hist) {
 
 // z[D_b[i]] = sum_j Ainv_b[i][j] r[D_b[j]]  (warp per row, rows of all blocks),
 // in double-float from float-pair copies of the block inverses and of r
-__global__ void __launch_bounds__(256) block_apply_kernel(const float2* __restrict__ Ainv,
-                                                          const int64_t* __restrict__ boff,
-                                                          const int64_t* __restrict__ bptr,
-                                                          const int32_t* __restrict__ bdofs,
-                                                          int nblk, int64_t N,
-                                                          const float2* __restrict__ rf,
-                                                          double* __restrict__ z,
-                                                          const PcgState* __restrict__ st) {
-  if (st->done) return;
+__device__ __forceinline__ void block_apply_body(int64_t cta, const float2* __restrict__ Ainv,
+                                                 const int64_t* __restrict__ boff, const int64_t* __restrict__ bptr,
+                                                 const int32_t* __restrict__ bdofs, int nblk, int64_t N,
+                                                 const float2* __restrict__ rf, double* __restrict__ z) {
   const int lane = threadIdx.x & 31;
-  const int64_t rho = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t rho = cta * 8 + (threadIdx.x >> 5);
   if (rho >= N) return;
   int lo = 0, hi = nblk - 1;
   while (lo < hi) {  // last block with bptr[b] <= rho
@@ -159,6 +162,18 @@ __global__ void __launch_bounds__(256) block_apply_kernel(const float2* __restri
     accl = accl + ol + se;
   }
   if (lane == 0) z[d[i]] = df_to_double(acch, accl);
+}
+
+__global__ void __launch_bounds__(256) block_apply_kernel(const float2* __restrict__ Ainv,
+                                                          const int64_t* __restrict__ boff,
+                                                          const int64_t* __restrict__ bptr,
+                                                          const int32_t* __restrict__ bdofs,
+                                                          int nblk, int64_t N,
+                                                          const float2* __restrict__ rf,
+                                                          double* __restrict__ z,
+                                                          const PcgState* __restrict__ st) {
+  if (st->done) return;
+  block_apply_body(blockIdx.x, Ainv, boff, bptr, bdofs, nblk, N, rf, z);
 }
 
 // ---- plain FP64 comparator: W and the block inverses read as FP64 -----------
@@ -248,13 +263,9 @@ __global__ void to_df_kernel(const double* __restrict__ x, float2* __restrict__ 
 
 // t = P^T r (CSC of P), one block per coarse dof (columns of P hold
 // thousands of fine entries)
-__global__ void restrict_kernel(const int64_t* __restrict__ cptr, const int32_t* __restrict__ crow,
-                                const double* __restrict__ cval, int64_t NH,
-                                const double* __restrict__ r, double* __restrict__ t,
-                                const PcgState* __restrict__ st) {
-  if (st->done) return;
-  __shared__ double s[8];
-  const int64_t mu = blockIdx.x;
+__device__ __forceinline__ void restrict_body1(int64_t mu, const int64_t* __restrict__ cptr,
+                                               const int32_t* __restrict__ crow, const double* __restrict__ cval,
+                                               const double* __restrict__ r, double* __restrict__ t, double* s) {
   double acc = 0.0;
   for (int64_t k = cptr[mu] + threadIdx.x; k < cptr[mu + 1]; k += blockDim.x)
     acc = fma(cval[k], r[crow[k]], acc);
@@ -267,6 +278,32 @@ __global__ void restrict_kernel(const int64_t* __restrict__ cptr, const int32_t*
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s[w];
     t[mu] = v;
   }
+}
+
+__global__ void restrict_kernel(const int64_t* __restrict__ cptr, const int32_t* __restrict__ crow,
+                                const double* __restrict__ cval, int64_t NH,
+                                const double* __restrict__ r, double* __restrict__ t,
+                                const PcgState* __restrict__ st) {
+  if (st->done) return;
+  __shared__ double s[8];
+  restrict_body1(blockIdx.x, cptr, crow, cval, r, t, s);
+}
+
+// The block solves (CTAs below nba, 8 rows each) and the coarse restriction
+// (one CTA per coarse dof after them) in one launch: both read r, their
+// outputs are disjoint.
+__global__ void __launch_bounds__(256) block_restrict_kernel(
+    const float2* __restrict__ Ainv, const int64_t* __restrict__ boff, const int64_t* __restrict__ bptr,
+    const int32_t* __restrict__ bdofs, int nblk, int64_t N, const float2* __restrict__ rf, double* __restrict__ z,
+    int64_t nba, const int64_t* __restrict__ cptr, const int32_t* __restrict__ crow,
+    const double* __restrict__ cval, const double* __restrict__ r, double* __restrict__ t,
+    const PcgState* __restrict__ st) {
+  if (st->done) return;
+  __shared__ double s[8];
+  if ((int64_t)blockIdx.x < nba)
+    block_apply_body(blockIdx.x, Ainv, boff, bptr, bdofs, nblk, N, rf, z);
+  else
+    restrict_body1((int64_t)blockIdx.x - nba, cptr, crow, cval, r, t, s);
 }
 
 // u = AHinv t (warp per row)
@@ -295,6 +332,32 @@ __global__ void prolong_kernel(const int64_t* __restrict__ pptr, const int32_t* 
   double acc = 0.0;
   for (int64_t k = pptr[i]; k < pptr[i + 1]; ++k) acc = fma(pval[k], u[pcol[k]], acc);
   z[i] += acc;
+}
+
+// z += P u, and the per-block partial sums of r . z over dot_kernel's row
+// partition (the prolongation fused with the reduction that follows it; the
+// same arithmetic in the same order as the two kernels)
+__global__ void prolong_dot_kernel(const int64_t* __restrict__ pptr, const int32_t* __restrict__ pcol,
+                                   const double* __restrict__ pval, int64_t N, const double* __restrict__ u,
+                                   double* __restrict__ z, const double* __restrict__ r,
+                                   double* __restrict__ part, const PcgState* __restrict__ st) {
+  if (st->done) return;
+  __shared__ double s[256];
+  double dot = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256) {
+    double acc = 0.0;
+    for (int64_t k = pptr[i]; k < pptr[i + 1]; ++k) acc = fma(pval[k], u[pcol[k]], acc);
+    const double zi = z[i] + acc;
+    z[i] = zi;
+    dot = fma(r[i], zi, dot);
+  }
+  s[threadIdx.x] = dot;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
 // beta = rz_new / rz; rz = rz_new
@@ -329,30 +392,53 @@ __global__ void copy_kernel(double* __restrict__ dst, const double* __restrict__
     dst[i] = src[i];
 }
 
+// z = M r.  in_iteration: inside a PCG iteration -- r's float-pair split is
+// already in g.d_rf (written by the residual update), and the last launch
+// also leaves the partial sums of r . z in part (dot_kernel's layout).
 static void apply_M(DevGeom& g, const double* r, double* z, double* t, double* u, int precondition,
-                    bool plain, const PcgState* st, cudaStream_t s) {
+                    bool plain, const PcgState* st, cudaStream_t s, bool in_iteration = false,
+                    double* part = nullptr) {
   const int64_t N = g.ndof;
   if (!precondition) {
     copy_kernel<<<RED_BLOCKS, 256, 0, s>>>(z, r, N, st);
     ++g.launches;
+    if (in_iteration) {
+      dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
+      ++g.launches;
+    }
     return;
   }
-  if (plain) {
-    block_apply64_kernel<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(g.d_binv, g.d_boff, g.d_bptr, g.d_bdofs,
-                                                                  (int)g.n_blocks, N, r, z, st);
-    g.launches += 1;
-  } else {
-    to_df_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, g.d_rf, N, st);
-    block_apply_kernel<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
-                                                                (int)g.n_blocks, N, g.d_rf, z, st);
-    g.launches += 2;
-  }
   const int64_t NH = g.use_coarse ? g.n_coarse : 0;
+  const int64_t nba = (N + 7) / 8;
+  if (plain) {
+    block_apply64_kernel<<<(unsigned)nba, 256, 0, s>>>(g.d_binv, g.d_boff, g.d_bptr, g.d_bdofs,
+                                                        (int)g.n_blocks, N, r, z, st);
+    g.launches += 1;
+    if (NH > 0) {
+      restrict_kernel<<<(unsigned)NH, 256, 0, s>>>(g.d_cptr, g.d_crow, g.d_cval, NH, r, t, st);
+      ++g.launches;
+    }
+  } else {
+    if (!in_iteration) {
+      to_df_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, g.d_rf, N, st);
+      ++g.launches;
+    }
+    // block solves and coarse restriction: one launch
+    block_restrict_kernel<<<(unsigned)(nba + NH), 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
+                                                               (int)g.n_blocks, N, g.d_rf, z, nba, g.d_cptr,
+                                                               g.d_crow, g.d_cval, r, t, st);
+    ++g.launches;
+  }
   if (NH > 0) {
-    restrict_kernel<<<(unsigned)NH, 256, 0, s>>>(g.d_cptr, g.d_crow, g.d_cval, NH, r, t, st);
     coarse_solve_kernel<<<(unsigned)((NH + 7) / 8), 256, 0, s>>>(g.d_AHinv, NH, t, u, st);
-    prolong_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(g.d_pptr, g.d_pcol, g.d_pval, N, u, z, st);
-    g.launches += 3;
+    if (in_iteration)
+      prolong_dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(g.d_pptr, g.d_pcol, g.d_pval, N, u, z, r, part, st);
+    else
+      prolong_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(g.d_pptr, g.d_pcol, g.d_pval, N, u, z, st);
+    g.launches += 2;
+  } else if (in_iteration) {
+    dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
+    ++g.launches;
   }
 }
 
@@ -375,8 +461,9 @@ static void enqueue_iteration(DevGeom& g, int precondition, bool plain, double* 
   double* part = scal + 16;
   const unsigned gemv_blocks = matvec_blocks(N, 0);
   if (count_only) {
-    g.launches += 10 + 1 + ((precondition && !plain) ? 1 : 0) +
-                  ((precondition && g.use_coarse && g.n_coarse > 0) ? 3 : 0);
+    // 9 + the product + the preconditioner's launches (which end with r . z)
+    const bool coarse = precondition && g.use_coarse && g.n_coarse > 0;
+    g.launches += 9 + (!precondition ? 2 : plain ? (coarse ? 4 : 2) : (coarse ? 3 : 2));
     return;
   }
   double* alpha_h = hist + hcap + 1;
@@ -387,15 +474,16 @@ static void enqueue_iteration(DevGeom& g, int precondition, bool plain, double* 
     launch_matvec(0, g.tm_W, g.tm_p, N, 1, p, q, part, &st->done, &st->err, s);
   reduce_kernel<<<1, 256, 0, s>>>(part, plain ? (unsigned)((N + 15) / 16) : gemv_blocks, scal + 1, st);
   alpha_kernel<<<1, 1, 0, s>>>(scal, st, alpha_h);
-  update_xr_kernel<<<RED_BLOCKS, 256, 0, s>>>(x, r, p, q, scal, N, part, st);
+  update_xr_kernel<<<RED_BLOCKS, 256, 0, s>>>(x, r, p, q, scal, N, part,
+                                             (precondition && !plain) ? g.d_rf : nullptr, st);
   reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 3, st);
   check_kernel<<<1, 1, 0, s>>>(scal, st, hist);
-  apply_M(g, r, z, t, u, precondition, plain, st, s);
-  dot_kernel<<<RED_BLOCKS, 256, 0, s>>>(r, z, N, part, st);
+  // z = M r and the partial sums of r . z (its last launch carries them)
+  apply_M(g, r, z, t, u, precondition, plain, st, s, true, part);
   reduce_kernel<<<1, 256, 0, s>>>(part, RED_BLOCKS, scal + 4, st);
   beta_kernel<<<1, 1, 0, s>>>(scal, st, beta_h);
   update_p_kernel<<<RED_BLOCKS, 256, 0, s>>>(p, g.d_pfp, g.ldw, z, scal, N, 0, st);
-  g.launches += 10;
+  g.launches += 9;
 }
 
 void drop_pcg_graphs(DevGeom& g) {

@@ -71,10 +71,12 @@ __global__ void balpha_kernel(ColState* cs, double* alpha_hist, int hcap, const 
 }
 
 // x_c += alpha_c p_c; r_c -= alpha_c q_c; per-column partial r.r
+// Rf (may be null): the residual's float-pair split, written beside it for
+// the block solves of the preconditioner that follow
 __global__ void bupdate_xr_kernel(double* __restrict__ X, double* __restrict__ R,
                                   const double* __restrict__ P, const double* __restrict__ Q, int64_t N,
                                   int kb, const ColState* __restrict__ cs, double* __restrict__ part,
-                                  const BatchState* __restrict__ bs) {
+                                  float2* __restrict__ Rf, const BatchState* __restrict__ bs) {
   if (bs->all_done) return;
   __shared__ double s[256];
   const int c = blockIdx.y;
@@ -88,6 +90,11 @@ __global__ void bupdate_xr_kernel(double* __restrict__ X, double* __restrict__ R
       X[o] = fma(alpha, P[o], X[o]);
       ri = fma(-alpha, Q[o], ri);
       R[o] = ri;
+    }
+    if (Rf) {
+      float h, l;
+      split_df(ri, h, l);
+      Rf[o] = make_float2(h, l);
     }
     acc = fma(ri, ri, acc);
   }
@@ -145,19 +152,15 @@ __global__ void bto_df_kernel(const double* __restrict__ X, float2* __restrict__
 #define BA_KC 128
 #define BA_PAD 132   // row pitch of the staged planes (keeps float4 reads aligned, staging 2-way)
 template <bool F32>
-__global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restrict__ Ainv,
-                                                          const int64_t* __restrict__ boff,
-                                                          const int64_t* __restrict__ bptr,
-                                                          const int32_t* __restrict__ bdofs,
-                                                          const int32_t* __restrict__ tiles,
-                                                          const float2* __restrict__ Rf,
-                                                          double* __restrict__ Z, int kb,
-                                                          const BatchState* __restrict__ bs) {
-  if (bs->all_done) return;
-  __shared__ __align__(16) float sRh[BK * BA_PAD];
-  __shared__ __align__(16) float sRl[BK * BA_PAD];
-  const int b = tiles[2 * blockIdx.x];
-  const int64_t r0 = tiles[2 * blockIdx.x + 1];
+__device__ __forceinline__ void block_tile_body(int tile, const float2* __restrict__ Ainv,
+                                                const int64_t* __restrict__ boff,
+                                                const int64_t* __restrict__ bptr,
+                                                const int32_t* __restrict__ bdofs,
+                                                const int32_t* __restrict__ tiles,
+                                                const float2* __restrict__ Rf, double* __restrict__ Z,
+                                                int kb, float* sRh, float* sRl) {
+  const int b = tiles[2 * tile];
+  const int64_t r0 = tiles[2 * tile + 1];
   const int64_t n = bptr[b + 1] - bptr[b];
   const int32_t* d = bdofs + bptr[b];
   const float2* A = Ainv + boff[b];
@@ -241,13 +244,26 @@ __global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restri
   }
 }
 
-// T[mu][c] = sum_k P[row_k, mu] R[row_k][c]  (block per coarse dof)
-__global__ void brestrict_kernel(const int64_t* __restrict__ cptr, const int32_t* __restrict__ crow,
-                                 const double* __restrict__ cval, const double* __restrict__ R, int kb,
-                                 double* __restrict__ T, const BatchState* __restrict__ bs) {
+template <bool F32>
+__global__ void __launch_bounds__(256) bblock_tile_kernel(const float2* __restrict__ Ainv,
+                                                          const int64_t* __restrict__ boff,
+                                                          const int64_t* __restrict__ bptr,
+                                                          const int32_t* __restrict__ bdofs,
+                                                          const int32_t* __restrict__ tiles,
+                                                          const float2* __restrict__ Rf,
+                                                          double* __restrict__ Z, int kb,
+                                                          const BatchState* __restrict__ bs) {
   if (bs->all_done) return;
-  __shared__ double s[8][BK];
-  const int64_t mu = blockIdx.x;
+  __shared__ __align__(16) float sRh[BK * BA_PAD];
+  __shared__ __align__(16) float sRl[BK * BA_PAD];
+  block_tile_body<F32>(blockIdx.x, Ainv, boff, bptr, bdofs, tiles, Rf, Z, kb, sRh, sRl);
+}
+
+// T[mu][c] = sum_k P[row_k, mu] R[row_k][c]  (block per coarse dof)
+__device__ __forceinline__ void restrict_body(int64_t mu, const int64_t* __restrict__ cptr,
+                                              const int32_t* __restrict__ crow, const double* __restrict__ cval,
+                                              const double* __restrict__ R, int kb, double* __restrict__ T,
+                                              double (*s)[BK]) {
   double acc[BK];
 #pragma unroll
   for (int c = 0; c < BK; ++c) acc[c] = 0.0;
@@ -270,6 +286,35 @@ __global__ void brestrict_kernel(const int64_t* __restrict__ cptr, const int32_t
     double v = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s[w][threadIdx.x];
     T[mu * kb + threadIdx.x] = v;
+  }
+}
+
+__global__ void brestrict_kernel(const int64_t* __restrict__ cptr, const int32_t* __restrict__ crow,
+                                 const double* __restrict__ cval, const double* __restrict__ R, int kb,
+                                 double* __restrict__ T, const BatchState* __restrict__ bs) {
+  if (bs->all_done) return;
+  __shared__ double s[8][BK];
+  restrict_body(blockIdx.x, cptr, crow, cval, R, kb, T, s);
+}
+
+// The subspace solves and the coarse restriction in one launch: CTAs below
+// ntiles apply the block inverses to their tiles, the others restrict the
+// residual onto one coarse dof each (the two read the residual and write
+// disjoint outputs).
+template <bool F32>
+__global__ void __launch_bounds__(256) bblock_restrict_kernel(
+    const float2* __restrict__ Ainv, const int64_t* __restrict__ boff, const int64_t* __restrict__ bptr,
+    const int32_t* __restrict__ bdofs, const int32_t* __restrict__ tiles, int ntiles,
+    const float2* __restrict__ Rf, double* __restrict__ Z, int kb, const int64_t* __restrict__ cptr,
+    const int32_t* __restrict__ crow, const double* __restrict__ cval, const double* __restrict__ R,
+    double* __restrict__ T, const BatchState* __restrict__ bs) {
+  if (bs->all_done) return;
+  __shared__ __align__(16) float sRh[BK * BA_PAD];
+  __shared__ __align__(16) float sRl[BK * BA_PAD];
+  if ((int)blockIdx.x < ntiles) {
+    block_tile_body<F32>(blockIdx.x, Ainv, boff, bptr, bdofs, tiles, Rf, Z, kb, sRh, sRl);
+  } else {
+    restrict_body((int64_t)blockIdx.x - ntiles, cptr, crow, cval, R, kb, T, (double (*)[BK])sRh);
   }
 }
 
@@ -298,6 +343,35 @@ __global__ void bprolong_kernel(const int64_t* __restrict__ pptr, const int32_t*
   double acc = 0.0;
   for (int64_t k = pptr[i]; k < pptr[i + 1]; ++k) acc = fma(pval[k], U[(int64_t)pcol[k] * kb + c], acc);
   Z[e] += acc;
+}
+
+// Z[i][c] += sum P[i, mu] U[mu][c], and the per-block partial sums of
+// R[:, c] . Z[:, c] over the same row partition as bdot_kernel (the coarse
+// prolongation fused with the r.z reduction that follows it; the same
+// arithmetic in the same order as the two kernels)
+__global__ void bprolong_dot_kernel(const int64_t* __restrict__ pptr, const int32_t* __restrict__ pcol,
+                                    const double* __restrict__ pval, int64_t N, const double* __restrict__ U,
+                                    int kb, double* __restrict__ Z, const double* __restrict__ R,
+                                    double* __restrict__ part, const BatchState* __restrict__ bs) {
+  if (bs->all_done) return;
+  __shared__ double s[256];
+  const int c = blockIdx.y;
+  double dot = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256) {
+    const int64_t o = i * kb + c;
+    double acc = 0.0;
+    for (int64_t k = pptr[i]; k < pptr[i + 1]; ++k) acc = fma(pval[k], U[(int64_t)pcol[k] * kb + c], acc);
+    const double z = Z[o] + acc;
+    Z[o] = z;
+    dot = fma(R[o], z, dot);
+  }
+  s[threadIdx.x] = dot;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(int64_t)c * gridDim.x + blockIdx.x] = s[0];
 }
 
 __global__ void bcopy_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t n,
@@ -363,31 +437,48 @@ __global__ void btranspose_kernel(const double* __restrict__ X, int64_t N, int k
 }
 
 
-void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precondition, int f32, cudaStream_t s) {
+void apply_M_batch(DevGeom& g, const BatchBuffers& b, int kb, int precondition, int f32, cudaStream_t s,
+                   bool in_iteration) {
   const int64_t N = g.ndof;
+  const dim3 rgrid(BRED, kb);
   if (!precondition) {
     bcopy_kernel<<<kStrideBlocks, 256, 0, s>>>(b.Z, b.R, N * kb, b.bs);
     ++g.launches;
+    if (in_iteration) {
+      bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
+      ++g.launches;
+    }
     return;
   }
-  bto_df_kernel<<<kStrideBlocks, 256, 0, s>>>(b.R, b.Rf, N * kb, b.bs);
-  if (g.n_btiles > 0) {
-    if (f32)
-      bblock_tile_kernel<true><<<(unsigned)g.n_btiles, 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
-                                                                    g.d_btile, b.Rf, b.Z, kb, b.bs);
-    else
-      bblock_tile_kernel<false><<<(unsigned)g.n_btiles, 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs,
-                                                                     g.d_btile, b.Rf, b.Z, kb, b.bs);
+  // in an iteration the residual's float-pair split was written by the update
+  if (!in_iteration) {
+    bto_df_kernel<<<kStrideBlocks, 256, 0, s>>>(b.R, b.Rf, N * kb, b.bs);
     ++g.launches;
   }
-  ++g.launches;
   const int64_t NH = g.use_coarse ? g.n_coarse : 0;
+  // block solves and coarse restriction: one launch
+  const unsigned nt = (unsigned)g.n_btiles, grid = nt + (unsigned)NH;
+  if (grid > 0) {
+    if (f32)
+      bblock_restrict_kernel<true><<<grid, 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs, g.d_btile, (int)nt,
+                                                        b.Rf, b.Z, kb, g.d_cptr, g.d_crow, g.d_cval, b.R, b.T, b.bs);
+    else
+      bblock_restrict_kernel<false><<<grid, 256, 0, s>>>(g.d_binvf, g.d_boff, g.d_bptr, g.d_bdofs, g.d_btile,
+                                                         (int)nt, b.Rf, b.Z, kb, g.d_cptr, g.d_crow, g.d_cval, b.R,
+                                                         b.T, b.bs);
+    ++g.launches;
+  }
   if (NH > 0) {
-    brestrict_kernel<<<(unsigned)NH, 256, 0, s>>>(g.d_cptr, g.d_crow, g.d_cval, b.R, kb, b.T, b.bs);
     bcoarse_kernel<<<(unsigned)((NH * kb + 127) / 128), 128, 0, s>>>(g.d_AHinv, NH, b.T, kb, b.U, b.bs);
-    bprolong_kernel<<<(unsigned)((N * kb + 255) / 256), 256, 0, s>>>(g.d_pptr, g.d_pcol, g.d_pval, N, b.U,
-                                                                      kb, b.Z, b.bs);
-    g.launches += 3;
+    if (in_iteration)
+      bprolong_dot_kernel<<<rgrid, 256, 0, s>>>(g.d_pptr, g.d_pcol, g.d_pval, N, b.U, kb, b.Z, b.R, b.part, b.bs);
+    else
+      bprolong_kernel<<<(unsigned)((N * kb + 255) / 256), 256, 0, s>>>(g.d_pptr, g.d_pcol, g.d_pval, N, b.U,
+                                                                        kb, b.Z, b.bs);
+    g.launches += 2;
+  } else if (in_iteration) {
+    bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
+    ++g.launches;
   }
 }
 
@@ -457,15 +548,16 @@ void enqueue_batch_iteration(DevGeom& g, const BatchBuffers& b, int kb, int prec
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, (int)matvec_blocks(N, mv_mode == 1 ? 1 : 0), b.cs,
                                     offsetof(ColState, pq), b.bs);
   balpha_kernel<<<1, BK, 0, s>>>(b.cs, alpha_h, hcap, b.bs);
-  bupdate_xr_kernel<<<rgrid, 256, 0, s>>>(b.X, b.R, b.P, b.Q, N, kb, b.cs, b.part, b.bs);
+  bupdate_xr_kernel<<<rgrid, 256, 0, s>>>(b.X, b.R, b.P, b.Q, N, kb, b.cs, b.part, precondition ? b.Rf : nullptr,
+                                          b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rr), b.bs);
   bcheck_kernel<<<1, 32, 0, s>>>(b.cs, rel_h, hcap, b.bs);
-  apply_M_batch(g, b, kb, precondition, mv_mode == 1 || mv_mode == 4, s);
-  bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
+  // z = M r and the partial sums of r . z (its last launch carries them)
+  apply_M_batch(g, b, kb, precondition, mv_mode == 1 || mv_mode == 4, s, true);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz_new), b.bs);
   bbeta_kernel<<<1, BK, 0, s>>>(b.cs, beta_h, hcap, b.bs);
   bupdate_p_kernel<<<kStrideBlocks, 256, 0, s>>>(b.P, b.Pf, g.ldw, b.Z, N, kb, b.cs, 0, b.bs);
-  g.launches += mv_mode >= 3 ? 9 : 10 + (split > 1 ? 1 : 0);   // (the tensor-core product counts its own)
+  g.launches += mv_mode >= 3 ? 8 : 9 + (split > 1 ? 1 : 0);   // (the tensor-core product counts its own)
 }
 
 // PCG from X = 0 on the kb right-hand sides Rin (device, N x kb row-major);
@@ -529,7 +621,7 @@ static cudaError_t pcg_batch_core(DevGeom& g, int kb, double rtol, int maxit, in
   const dim3 rgrid(BRED, kb);
   bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.R, N, kb, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, nL2), b.bs);
-  apply_M_batch(g, b, kb, precondition, mv_mode == 1 || mv_mode == 4, s);
+  apply_M_batch(g, b, kb, precondition, mv_mode == 1 || mv_mode == 4, s, false);
   bupdate_p_kernel<<<kStrideBlocks, 256, 0, s>>>(b.P, b.Pf, g.ldw, b.Z, N, kb, b.cs, 1, b.bs);
   bdot_kernel<<<rgrid, 256, 0, s>>>(b.R, b.Z, N, kb, b.part, b.bs);
   breduce_kernel<<<kb, 256, 0, s>>>(b.part, BRED, b.cs, offsetof(ColState, rz), b.bs);

@@ -634,7 +634,7 @@ void schedule(msbem_server* S, GeomEntry& e) {
     s_copy_cols<<<grid, 256, 0, s>>>(B.b.X, nullptr, N, kb, B.mask);
     bdot_kernel<<<rgrid, 256, 0, s>>>(B.b.R, B.b.R, N, kb, B.b.part, B.fl);
     s_reduce_cols<<<kb, 256, 0, s>>>(B.b.part, BRED, B.b.cs, offsetof(ColState, nL2), B.mask);
-    apply_M_batch(g, B.b, kb, 1, f32, s);
+    apply_M_batch(g, B.b, kb, 1, f32, s, false);
     s_setp_cols<<<grid, 256, 0, s>>>(B.b.P, B.b.Pf, g.ldw, B.b.Z, N, kb, B.mask);
     bdot_kernel<<<rgrid, 256, 0, s>>>(B.b.R, B.b.Z, N, kb, B.b.part, B.fl);
     s_reduce_cols<<<kb, 256, 0, s>>>(B.b.part, BRED, B.b.cs, offsetof(ColState, rz), B.mask);
