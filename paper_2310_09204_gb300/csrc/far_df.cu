@@ -116,7 +116,7 @@ __device__ __forceinline__ void far_row(float Uxh, float Uxl, float Uyh, float U
 // PANEL: rows of tiles tb0 .. (V holds triangle rows tb0*64 ..), every column
 // tile, no mirrored write; otherwise the upper triangle of tiles, mirrored.
 template <bool PANEL>
-__global__ void __launch_bounds__(256) far_df_kernel(const double* __restrict__ cen,
+__global__ void __launch_bounds__(256, 3) far_df_kernel(const double* __restrict__ cen,
                                                      const float* __restrict__ qoff,
                                                      const double* __restrict__ area,
                                                      const float2* __restrict__ cendf,
