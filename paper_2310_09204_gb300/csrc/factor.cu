@@ -296,6 +296,10 @@ __global__ void __launch_bounds__(256) bgj_update_kernel(BgjArgs g, int active, 
 // of a double-float product of 13 FP32 operations, and the matrices stay in
 // FP32 (half the bytes per pass).  The result is symmetrised.
 // ---------------------------------------------------------------------------
+// row stride of the FP32 copies: n rounded up to 4 floats, so that every row
+// starts on a 16-byte boundary (vector accesses in the update)
+__host__ __device__ __forceinline__ int64_t f32_ld(int64_t n) { return (n + 3) & ~(int64_t)3; }
+
 struct Bgj32Args {
   float* const* Ap;       // per matrix id: the matrix (row-major FP32, bsize x bsize)
   const int64_t* bsize;   // per matrix id
@@ -319,9 +323,10 @@ __global__ void __launch_bounds__(1024) bgj32_pivot_kernel(Bgj32Args g, int64_t 
   const int64_t n = g.bsize[b];
   const int kb = (int)(n - k0 < GB ? n - k0 : GB);
   const float* A = g.Ap[b];
+  const int64_t ld = f32_ld(n);
   for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
     const int i = e / GB, j = e % GB;
-    S[i][j] = (i < kb && j < kb) ? A[(k0 + i) * n + k0 + j] : (i == j ? 1.0f : 0.0f);
+    S[i][j] = (i < kb && j < kb) ? A[(k0 + i) * ld + k0 + j] : (i == j ? 1.0f : 0.0f);
   }
   __syncthreads();
   for (int k = 0; k < GB; ++k) {
@@ -367,14 +372,14 @@ __global__ void __launch_bounds__(256) bgj32_panel_kernel(Bgj32Args g, int activ
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int m = ty; m < kb; m += 8) {
     const int64_t col = r0 + tx;
-    if (col < n) R[m * n + col] = A[(k0 + m) * n + col];
+    if (col < n) R[m * n + col] = A[(k0 + m) * f32_ld(n) + col];
   }
   if (r0 == k0) return;
   const float* P = g.Pf + (int64_t)a * GB * GB;
   for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) sP[e / GB][e % GB] = P[e];
   for (int i = ty; i < GB; i += 8) {
     const int64_t row = r0 + i;
-    sA[i][tx] = (row < n && tx < kb) ? A[row * n + k0 + tx] : 0.f;
+    sA[i][tx] = (row < n && tx < kb) ? A[row * f32_ld(n) + k0 + tx] : 0.f;
   }
   __syncthreads();
   for (int i = ty; i < GB; i += 8) {
@@ -435,20 +440,34 @@ __global__ void __launch_bounds__(256) bgj32_update_kernel(Bgj32Args g, int acti
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(lv[u], rv[v], acc[u][v]);
   }
+  const int64_t ld = f32_ld(n);
+  const int64_t cb = c0 + 4 * tx;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int64_t r = r0 + 4 * ty + u;
     if (r >= n) continue;
     const bool rK = r >= k0 && r < k0 + kb;
+    float* dst = A + r * ld + cb;
+    if (cb + 3 < n) {
+      // four columns in one 16-byte access (rows start on 16-byte boundaries)
+      float4 o = rK ? make_float4(0.f, 0.f, 0.f, 0.f) : *(const float4*)dst;
+      float ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int64_t c = c0 + 4 * tx + v;
-      if (c >= n) continue;
-      float* dst = A + r * n + c;
-      if (c >= k0 && c < k0 + kb)
-        *dst = sLT[c - k0][4 * ty + u];
-      else
-        *dst = (rK ? 0.f : *dst) + acc[u][v];
+      for (int v = 0; v < 4; ++v) {
+        const int64_t c = cb + v;
+        ov[v] = (c >= k0 && c < k0 + kb) ? sLT[c - k0][4 * ty + u] : ov[v] + acc[u][v];
+      }
+      *(float4*)dst = make_float4(ov[0], ov[1], ov[2], ov[3]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int64_t c = cb + v;
+        if (c >= n) continue;
+        if (c >= k0 && c < k0 + kb)
+          dst[v] = sLT[c - k0][4 * ty + u];
+        else
+          dst[v] = (rK ? 0.f : dst[v]) + acc[u][v];
+      }
     }
   }
 }
@@ -458,11 +477,13 @@ __global__ void __launch_bounds__(256) bgj32_update_kernel(Bgj32Args g, int acti
 __global__ void f64_to_f32_kernel(double* const* src, float* const* dst, const int64_t* bsize,
                                   const int32_t* ids) {
   const int b = ids[blockIdx.y];
-  const int64_t nn = bsize[b] * bsize[b];
+  const int64_t n = bsize[b], ld = f32_ld(n);
   const double* s = src[b];
   float* d = dst[b];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x)
-    d[e] = (float)s[e];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    d[i * ld + j] = (float)s[e];
+  }
 }
 
 __global__ void f32_sym_to_f64_kernel(float* const* src, double* const* dst, const int64_t* bsize,
@@ -472,8 +493,8 @@ __global__ void f32_sym_to_f64_kernel(float* const* src, double* const* dst, con
   const float* s = src[b];
   double* d = dst[b];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / n, j = e - i * n;
-    d[e] = 0.5 * ((double)s[i * n + j] + (double)s[j * n + i]);
+    const int64_t i = e / n, j = e - i * n, ld = f32_ld(n);
+    d[e] = 0.5 * ((double)s[i * ld + j] + (double)s[j * ld + i]);
   }
 }
 
@@ -551,7 +572,7 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
     const int64_t nt64 = (n + UT - 1) / UT;
     pt3[a + 1] = pt3[a] + nt64 * nt64;
     soff[a + 1] = soff[a] + n * GB;
-    elems += n * n;
+    elems += n * f32_ld(n);
   }
   PoolScratch scratch(pool, s);
   cudaError_t e;
@@ -561,7 +582,7 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   int64_t off = 0;
   for (int a = 0; a < nb; ++a) {
     fptr[order[a]] = mats + off;
-    off += bsize[order[a]] * bsize[order[a]];
+    off += bsize[order[a]] * f32_ld(bsize[order[a]]);
   }
   Bgj32Args args{};
   double** d_dptr = nullptr;
