@@ -42,13 +42,13 @@ UNIT = "solves/s"
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # double-float far-field kernel: thread instructions issued per unordered
 # separated pair, from an ncu capture of the h=1/32 book (smsp__inst_executed
-# x active threads per instruction / pairs: 1.514e9 x 29.47 / 1.88e7)
-FP32_OPS_PER_FAR_PAIR = 2370
+# x active threads per instruction / pairs: 1.5236e9 x 29.48 / 1.88e7)
+FP32_OPS_PER_FAR_PAIR = 2389
 # DRAM bytes (read + write) of one far_df_kernel launch, from an ncu capture of
-# the h=1/32 book (6,144 triangles: 1.42 MB read + 258.60 MB written), scaled
+# the h=1/32 book (6,144 triangles: 2.15 MB read + 307.85 MB written), scaled
 # to the h=1/64 book by the number of triangle pairs (x16).  Valid for the
 # kernel as captured; reset to None when the kernel changes.
-FAR_DF_TRAFFIC_BOOK64 = 16 * (1.421568e6 + 258.601984e6)
+FAR_DF_TRAFFIC_BOOK64 = 16 * (2.151168e6 + 307.84512e6)
 # the method's work per far pair (the unit of the far-field roofline): 36
 # evaluations of w_p w_q / |x_p - y_q| at about 13 FP64 operations each (3
 # subtractions, r^2, an rsqrt from an FP32 seed and two Newton steps, one
@@ -1119,7 +1119,7 @@ def far_roofline(far_pairs: int, far_ms: float, source: str) -> dict:
             "achieved": method / sec / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": method / sec / peak,
             "traffic": None,
             "traffic_note": "per launch it varies with the geometry; the ncu capture of the h=1/32 book measured "
-                            "13.8 DRAM bytes per unit (1.42 MB read + 258.6 MB written for 1.88e7 pairs: the V "
+                            "16.5 DRAM bytes per unit (2.15 MB read + 307.8 MB written for 1.88e7 pairs: the V "
                             "output only)",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (no FP32 entry in MEASURED_PEAKS.json)",
             "work_per_unit": f"{METHOD_OPS_PER_FAR_PAIR} method operations per pair (36 x 13)",
