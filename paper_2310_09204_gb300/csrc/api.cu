@@ -43,6 +43,8 @@ int fail(msbem_ctx* c, int status, const std::string& msg) {
 int cuda_fail(msbem_ctx* c, cudaError_t e, const char* where) {
   if (e == cudaErrorMemoryAllocation)
     return fail(c, MSBEM_OOM, std::string(where) + ": out of device memory");
+  if (e == cudaErrorTimeout)
+    return fail(c, MSBEM_DEVICE_TIMEOUT, std::string(where) + ": a bounded device-side wait expired");
   return fail(c, MSBEM_CUDA_ERROR, std::string(where) + ": " + cudaGetErrorString(e));
 }
 

@@ -650,13 +650,16 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
   const std::vector<int64_t>& bsize = plan.size;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bsize[a] > bsize[b]; });
   const int nb = (int)order.size();
-  std::vector<int64_t> pt1(nb + 1, 0), pt2(nb + 1, 0), soff(nb + 1, 0);
+  std::vector<int64_t> pt1(nb + 1, 0), pt2(nb + 1, 0), soff(nb + 1, 0), pl(nb + 1, 0), pr(nb + 1, 0), ptc(nb + 1, 0);
   for (int a = 0; a < nb; ++a) {
     int64_t n = bsize[order[a]];
     int64_t nti = (n + GB - 1) / GB;
     pt1[a + 1] = pt1[a] + nti;
     pt2[a + 1] = pt2[a] + nti * nti;
     soff[a + 1] = soff[a] + n * GB;
+    pl[a + 1] = pl[a] + (n + 127) / 128 * 128;
+    pr[a + 1] = pr[a] + (n + 63) / 64 * 64;
+    ptc[a + 1] = ptc[a] + ((n + 127) / 128) * ((n + 63) / 64);
   }
   BgjArgs args{};
   double** d_ptr = nullptr;
@@ -681,16 +684,46 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
   args.pt1 = d_pt1;
   args.pt2 = d_pt2;
   args.soff = d_soff;
+  // the rank-32 updates on the tensor cores: digit tiles and exponents of
+  // both operands, made per step
+  TcuDev tc{};
+  int64_t *d_pl = nullptr, *d_pr = nullptr, *d_ptc = nullptr;
+  unsigned char* slices = nullptr;
+  if ((e = tc_update_init()) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_pl, pl)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_pr, pr)) != cudaSuccess) return e;
+  if ((e = scratch.put(&d_ptc, ptc)) != cudaSuccess) return e;
+  if ((e = scratch.take(&slices, tc_update_bytes(pl[nb], pr[nb]))) != cudaSuccess) return e;
+  if ((e = scratch.take(&tc.exL, (size_t)pl[nb])) != cudaSuccess) return e;
+  if ((e = scratch.take(&tc.exR, (size_t)pr[nb])) != cudaSuccess) return e;
+  if ((e = scratch.take(&tc.err, 1)) != cudaSuccess) return e;
+  cudaMemsetAsync(tc.err, 0, sizeof(int), s);
+  tc.Ap = d_ptr;
+  tc.bsize = d_bsize;
+  tc.order = d_order;
+  tc.soff = d_soff;
+  tc.Pf = args.Pf;
+  tc.Cf = args.Cf;
+  tc.Rf = args.Rf;
+  tc.pl = d_pl;
+  tc.pr = d_pr;
+  tc.pt = d_ptc;
+  tc.Lsl = slices;
+  tc.Rsl = slices + tc_update_bytes(pl[nb], 0);
   const int64_t nmax = bsize[order[0]];
   int active = nb;
-  for (int64_t k0 = 0; k0 < nmax; k0 += GB) {
+  for (int64_t k0 = 0; k0 < nmax && e == cudaSuccess; k0 += GB) {
     while (active > 0 && bsize[order[active - 1]] <= k0) --active;
     bgj_pivot_kernel<<<active, GB * GB, 0, s>>>(args, k0);
     bgj_panel_kernel<<<(unsigned)pt1[active], 256, 0, s>>>(args, active, k0);
-    bgj_update_kernel<<<(unsigned)pt2[active], 256, 0, s>>>(args, active, k0);
-    *launches += 3;
+    e = launch_tc_update(tc, active, k0, pl[active], pr[active], ptc[active], s);
+    *launches += 5;
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return e;
+  int h_err = 0;
+  if ((e = cudaMemcpyAsync(&h_err, tc.err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  if (h_err) return cudaErrorTimeout;
   if ((e = cudaMemcpyAsync(bad.data(), args.flag, sizeof(int) * nm, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;

@@ -258,6 +258,36 @@ cudaError_t factor_finish(DevGeom& g, const std::vector<int64_t>& bptr, cudaStre
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag,
                           cudaStream_t s, int* not_spd, int prec32 = 0);
 
+// The rank-32 update of the double-float Gauss-Jordan recursion on the
+// tensor cores (factor_tc.cu): device pointers of one grouped inversion,
+// matrices in sorted order (largest first); pl / pr / pt are prefixes over the
+// sorted matrices of rows rounded up to 128, columns rounded up to 64 and
+// 128 x 64 output tiles; Lsl / Rsl hold tc_update_bytes(pl[nb], pr[nb]) bytes
+// of digit tiles (Lsl first), exL / exR one exponent per padded row / column.
+struct TcuDev {
+  double* const* Ap;
+  const int64_t* bsize;
+  const int32_t* order;
+  const int64_t* soff;
+  const float2* Pf;
+  const float2* Cf;
+  const float2* Rf;
+  const int64_t* pl;
+  const int64_t* pr;
+  const int64_t* pt;
+  unsigned char* Lsl;
+  unsigned char* Rsl;
+  int* exL;
+  int* exR;
+  int* err;        // set to 1 when a bounded wait gave up
+};
+size_t tc_update_bytes(int64_t rows, int64_t cols);
+cudaError_t tc_update_init();   // per device, before the first launch_tc_update
+// one step (pivot columns k0 ..) over the first `active` sorted matrices:
+// rows = pl[active], cols = pr[active], tiles = pt[active]
+cudaError_t launch_tc_update(const TcuDev& d, int active, int64_t k0, int64_t rows, int64_t cols, int64_t tiles,
+                             cudaStream_t s);
+
 // Single-matrix blocked Gauss-Jordan inversion with caller-provided scratch
 // (factor.cu); used by the allocation-free entry point.
 size_t bgj_scratch_bytes(int64_t n);
