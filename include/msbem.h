@@ -316,6 +316,29 @@ int msbem_dl_potential(msbem_geom* g, const double* density, const double* targe
  * t[4] solve.  Any entry not yet measured is 0. */
 int msbem_last_timings(const msbem_geom* g, double t[5]);
 
+/* In-place inverses of `count` symmetric positive definite matrices by the
+ * grouped blocked Gauss-Jordan recursion that msbem_factor runs over the face,
+ * wire-basket and coarse blocks (Sec. 5, eq. jumpSplit: the blocks of M(H;h)
+ * are inverted explicitly): per 32-column step one pivot, one panel and one
+ * update sequence over all matrices at once.  With precision 0 the update is
+ * the tensor-core form (each rank-32 product from exact 8-bit slices of both
+ * operands, folded into double-float; the inverse to about 1e-15 cond(A)
+ * relative); precision 1 inverts in FP32 and symmetrises.
+ *   ctx       context: its device, stream and memory pool are used
+ *   A[count]  host array of device pointers, each an n[i] x n[i] row-major
+ *             FP64 matrix on the context's device, overwritten by its inverse;
+ *             distinct, non-overlapping
+ *   n[count]  host array of orders, each >= 1
+ *   status    NULL or count ints (host): MSBEM_OK or MSBEM_BREAKDOWN (a pivot
+ *             that was not positive; that matrix then holds no inverse)
+ * The call allocates its scratch (operand slices, panels, index words) from
+ * the context's pool and waits for the stream before it returns.
+ * Errors: INVALID_ARG (ctx or an array NULL, count < 1, an order < 1, a
+ * precision other than 0 or 1), BREAKDOWN (some matrix), OOM, DEVICE_TIMEOUT,
+ * CUDA_ERROR. */
+int msbem_spd_inverse_group(msbem_ctx* ctx, double* const* A, const int64_t* n, int count, int precision,
+                            int* status);
+
 /* Largest matrix order msbem_spd_inverse_noalloc accepts. */
 #define MSBEM_NOALLOC_MAX_N 2048
 

@@ -90,6 +90,7 @@ def lib():
         "msbem_last_timings": ([P, P], i32),
         "msbem_counters": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
         "msbem_spd_inverse_noalloc": ([P, i64, P, P], i32),
+        "msbem_spd_inverse_group": ([P, P, P, i32, i32, P], i32),
         "msbem_solve_batch": ([P, P, i32, ctypes.POINTER(SolveOpts), P, P, P, P], i32),
         "msbem_apply": ([P, P, i32, i32, P, P], i32),
         "msbem_cells": ([P, ctypes.POINTER(i32), P, ctypes.POINTER(ctypes.c_double)], i32),
@@ -226,6 +227,45 @@ def msbem_spd_inverse_noalloc(A, Ainv, stream: int = 0) -> int:
         raise ValueError(f"msbem_spd_inverse_noalloc: order {n} outside 1..{NOALLOC_MAX_N}")
     with torch.cuda.device(A.device):
         return lib().msbem_spd_inverse_noalloc(_ptr(A), n, _ptr(Ainv), stream)
+
+
+def msbem_spd_inverse_group(mats, precision: str = "df", device: int = 0):
+    """In-place inverses of a list of SPD matrices (CUDA float64 tensors,
+    square, contiguous, on `device`) by the grouped Gauss-Jordan recursion of
+    the preconditioner set-up; precision "df" (tensor-core update, double-float
+    accuracy) or "fp32".  Returns the per-matrix C status list (0, or
+    MSBEM_BREAKDOWN for a matrix whose recursion met a non-positive pivot).
+    Shapes, dtypes and devices are checked before the library is called."""
+    import torch
+    if precision not in ("df", "fp32"):
+        raise ValueError(f"msbem_spd_inverse_group: precision must be 'df' or 'fp32', got {precision!r}")
+    mats = list(mats)
+    if not mats:
+        raise ValueError("msbem_spd_inverse_group: no matrices")
+    dev = torch.device("cuda", device)
+    for i, t in enumerate(mats):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device != dev:
+            raise ValueError(f"msbem_spd_inverse_group: matrix {i} must be a CUDA tensor on {dev}")
+        if t.dtype != torch.float64 or t.dim() != 2 or t.shape[0] != t.shape[1] or t.shape[0] < 1:
+            raise ValueError(f"msbem_spd_inverse_group: matrix {i} must be square float64, got {t.dtype} {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"msbem_spd_inverse_group: matrix {i} must be contiguous")
+    ptrs = set(t.data_ptr() for t in mats)
+    if len(ptrs) != len(mats):
+        raise ValueError("msbem_spd_inverse_group: repeated matrix")
+    k = len(mats)
+    A = (ctypes.c_void_p * k)(*[t.data_ptr() for t in mats])
+    n = (ctypes.c_int64 * k)(*[int(t.shape[0]) for t in mats])
+    st = (ctypes.c_int * k)()
+    with torch.cuda.device(dev):
+        ctx = msbem_create(device, torch.cuda.current_stream(dev).cuda_stream)
+        try:
+            rc = lib().msbem_spd_inverse_group(ctx, A, n, k, 0 if precision == "df" else 1, st)
+            if rc not in (MSBEM_OK, -6):   # -6: BREAKDOWN, reported per matrix
+                _check(ctx, rc)
+        finally:
+            lib().msbem_destroy(ctx)
+    return list(st)
 
 
 def msbem_test_fail_alloc(after: int) -> int:

@@ -726,6 +726,34 @@ int msbem_factor_group(msbem_geom* const* geoms, int n, const msbem_precond_opts
   return MSBEM_OK;
 }
 
+int msbem_spd_inverse_group(msbem_ctx* c, double* const* A, const int64_t* n, int count, int precision,
+                            int* status) {
+  if (!c || !A || !n || count < 1) return MSBEM_INVALID_ARG;
+  if (precision < 0 || precision > 1) return fail(c, MSBEM_INVALID_ARG, "precision must be 0 or 1");
+  InvPlan plan;
+  for (int i = 0; i < count; ++i) {
+    if (!A[i] || n[i] < 1) return fail(c, MSBEM_INVALID_ARG, "msbem_spd_inverse_group: NULL matrix or order < 1");
+    plan.ptr.push_back(A[i]);
+    plan.size.push_back(n[i]);
+    plan.owner.push_back(i);
+    plan.inv.push_back(i);
+    plan.f32.push_back((char)precision);
+  }
+  cudaSetDevice(c->device);
+  std::vector<int> bad;
+  int64_t launches = 0;
+  cudaError_t e = factor_invert(plan, c->pool, c->stream, bad, &launches);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "msbem_spd_inverse_group");
+  int any = 0;
+  for (int i = 0; i < count; ++i) {
+    if (status) status[i] = bad[i] ? MSBEM_BREAKDOWN : MSBEM_OK;
+    any |= bad[i];
+  }
+  if (any) return fail(c, MSBEM_BREAKDOWN, "msbem_spd_inverse_group: a matrix is not positive definite");
+  return MSBEM_OK;
+}
+
 int msbem_solve(msbem_geom* g, const double gv[3], const msbem_solve_opts* opts, double* density,
                 int* iters, double* hist, int hist_cap, double* kappa) {
   if (!g || !gv || !density) return MSBEM_INVALID_ARG;

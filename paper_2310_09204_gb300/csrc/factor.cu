@@ -632,6 +632,42 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   return cudaSuccess;
 }
 
+// Symmetric power-of-two equilibration of the double-float inversions:
+// A <- S A S with S = diag(2^x_i), x_i = -floor(k_i / 2) for A_ii in
+// [2^(k_i - 1), 2^k_i), so that the scaled diagonal lies in [1/2, 2); after the
+// recursion the same S gives A^-1 = S (S A S)^-1 S.  Every product by a power
+// of two is exact.  The point is the tensor-core update: its error is relative
+// to the largest entries of the row of one operand and the column of the other,
+// which for a graded matrix (D B D with D spanning many binades) would be far
+// above the entries themselves; after the scaling the rows and columns of an
+// SPD matrix have comparable scales (|a_ij| <= sqrt(a_ii a_jj) < 2).
+__global__ void equil_exp_kernel(double* const* Ap, const int64_t* bsize, const int32_t* order,
+                                 const int64_t* prow, int nb, int* ex) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= prow[nb]) return;
+  const int a = find_prefix(prow, nb, t);
+  const int b = order[a];
+  const int64_t n = bsize[b], i = t - prow[a];
+  const double d = Ap[b][i * n + i];
+  int k = 0;
+  if (d > 0.0 && isfinite(d)) frexp(d, &k);   // d in [2^(k-1), 2^k)
+  ex[t] = -(k >= 0 ? k / 2 : -((1 - k) / 2));  // -floor(k / 2); 0 for a pivot the recursion will reject
+}
+
+// one block per row of the matrices: A_ij <- 2^(x_i + x_j) A_ij
+__global__ void __launch_bounds__(128) equil_scale_kernel(double* const* Ap, const int64_t* bsize,
+                                                          const int32_t* order, const int64_t* prow, int nb,
+                                                          const int* ex) {
+  const int64_t t = blockIdx.x;
+  const int a = find_prefix(prow, nb, t);
+  const int b = order[a];
+  const int64_t n = bsize[b], i = t - prow[a];
+  double* row = Ap[b] + i * n;
+  const int xi = ex[t];
+  const int* xr = ex + prow[a];
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) row[j] = ldexp(row[j], xi + xr[j]);
+}
+
 }  // namespace
 
 // Inverts in place the matrices plan.inv lists (ids into plan.ptr / plan.size),
@@ -710,6 +746,17 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
   tc.pt = d_ptc;
   tc.Lsl = slices;
   tc.Rsl = slices + tc_update_bytes(pl[nb], 0);
+  // the power-of-two equilibration (prow: prefix of the orders)
+  std::vector<int64_t> prow(nb + 1, 0);
+  for (int a = 0; a < nb; ++a) prow[a + 1] = prow[a] + bsize[order[a]];
+  int64_t* d_prow = nullptr;
+  int* d_ex = nullptr;
+  if ((e = scratch.put(&d_prow, prow)) != cudaSuccess) return e;
+  if ((e = scratch.take(&d_ex, (size_t)prow[nb])) != cudaSuccess) return e;
+  if (prow[nb] > 0x7fffffff) return cudaErrorInvalidValue;
+  equil_exp_kernel<<<(unsigned)((prow[nb] + 255) / 256), 256, 0, s>>>(d_ptr, d_bsize, d_order, d_prow, nb, d_ex);
+  equil_scale_kernel<<<(unsigned)prow[nb], 128, 0, s>>>(d_ptr, d_bsize, d_order, d_prow, nb, d_ex);
+  *launches += 2;
   const int64_t nmax = bsize[order[0]];
   int active = nb;
   for (int64_t k0 = 0; k0 < nmax && e == cudaSuccess; k0 += GB) {
@@ -719,7 +766,10 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
     e = launch_tc_update(tc, active, k0, pl[active], pr[active], ptc[active], s);
     *launches += 5;
   }
-  if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return e;
+  if (e != cudaSuccess) return e;
+  equil_scale_kernel<<<(unsigned)prow[nb], 128, 0, s>>>(d_ptr, d_bsize, d_order, d_prow, nb, d_ex);
+  *launches += 1;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int h_err = 0;
   if ((e = cudaMemcpyAsync(&h_err, tc.err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;

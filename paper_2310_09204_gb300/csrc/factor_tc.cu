@@ -59,6 +59,7 @@ __device__ __forceinline__ int tcu_find(const int64_t* pre, int active, int64_t 
 }
 
 // e with |x| < 2^(e-1) for every x of the float pairs whose largest |hi| is m
+// (0 for a zero row, whose digits are all zero)
 __device__ __forceinline__ int tcu_exp(float m) {
   if (!(m > 0.f)) return 0;
   int k = 0;
@@ -96,7 +97,7 @@ __device__ __forceinline__ int tcu_slice_row(const float2* v, int64_t vstride, i
     for (int q = 0; q < 8; ++q) {
       const int k = 8 * j + q;
       int d[ND] = {0, 0, 0, 0, 0, 0};
-      if (k < kb && e != 0) {
+      if (k < kb && m > 0.f) {   // (e = 0 is also the exponent of a row whose largest |hi| is in [1/4, 1/2))
         const float2 x = v[k * vstride];
         tcu_digits((widen(x.x) + widen(x.y)) * sc, d);
       }
