@@ -215,10 +215,11 @@ __global__ void __launch_bounds__(256) bgj_panel_kernel(BgjArgs g, int active, i
   }
 }
 
-__global__ void __launch_bounds__(256) bgj_update_kernel(BgjArgs g, int active, int64_t k0) {
+// tiles tile0 + blockIdx.x of the active matrices' 32 x 32 tiles
+__global__ void __launch_bounds__(256) bgj_update_kernel(BgjArgs g, int active, int64_t k0, int64_t tile0) {
   __shared__ float2 sL[GB][GB + 1];
   __shared__ float2 sR[GB][GB + 1];
-  const int64_t t = blockIdx.x;
+  const int64_t t = tile0 + blockIdx.x;
   const int a = find_prefix(g.pt2, active, t);
   const int b = g.order[a];
   const int64_t n = g.bsize[b];
@@ -306,7 +307,7 @@ struct Bgj32Args {
   const int32_t* order;   // matrix ids sorted by size (descending)
   const int64_t* pt1;     // prefix over sorted matrices of tiles per side
   const int64_t* pt2;     // prefix of tiles^2
-  const int64_t* pt3;     // prefix of 64 x 64 update tiles
+  const int64_t* pt3;     // prefix of 128 x 128 update tiles
   const int64_t* soff;    // prefix of n * GB (scratch panels), sorted order
   float* Pf;              // [sorted][GB*GB]
   float* Cf;              // [soff] n x GB
@@ -314,46 +315,40 @@ struct Bgj32Args {
   int* flag;              // per matrix id: 1 when a pivot was not positive
 };
 
-__global__ void __launch_bounds__(1024) bgj32_pivot_kernel(Bgj32Args g, int64_t k0) {
-  __shared__ float S[GB][GB + 1];
-  __shared__ float rowk[GB], colk[GB];
-  __shared__ float s_ip;
+// The 32 x 32 pivot block inverted in place by one warp: lane j holds column
+// j of the block in registers; per pivot k the warp forms 1/p, scales row k
+// and eliminates column k, the column entries S[i][k] broadcast by shuffles.
+// Rows / columns past kb hold the identity.
+__global__ void __launch_bounds__(32) bgj32_pivot_kernel(Bgj32Args g, int64_t k0) {
   const int a = blockIdx.x;
   const int b = g.order[a];
   const int64_t n = g.bsize[b];
   const int kb = (int)(n - k0 < GB ? n - k0 : GB);
   const float* A = g.Ap[b];
   const int64_t ld = f32_ld(n);
-  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
-    const int i = e / GB, j = e % GB;
-    S[i][j] = (i < kb && j < kb) ? A[(k0 + i) * ld + k0 + j] : (i == j ? 1.0f : 0.0f);
-  }
-  __syncthreads();
+  const int j = threadIdx.x;
+  float s[GB];
+#pragma unroll
+  for (int i = 0; i < GB; ++i) s[i] = (i < kb && j < kb) ? A[(k0 + i) * ld + k0 + j] : (i == j ? 1.0f : 0.0f);
+  bool ok = true;
+#pragma unroll
   for (int k = 0; k < GB; ++k) {
-    if (threadIdx.x < 32) {
-      const float pk = S[k][k];
-      const float ip = 1.0f / pk;
-      if (threadIdx.x == 0) {
-        s_ip = ip;
-        if (!(pk > 0.f && isfinite(pk))) g.flag[b] = 1;
-      }
-      rowk[threadIdx.x] = S[k][threadIdx.x] * ip;
-      colk[threadIdx.x] = S[threadIdx.x][k];
+    const float pk = __shfl_sync(0xffffffffu, s[k], k);
+    ok = ok && pk > 0.f && isfinite(pk);
+    const float ip = 1.0f / pk;
+    const float rk = (j == k) ? ip : s[k] * ip;   // the new row k
+#pragma unroll
+    for (int i = 0; i < GB; ++i) {
+      if (i == k) continue;
+      const float cik = __shfl_sync(0xffffffffu, s[i], k);   // S[i][k] before the step
+      s[i] = (j == k) ? -cik * ip : fmaf(-cik, rk, s[i]);
     }
-    __syncthreads();
-    const float ip = s_ip;
-    for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) {
-      const int i = e / GB, j = e % GB;
-      float v;
-      if (i == k) v = (j == k) ? ip : rowk[j];
-      else if (j == k) v = -colk[i] * ip;
-      else v = fmaf(-colk[i], rowk[j], S[i][j]);
-      S[i][j] = v;
-    }
-    __syncthreads();
+    s[k] = rk;
   }
+  if (j == 0 && !ok) g.flag[b] = 1;
   float* P = g.Pf + (int64_t)a * GB * GB;
-  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) P[e] = S[e / GB][e % GB];
+#pragma unroll
+  for (int i = 0; i < GB; ++i) P[i * GB + j] = s[i];
 }
 
 __global__ void __launch_bounds__(256) bgj32_panel_kernel(Bgj32Args g, int active, int64_t k0) {
@@ -391,16 +386,23 @@ __global__ void __launch_bounds__(256) bgj32_panel_kernel(Bgj32Args g, int activ
   }
 }
 
-// Update of one 64 x 64 tile per CTA, 4 x 4 outputs per thread.  With K the
-// pivot rows / columns [k0, k0 + kb), L(r) = P[r - k0] for r in K, else C'_r,
-// and R[m][c] the old A[k0 + m][c]:
+// Update of one 128 x 128 tile per CTA, 8 x 8 outputs per thread.  With K
+// the pivot rows / columns [k0, k0 + kb), L(r) = P[r - k0] for r in K, else
+// C'_r, and R[m][c] the old A[k0 + m][c]:
 //   A[r][c] = L(r)[c - k0]                         for c in K,
 //   A[r][c] = [r not in K] A[r][c] + L(r) . R[:, c]  otherwise,
-// which is the scalar Gauss-Jordan step on 32 pivots at once.
-#define UT 64
-__global__ void __launch_bounds__(256) bgj32_update_kernel(Bgj32Args g, int active, int64_t k0) {
-  __shared__ __align__(16) float sLT[GB][UT + 4];   // sLT[m][i] = L(r0 + i)[m] (padded: 4-way stores)
-  __shared__ __align__(16) float sR[GB][UT];    // sR[m][j]  = R[m][c0 + j]
+// which is the scalar Gauss-Jordan step on 32 pivots at once.  The tile of A
+// comes in by 16-byte asynchronous copies at the start (rows start on 16-byte
+// boundaries), so that the pass over the matrix overlaps the panel loads and
+// the products; two CTAs per SM.
+#define UT 128
+constexpr int UT_LDL = UT + 4;    // row stride of sLT (16-byte rows, 4-way conflicts on the transposing stores)
+constexpr size_t UT_SMEM = sizeof(float) * ((size_t)GB * UT_LDL + (size_t)GB * UT + (size_t)UT * UT);
+__global__ void __launch_bounds__(256, 2) bgj32_update_kernel(Bgj32Args g, int active, int64_t k0) {
+  extern __shared__ __align__(16) float sm32[];
+  float* sLT = sm32;                     // sLT[m * UT_LDL + i] = L(r0 + i)[m]
+  float* sR = sm32 + GB * UT_LDL;        // sR[m * UT + j] = R[m][c0 + j]
+  float* sT = sR + GB * UT;              // sT[i * UT + j] = A[r0 + i][c0 + j]
   const int64_t t = blockIdx.x;
   const int a = find_prefix(g.pt3, active, t);
   const int b = g.order[a];
@@ -414,59 +416,82 @@ __global__ void __launch_bounds__(256) bgj32_update_kernel(Bgj32Args g, int acti
   const float* R = g.Rf + g.soff[a];
   const float* P = g.Pf + (int64_t)a * GB * GB;
   const int tid = threadIdx.x;
-  for (int e = tid; e < GB * UT; e += 256) {
+  const int64_t ld = f32_ld(n);
+  for (int e = tid; e < UT * UT / 4; e += 256) {
+    const int i = e / (UT / 4), q = e % (UT / 4);   // consecutive threads: consecutive 16-byte chunks of a row
+    const int64_t r = r0 + i, c = c0 + 4 * q;
+    if (r < n && c < ld && !(r >= k0 && r < k0 + kb))
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sT + i * UT + 4 * q)),
+                   "l"(A + r * ld + c) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  // the panels: all 32 loads of a thread in flight before its stores
+  constexpr int PQ = GB * UT / 256;
+  float lq[PQ], rq[PQ];
+#pragma unroll
+  for (int q = 0; q < PQ; ++q) {
+    const int e = tid + 256 * q;
     const int i = e / GB, m = e % GB;           // consecutive threads: consecutive m (one row of L)
     const int64_t r = r0 + i;
-    float v = 0.f;
-    if (r < n && m < kb) v = (r >= k0 && r < k0 + kb) ? P[(r - k0) * GB + m] : C[r * GB + m];
-    sLT[m][i] = v;
+    lq[q] = 0.f;
+    if (r < n && m < kb) lq[q] = (r >= k0 && r < k0 + kb) ? P[(r - k0) * GB + m] : C[r * GB + m];
     const int mm = e / UT, jj = e % UT;         // consecutive threads: consecutive columns
     const int64_t c = c0 + jj;
-    sR[mm][jj] = (mm < kb && c < n) ? R[mm * n + c] : 0.f;
+    rq[q] = (mm < kb && c < n) ? R[mm * n + c] : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < PQ; ++q) {
+    const int e = tid + 256 * q;
+    sLT[(e % GB) * UT_LDL + e / GB] = lq[q];
+    sR[e] = rq[q];                              // (e / UT) * UT + e % UT
   }
   __syncthreads();
-  const int ty = tid >> 4, tx = tid & 15;       // rows 4ty .. 4ty+3, columns 4tx .. 4tx+3
-  float acc[4][4];
+  // rows 4ty + u and 64 + 4ty + u, columns 4tx + v and 64 + 4tx + v
+  const int ty = tid >> 4, tx = tid & 15;
+  float acc[8][8];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 8; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
   for (int m = 0; m < kb; ++m) {
-    const float4 l = *(const float4*)&sLT[m][4 * ty];
-    const float4 rr = *(const float4*)&sR[m][4 * tx];
-    const float lv[4] = {l.x, l.y, l.z, l.w}, rv[4] = {rr.x, rr.y, rr.z, rr.w};
+    const float4 l0 = *(const float4*)&sLT[m * UT_LDL + 4 * ty];
+    const float4 l1 = *(const float4*)&sLT[m * UT_LDL + 64 + 4 * ty];
+    const float4 q0 = *(const float4*)&sR[m * UT + 4 * tx];
+    const float4 q1 = *(const float4*)&sR[m * UT + 64 + 4 * tx];
+    const float lv[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+    const float rv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 8; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(lv[u], rv[v], acc[u][v]);
+      for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(lv[u], rv[v], acc[u][v]);
   }
-  const int64_t ld = f32_ld(n);
-  const int64_t cb = c0 + 4 * tx;
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int64_t r = r0 + 4 * ty + u;
+  for (int u = 0; u < 8; ++u) {
+    const int i = (u < 4 ? 0 : 64) + 4 * ty + (u & 3);
+    const int64_t r = r0 + i;
     if (r >= n) continue;
     const bool rK = r >= k0 && r < k0 + kb;
-    float* dst = A + r * ld + cb;
-    if (cb + 3 < n) {
-      // four columns in one 16-byte access (rows start on 16-byte boundaries)
-      float4 o = rK ? make_float4(0.f, 0.f, 0.f, 0.f) : *(const float4*)dst;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jb = 64 * h + 4 * tx;
+      const int64_t cb = c0 + jb;
+      if (cb >= n) continue;
+      const float4 o = rK ? make_float4(0.f, 0.f, 0.f, 0.f) : *(const float4*)&sT[i * UT + jb];
       float ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int64_t c = cb + v;
-        ov[v] = (c >= k0 && c < k0 + kb) ? sLT[c - k0][4 * ty + u] : ov[v] + acc[u][v];
+        ov[v] = (c >= k0 && c < k0 + kb) ? sLT[(c - k0) * UT_LDL + i] : ov[v] + acc[u][4 * h + v];
       }
-      *(float4*)dst = make_float4(ov[0], ov[1], ov[2], ov[3]);
-    } else {
+      float* dst = A + r * ld + cb;
+      if (cb + 3 < n) {
+        *(float4*)dst = make_float4(ov[0], ov[1], ov[2], ov[3]);   // 16-byte aligned
+      } else {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int64_t c = cb + v;
-        if (c >= n) continue;
-        if (c >= k0 && c < k0 + kb)
-          dst[v] = sLT[c - k0][4 * ty + u];
-        else
-          dst[v] = (rK ? 0.f : dst[v]) + acc[u][v];
+        for (int v = 0; v < 4; ++v)
+          if (cb + v < n) dst[v] = ov[v];
       }
     }
   }
@@ -552,6 +577,42 @@ cudaError_t upload(T** d, const std::vector<T>& h, cudaMemPool_t pool, cudaStrea
 
 namespace {
 
+// Symmetric power-of-two equilibration of the double-float inversions:
+// A <- S A S with S = diag(2^x_i), x_i = -floor(k_i / 2) for A_ii in
+// [2^(k_i - 1), 2^k_i), so that the scaled diagonal lies in [1/2, 2); after the
+// recursion the same S gives A^-1 = S (S A S)^-1 S.  Every product by a power
+// of two is exact.  The point is the tensor-core update: its error is relative
+// to the largest entries of the row of one operand and the column of the other,
+// which for a graded matrix (D B D with D spanning many binades) would be far
+// above the entries themselves; after the scaling the rows and columns of an
+// SPD matrix have comparable scales (|a_ij| <= sqrt(a_ii a_jj) < 2).
+__global__ void equil_exp_kernel(double* const* Ap, const int64_t* bsize, const int32_t* order,
+                                 const int64_t* prow, int nb, int* ex) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= prow[nb]) return;
+  const int a = find_prefix(prow, nb, t);
+  const int b = order[a];
+  const int64_t n = bsize[b], i = t - prow[a];
+  const double d = Ap[b][i * n + i];
+  int k = 0;
+  if (d > 0.0 && isfinite(d)) frexp(d, &k);   // d in [2^(k-1), 2^k)
+  ex[t] = -(k >= 0 ? k / 2 : -((1 - k) / 2));  // -floor(k / 2); 0 for a pivot the recursion will reject
+}
+
+// one block per row of the matrices: A_ij <- 2^(x_i + x_j) A_ij
+__global__ void __launch_bounds__(128) equil_scale_kernel(double* const* Ap, const int64_t* bsize,
+                                                          const int32_t* order, const int64_t* prow, int nb,
+                                                          const int* ex) {
+  const int64_t t = blockIdx.x;
+  const int a = find_prefix(prow, nb, t);
+  const int b = order[a];
+  const int64_t n = bsize[b], i = t - prow[a];
+  double* row = Ap[b] + i * n;
+  const int xi = ex[t];
+  const int* xr = ex + prow[a];
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) row[j] = ldexp(row[j], xi + xr[j]);
+}
+
 // Inverts the FP32 matrices of `ids` (their FP64 copies in plan.ptr, in place:
 // converted to FP32, inverted, symmetrised and written back).
 cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cudaMemPool_t pool, cudaStream_t s,
@@ -569,8 +630,8 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
     const int64_t nti = (n + GB - 1) / GB;
     pt1[a + 1] = pt1[a] + nti;
     pt2[a + 1] = pt2[a] + nti * nti;
-    const int64_t nt64 = (n + UT - 1) / UT;
-    pt3[a + 1] = pt3[a] + nt64 * nt64;
+    const int64_t ntu = (n + UT - 1) / UT;
+    pt3[a + 1] = pt3[a] + ntu * ntu;
     soff[a + 1] = soff[a] + n * GB;
     elems += n * f32_ld(n);
   }
@@ -609,6 +670,9 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   args.pt2 = d_pt2;
   args.pt3 = d_pt3;
   args.soff = d_soff;
+  if ((e = cudaFuncSetAttribute(bgj32_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UT_SMEM)) !=
+      cudaSuccess)
+    return e;
   const dim3 cgrid(std::min<unsigned>(1024u, (unsigned)((bsize[order[0]] * bsize[order[0]] + 255) / 256)),
                    (unsigned)nb);
   f64_to_f32_kernel<<<cgrid, 256, 0, s>>>(d_dptr, d_fptr, d_bsize, d_order);
@@ -616,9 +680,9 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   int active = nb;
   for (int64_t k0 = 0; k0 < nmax; k0 += GB) {
     while (active > 0 && bsize[order[active - 1]] <= k0) --active;
-    bgj32_pivot_kernel<<<active, GB * GB, 0, s>>>(args, k0);
+    bgj32_pivot_kernel<<<active, 32, 0, s>>>(args, k0);
     bgj32_panel_kernel<<<(unsigned)pt1[active], 256, 0, s>>>(args, active, k0);
-    bgj32_update_kernel<<<(unsigned)pt3[active], 256, 0, s>>>(args, active, k0);
+    bgj32_update_kernel<<<(unsigned)pt3[active], 256, UT_SMEM, s>>>(args, active, k0);
     *launches += 3;
   }
   f32_sym_to_f64_kernel<<<cgrid, 256, 0, s>>>(d_fptr, d_dptr, d_bsize, d_order);
@@ -632,43 +696,11 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   return cudaSuccess;
 }
 
-// Symmetric power-of-two equilibration of the double-float inversions:
-// A <- S A S with S = diag(2^x_i), x_i = -floor(k_i / 2) for A_ii in
-// [2^(k_i - 1), 2^k_i), so that the scaled diagonal lies in [1/2, 2); after the
-// recursion the same S gives A^-1 = S (S A S)^-1 S.  Every product by a power
-// of two is exact.  The point is the tensor-core update: its error is relative
-// to the largest entries of the row of one operand and the column of the other,
-// which for a graded matrix (D B D with D spanning many binades) would be far
-// above the entries themselves; after the scaling the rows and columns of an
-// SPD matrix have comparable scales (|a_ij| <= sqrt(a_ii a_jj) < 2).
-__global__ void equil_exp_kernel(double* const* Ap, const int64_t* bsize, const int32_t* order,
-                                 const int64_t* prow, int nb, int* ex) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= prow[nb]) return;
-  const int a = find_prefix(prow, nb, t);
-  const int b = order[a];
-  const int64_t n = bsize[b], i = t - prow[a];
-  const double d = Ap[b][i * n + i];
-  int k = 0;
-  if (d > 0.0 && isfinite(d)) frexp(d, &k);   // d in [2^(k-1), 2^k)
-  ex[t] = -(k >= 0 ? k / 2 : -((1 - k) / 2));  // -floor(k / 2); 0 for a pivot the recursion will reject
-}
-
-// one block per row of the matrices: A_ij <- 2^(x_i + x_j) A_ij
-__global__ void __launch_bounds__(128) equil_scale_kernel(double* const* Ap, const int64_t* bsize,
-                                                          const int32_t* order, const int64_t* prow, int nb,
-                                                          const int* ex) {
-  const int64_t t = blockIdx.x;
-  const int a = find_prefix(prow, nb, t);
-  const int b = order[a];
-  const int64_t n = bsize[b], i = t - prow[a];
-  double* row = Ap[b] + i * n;
-  const int xi = ex[t];
-  const int* xr = ex + prow[a];
-  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) row[j] = ldexp(row[j], xi + xr[j]);
-}
-
 }  // namespace
+
+// Order from which a matrix's double-float update runs on the tensor cores
+// (the measured crossover of the two updates lies between 1536 and 2048).
+constexpr int64_t kTcMinOrder = 2048;
 
 // Inverts in place the matrices plan.inv lists (ids into plan.ptr / plan.size),
 // all of them in one grouped sequence of launches: per 32-column step, one
@@ -693,9 +725,10 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
     pt1[a + 1] = pt1[a] + nti;
     pt2[a + 1] = pt2[a] + nti * nti;
     soff[a + 1] = soff[a] + n * GB;
+    const int64_t tn = tcp_tile_cols();
     pl[a + 1] = pl[a] + (n + 127) / 128 * 128;
-    pr[a + 1] = pr[a] + (n + 63) / 64 * 64;
-    ptc[a + 1] = ptc[a] + ((n + 127) / 128) * ((n + 63) / 64);
+    pr[a + 1] = pr[a] + (n + tn - 1) / tn * tn;
+    ptc[a + 1] = ptc[a] + ((n + 127) / 128) * ((n + tn - 1) / tn);
   }
   BgjArgs args{};
   double** d_ptr = nullptr;
@@ -720,18 +753,23 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
   args.pt1 = d_pt1;
   args.pt2 = d_pt2;
   args.soff = d_soff;
-  // the rank-32 updates on the tensor cores: digit tiles and exponents of
-  // both operands, made per step
-  TcuDev tc{};
+  // the rank-32 updates of the matrices of order >= kTcMinOrder on the
+  // tensor cores (digit tiles and exponents of both operands made per step);
+  // for smaller ones the three launches of a tensor-core update cost more
+  // than the CUDA-core update saves
+  int nbig = 0;
+  while (nbig < nb && bsize[order[nbig]] >= kTcMinOrder) ++nbig;
+  int sms = 0;
+  if (nbig > 0 && (e = tcp_init(&sms)) != cudaSuccess) return e;
+  TcpDev<double, float2> tc{};
   int64_t *d_pl = nullptr, *d_pr = nullptr, *d_ptc = nullptr;
   unsigned char* slices = nullptr;
-  if ((e = tc_update_init()) != cudaSuccess) return e;
   if ((e = scratch.put(&d_pl, pl)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_pr, pr)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_ptc, ptc)) != cudaSuccess) return e;
-  if ((e = scratch.take(&slices, tc_update_bytes(pl[nb], pr[nb]))) != cudaSuccess) return e;
-  if ((e = scratch.take(&tc.exL, (size_t)pl[nb])) != cudaSuccess) return e;
-  if ((e = scratch.take(&tc.exR, (size_t)pr[nb])) != cudaSuccess) return e;
+  if ((e = scratch.take(&slices, tcp_slice_bytes(pl[nbig], pr[nbig]))) != cudaSuccess) return e;
+  if ((e = scratch.take(&tc.exL, (size_t)pl[nbig])) != cudaSuccess) return e;
+  if ((e = scratch.take(&tc.exR, (size_t)pr[nbig])) != cudaSuccess) return e;
   if ((e = scratch.take(&tc.err, 1)) != cudaSuccess) return e;
   cudaMemsetAsync(tc.err, 0, sizeof(int), s);
   tc.Ap = d_ptr;
@@ -745,7 +783,7 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
   tc.pr = d_pr;
   tc.pt = d_ptc;
   tc.Lsl = slices;
-  tc.Rsl = slices + tc_update_bytes(pl[nb], 0);
+  tc.Rsl = slices + tcp_slice_bytes(pl[nbig], 0);
   // the power-of-two equilibration (prow: prefix of the orders)
   std::vector<int64_t> prow(nb + 1, 0);
   for (int a = 0; a < nb; ++a) prow[a + 1] = prow[a] + bsize[order[a]];
@@ -763,8 +801,19 @@ cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t 
     while (active > 0 && bsize[order[active - 1]] <= k0) --active;
     bgj_pivot_kernel<<<active, GB * GB, 0, s>>>(args, k0);
     bgj_panel_kernel<<<(unsigned)pt1[active], 256, 0, s>>>(args, active, k0);
-    e = launch_tc_update(tc, active, k0, pl[active], pr[active], ptc[active], s);
-    *launches += 5;
+    // the matrices of order >= kTcMinOrder (sorted first) on the tensor
+    // cores, the others on the CUDA cores: each matrix's arithmetic depends
+    // on its own order only, whatever it is grouped with
+    const int abig = std::min(active, nbig);
+    *launches += 2;
+    if (abig > 0) {
+      e = launch_tcp_update(tc, abig, k0, pl[abig], pr[abig], ptc[abig], sms, s);
+      *launches += 3;
+    }
+    if (active > abig) {
+      bgj_update_kernel<<<(unsigned)(pt2[active] - pt2[abig]), 256, 0, s>>>(args, active, k0, pt2[abig]);
+      *launches += 1;
+    }
   }
   if (e != cudaSuccess) return e;
   equil_scale_kernel<<<(unsigned)prow[nb], 128, 0, s>>>(d_ptr, d_bsize, d_order, d_prow, nb, d_ex);
@@ -818,7 +867,7 @@ cudaError_t bgj_invert_single(double* A, int64_t n, unsigned char* scratch, size
   for (int64_t k0 = 0; k0 < n; k0 += GB) {
     bgj_pivot_kernel<<<1, GB * GB, 0, s>>>(args, k0);
     bgj_panel_kernel<<<(unsigned)nti, 256, 0, s>>>(args, 1, k0);
-    bgj_update_kernel<<<(unsigned)(nti * nti), 256, 0, s>>>(args, 1, k0);
+    bgj_update_kernel<<<(unsigned)(nti * nti), 256, 0, s>>>(args, 1, k0, 0);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int flag = 0;

@@ -258,20 +258,22 @@ cudaError_t factor_finish(DevGeom& g, const std::vector<int64_t>& bptr, cudaStre
 cudaError_t factor_blocks(DevGeom& g, const std::vector<int64_t>& bptr, int wb_diag,
                           cudaStream_t s, int* not_spd, int prec32 = 0);
 
-// The rank-32 update of the double-float Gauss-Jordan recursion on the
-// tensor cores (factor_tc.cu): device pointers of one grouped inversion,
-// matrices in sorted order (largest first); pl / pr / pt are prefixes over the
-// sorted matrices of rows rounded up to 128, columns rounded up to 64 and
-// 128 x 64 output tiles; Lsl / Rsl hold tc_update_bytes(pl[nb], pr[nb]) bytes
-// of digit tiles (Lsl first), exL / exR one exponent per padded row / column.
-struct TcuDev {
-  double* const* Ap;
+// The rank-32 update of the double-float Gauss-Jordan recursion on the tensor
+// cores (factor_tcp.cu): device pointers of one grouped inversion, matrices in
+// sorted order (largest first); pl / pr / pt are prefixes over the sorted
+// matrices of rows rounded up to 128, columns rounded up to tcp_tile_cols()
+// and 128 x tcp_tile_cols() output tiles; Lsl / Rsl hold the digit tiles
+// (tcp_slice_bytes(pl[nb], pr[nb]) bytes, Lsl first, Rsl at
+// tcp_slice_bytes(pl[nb], 0)), exL / exR one exponent per padded row / column.
+template <class Elem, class Op>
+struct TcpDev {
+  Elem* const* Ap;
   const int64_t* bsize;
   const int32_t* order;
   const int64_t* soff;
-  const float2* Pf;
-  const float2* Cf;
-  const float2* Rf;
+  const Op* Pf;
+  const Op* Cf;
+  const Op* Rf;
   const int64_t* pl;
   const int64_t* pr;
   const int64_t* pt;
@@ -281,12 +283,13 @@ struct TcuDev {
   int* exR;
   int* err;        // set to 1 when a bounded wait gave up
 };
-size_t tc_update_bytes(int64_t rows, int64_t cols);
-cudaError_t tc_update_init();   // per device, before the first launch_tc_update
+size_t tcp_slice_bytes(int64_t rows, int64_t cols);
+int tcp_tile_cols();
+cudaError_t tcp_init(int* sms);   // per device, before the first launch; *sms = SM count
 // one step (pivot columns k0 ..) over the first `active` sorted matrices:
-// rows = pl[active], cols = pr[active], tiles = pt[active]
-cudaError_t launch_tc_update(const TcuDev& d, int active, int64_t k0, int64_t rows, int64_t cols, int64_t tiles,
-                             cudaStream_t s);
+// rows = pl[active], cols = pr[active], tiles = pt[active]; three launches
+cudaError_t launch_tcp_update(const TcpDev<double, float2>& d, int active, int64_t k0, int64_t rows, int64_t cols,
+                              int64_t tiles, int sms, cudaStream_t s);
 
 // Single-matrix blocked Gauss-Jordan inversion with caller-provided scratch
 // (factor.cu); used by the allocation-free entry point.

@@ -135,3 +135,31 @@ def test_rejects_bad_arguments():
         M.msbem_spd_inverse_group([t, t])
     with pytest.raises(ValueError):
         M.msbem_spd_inverse_group([t], precision="fp16")
+
+
+def test_tensor_core_update_against_the_definition():
+    # orders >= 2048 take the tensor-core update (exact 8-bit slices of both
+    # operands, 26 slice pairs in tensor memory, folded into double-float),
+    # smaller ones the CUDA-core update, in the same grouped steps
+    mats = [_spd(2100, 91), _spd(2333, 92, kind="decay"), _spd(130, 93), _spd(33, 94)]
+    X, st = _inv_group(mats)
+    assert st == [0] * len(mats)
+    for A, Xi in zip(mats, X):
+        rel, cond = _rel(Xi, A)
+        assert rel <= 64 * 2.0 ** -48 * cond * max(1.0, A.shape[0] / 32), (A.shape[0], rel, cond)
+    # the large ones alone: the same bits (the path depends on a matrix's own order)
+    (X0,), _ = _inv_group([mats[0]])
+    assert np.array_equal(X0, X[0])
+    (X3,), _ = _inv_group([mats[3]])
+    assert np.array_equal(X3, X[3])
+
+
+def test_tensor_core_update_on_a_graded_matrix():
+    # rows and columns over 2^+-20: the equilibration keeps the sliced
+    # products' error at the scale of the entries
+    A = _spd(2050, 95, kind="graded")
+    (X,), st = _inv_group([A])
+    assert st == [0]
+    Ai = np.linalg.inv(A)
+    d = np.sqrt(np.abs(np.diag(Ai)))
+    assert (np.abs(X - Ai) / np.outer(d, d)).max() <= 1e-9
