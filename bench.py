@@ -103,6 +103,11 @@ def parse():
                     help="c5: seconds of oracle work in the CPU baseline")
     ap.add_argument("--serve-precision", default="mixed", choices=["mixed", "mixed-tc", "mixed-fp16", "df", "tc"])
     ap.add_argument("--no-cube", action="store_true", help="skip the cube-with-mid-planes section")
+    ap.add_argument("--no-setup", action="store_true",
+                    help="skip the preconditioner set-up section (grouped SPD inverse, double-float and FP32)")
+    ap.add_argument("--setup-only", type=int, default=0,
+                    help="only invert one synthetic SPD matrix of this order (double-float, then FP32) and print "
+                         "the times (for profiling the set-up kernels)")
     ap.add_argument("--no-panels", action="store_true",
                     help="skip the sixteen hinged-panel instances (grouped factorisation, batched solves)")
     ap.add_argument("--workload", default="c5", choices=["c5", "book64", "book48", "book32", "flat"],
@@ -585,6 +590,49 @@ def matvec_rooflines(S, N, stream, reps=5):
             out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                          "launch_ms": ms, "algorithmic": f"{MATVEC_BYTES[prec]} B x N^2 (W read once)",
                          "peak_source": src}
+    return out
+
+
+SETUP_ORDER = 7407   # the wire basket of the cube with mid-planes at h = 1/66
+
+
+def setup_bench(n: int = SETUP_ORDER, reps: int = 3) -> dict:
+    """The preconditioner set-up's inversion alone (msbem_spd_inverse_group,
+    Sec. 5 eq. jumpSplit: the blocks of M(H;h) inverted explicitly) on one
+    synthetic SPD matrix of the order of the cube's wire basket: B B^T / n + I,
+    B uniform in (-1, 1), seed 1.  Double-float: n / 32 steps of pivot, panel,
+    slicing and the tensor-core update (orders >= 2048); FP32: the CUDA-core
+    update.  Times are CUDA events around the call on its stream (best of
+    `reps`); `update_roofline` relates the double-float steps to the pass over
+    the FP64 matrix that every step makes (16 n^2 bytes read and written)."""
+    import math
+    import torch
+    import paper_2310_09204_gb300 as M
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev).manual_seed(1)
+    B = torch.rand(n, n, dtype=torch.float64, device=dev, generator=g) * 2 - 1
+    A0 = B @ B.T / n + torch.eye(n, dtype=torch.float64, device=dev)
+    del B
+    eye = torch.eye(n, dtype=torch.float64, device=dev)
+    out = {"order": n, "matrix": "B B^T / n + I, B uniform(-1, 1), seed 1 (cube h=1/66 wire-basket order)"}
+    for prec in ("df", "fp32"):
+        best, st, A = None, None, None
+        for _ in range(reps):
+            A = A0.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = M.msbem_spd_inverse_group([A], precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        err = (A @ A0 - eye).abs().max().item()
+        out[prec] = {"ms": best, "status": st[0], "max_abs_AX_minus_I": err}
+    steps = math.ceil(n / 32)
+    peak, src = measured_peaks()
+    bound_ms = steps * 16.0 * n * n / (peak * 1e9) * 1e3
+    out["update_roofline"] = {"steps": steps, "bytes_per_step": 16.0 * n * n, "hbm_gbs": peak, "peak_source": src,
+                              "hbm_bound_ms": bound_ms, "df_frac_of_hbm_bound": bound_ms / out["df"]["ms"]}
     return out
 
 
@@ -1237,6 +1285,7 @@ def run_serving(args, world, rank, local, pg):
         cube = cube_bench(local, torch.cuda.current_stream(dev))
     if not args.no_panels:
         panels = panels_bench(local, torch.cuda.current_stream(dev))
+    setup = None if args.no_setup else setup_bench()
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = c5_cpu_baseline(geoms, reqs, budget_s=args.cpu_seconds)
@@ -1259,7 +1308,7 @@ def run_serving(args, world, rank, local, pg):
                                                            "speedup_vs_plain_fp64_grouped")} if comp else None),
         "roofline": far_roofline(run["far_pairs"], run["far_ms"],
                                  "CUDA events inside each assembly on its stream, summed over the timed region"),
-        "serving": serving, "book": book, "cube": cube, "panels16": panels,
+        "serving": serving, "book": book, "cube": cube, "panels16": panels, "setup_inverse": setup,
         "clocks": ck, "gpu_launches": run["launches"], "e2e": e2e, "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -1334,6 +1383,11 @@ def main():
     args = parse()
     if args.matvec:
         run_matvec(args)
+        return
+    if args.setup_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"setup_inverse": setup_bench(args.setup_only, reps=1)}), flush=True)
         return
     world, rank, local, pg = dist_setup(args)
     try:
