@@ -991,7 +991,7 @@ def serve_bench(R: int, device: int, stream, load: float = 1.5, precision: str =
 
 
 def engine_run(geoms, ndof, reqs, device, precision="mixed", budget=C5_BUDGET, arrivals=None, out="device",
-               register="all", density_tol=C5_DENSITY_TOL, sample=()):
+               register="all", density_tol=C5_DENSITY_TOL, sample=(), admission_threads=0):
     """Serve `reqs` [(key, g)] on a fresh engine.
 
     arrivals None: every request is queued at once (saturated: the engine's
@@ -1014,7 +1014,8 @@ def engine_run(geoms, ndof, reqs, device, precision="mixed", budget=C5_BUDGET, a
         buf = torch.empty(int(offs[-1]), dtype=torch.float64).pin_memory()
     views = [buf[int(offs[i]):int(offs[i + 1])] for i in range(R)]
     gpin = torch.from_numpy(np.array([g for _, g in reqs], np.float64)).pin_memory().numpy()
-    E = M.Server(device=device, precision=precision, hbm_budget=budget, density_tol=density_tol)
+    E = M.Server(device=device, precision=precision, hbm_budget=budget, density_tol=density_tol,
+                 admission_threads=admission_threads)
     registered = set()
     try:
         if register == "all":

@@ -453,7 +453,10 @@ __global__ void __launch_bounds__(256, 2) bgj32_update_kernel(Bgj32Args g, int a
   for (int u = 0; u < 8; ++u)
 #pragma unroll
     for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
-  for (int m = 0; m < kb; ++m) {
+  // the panel entries past kb are zero, so a full 32-term loop (unrolled) is
+  // exact for every step
+#pragma unroll 8
+  for (int m = 0; m < GB; ++m) {
     const float4 l0 = *(const float4*)&sLT[m * UT_LDL + 4 * ty];
     const float4 l1 = *(const float4*)&sLT[m * UT_LDL + 64 + 4 * ty];
     const float4 q0 = *(const float4*)&sR[m * UT + 4 * tx];
@@ -467,6 +470,24 @@ __global__ void __launch_bounds__(256, 2) bgj32_update_kernel(Bgj32Args g, int a
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
+  if (c0 + UT <= n && (c0 + UT <= k0 || c0 >= k0 + kb)) {
+    // no pivot column and no column past the matrix in this tile
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = (u < 4 ? 0 : 64) + 4 * ty + (u & 3);
+      const int64_t r = r0 + i;
+      if (r >= n) continue;
+      const bool rK = r >= k0 && r < k0 + kb;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int jb = 64 * h + 4 * tx;
+        const float4 o = rK ? make_float4(0.f, 0.f, 0.f, 0.f) : *(const float4*)&sT[i * UT + jb];
+        *(float4*)(A + r * ld + c0 + jb) = make_float4(o.x + acc[u][4 * h], o.y + acc[u][4 * h + 1],
+                                                      o.z + acc[u][4 * h + 2], o.w + acc[u][4 * h + 3]);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int i = (u < 4 ? 0 : 64) + 4 * ty + (u & 3);
