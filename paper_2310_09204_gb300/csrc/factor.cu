@@ -315,18 +315,13 @@ struct Bgj32Args {
   int* flag;              // per matrix id: 1 when a pivot was not positive
 };
 
-// The 32 x 32 pivot block inverted in place by one warp: lane j holds column
-// j of the block in registers; per pivot k the warp forms 1/p, scales row k
-// and eliminates column k, the column entries S[i][k] broadcast by shuffles.
-// Rows / columns past kb hold the identity.
-__global__ void __launch_bounds__(32) bgj32_pivot_kernel(Bgj32Args g, int64_t k0) {
-  const int a = blockIdx.x;
-  const int b = g.order[a];
-  const int64_t n = g.bsize[b];
-  const int kb = (int)(n - k0 < GB ? n - k0 : GB);
-  const float* A = g.Ap[b];
-  const int64_t ld = f32_ld(n);
-  const int j = threadIdx.x;
+// The 32 x 32 pivot block inverted by one warp: lane j holds column j of the
+// block in registers; per pivot k the warp forms 1/p, scales row k and
+// eliminates column k, the column entries S[i][k] broadcast by shuffles.  Rows
+// / columns past kb hold the identity.  P[i][j] is written to sP (row stride
+// GB + 1); the result is false if a pivot was not positive.
+__device__ __forceinline__ bool pivot32_warp(const float* A, int64_t ld, int64_t k0, int kb, float* sP) {
+  const int j = threadIdx.x & 31;
   float s[GB];
 #pragma unroll
   for (int i = 0; i < GB; ++i) s[i] = (i < kb && j < kb) ? A[(k0 + i) * ld + k0 + j] : (i == j ? 1.0f : 0.0f);
@@ -345,12 +340,17 @@ __global__ void __launch_bounds__(32) bgj32_pivot_kernel(Bgj32Args g, int64_t k0
     }
     s[k] = rk;
   }
-  if (j == 0 && !ok) g.flag[b] = 1;
-  float* P = g.Pf + (int64_t)a * GB * GB;
 #pragma unroll
-  for (int i = 0; i < GB; ++i) P[i * GB + j] = s[i];
+  for (int i = 0; i < GB; ++i) sP[i * (GB + 1) + j] = s[i];
+  return ok;
 }
 
+// One step's panels, one CTA per 32-row tile of every active matrix: warp 0
+// inverts the pivot block (each CTA for itself: no separate launch, no
+// dependency between CTAs), while the other warps copy the old pivot rows R
+// over the tile's 32 columns; then C'_I = -A_IK P for the tile's rows.  The
+// CTA of the pivot tile writes P (read by the update for the rows in K) and
+// the breakdown flag.
 __global__ void __launch_bounds__(256) bgj32_panel_kernel(Bgj32Args g, int active, int64_t k0) {
   __shared__ float sP[GB][GB + 1];
   __shared__ float sA[GB][GB + 1];
@@ -361,21 +361,30 @@ __global__ void __launch_bounds__(256) bgj32_panel_kernel(Bgj32Args g, int activ
   const int I = (int)(t - g.pt1[a]);
   const int kb = (int)(n - k0 < GB ? n - k0 : GB);
   const float* A = g.Ap[b];
+  const int64_t ld = f32_ld(n);
   float* C = g.Cf + g.soff[a];
   float* R = g.Rf + g.soff[a];
   const int64_t r0 = (int64_t)I * GB;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int m = ty; m < kb; m += 8) {
-    const int64_t col = r0 + tx;
-    if (col < n) R[m * n + col] = A[(k0 + m) * f32_ld(n) + col];
+  if (ty == 0) {
+    const bool ok = pivot32_warp(A, ld, k0, kb, &sP[0][0]);
+    if (r0 == k0) {
+      float* P = g.Pf + (int64_t)a * GB * GB;
+#pragma unroll 4
+      for (int i = 0; i < GB; ++i) P[i * GB + tx] = sP[i][tx];
+      if (tx == 0 && !ok) g.flag[b] = 1;
+    }
+  } else {
+    for (int m = ty - 1; m < kb; m += 7) {
+      const int64_t col = r0 + tx;
+      if (col < n) R[m * n + col] = A[(k0 + m) * ld + col];
+    }
+    for (int i = ty - 1; i < GB; i += 7) {
+      const int64_t row = r0 + i;
+      sA[i][tx] = (row < n && tx < kb) ? A[row * ld + k0 + tx] : 0.f;
+    }
   }
   if (r0 == k0) return;
-  const float* P = g.Pf + (int64_t)a * GB * GB;
-  for (int e = threadIdx.x; e < GB * GB; e += blockDim.x) sP[e / GB][e % GB] = P[e];
-  for (int i = ty; i < GB; i += 8) {
-    const int64_t row = r0 + i;
-    sA[i][tx] = (row < n && tx < kb) ? A[row * f32_ld(n) + k0 + tx] : 0.f;
-  }
   __syncthreads();
   for (int i = ty; i < GB; i += 8) {
     const int64_t row = r0 + i;
@@ -701,10 +710,9 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   int active = nb;
   for (int64_t k0 = 0; k0 < nmax; k0 += GB) {
     while (active > 0 && bsize[order[active - 1]] <= k0) --active;
-    bgj32_pivot_kernel<<<active, 32, 0, s>>>(args, k0);
     bgj32_panel_kernel<<<(unsigned)pt1[active], 256, 0, s>>>(args, active, k0);
     bgj32_update_kernel<<<(unsigned)pt3[active], 256, UT_SMEM, s>>>(args, active, k0);
-    *launches += 3;
+    *launches += 2;
   }
   f32_sym_to_f64_kernel<<<cgrid, 256, 0, s>>>(d_fptr, d_dptr, d_bsize, d_order);
   *launches += 2;
