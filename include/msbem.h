@@ -175,8 +175,8 @@ int msbem_factor(msbem_geom* g, const msbem_precond_opts* opts);
 /* msbem_factor for n geometries of ONE context at once: the face, wire-basket
  * and coarse blocks of all of them (Sec. 5, eq. jumpSplit) are inverted by one
  * grouped sequence of launches (per 32-column step of the blocked Gauss-Jordan
- * recursion, one pivot, one panel and one update launch over every block of
- * every geometry), so that many small instances fill the GPU together.  The
+ * recursion, the pivot, panel and update launches cover every block of every
+ * geometry at once), so that many small instances fill the GPU together.  The
  * inverses are the same, bit for bit, as those msbem_factor gives each
  * geometry alone.
  *   geoms   n distinct geometries (caller-owned array), all assembled, all
@@ -319,11 +319,13 @@ int msbem_last_timings(const msbem_geom* g, double t[5]);
 /* In-place inverses of `count` symmetric positive definite matrices by the
  * grouped blocked Gauss-Jordan recursion that msbem_factor runs over the face,
  * wire-basket and coarse blocks (Sec. 5, eq. jumpSplit: the blocks of M(H;h)
- * are inverted explicitly): per 32-column step one pivot, one panel and one
- * update sequence over all matrices at once.  With precision 0 the update is
- * the tensor-core form (each rank-32 product from exact 8-bit slices of both
- * operands, folded into double-float; the inverse to about 1e-15 cond(A)
- * relative); precision 1 inverts in FP32 and symmetrises.
+ * are inverted explicitly): per 32-column step, the pivot, panel and update
+ * launches cover all matrices at once.  With precision 0 (double-float) the
+ * update of a matrix of order >= 2048 is the tensor-core form (each rank-32
+ * product from exact 8-bit slices of both operands, folded into double-float)
+ * and that of a smaller one the CUDA-core form; the result depends on each
+ * matrix's own order only, and is accurate to about 1e-15 cond(A) relative.
+ * Precision 1 inverts in FP32 and symmetrises.
  *   ctx       context: its device, stream and memory pool are used
  *   A[count]  host array of device pointers, each an n[i] x n[i] row-major
  *             FP64 matrix on the context's device, overwritten by its inverse;

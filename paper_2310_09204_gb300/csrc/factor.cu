@@ -76,10 +76,13 @@ __global__ void ah_kernel(const double* __restrict__ WPt, int64_t N, int64_t NH,
 //   P = A_KK^{-1}                       (bgj_pivot_kernel, double-float in shared memory)
 //   C'_I = -A_IK P,  R_J = A_KJ (old)   (bgj_panel_kernel, double-float)
 //   A_IJ += C'_I R_J, A_KJ = P R_J, A_IK = C'_I, A_KK = P
-//                                       (bgj_update_kernel, double-float tiles)
+//                                       (bgj_update_kernel, double-float tiles;
+//                                        factor_tcp.cu on the tensor cores for
+//                                        matrices of order >= kTcMinOrder)
 // which is the scalar Gauss-Jordan recursion applied 32 pivots at a time; after
 // the last panel A holds A^{-1}.  Rank-32 updates run as double-float products
-// on the FP32 pipe (GB300 FP64 is ~1/70 of FP32), and so is P.
+// on the FP32 pipe (GB300 FP64 is ~1/70 of FP32) or as exact integer-slice
+// products on the tensor cores, and P in double-float on the FP32 pipe.
 // ---------------------------------------------------------------------------
 #define GB 32
 
@@ -732,9 +735,11 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
 constexpr int64_t kTcMinOrder = 2048;
 
 // Inverts in place the matrices plan.inv lists (ids into plan.ptr / plan.size),
-// all of them in one grouped sequence of launches: per 32-column step, one
-// pivot, one panel and one update launch over the tiles of every matrix still
-// active (matrices sorted by order, largest first).  bad[m] = 1 for each id m
+// all of them in one grouped sequence of launches: per 32-column step, the
+// pivot, panel and update launches cover the tiles of every matrix still
+// active (matrices sorted by order, largest first).  The double-float ones
+// are equilibrated first (and unscaled after); the FP32 ones (plan.f32) go to
+// invert_f32.  bad[m] = 1 for each id m
 // whose recursion met a pivot that was not positive.
 cudaError_t factor_invert(const InvPlan& plan, cudaMemPool_t pool, cudaStream_t s, std::vector<int>& bad,
                           int64_t* launches) {
