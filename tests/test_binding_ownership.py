@@ -143,3 +143,24 @@ def test_noalloc_binding_rejects_host_and_mistyped_tensors(monkeypatch):
     for A, Ainv in ((eye, eye), (eye.float(), eye), (torch.zeros(4, 3, dtype=torch.float64),) * 2):
         with pytest.raises(ValueError):
             M.msbem_spd_inverse_noalloc(A, Ainv)
+
+
+def test_inverse_group_binding_rejects_before_the_library(monkeypatch):
+    """msbem_spd_inverse_group's binding refuses an empty list, host or
+    mistyped or non-square matrices, a repeated matrix and an unknown
+    precision before reaching the library (a library call fails this test)."""
+    import torch
+
+    class NoCall:
+        def __getattr__(self, name):
+            raise AssertionError(f"library called: {name}")
+
+    monkeypatch.setattr(M, "_lib", NoCall())
+    eye = torch.eye(4, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        M.msbem_spd_inverse_group([])
+    for mats in ([eye], [eye.float()], [torch.zeros(4, 3, dtype=torch.float64)], [eye, eye]):
+        with pytest.raises(ValueError):
+            M.msbem_spd_inverse_group(mats)
+    with pytest.raises(ValueError):
+        M.msbem_spd_inverse_group([eye], precision="bf16")
