@@ -309,7 +309,6 @@ struct Bgj32Args {
   const int64_t* bsize;   // per matrix id
   const int32_t* order;   // matrix ids sorted by size (descending)
   const int64_t* pt1;     // prefix over sorted matrices of tiles per side
-  const int64_t* pt2;     // prefix of tiles^2
   const int64_t* pt3;     // prefix of 128 x 128 update tiles
   const int64_t* soff;    // prefix of n * GB (scratch panels), sorted order
   float* Pf;              // [sorted][GB*GB]
@@ -656,13 +655,12 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   const std::vector<int64_t>& bsize = plan.size;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bsize[a] > bsize[b]; });
   const int nb = (int)order.size();
-  std::vector<int64_t> pt1(nb + 1, 0), pt2(nb + 1, 0), pt3(nb + 1, 0), soff(nb + 1, 0);
+  std::vector<int64_t> pt1(nb + 1, 0), pt3(nb + 1, 0), soff(nb + 1, 0);
   int64_t elems = 0;
   for (int a = 0; a < nb; ++a) {
     const int64_t n = bsize[order[a]];
     const int64_t nti = (n + GB - 1) / GB;
     pt1[a + 1] = pt1[a] + nti;
-    pt2[a + 1] = pt2[a] + nti * nti;
     const int64_t ntu = (n + UT - 1) / UT;
     pt3[a + 1] = pt3[a] + ntu * ntu;
     soff[a + 1] = soff[a] + n * GB;
@@ -681,14 +679,13 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   Bgj32Args args{};
   double** d_dptr = nullptr;
   float** d_fptr = nullptr;
-  int64_t *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt2 = nullptr, *d_pt3 = nullptr, *d_soff = nullptr;
+  int64_t *d_bsize = nullptr, *d_pt1 = nullptr, *d_pt3 = nullptr, *d_soff = nullptr;
   int32_t* d_order = nullptr;
   if ((e = scratch.put(&d_dptr, plan.ptr)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_pt3, pt3)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_fptr, fptr)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_bsize, bsize)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_pt1, pt1)) != cudaSuccess) return e;
-  if ((e = scratch.put(&d_pt2, pt2)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_soff, soff)) != cudaSuccess) return e;
   if ((e = scratch.put(&d_order, order)) != cudaSuccess) return e;
   if ((e = scratch.take(&args.Pf, (size_t)nb * GB * GB)) != cudaSuccess) return e;
@@ -700,7 +697,6 @@ cudaError_t invert_f32(const InvPlan& plan, const std::vector<int32_t>& ids, cud
   args.bsize = d_bsize;
   args.order = d_order;
   args.pt1 = d_pt1;
-  args.pt2 = d_pt2;
   args.pt3 = d_pt3;
   args.soff = d_soff;
   if ((e = cudaFuncSetAttribute(bgj32_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UT_SMEM)) !=
